@@ -1,0 +1,144 @@
+"""ctypes wrapper around the plain-C FP64 oracle (tt_oracle.c). TEST INFRASTRUCTURE ONLY."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tt_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "libttoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB
+
+
+def build(force: bool = False) -> str:
+    """Compile tt_oracle.c with gcc (-O2, OpenMP) into oracle/_build/libttoracle.so."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _UE(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint32), ("nsym", C.c_uint32), ("sym_len", C.POINTER(C.c_uint32)),
+        ("n_tx", C.c_uint32), ("n_rx", C.c_uint32), ("n_taps", C.c_uint32),
+        ("delays", C.POINTER(C.c_int32)), ("taps", C.POINTER(C.c_float)),
+        ("n_anchors", C.c_uint32), ("step_samples", C.c_double), ("loop", C.c_int32),
+        ("seed", C.c_uint64), ("ue_id", C.c_uint32), ("noise_var", C.c_double),
+        ("top_n", C.c_uint32),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = C.CDLL(_LIB)
+            lib.tto_run.argtypes = [C.POINTER(_UE), C.c_uint64, C.c_uint32, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int]
+            lib.tto_run.restype = C.c_int
+            lib.tto_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+            lib.tto_noise.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64, C.c_double,
+                                      C.c_void_p]
+            lib.tto_anchor.argtypes = [C.POINTER(_UE), C.c_uint64, C.c_void_p]
+            lib.tto_max_threads.restype = C.c_int
+            _lib = lib
+    return _lib
+
+
+class OracleUE:
+    """Keeps the numpy arrays alive that the C struct points into."""
+
+    def __init__(self, symbol_len: Sequence[int], n_tx: int, n_rx: int, delays, taps,
+                 step_samples: float = 0.0, loop: bool = False, seed: int = 0, ue_id: int = 0,
+                 noise_var: float = 0.0, top_n: int = 0):
+        self.sym_len = np.ascontiguousarray(symbol_len, dtype=np.uint32)
+        self.delays = np.ascontiguousarray(delays, dtype=np.int32)
+        t = np.asarray(taps)
+        if np.iscomplexobj(t):
+            t = t.astype(np.complex64)
+        self.taps = np.ascontiguousarray(t).view(np.float32).reshape(-1)
+        k = len(self.delays)
+        n_anchors = self.taps.size // (2 * n_rx * n_tx * k)
+        if n_anchors * 2 * n_rx * n_tx * k != self.taps.size:
+            raise ValueError("taps size does not match [T][n_rx][n_tx][K]")
+        self.s = _UE(n=int(self.sym_len.sum()), nsym=len(self.sym_len),
+                     sym_len=self.sym_len.ctypes.data_as(C.POINTER(C.c_uint32)),
+                     n_tx=n_tx, n_rx=n_rx, n_taps=k,
+                     delays=self.delays.ctypes.data_as(C.POINTER(C.c_int32)),
+                     taps=self.taps.ctypes.data_as(C.POINTER(C.c_float)), n_anchors=n_anchors,
+                     step_samples=float(step_samples), loop=int(bool(loop)), seed=int(seed),
+                     ue_id=int(ue_id), noise_var=float(noise_var), top_n=int(top_n))
+
+    @classmethod
+    def from_spec(cls, spec, top_n: int = 0) -> "OracleUE":
+        return cls(spec.symbol_len, spec.n_tx, spec.n_rx, spec.delays, spec.taps,
+                   spec.step_samples, spec.loop, spec.seed, spec.ue_id, spec.noise_var, top_n)
+
+
+def run_ue(ue: OracleUE, x: np.ndarray, s_first: int = 0, nthreads: int = 0,
+           want_y: bool = True, want_q: bool = True):
+    """Run slots [s_first, s_first + n_slots) of one UE; x is int16 [n_tx][n_slots*N][2].
+
+    Returns (y, q): y complex128 [n_rx][n_slots*N] (or None), q int16 [n_rx][n_slots*N][2] (or None).
+    """
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.int16)
+    n = ue.s.n
+    if x.ndim != 3 or x.shape[0] != ue.s.n_tx or x.shape[2] != 2 or x.shape[1] % n:
+        raise ValueError("x must be int16 [n_tx][n_slots*N][2]")
+    n_slots = x.shape[1] // n
+    y = np.empty((ue.s.n_rx, x.shape[1], 2), dtype=np.float64) if want_y else None
+    q = np.empty((ue.s.n_rx, x.shape[1], 2), dtype=np.int16) if want_q else None
+    rc = lib.tto_run(C.byref(ue.s), s_first, n_slots, x.ctypes.data,
+                     None if y is None else y.ctypes.data, None if q is None else q.ctypes.data,
+                     int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    yc = None if y is None else (y[..., 0] + 1j * y[..., 1])
+    return yc, q
+
+
+def philox4x32_10(ctr: Sequence[int], key: Sequence[int]) -> np.ndarray:
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    o = np.zeros(4, dtype=np.uint32)
+    lib.tto_philox4x32_10(c.ctypes.data, k.ctypes.data, o.ctypes.data)
+    return o
+
+
+def noise(seed: int, ue_id: int, rx: int, m: int, noise_var: float) -> complex:
+    lib = _load()
+    o = np.zeros(2, dtype=np.float64)
+    lib.tto_noise(seed, ue_id, rx, m, noise_var, o.ctypes.data)
+    return complex(o[0], o[1])
+
+
+def anchor(ue: OracleUE, a: int) -> np.ndarray:
+    """H[a] as complex128 [n_rx][n_tx][K]."""
+    lib = _load()
+    per = ue.s.n_rx * ue.s.n_tx * ue.s.n_taps
+    o = np.zeros(2 * per, dtype=np.float64)
+    lib.tto_anchor(C.byref(ue.s), a, o.ctypes.data)
+    return (o[0::2] + 1j * o[1::2]).reshape(ue.s.n_rx, ue.s.n_tx, ue.s.n_taps)
+
+
+def max_threads() -> int:
+    return int(_load().tto_max_threads())
