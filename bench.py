@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-UE time-varying channel convolution on GB300.
+
+Workload (default): 16 UEs SISO at 40 MHz NR (61.44 Msps, 30720 samples per
+0.5 ms slot), 1000 slots each, 24-tap Jakes channels (delays <= 256, 100 Hz),
+AWGN at 20 dB from Philox4x32-10, int16 IQ in and out, FP32 arithmetic.
+One step = every slot of every UE through the whole path (trace anchors,
+ingest, interpolated convolution, AWGN, packing, delay-line carry) in the
+batched form; the plain one-launch-per-UE-per-slot form is timed beside it.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own
+16 UEs (weak scaling, no collective on the data path); value = all ranks'
+UE-slots / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_UES, N_SLOTS, N_FFT, N_TAPS, D_MAX = 16, 1000, 2048, 24, 256
+SLOT_SAMPLES = 30720
+FLOP_PER_TAP_SAMPLE = 12      # complex MAC (8) + tap interpolation h = H + tau*dH (2 FMA = 4)
+DISTINCT_IQ_SLOTS = 64        # synthetic IQ slots per UE, cycled through the replay
+METRIC = "UE-slots/s and GMAC/s at 1 GB300 vs plain form; p99 slot latency vs 0.5 ms"
+WORKLOAD = ("16 UEs SISO, 40 MHz (30720 samples/slot), 1000 slots each, 24 taps (delays <= 256), "
+            "100 Hz Jakes, AWGN 20 dB, int16 IQ, FP32 accumulation")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    out = {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0, "src": "fallback"}
+    if os.path.exists(p):
+        d = json.load(open(p))
+        out.update({k: d[k] for k in ("sm_max_mhz", "hbm_gbs") if k in d})
+        out["src"] = "measured"
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_workload(rank: int):
+    from paper_2601_08217_gb300 import inputs
+    specs = inputs.workload_plain_16ue(n_slots=N_SLOTS, n_ues=N_UES)
+    for s in specs:
+        s.loop = True            # repeated steps keep replaying the trace
+        s.ue_id += rank * N_UES
+    iq = [inputs.make_iq(2, s, DISTINCT_IQ_SLOTS) for s in specs]
+    return specs, iq
+
+
+def cycled_slots(x, n, count, first=0):
+    """[count][n_tx][N][2] int16 from the distinct slots of x ([n_tx][D*N][2]), cycled."""
+    from paper_2601_08217_gb300 import tt_chan as tc
+    sm = tc.slots_major(x, n)
+    idx = (np.arange(count) + first) % sm.shape[0]
+    return np.ascontiguousarray(sm[idx])
+
+
+def tap_samples(specs):
+    return sum(s.n * len(s.delays) * s.n_tx * s.n_rx for s in specs)
+
+
+def run_ours(args, rank, world, device):
+    import torch
+    from paper_2601_08217_gb300 import tt_chan as tc
+
+    specs, iq = make_workload(rank)
+    n = specs[0].n
+    eng = tc.Engine(device=device, form="batched", persistent=bool(args.persistent))
+    q = N_SLOTS + 1
+    chans = [tc.Chan(eng, s, ring_slots=q) for s in specs]
+    stream = torch.cuda.ExternalStream(eng.stream)
+    # fill every ring position once (slots 0..1000), then replay in place
+    for ch, x in zip(chans, iq):
+        ch.push(0, cycled_slots(x, n, N_SLOTS))
+    eng.run()
+    for ch in chans:
+        tc.tt_chan_release_slots(ch.h, 0, N_SLOTS)
+    for ch, x in zip(chans, iq):
+        ch.push(N_SLOTS, cycled_slots(x, n, 1, N_SLOTS))
+    eng.run()
+    for ch in chans:
+        tc.tt_chan_release_slots(ch.h, N_SLOTS, 1)
+    eng.sync()
+    next_slot = [N_SLOTS + 1]
+
+    def step(ev=None):
+        s0 = next_slot[0]
+        for ch in chans:
+            tc.tt_chan_commit_slots(ch.h, s0, N_SLOTS)
+        if ev is not None:
+            ev[0].record(stream)
+        eng.run()
+        if ev is not None:
+            ev[1].record(stream)
+        for ch in chans:
+            tc.tt_chan_release_slots(ch.h, s0, N_SLOTS)
+        next_slot[0] = s0 + N_SLOTS
+
+    for _ in range(args.warmup):
+        step()
+    eng.sync()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    launches0 = eng.stats()["launches"]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(device) as clk:
+        t0.record(stream)
+        for i in range(args.steps):
+            step(kev[i])
+        t1.record(stream)
+        eng.sync()
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = eng.stats()["launches"] - launches0
+    ms_total = t0.elapsed_time(t1)
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+
+    # ---- e2e through the public API with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        h_in = [torch.from_numpy(cycled_slots(x, n, N_SLOTS)).pin_memory() for x in iq]
+        h_out = [torch.empty((N_SLOTS, 1, n, 2), dtype=torch.int16).pin_memory() for _ in chans]
+        e2e_steps = max(1, min(args.steps, 5))
+
+        def e2e_step():
+            s0 = next_slot[0]
+            for ch, hi in zip(chans, h_in):
+                tc.tt_chan_push_slots(ch.h, s0, N_SLOTS, hi.data_ptr())
+            eng.run()
+            for ch, ho in zip(chans, h_out):
+                tc.tt_chan_pull_slots(ch.h, s0, N_SLOTS, ho.data_ptr(), -1)
+            next_slot[0] = s0 + N_SLOTS
+
+        e2e_step()
+        if world > 1:
+            torch.distributed.barrier()
+        ts = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        te = time.perf_counter() - ts
+        if world > 1:
+            t = torch.tensor([te], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        bytes_in = sum(h.numel() * 2 for h in h_in)
+        bytes_out = sum(h.numel() * 2 for h in h_out)
+        e2e = {"value": N_UES * N_SLOTS * world * e2e_steps / te, "unit": "UE-slots/s",
+               "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_out, "steps": e2e_steps}
+    eng.close()
+
+    # ---- plain form on the same GPU, same workload ----
+    plain = None
+    if not args.no_plain:
+        engp = tc.Engine(device=device, form="plain")
+        chp = [tc.Chan(engp, s, ring_slots=q) for s in specs]
+        for ch, x in zip(chp, iq):
+            ch.push(0, cycled_slots(x, n, N_SLOTS))
+        sp = torch.cuda.ExternalStream(engp.stream)
+        engp.run()
+        for ch in chp:
+            tc.tt_chan_release_slots(ch.h, 0, N_SLOTS)
+        engp.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for ch in chp:
+            tc.tt_chan_commit_slots(ch.h, N_SLOTS, N_SLOTS - 1)
+        a.record(sp)
+        engp.run()
+        b.record(sp)
+        engp.sync()
+        pms = a.elapsed_time(b)
+        plain = {"value": N_UES * (N_SLOTS - 1) / (pms / 1e3), "unit": "UE-slots/s", "ms_per_step": pms,
+                 "launches_per_step": N_UES * (N_SLOTS - 1)}
+        engp.close()
+    return dict(ms_total=ms_total, kern_ms=kern_ms, launches=launches, clocks=clk.summary(), e2e=e2e,
+                plain=plain, specs=specs)
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload."""
+    import oracle
+    from paper_2601_08217_gb300 import inputs
+    specs = inputs.workload_plain_16ue(n_slots=N_SLOTS, n_ues=N_UES)
+    sp = specs[0]
+    x = inputs.make_iq(2, sp, 4)
+    ue = oracle.OracleUE.from_spec(sp)
+    t = time.perf_counter()
+    oracle.run_ue(ue, x[:, : sp.n], want_y=False)
+    one = max(time.perf_counter() - t, 1e-3)
+    slots = int(max(1, min(4, budget_s / one)))
+    t = time.perf_counter()
+    oracle.run_ue(ue, x[:, : slots * sp.n], want_y=False)
+    dt = time.perf_counter() - t
+    return {"value": slots / dt, "unit": "UE-slots/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"UE 0, slots 0-{slots - 1} of the workload ({slots} UE-slots, "
+                      f"{slots * sp.n * len(sp.delays) / 1e6:.1f} M complex MAC, FP64), {dt:.2f} s",
+            "seconds": dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        # the reference arm is the oracle on the host's cores; rank 0 only
+        if rank != 0:
+            return
+        runs = []
+        for _ in range(max(args.warmup, 0)):
+            cpu_baseline(budget_s=2.0)
+        for _ in range(max(args.steps, 1)):
+            runs.append(cpu_baseline(budget_s=6.0))
+        v = statistics.median(r["value"] for r in runs)
+        ms = statistics.median(r["seconds"] for r in runs) * 1e3
+        cb = dict(runs[0])
+        cb["value"] = v
+        cb.pop("seconds", None)
+        print(json.dumps({"metric": METRIC, "value": v, "unit": "UE-slots/s", "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "impl": "reference",
+                          "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": "UE-slots/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        torch.distributed.barrier()
+    __graft_entry__.build()
+
+    r = run_ours(args, rank, world, local)
+    ms_step = r["ms_total"] / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    ue_slots = N_UES * N_SLOTS * world
+    value = ue_slots / (ms_step / 1e3)
+    ts = tap_samples(r["specs"]) * N_SLOTS
+    gmac = ts * world / (ms_step / 1e3) / 1e9
+    pk = peaks()
+    kms = statistics.mean(r["kern_ms"])
+    peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    achieved = ts * FLOP_PER_TAP_SAMPLE / (kms / 1e3) / 1e12
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline()
+        cpu.pop("seconds", None)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "UE-slots/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "ues_per_gpu": N_UES, "slots": N_SLOTS,
+                   "samples_per_slot": SLOT_SAMPLES, "taps": N_TAPS, "max_delay": D_MAX,
+                   "form": "batched" + (" persistent" if args.persistent else ""),
+                   "iq": f"{DISTINCT_IQ_SLOTS} distinct synthetic slots per UE cycled",
+                   "l2": "inputs larger than L2 (1.97 GB of IQ read per step per GPU)"},
+        "gmac_per_s": gmac, "samples_per_s": N_UES * N_SLOTS * SLOT_SAMPLES * world / (ms_step / 1e3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "tt_conv_fp32_kernel<8,1,512>", "kernel_ms": kms,
+                     "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz ({pk['src']})"},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "e2e": r["e2e"],
+        "plain": r["plain"],
+        "vs_plain": (value / r["plain"]["value"]) if r["plain"] else None,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

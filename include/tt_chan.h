@@ -1,0 +1,229 @@
+/*
+ * tt_chan.h -- C ABI of the GB300 per-UE channel-convolution engine.
+ *
+ * The operation (paper Sec. III-B): every UE u gets its own linear,
+ * time-varying convolution of the transmitted complex baseband IQ stream,
+ *     y_u(t) = x(t) * h_u(t),
+ * with h_u read from a channel trace of discrete complex taps on a fixed
+ * delay grid per time step (Sec. IV, "Tiny-Twin compatible channel traces"),
+ * convolution kept per UE so that UEs are isolated from one another
+ * (Sec. III-C, "Parallelizing Convolution Computation").  In sample form, for
+ * Rx antenna r and absolute sample index m:
+ *
+ *     y_r[m] = sum_t sum_k h_{r,t,k}(m) * x_t[m - d_k] + w_r[m]
+ *
+ *   h(m)  = H[a] + ((m - b_a) / L_a) * (H[a+1] - H[a])   for b_a <= m < b_a + L_a,
+ *           a = absolute OFDM symbol index, b_a its first sample, L_a its length;
+ *   H[a]  = the trace entry of symbol a (step_samples == 0), or the FP64 linear
+ *           interpolation of the trace in time at sample b_a (step_samples > 0);
+ *   d_k   = integer sample delays shared by all antenna pairs of a UE;
+ *   x_t[m] = 0 before the first slot a UE ever processes (empty delay line);
+ *   w_r[m] = optional AWGN, variance noise_var per complex sample, from
+ *           Philox4x32-10 (key = seed, counter = (m>>1, ue_id, r)) and Box-Muller;
+ *   output = clamp(round_half_even(y), -32768, 32767) per I and Q.
+ *
+ * Units.  A slot is samples_per_slot complex samples per antenna, split into
+ * symbols_per_slot OFDM symbols.  IQ buffers are int16, I and Q interleaved,
+ * laid out [antenna][sample][2]: a slot of input is n_tx*N*2 int16 values,
+ * a slot of output n_rx*N*2 (or n_rx*N complex64 with TT_OUT_CF32).
+ * Several consecutive slots are laid out slot-major: [slot][antenna][sample][2].
+ *
+ * Ownership.  The library owns every device allocation it makes.  Caller
+ * buffers (host or device) are borrowed only for the duration of the call,
+ * except where a function says it works asynchronously on the caller's stream.
+ * Handles are not thread-safe individually: use one tt_chan from one thread
+ * at a time; an engine serialises its own state, so different channels of one
+ * engine may be used from different threads.
+ *
+ * Errors.  Every function returns a tt_status.  On error no out-parameter is
+ * written, and tt_last_error() returns a thread-local message.  There is no CPU
+ * fallback: without a usable CUDA device tt_engine_create fails with
+ * TT_ERR_CUDA.
+ */
+#ifndef TT_CHAN_H
+#define TT_CHAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TT_CHAN_ABI_VERSION 1
+
+typedef struct tt_engine tt_engine; /* one per GPU: stream, HBM budget, form, UE table */
+typedef struct tt_chan tt_chan;     /* one per UE link: config, trace, delay line, rings */
+
+typedef int32_t tt_status;
+enum {
+  TT_OK = 0,
+  TT_ERR_INVALID = -1,   /* bad argument, size or layout */
+  TT_ERR_NO_MEMORY = -2, /* admission refused by the HBM budget, or an allocation failed */
+  TT_ERR_CUDA = -3,      /* CUDA runtime failure (no device, launch error, ...) */
+  TT_ERR_TRACE = -4,     /* malformed trace: sizes, delays out of range, non-finite taps */
+  TT_ERR_AGAIN = -5,     /* nothing ready yet, or the slot ring is full */
+  TT_ERR_TIMEOUT = -6,   /* a bounded wait ran out */
+  TT_ERR_STATE = -7      /* out-of-order slot, no trace loaded, wrong form, bad state blob */
+};
+
+/* How tt_engine_run executes pending slots. */
+enum {
+  TT_FORM_BATCHED = 0, /* one tiled kernel over every pending (UE, slot) of all UEs */
+  TT_FORM_PLAIN = 1    /* comparison form: one simple launch per UE per slot */
+};
+
+/* Arithmetic of a channel. TT_FP32 is the reference-accuracy CUDA-core path. */
+enum { TT_FP32 = 0, TT_BF16_TC = 1, TT_FP16_TC = 2 };
+
+/* Output sample format.  TT_OUT_CF32 skips the int16 packing and returns y
+ * itself as complex64 (re, im float32): output buffers are then
+ * [n_rx][N] x 8 bytes per slot instead of [n_rx][N][2] int16. */
+enum { TT_OUT_INT16 = 0, TT_OUT_CF32 = 1 };
+
+typedef struct {
+  uint32_t struct_size;      /* sizeof(tt_engine_config) */
+  int32_t device;            /* CUDA device ordinal */
+  uint64_t hbm_budget_bytes; /* admission limit for all channels; 0 = no limit */
+  uint32_t form;             /* TT_FORM_* */
+  uint32_t max_ues;          /* capacity of the device UE table; 0 = 1024 */
+  uint32_t samples_per_thread; /* cap on the tiled kernel's samples per thread: 0 = 8; else 1, 2, 4 or 8.
+                                  Each channel uses the largest allowed value dividing all its symbol lengths. */
+  uint32_t threads_per_block;  /* reserved: 0 (the tiled kernel runs 128 threads per CTA) */
+  uint32_t persistent;       /* 1: persistent CTAs claim work from a device counter; 0: one CTA per item */
+} tt_engine_config;
+
+typedef struct {
+  uint32_t struct_size;       /* sizeof(tt_chan_config) */
+  uint32_t ue_id;             /* keys the AWGN stream; need not be unique */
+  uint32_t samples_per_slot;  /* N, 1 .. 2^24 */
+  uint32_t symbols_per_slot;  /* 1 .. 32 (14 for NR) */
+  const uint32_t *symbol_len; /* [symbols_per_slot], summing to N; copied */
+  uint32_t n_tx, n_rx;        /* 1 .. 4 each */
+  uint32_t max_taps;          /* upper bound on the trace's tap count, 1 .. 128 */
+  uint32_t max_delay;         /* upper bound on the delays, samples, <= 1024 */
+  uint32_t ring_slots;        /* slot ring depth Q (>= 2 + ceil(max_delay/N)); 0 = that minimum + 2 */
+  uint64_t seed;              /* AWGN key */
+  float noise_var;            /* sigma^2 per complex sample; 0 disables AWGN */
+  uint32_t precision;         /* TT_FP32 (tensor-core forms use their own entry points) */
+  uint32_t output_format;     /* TT_OUT_INT16 (packed IQ) or TT_OUT_CF32 (complex64 before packing) */
+} tt_chan_config;
+
+typedef struct {
+  uint32_t struct_size;    /* sizeof(tt_trace_desc) */
+  const float *taps;       /* complex64, re/im interleaved, [n_anchors][n_rx][n_tx][n_taps]; copied */
+  const int32_t *delays;   /* [n_taps], non-decreasing, 0 <= d <= max_delay; copied */
+  uint32_t n_anchors;      /* >= 1 */
+  uint32_t n_taps;         /* 1 .. max_taps */
+  double step_samples;     /* 0: one trace entry per OFDM symbol; > 0: entry i sits at sample i*step */
+  int32_t loop;            /* 1: the trace wraps around; 0: it holds its last entry */
+} tt_trace_desc;
+
+typedef struct {
+  uint64_t hbm_in_use;      /* bytes allocated for admitted channels */
+  uint64_t hbm_budget;      /* the admission limit (0 = none) */
+  uint32_t n_chans;         /* admitted channels */
+  uint32_t pad;
+  uint64_t launches;        /* kernel launches issued by tt_engine_run so far */
+  uint64_t slots_processed; /* (UE, slot) pairs launched so far */
+} tt_engine_stats;
+
+/* ---------------------------------------------------------------- engine */
+
+/* Create an engine on cfg->device.  Fails with TT_ERR_CUDA if there is no
+ * such device.  *out receives the handle. */
+tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out);
+
+/* Wait for all work, then free everything, including channels not yet destroyed. */
+tt_status tt_engine_destroy(tt_engine *e);
+
+/* Launch every pushed-but-not-launched slot of every channel (in push order
+ * per channel).  Asynchronous: returns once the work is queued on the
+ * engine's stream.  Channels without a trace are skipped. */
+tt_status tt_engine_run(tt_engine *e);
+
+/* Block until all launched work is complete, at most timeout_us (< 0: no limit).
+ * TT_ERR_TIMEOUT if it is still running. */
+tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us);
+
+/* The engine's CUDA stream (a cudaStream_t) for ordering caller work. */
+tt_status tt_engine_stream(tt_engine *e, void **stream);
+
+tt_status tt_engine_get_stats(tt_engine *e, tt_engine_stats *out);
+
+/* ---------------------------------------------------------------- channel */
+
+/* Admit a channel: allocates its slot rings if they fit in the budget
+ * (TT_ERR_NO_MEMORY otherwise).  The delay line starts empty (zeros). */
+tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out);
+
+/* Free the channel's device memory (after its launched work completes). */
+tt_status tt_chan_destroy(tt_chan *c);
+
+/* Copy a trace to the device (replacing any previous one).  Counted against
+ * the budget: TT_ERR_NO_MEMORY if it does not fit, TT_ERR_TRACE if malformed.
+ * Not allowed while the channel has launched work in flight (TT_ERR_STATE). */
+tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *trace);
+
+/* Queue input slots [first, first+n).  The first push fixes the channel's
+ * starting slot; after that slots must continue in order (TT_ERR_STATE).
+ * TT_ERR_AGAIN if the ring has no room (pull or release outputs first).
+ *   push_slots:     host buffer [n][n_tx][N][2], copied before return.
+ *   push_slots_dev: device buffer, copied asynchronously after all work
+ *                   previously queued on `stream` (a cudaStream_t, NULL = legacy
+ *                   default stream); the buffer may be reused once that stream
+ *                   has passed an event recorded after this call. */
+tt_status tt_chan_push_slot(tt_chan *c, uint64_t slot, const int16_t *iq_in);
+tt_status tt_chan_push_slots(tt_chan *c, uint64_t first, uint32_t n, const int16_t *iq_in);
+tt_status tt_chan_push_slots_dev(tt_chan *c, uint64_t first, uint32_t n, const int16_t *d_iq_in,
+                                 void *stream);
+
+/* Zero-copy input: *d_ptr receives the device address inside the ring where
+ * slot `slot`'s input ([n_tx][N][2]) lives.  Write it (on any stream, then
+ * order that stream before the next tt_engine_run, e.g. by synchronising) and
+ * commit it.  Valid for the next slot to push and the ring's free positions. */
+tt_status tt_chan_slot_input(tt_chan *c, uint64_t slot, int16_t **d_ptr);
+tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n);
+
+/* Pull the oldest not-yet-pulled slot into a host buffer [n_rx][N][2].
+ * Waits at most timeout_us for it to complete (0: do not wait, < 0: no limit);
+ * TT_ERR_AGAIN if it has not been launched, TT_ERR_TIMEOUT if it is still running. */
+tt_status tt_chan_pull_slot(tt_chan *c, uint64_t *slot, void *iq_out, int64_t timeout_us);
+
+/* Pull slots [first, first+n) (must be the oldest not yet pulled) into a host
+ * buffer [n][n_rx][N][2], waiting as tt_chan_pull_slot does. */
+tt_status tt_chan_pull_slots(tt_chan *c, uint64_t first, uint32_t n, void *iq_out,
+                             int64_t timeout_us);
+
+/* Device-side pull: copy slots [first, first+n) to a device buffer after
+ * their computation; `stream` is made to wait for the copy.  Frees the ring
+ * positions.  The slots must be launched already (TT_ERR_AGAIN otherwise). */
+tt_status tt_chan_pull_slots_dev(tt_chan *c, uint64_t first, uint32_t n, void *d_iq_out,
+                                 void *stream);
+
+/* Zero-copy output: device address of slot `slot`'s output ([n_rx][N][2]) in
+ * the ring, valid until the slot is released.  Order reads after
+ * tt_engine_sync or the engine stream.  Release frees ring positions of the
+ * oldest not-yet-pulled slots. */
+tt_status tt_chan_slot_output(tt_chan *c, uint64_t slot, const void **d_ptr);
+tt_status tt_chan_release_slots(tt_chan *c, uint64_t first, uint32_t n);
+
+/* Checkpoint / resume.  The state is the next slot index, the last
+ * max_delay input samples per Tx antenna and the AWGN key; outputs that have
+ * not been pulled are not part of it.  get_state with buf == NULL sets *len
+ * to the size needed.  Both require no launched work in flight for this
+ * channel (call tt_engine_sync first; TT_ERR_STATE otherwise).  After
+ * set_state the next push must be the saved next slot; results are then
+ * bit-identical to an uninterrupted run. */
+tt_status tt_chan_get_state(const tt_chan *c, void *buf, size_t *len);
+tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len);
+
+/* ---------------------------------------------------------------- misc */
+
+const char *tt_last_error(void);
+int32_t tt_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TT_CHAN_H */

@@ -1,0 +1,103 @@
+// Launch dispatch for the tiled FP32 kernel, its shared-memory sizing, and the
+// plain comparison form (one launch per UE per slot, one thread per output
+// sample, taps and input read straight from global memory).
+#include "tt_conv_kernel.cuh"
+#include "tt_internal.h"
+#include "tt_philox.cuh"
+
+size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int n_rx, int n_taps, int max_sym_touched) {
+  const int np = tt_geo_np(spt, tt_dclass_max(dclass));
+  const size_t taps = (size_t)max_sym_touched * n_rx * n_tx * n_taps * sizeof(float4);
+  const size_t offk = (size_t)((n_taps + 3) & ~3) * sizeof(int);
+  const size_t planes = (size_t)n_tx * 2 * spt * np * sizeof(float2);
+  return taps + offk + planes;
+}
+
+// Largest number of symbols one work item (TT_TPB groups of spt samples) can touch.
+int tt_conv_max_sym_touched(int spt, const int32_t *sym_len, int nsym) {
+  int n = 0;
+  for (int j = 0; j < nsym; ++j) n += sym_len[j];
+  const int groups = n / spt;
+  int best = 1;
+  for (int g0 = 0; g0 < groups; g0 += TT_TPB) {
+    const int w0 = g0 * spt;
+    const int wl = (g0 + TT_TPB < groups ? g0 + TT_TPB : groups) * spt - 1;
+    int b = 0, j0 = -1, j1 = -1;
+    for (int j = 0; j < nsym; ++j) {
+      if (j0 < 0 && w0 < b + sym_len[j]) j0 = j;
+      if (j1 < 0 && wl < b + sym_len[j]) j1 = j;
+      b += sym_len[j];
+    }
+    if (j1 - j0 + 1 > best) best = j1 - j0 + 1;
+  }
+  return best;
+}
+
+cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st) {
+  switch (L.spt) {
+    case 1: return tt_launch_conv_s1(L, st);
+    case 2: return tt_launch_conv_s2(L, st);
+    case 4: return tt_launch_conv_s4(L, st);
+    case 8: return tt_launch_conv_s8(L, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plain form: the straightforward mapping, kept as the comparison point.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) tt_plain_kernel(const TTUEDesc *__restrict__ U, uint64_t slot) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = U->n;
+  if (w >= n) return;
+  const int nsym = U->nsym, n_tx = U->n_tx, n_rx = U->n_rx, K = U->n_taps, Q = U->ring_q;
+  int j = 0;
+  while (j + 1 < nsym && U->sym_start[j + 1] <= w) ++j;
+  const float tau = (float)(w - U->sym_start[j]) / (float)(U->sym_start[j + 1] - U->sym_start[j]);
+  const uint64_t a = slot * (uint64_t)nsym + (uint64_t)j;
+  const int per = n_rx * n_tx * K;
+  const int slot_pos = (int)(slot % (uint64_t)Q);
+  const uint32_t *rin = reinterpret_cast<const uint32_t *>(U->ring_in);
+  const uint64_t m = slot * (uint64_t)n + (uint64_t)w;
+  for (int r = 0; r < n_rx; ++r) {
+    float yr = 0.f, yi = 0.f;
+    for (int t = 0; t < n_tx; ++t) {
+      for (int k = 0; k < K; ++k) {
+        const int e = (r * n_tx + t) * K + k;
+        const float2 h0 = tt::tt_anchor(U, a, e, per);
+        const float2 h1 = tt::tt_anchor(U, a + 1, e, per);
+        const float hr = fmaf(tau, h1.x - h0.x, h0.x);
+        const float hi = fmaf(tau, h1.y - h0.y, h0.y);
+        int src = w - U->delays[k];
+        int pos = slot_pos;
+        if (src < 0) {
+          const int back = (-src + n - 1) / n;
+          src += back * n;
+          pos -= back;
+          while (pos < 0) pos += Q;
+        }
+        const float2 x = tt_unpack_iq(rin[(size_t)(pos * n_tx + t) * n + src]);
+        yr = fmaf(hr, x.x, yr);
+        yr = fmaf(-hi, x.y, yr);
+        yi = fmaf(hr, x.y, yi);
+        yi = fmaf(hi, x.x, yi);
+      }
+    }
+    if (U->noise_std > 0.f) {
+      const float2 z = tt_awgn_one(U->seed, U->ue_id, (uint32_t)r, m);
+      yr = fmaf(U->noise_std, z.x, yr);
+      yi = fmaf(U->noise_std, z.y, yi);
+    }
+    const size_t o = (size_t)(slot_pos * n_rx + r) * n + w;
+    if (U->out_f32)
+      reinterpret_cast<float2 *>(U->ring_out)[o] = make_float2(yr, yi);
+    else
+      reinterpret_cast<uint32_t *>(U->ring_out)[o] = tt_pack_iq(yr, yi);
+  }
+}
+
+cudaError_t tt_launch_plain(const TTUEDesc *ue_dev, uint64_t slot, int n, cudaStream_t st) {
+  const int tpb = 256;
+  tt_plain_kernel<<<(n + tpb - 1) / tpb, tpb, 0, st>>>(ue_dev, slot);
+  return cudaGetLastError();
+}

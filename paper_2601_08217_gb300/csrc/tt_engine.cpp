@@ -1,0 +1,878 @@
+// Host side of the channel engine: the C ABI declared in include/tt_chan.h.
+//
+// One engine per GPU owns a CUDA stream, the device table of UE descriptors,
+// and the admission budget.  One channel per UE link owns a slot ring for
+// input and output on the device, its trace, and the cursors that keep its
+// slots in order.  Per-UE isolation (paper Sec. III-C, "Parallelizing
+// Convolution Computation") is kept by construction: every channel has its
+// own ring, trace and descriptor, and no kernel mixes data of two UEs.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <chrono>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <utility>
+#include <vector>
+
+#include "tt_chan.h"
+#include "tt_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+tt_status fail(tt_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define TT_CK(call)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return fail(TT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int64_t now_us() {
+  return std::chrono::duration_cast<std::chrono::microseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+}  // namespace
+
+struct tt_chan;
+
+struct tt_engine {
+  int device = 0;
+  uint64_t budget = 0;
+  uint64_t in_use = 0;
+  uint32_t form = TT_FORM_BATCHED;
+  uint32_t max_ues = 1024;
+  uint32_t spt_override = 0;
+  uint32_t persistent = 0;
+  int num_sms = 1;
+  cudaStream_t stream = nullptr;  // all compute and device copies, in order
+  cudaStream_t copy = nullptr;    // host pulls
+  std::mutex mu;
+  std::vector<tt_chan *> table;   // UE table slot -> channel
+  TTUEDesc *d_ues = nullptr;
+  TTSeg *d_segs = nullptr;
+  size_t seg_cap = 0;
+  uint32_t *d_counters = nullptr;  // one work counter per launch class
+  int counter_cap = 64;
+  uint64_t launch_seq = 0;         // batches issued
+  uint64_t completed_seq = 0;      // batches known complete
+  std::deque<std::pair<uint64_t, cudaEvent_t>> events;  // (seq, event) not yet known complete
+  std::vector<cudaEvent_t> pool;
+  uint64_t launches = 0, slots_processed = 0;
+};
+
+struct tt_chan {
+  tt_engine *e = nullptr;
+  uint32_t index = 0;
+  tt_chan_config cfg{};
+  std::vector<uint32_t> sym_len;
+  int n = 0, Q = 0, hist = 0;
+  size_t slot_in_elems = 0, slot_out_elems = 0;  // int16 values per slot
+  int16_t *d_in = nullptr, *d_out = nullptr;
+  uint64_t ring_bytes = 0;
+  float2 *d_taps = nullptr;
+  int32_t *d_delays = nullptr;
+  uint64_t trace_bytes = 0;
+  bool has_trace = false;
+  int spt = 1, dclass = 0, max_sym_touched = 1;
+  size_t smem = 0;
+  TTUEDesc desc{};
+  bool started = false;
+  uint64_t pushed_end = 0, launched_end = 0, completed_end = 0, pulled_end = 0;
+  std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
+};
+
+namespace {
+
+cudaEvent_t get_event(tt_engine *e) {
+  if (!e->pool.empty()) {
+    cudaEvent_t ev = e->pool.back();
+    e->pool.pop_back();
+    return ev;
+  }
+  cudaEvent_t ev = nullptr;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+  return ev;
+}
+
+// Poll batch events in order; returns the first hard CUDA error seen.
+cudaError_t update_completed(tt_engine *e) {
+  while (!e->events.empty()) {
+    cudaError_t q = cudaEventQuery(e->events.front().second);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) return q;
+    e->completed_seq = e->events.front().first;
+    e->pool.push_back(e->events.front().second);
+    e->events.pop_front();
+  }
+  return cudaSuccess;
+}
+
+void update_chan(tt_chan *c) {
+  while (!c->inflight.empty() && c->inflight.front().second <= c->e->completed_seq) {
+    c->completed_end = c->inflight.front().first;
+    c->inflight.pop_front();
+  }
+}
+
+cudaEvent_t event_of(tt_engine *e, uint64_t seq) {
+  for (auto &p : e->events)
+    if (p.first == seq) return p.second;
+  return nullptr;
+}
+
+// Wait (bounded) until batch `seq` is complete.
+tt_status wait_seq(tt_engine *e, uint64_t seq, int64_t timeout_us, std::unique_lock<std::mutex> &lk) {
+  const int64_t deadline = timeout_us < 0 ? INT64_MAX : now_us() + timeout_us;
+  for (;;) {
+    cudaError_t q = update_completed(e);
+    if (q != cudaSuccess) return fail(TT_ERR_CUDA, "kernel failed: %s", cudaGetErrorString(q));
+    if (e->completed_seq >= seq) return TT_OK;
+    if (timeout_us == 0) return fail(TT_ERR_TIMEOUT, "slot still running");
+    if (timeout_us < 0) {
+      cudaEvent_t ev = event_of(e, seq);
+      if (ev) {
+        lk.unlock();
+        cudaError_t s = cudaEventSynchronize(ev);
+        lk.lock();
+        if (s != cudaSuccess) return fail(TT_ERR_CUDA, "kernel failed: %s", cudaGetErrorString(s));
+      }
+      continue;
+    }
+    if (now_us() > deadline) return fail(TT_ERR_TIMEOUT, "slot still running after %lld us",
+                                         (long long)timeout_us);
+    lk.unlock();
+    std::this_thread::yield();
+    lk.lock();
+  }
+}
+
+int pick_spt(const std::vector<uint32_t> &L, uint32_t override_spt) {
+  static const int cands[] = {8, 4, 2, 1};
+  for (int s : cands) {
+    if (override_spt && (uint32_t)s > override_spt) continue;
+    bool ok = true;
+    for (uint32_t v : L) ok = ok && (v % (uint32_t)s == 0);
+    if (ok) return s;
+  }
+  return 1;
+}
+
+int pick_dclass(int d_max) {
+  if (d_max <= TT_DCLASS0) return 0;
+  if (d_max <= TT_DCLASS1) return 1;
+  return 2;
+}
+
+// Copy [first, first+n) slots between a linear buffer and the ring (<= 2 copies).
+cudaError_t ring_copy(int16_t *ring, size_t slot_elems, int Q, uint64_t first, uint32_t n, const void *src,
+                      void *dst, cudaMemcpyKind kind, cudaStream_t st, bool to_ring) {
+  uint32_t done = 0;
+  while (done < n) {
+    const uint32_t pos = (uint32_t)((first + done) % (uint64_t)Q);
+    const uint32_t run = std::min<uint32_t>(n - done, (uint32_t)Q - pos);
+    const size_t bytes = (size_t)run * slot_elems * sizeof(int16_t);
+    int16_t *r = ring + (size_t)pos * slot_elems;
+    cudaError_t err;
+    if (to_ring)
+      err = cudaMemcpyAsync(r, static_cast<const int16_t *>(src) + (size_t)done * slot_elems, bytes, kind, st);
+    else
+      err = cudaMemcpyAsync(static_cast<int16_t *>(dst) + (size_t)done * slot_elems, r, bytes, kind, st);
+    if (err != cudaSuccess) return err;
+    done += run;
+  }
+  return cudaSuccess;
+}
+
+tt_status upload_desc(tt_chan *c) {
+  tt_engine *e = c->e;
+  TT_CK(cudaMemcpyAsync(e->d_ues + c->index, &c->desc, sizeof(TTUEDesc), cudaMemcpyHostToDevice, e->stream));
+  // the host copy of the descriptor may change again before the copy runs
+  TT_CK(cudaStreamSynchronize(e->stream));
+  return TT_OK;
+}
+
+tt_status check_room(tt_chan *c, uint64_t first, uint32_t n) {
+  const uint64_t start = c->started ? c->pulled_end : first;
+  if (c->started && first != c->pushed_end)
+    return fail(TT_ERR_STATE, "slot %llu pushed, expected %llu", (unsigned long long)first,
+                (unsigned long long)c->pushed_end);
+  if (first + n - start + (uint64_t)c->hist > (uint64_t)c->Q)
+    return fail(TT_ERR_AGAIN, "slot ring full (depth %d): pull or release outputs first", c->Q);
+  return TT_OK;
+}
+
+void mark_pushed(tt_chan *c, uint64_t first, uint32_t n) {
+  if (!c->started) {
+    c->started = true;
+    c->pushed_end = c->launched_end = c->completed_end = c->pulled_end = first;
+  }
+  c->pushed_end = first + n;
+}
+
+bool valid_chan(const tt_chan *c) { return c && c->e; }
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+const char *tt_last_error(void) { return g_err.c_str(); }
+int32_t tt_abi_version(void) { return TT_CHAN_ABI_VERSION; }
+
+tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
+  if (!cfg || !out || cfg->struct_size < sizeof(tt_engine_config))
+    return fail(TT_ERR_INVALID, "tt_engine_create: bad config");
+  if (cfg->form > TT_FORM_PLAIN) return fail(TT_ERR_INVALID, "unknown form %u", cfg->form);
+  if (cfg->samples_per_thread && cfg->samples_per_thread != 1 && cfg->samples_per_thread != 2 &&
+      cfg->samples_per_thread != 4 && cfg->samples_per_thread != 8)
+    return fail(TT_ERR_INVALID, "samples_per_thread must be 0, 1, 2, 4 or 8");
+  int ndev = 0;
+  cudaError_t q = cudaGetDeviceCount(&ndev);
+  if (q != cudaSuccess || ndev == 0) return fail(TT_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(q));
+  if (cfg->device < 0 || cfg->device >= ndev) return fail(TT_ERR_CUDA, "no CUDA device %d", cfg->device);
+  TT_CK(cudaSetDevice(cfg->device));
+  tt_engine *e = new tt_engine();
+  e->device = cfg->device;
+  e->budget = cfg->hbm_budget_bytes;
+  e->form = cfg->form;
+  e->max_ues = cfg->max_ues ? cfg->max_ues : 1024;
+  e->spt_override = cfg->samples_per_thread;
+  e->persistent = cfg->persistent;
+  cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
+  e->table.assign(e->max_ues, nullptr);
+  cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_ues, sizeof(TTUEDesc) * e->max_ues);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_counters, sizeof(uint32_t) * e->counter_cap);
+  if (err != cudaSuccess) {
+    tt_engine_destroy(e);
+    return fail(TT_ERR_CUDA, "engine setup: %s", cudaGetErrorString(err));
+  }
+  *out = e;
+  return TT_OK;
+}
+
+tt_status tt_engine_destroy(tt_engine *e) {
+  if (!e) return fail(TT_ERR_INVALID, "null engine");
+  cudaSetDevice(e->device);
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  for (tt_chan *c : e->table)
+    if (c) {
+      cudaFree(c->d_in);
+      cudaFree(c->d_out);
+      cudaFree(c->d_taps);
+      cudaFree(c->d_delays);
+      c->e = nullptr;
+      delete c;
+    }
+  for (auto &p : e->events) cudaEventDestroy(p.second);
+  for (auto ev : e->pool) cudaEventDestroy(ev);
+  cudaFree(e->d_ues);
+  cudaFree(e->d_segs);
+  cudaFree(e->d_counters);
+  if (e->stream) cudaStreamDestroy(e->stream);
+  if (e->copy) cudaStreamDestroy(e->copy);
+  delete e;
+  return TT_OK;
+}
+
+tt_status tt_engine_stream(tt_engine *e, void **stream) {
+  if (!e || !stream) return fail(TT_ERR_INVALID, "null argument");
+  *stream = (void *)e->stream;
+  return TT_OK;
+}
+
+tt_status tt_engine_get_stats(tt_engine *e, tt_engine_stats *out) {
+  if (!e || !out) return fail(TT_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(e->mu);
+  tt_engine_stats s{};
+  s.hbm_in_use = e->in_use;
+  s.hbm_budget = e->budget;
+  for (tt_chan *c : e->table) s.n_chans += c ? 1 : 0;
+  s.launches = e->launches;
+  s.slots_processed = e->slots_processed;
+  *out = s;
+  return TT_OK;
+}
+
+tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out) {
+  if (!e || !cfg || !out || cfg->struct_size < sizeof(tt_chan_config))
+    return fail(TT_ERR_INVALID, "tt_chan_create: bad config");
+  const uint32_t N = cfg->samples_per_slot;
+  if (N == 0 || N > (1u << 24)) return fail(TT_ERR_INVALID, "samples_per_slot out of range");
+  if (cfg->symbols_per_slot == 0 || cfg->symbols_per_slot > TT_MAX_SYM || !cfg->symbol_len)
+    return fail(TT_ERR_INVALID, "symbols_per_slot must be 1..%d with symbol_len given", TT_MAX_SYM);
+  if (cfg->n_tx < 1 || cfg->n_tx > TT_MAX_ANT || cfg->n_rx < 1 || cfg->n_rx > TT_MAX_ANT)
+    return fail(TT_ERR_INVALID, "n_tx and n_rx must be 1..%d", TT_MAX_ANT);
+  if (cfg->max_taps < 1 || cfg->max_taps > TT_MAX_TAPS)
+    return fail(TT_ERR_INVALID, "max_taps must be 1..%d", TT_MAX_TAPS);
+  if (cfg->max_delay > TT_MAX_DELAY) return fail(TT_ERR_INVALID, "max_delay must be <= %d", TT_MAX_DELAY);
+  if (cfg->precision != TT_FP32) return fail(TT_ERR_INVALID, "only TT_FP32 channels run through the engine");
+  if (cfg->output_format > TT_OUT_CF32) return fail(TT_ERR_INVALID, "unknown output_format");
+  if (!(cfg->noise_var >= 0.0f) || !std::isfinite(cfg->noise_var)) return fail(TT_ERR_INVALID, "bad noise_var");
+  uint64_t sum = 0;
+  for (uint32_t j = 0; j < cfg->symbols_per_slot; ++j) {
+    if (cfg->symbol_len[j] == 0) return fail(TT_ERR_INVALID, "zero symbol length");
+    sum += cfg->symbol_len[j];
+  }
+  if (sum != N) return fail(TT_ERR_INVALID, "symbol lengths sum to %llu, not %u", (unsigned long long)sum, N);
+  const int hist = (int)((cfg->max_delay + N - 1) / N);
+  int Q = (int)cfg->ring_slots;
+  if (Q == 0) Q = hist + 4;
+  if (Q < hist + 2 || Q > (1 << 20)) return fail(TT_ERR_INVALID, "ring_slots must be >= %d", hist + 2);
+
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  uint32_t idx = 0;
+  while (idx < e->max_ues && e->table[idx]) ++idx;
+  if (idx == e->max_ues) return fail(TT_ERR_NO_MEMORY, "UE table full (%u)", e->max_ues);
+  const size_t in_e = (size_t)cfg->n_tx * N * 2;
+  const size_t out_e = (size_t)cfg->n_rx * N * (cfg->output_format == TT_OUT_CF32 ? 4 : 2);
+  const uint64_t bytes = (uint64_t)Q * (in_e + out_e) * sizeof(int16_t);
+  if (e->budget && e->in_use + bytes > e->budget)
+    return fail(TT_ERR_NO_MEMORY, "admission refused: %llu B needed, %llu of %llu B in use",
+                (unsigned long long)bytes, (unsigned long long)e->in_use, (unsigned long long)e->budget);
+  tt_chan *c = new tt_chan();
+  c->e = e;
+  c->index = idx;
+  c->cfg = *cfg;
+  c->sym_len.assign(cfg->symbol_len, cfg->symbol_len + cfg->symbols_per_slot);
+  c->cfg.symbol_len = nullptr;
+  c->n = (int)N;
+  c->Q = Q;
+  c->hist = hist;
+  c->slot_in_elems = in_e;
+  c->slot_out_elems = out_e;
+  cudaError_t err = cudaMalloc(&c->d_in, (size_t)Q * in_e * sizeof(int16_t));
+  if (err == cudaSuccess) err = cudaMalloc(&c->d_out, (size_t)Q * out_e * sizeof(int16_t));
+  if (err == cudaSuccess) err = cudaMemsetAsync(c->d_in, 0, (size_t)Q * in_e * sizeof(int16_t), e->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(c->d_out, 0, (size_t)Q * out_e * sizeof(int16_t), e->stream);
+  if (err != cudaSuccess) {
+    cudaFree(c->d_in);
+    cudaFree(c->d_out);
+    delete c;
+    return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "ring allocation: %s",
+                cudaGetErrorString(err));
+  }
+  c->ring_bytes = bytes;
+  e->in_use += bytes;
+  c->spt = pick_spt(c->sym_len, e->spt_override);
+  TTUEDesc &d = c->desc;
+  d.ring_in = c->d_in;
+  d.ring_out = c->d_out;
+  d.n = (int)N;
+  d.nsym = (int)cfg->symbols_per_slot;
+  d.n_tx = (int)cfg->n_tx;
+  d.n_rx = (int)cfg->n_rx;
+  d.ring_q = Q;
+  d.ue_id = cfg->ue_id;
+  d.seed = cfg->seed;
+  d.noise_std = cfg->noise_var > 0.f ? (float)std::sqrt((double)cfg->noise_var / 2.0) : 0.f;
+  d.out_f32 = cfg->output_format == TT_OUT_CF32 ? 1 : 0;
+  d.spt = c->spt;
+  d.groups = (int)N / c->spt;
+  d.items_per_slot = (d.groups + TT_TPB - 1) / TT_TPB;
+  int b = 0, g = 0;
+  for (int j = 0; j < d.nsym; ++j) {
+    d.sym_start[j] = b;
+    d.grp_start[j] = g;
+    b += (int)c->sym_len[j];
+    g += (int)c->sym_len[j] / c->spt;
+  }
+  d.sym_start[d.nsym] = b;
+  d.grp_start[d.nsym] = g;
+  std::vector<int32_t> L32(c->sym_len.begin(), c->sym_len.end());
+  c->max_sym_touched = tt_conv_max_sym_touched(c->spt, L32.data(), d.nsym);
+  e->table[idx] = c;
+  tt_status st = upload_desc(c);
+  if (st != TT_OK) return st;
+  *out = c;
+  return TT_OK;
+}
+
+tt_status tt_chan_destroy(tt_chan *c) {
+  if (!valid_chan(c)) return fail(TT_ERR_INVALID, "null channel");
+  tt_engine *e = c->e;
+  std::lock_guard<std::mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  cudaStreamSynchronize(e->stream);
+  cudaFree(c->d_in);
+  cudaFree(c->d_out);
+  cudaFree(c->d_taps);
+  cudaFree(c->d_delays);
+  e->in_use -= c->ring_bytes + c->trace_bytes;
+  e->table[c->index] = nullptr;
+  c->e = nullptr;
+  delete c;
+  return TT_OK;
+}
+
+tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
+  if (!valid_chan(c) || !tr || tr->struct_size < sizeof(tt_trace_desc))
+    return fail(TT_ERR_INVALID, "tt_chan_load_trace: bad argument");
+  tt_engine *e = c->e;
+  if (!tr->taps || !tr->delays || tr->n_anchors == 0 || tr->n_taps == 0)
+    return fail(TT_ERR_TRACE, "empty trace");
+  if (tr->n_taps > c->cfg.max_taps) return fail(TT_ERR_TRACE, "trace has %u taps, max_taps is %u", tr->n_taps,
+                                                c->cfg.max_taps);
+  if (!(tr->step_samples >= 0.0) || !std::isfinite(tr->step_samples))
+    return fail(TT_ERR_TRACE, "bad step_samples");
+  int d_max = 0;
+  for (uint32_t k = 0; k < tr->n_taps; ++k) {
+    const int32_t d = tr->delays[k];
+    if (d < 0 || (uint32_t)d > c->cfg.max_delay) return fail(TT_ERR_TRACE, "delay %d outside 0..%u", d,
+                                                            c->cfg.max_delay);
+    if (k && d < tr->delays[k - 1]) return fail(TT_ERR_TRACE, "delays must be non-decreasing");
+    d_max = std::max(d_max, (int)d);
+  }
+  const size_t per = (size_t)c->cfg.n_rx * c->cfg.n_tx * tr->n_taps;
+  const size_t nval = per * tr->n_anchors * 2;
+  for (size_t i = 0; i < nval; ++i)
+    if (!std::isfinite(tr->taps[i])) return fail(TT_ERR_TRACE, "non-finite tap value at %zu", i);
+  const int dclass = pick_dclass(d_max);
+  int spt = c->spt;
+  size_t smem = tt_conv_smem_bytes(spt, dclass, c->cfg.n_tx, c->cfg.n_rx, tr->n_taps, c->max_sym_touched);
+  if (smem > 200 * 1024) return fail(TT_ERR_INVALID, "channel too large for the tiled kernel (%zu B smem)", smem);
+
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  update_chan(c);
+  if (c->launched_end != c->completed_end) {
+    cudaError_t q = update_completed(e);
+    if (q != cudaSuccess) return fail(TT_ERR_CUDA, "%s", cudaGetErrorString(q));
+    update_chan(c);
+    if (c->launched_end != c->completed_end) return fail(TT_ERR_STATE, "work in flight; sync first");
+  }
+  const uint64_t bytes = nval * sizeof(float) + tr->n_taps * sizeof(int32_t);
+  if (e->budget && e->in_use - c->trace_bytes + bytes > e->budget)
+    return fail(TT_ERR_NO_MEMORY, "admission refused: trace of %llu B does not fit the budget",
+                (unsigned long long)bytes);
+  TT_CK(cudaStreamSynchronize(e->stream));
+  float2 *taps = nullptr;
+  int32_t *delays = nullptr;
+  cudaError_t err = cudaMalloc(&taps, nval * sizeof(float));
+  if (err == cudaSuccess) err = cudaMalloc(&delays, tr->n_taps * sizeof(int32_t));
+  if (err == cudaSuccess) err = cudaMemcpy(taps, tr->taps, nval * sizeof(float), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(delays, tr->delays, tr->n_taps * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    cudaFree(taps);
+    cudaFree(delays);
+    return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "trace upload: %s",
+                cudaGetErrorString(err));
+  }
+  cudaFree(c->d_taps);
+  cudaFree(c->d_delays);
+  e->in_use = e->in_use - c->trace_bytes + bytes;
+  c->trace_bytes = bytes;
+  c->d_taps = taps;
+  c->d_delays = delays;
+  c->has_trace = true;
+  c->dclass = dclass;
+  c->smem = smem;
+  TTUEDesc &d = c->desc;
+  d.taps = taps;
+  d.delays = delays;
+  d.step_samples = tr->step_samples;
+  d.n_taps = (int)tr->n_taps;
+  d.d_max = d_max;
+  d.n_anchors = (int)tr->n_anchors;
+  d.loop = tr->loop ? 1 : 0;
+  return upload_desc(c);
+}
+
+tt_status tt_chan_push_slot(tt_chan *c, uint64_t slot, const int16_t *iq_in) {
+  return tt_chan_push_slots(c, slot, 1, iq_in);
+}
+
+tt_status tt_chan_push_slots(tt_chan *c, uint64_t first, uint32_t n, const int16_t *iq_in) {
+  if (!valid_chan(c) || (!iq_in && n)) return fail(TT_ERR_INVALID, "tt_chan_push_slots: bad argument");
+  if (n == 0) return TT_OK;
+  tt_engine *e = c->e;
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  tt_status s = check_room(c, first, n);
+  if (s != TT_OK) return s;
+  // In stream order after every queued kernel (they may still read the ring
+  // positions being overwritten), then wait so the caller's buffer is free.
+  cudaError_t err = ring_copy(c->d_in, c->slot_in_elems, c->Q, first, n, iq_in, nullptr,
+                              cudaMemcpyHostToDevice, e->stream, true);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "push copy: %s", cudaGetErrorString(err));
+  mark_pushed(c, first, n);
+  return TT_OK;
+}
+
+tt_status tt_chan_push_slots_dev(tt_chan *c, uint64_t first, uint32_t n, const int16_t *d_iq_in,
+                                 void *stream) {
+  if (!valid_chan(c) || (!d_iq_in && n)) return fail(TT_ERR_INVALID, "tt_chan_push_slots_dev: bad argument");
+  if (n == 0) return TT_OK;
+  tt_engine *e = c->e;
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  tt_status s = check_room(c, first, n);
+  if (s != TT_OK) return s;
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  cudaError_t err = cudaEventRecord(ev, (cudaStream_t)stream);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, ev, 0);
+  if (err == cudaSuccess)
+    err = ring_copy(c->d_in, c->slot_in_elems, c->Q, first, n, d_iq_in, nullptr, cudaMemcpyDeviceToDevice,
+                    e->stream, true);
+  e->pool.push_back(ev);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "push copy: %s", cudaGetErrorString(err));
+  mark_pushed(c, first, n);
+  return TT_OK;
+}
+
+tt_status tt_chan_slot_input(tt_chan *c, uint64_t slot, int16_t **d_ptr) {
+  if (!valid_chan(c) || !d_ptr) return fail(TT_ERR_INVALID, "tt_chan_slot_input: bad argument");
+  std::lock_guard<std::mutex> lk(c->e->mu);
+  const uint64_t start = c->started ? c->pulled_end : slot;
+  if (c->started && slot < c->pushed_end) return fail(TT_ERR_STATE, "slot %llu already pushed",
+                                                      (unsigned long long)slot);
+  if (slot + 1 - start + (uint64_t)c->hist > (uint64_t)c->Q) return fail(TT_ERR_AGAIN, "slot ring full");
+  *d_ptr = c->d_in + (size_t)(slot % (uint64_t)c->Q) * c->slot_in_elems;
+  return TT_OK;
+}
+
+tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n) {
+  if (!valid_chan(c)) return fail(TT_ERR_INVALID, "null channel");
+  if (n == 0) return TT_OK;
+  std::lock_guard<std::mutex> lk(c->e->mu);
+  tt_status s = check_room(c, first, n);
+  if (s != TT_OK) return s;
+  mark_pushed(c, first, n);
+  return TT_OK;
+}
+
+tt_status tt_engine_run(tt_engine *e) {
+  if (!e) return fail(TT_ERR_INVALID, "null engine");
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  std::vector<tt_chan *> ready;
+  for (tt_chan *c : e->table)
+    if (c && c->has_trace && c->started && c->pushed_end > c->launched_end) ready.push_back(c);
+  if (ready.empty()) return TT_OK;
+
+  if (e->form == TT_FORM_PLAIN) {
+    for (tt_chan *c : ready) {
+      for (uint64_t s = c->launched_end; s < c->pushed_end; ++s) {
+        cudaError_t err = tt_launch_plain(e->d_ues + c->index, s, c->n, e->stream);
+        if (err != cudaSuccess) return fail(TT_ERR_CUDA, "plain launch: %s", cudaGetErrorString(err));
+        ++e->launches;
+      }
+    }
+  } else {
+    // group by kernel variant; inside a group, heaviest items first
+    struct Entry { tt_chan *c; double cost; };
+    std::vector<std::vector<Entry>> groups;
+    std::vector<int> keys;
+    for (tt_chan *c : ready) {
+      const int key = (c->spt * 8 + c->cfg.n_rx) * 4 + c->dclass;
+      size_t gi = std::find(keys.begin(), keys.end(), key) - keys.begin();
+      if (gi == keys.size()) {
+        keys.push_back(key);
+        groups.emplace_back();
+      }
+      groups[gi].push_back({c, (double)c->desc.n_taps * c->cfg.n_tx * c->cfg.n_rx});
+    }
+    size_t nseg = ready.size();
+    if (nseg > e->seg_cap) {
+      cudaFree(e->d_segs);
+      e->d_segs = nullptr;
+      e->seg_cap = 0;
+      TT_CK(cudaMalloc(&e->d_segs, sizeof(TTSeg) * nseg * 2));
+      e->seg_cap = nseg * 2;
+    }
+    if ((int)groups.size() > e->counter_cap) return fail(TT_ERR_INVALID, "too many kernel variants");
+    std::vector<TTSeg> segs;
+    segs.reserve(nseg);
+    struct GL { size_t seg0; int nseg; uint32_t items; size_t smem; int spt, nrx, dclass; };
+    std::vector<GL> gls;
+    for (auto &g : groups) {
+      std::stable_sort(g.begin(), g.end(), [](const Entry &a, const Entry &b) { return a.cost > b.cost; });
+      GL gl{segs.size(), 0, 0, 0, g[0].c->spt, (int)g[0].c->cfg.n_rx, g[0].c->dclass};
+      for (auto &en : g) {
+        tt_chan *c = en.c;
+        TTSeg s{};
+        s.first_slot = c->launched_end;
+        s.ue = c->index;
+        s.n_slots = (uint32_t)(c->pushed_end - c->launched_end);
+        s.item_begin = gl.items;
+        s.items = s.n_slots * (uint32_t)c->desc.items_per_slot;
+        gl.items += s.items;
+        gl.smem = std::max(gl.smem, c->smem);
+        segs.push_back(s);
+        ++gl.nseg;
+      }
+      gls.push_back(gl);
+    }
+    TT_CK(cudaMemcpyAsync(e->d_segs, segs.data(), sizeof(TTSeg) * segs.size(), cudaMemcpyHostToDevice,
+                          e->stream));
+    if (e->persistent) TT_CK(cudaMemsetAsync(e->d_counters, 0, sizeof(uint32_t) * gls.size(), e->stream));
+    for (size_t gi = 0; gi < gls.size(); ++gi) {
+      const GL &gl = gls[gi];
+      TTLaunch L{};
+      L.ues = e->d_ues;
+      L.segs = e->d_segs + gl.seg0;
+      L.n_segs = gl.nseg;
+      L.total_items = gl.items;
+      L.spt = gl.spt;
+      L.nrx = gl.nrx;
+      L.dclass = gl.dclass;
+      L.smem = gl.smem;
+      L.counter = nullptr;
+      if (e->persistent) {
+        L.grid = -1;  // occupancy query
+        tt_launch_conv_fp32(L, e->stream);
+        const int per_sm = -L.grid;
+        L.counter = e->d_counters + gi;
+        L.grid = (int)std::min<uint64_t>((uint64_t)per_sm * e->num_sms, gl.items);
+      }
+      cudaError_t err = tt_launch_conv_fp32(L, e->stream);
+      if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tiled launch: %s", cudaGetErrorString(err));
+      ++e->launches;
+    }
+  }
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  TT_CK(cudaEventRecord(ev, e->stream));
+  const uint64_t seq = ++e->launch_seq;
+  e->events.emplace_back(seq, ev);
+  for (tt_chan *c : ready) {
+    e->slots_processed += c->pushed_end - c->launched_end;
+    c->inflight.emplace_back(c->pushed_end, seq);
+    c->launched_end = c->pushed_end;
+  }
+  return TT_OK;
+}
+
+tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us) {
+  if (!e) return fail(TT_ERR_INVALID, "null engine");
+  std::unique_lock<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  tt_status s = wait_seq(e, e->launch_seq, timeout_us, lk);
+  if (s != TT_OK) return s;
+  if (timeout_us < 0) TT_CK(cudaStreamSynchronize(e->stream));
+  for (tt_chan *c : e->table)
+    if (c) update_chan(c);
+  return TT_OK;
+}
+
+static tt_status pull_common(tt_chan *c, uint64_t first, uint32_t n, void *out, int64_t timeout_us) {
+  tt_engine *e = c->e;
+  std::unique_lock<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  if (!c->started || first != c->pulled_end)
+    return fail(TT_ERR_STATE, "pull must start at the oldest unpulled slot %llu", (unsigned long long)c->pulled_end);
+  if (first + n > c->launched_end) return fail(TT_ERR_AGAIN, "slot not launched yet");
+  update_chan(c);
+  if (first + n > c->completed_end) {
+    uint64_t need = 0;
+    for (auto &p : c->inflight)
+      if (p.first >= first + n) { need = p.second; break; }
+    tt_status s = wait_seq(e, need, timeout_us, lk);
+    if (s != TT_OK) return s;
+    update_chan(c);
+  }
+  cudaError_t err = ring_copy(c->d_out, c->slot_out_elems, c->Q, first, n, nullptr, out,
+                              cudaMemcpyDeviceToHost, e->copy, false);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(e->copy);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "pull copy: %s", cudaGetErrorString(err));
+  c->pulled_end = first + n;
+  return TT_OK;
+}
+
+tt_status tt_chan_pull_slot(tt_chan *c, uint64_t *slot, void *iq_out, int64_t timeout_us) {
+  if (!valid_chan(c) || !slot || !iq_out) return fail(TT_ERR_INVALID, "tt_chan_pull_slot: bad argument");
+  const uint64_t s = c->pulled_end;
+  tt_status st = pull_common(c, s, 1, iq_out, timeout_us);
+  if (st == TT_OK) *slot = s;
+  return st;
+}
+
+tt_status tt_chan_pull_slots(tt_chan *c, uint64_t first, uint32_t n, void *iq_out, int64_t timeout_us) {
+  if (!valid_chan(c) || (!iq_out && n)) return fail(TT_ERR_INVALID, "tt_chan_pull_slots: bad argument");
+  if (n == 0) return TT_OK;
+  return pull_common(c, first, n, iq_out, timeout_us);
+}
+
+tt_status tt_chan_pull_slots_dev(tt_chan *c, uint64_t first, uint32_t n, void *d_iq_out, void *stream) {
+  if (!valid_chan(c) || (!d_iq_out && n)) return fail(TT_ERR_INVALID, "tt_chan_pull_slots_dev: bad argument");
+  if (n == 0) return TT_OK;
+  tt_engine *e = c->e;
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  if (!c->started || first != c->pulled_end)
+    return fail(TT_ERR_STATE, "pull must start at the oldest unpulled slot %llu", (unsigned long long)c->pulled_end);
+  if (first + n > c->launched_end) return fail(TT_ERR_AGAIN, "slot not launched yet");
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  cudaError_t err = ring_copy(c->d_out, c->slot_out_elems, c->Q, first, n, nullptr, d_iq_out,
+                              cudaMemcpyDeviceToDevice, e->stream, false);
+  if (err == cudaSuccess) err = cudaEventRecord(ev, e->stream);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent((cudaStream_t)stream, ev, 0);
+  e->pool.push_back(ev);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "pull copy: %s", cudaGetErrorString(err));
+  c->pulled_end = first + n;
+  return TT_OK;
+}
+
+tt_status tt_chan_slot_output(tt_chan *c, uint64_t slot, const void **d_ptr) {
+  if (!valid_chan(c) || !d_ptr) return fail(TT_ERR_INVALID, "tt_chan_slot_output: bad argument");
+  std::lock_guard<std::mutex> lk(c->e->mu);
+  if (!c->started || slot < c->pulled_end || slot >= c->launched_end)
+    return fail(TT_ERR_STATE, "slot %llu is not a launched, unreleased slot", (unsigned long long)slot);
+  *d_ptr = c->d_out + (size_t)(slot % (uint64_t)c->Q) * c->slot_out_elems;
+  return TT_OK;
+}
+
+tt_status tt_chan_release_slots(tt_chan *c, uint64_t first, uint32_t n) {
+  if (!valid_chan(c)) return fail(TT_ERR_INVALID, "null channel");
+  std::lock_guard<std::mutex> lk(c->e->mu);
+  if (!c->started || first != c->pulled_end || first + n > c->launched_end)
+    return fail(TT_ERR_STATE, "release must cover launched slots from %llu", (unsigned long long)c->pulled_end);
+  c->pulled_end = first + n;
+  return TT_OK;
+}
+
+// ---- checkpoint / resume ----
+namespace {
+struct StateHeader {
+  uint32_t magic;  // 'TTS1'
+  uint32_t version;
+  uint32_t n, n_tx, hist_samples, started;
+  uint64_t next_slot, seed;
+  uint32_t ue_id, pad;
+};
+const uint32_t kStateMagic = 0x31535454u;
+}  // namespace
+
+tt_status tt_chan_get_state(const tt_chan *cc, void *buf, size_t *len) {
+  tt_chan *c = const_cast<tt_chan *>(cc);
+  if (!valid_chan(c) || !len) return fail(TT_ERR_INVALID, "tt_chan_get_state: bad argument");
+  const uint32_t D = c->cfg.max_delay;
+  const size_t need = sizeof(StateHeader) + (size_t)c->cfg.n_tx * D * 2 * sizeof(int16_t);
+  if (!buf) {
+    *len = need;
+    return TT_OK;
+  }
+  if (*len < need) return fail(TT_ERR_INVALID, "state buffer too small (%zu < %zu)", *len, need);
+  tt_engine *e = c->e;
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  cudaError_t q = update_completed(e);
+  if (q != cudaSuccess) return fail(TT_ERR_CUDA, "%s", cudaGetErrorString(q));
+  update_chan(c);
+  if (c->launched_end != c->pushed_end || c->completed_end != c->launched_end)
+    return fail(TT_ERR_STATE, "channel has pending or running slots; run and sync first");
+  TT_CK(cudaStreamSynchronize(e->stream));
+  StateHeader h{};
+  h.magic = kStateMagic;
+  h.version = 1;
+  h.n = (uint32_t)c->n;
+  h.n_tx = c->cfg.n_tx;
+  h.hist_samples = D;
+  h.started = c->started ? 1u : 0u;
+  h.next_slot = c->pushed_end;
+  h.seed = c->cfg.seed;
+  h.ue_id = c->cfg.ue_id;
+  std::memcpy(buf, &h, sizeof h);
+  int16_t *out = reinterpret_cast<int16_t *>(static_cast<char *>(buf) + sizeof h);
+  std::memset(out, 0, (size_t)c->cfg.n_tx * D * 2 * sizeof(int16_t));
+  if (c->started) {
+    // samples m in [next*N - D, next*N) of every Tx antenna, from the ring slots holding them
+    const uint64_t next = c->pushed_end;
+    std::vector<int16_t> slotbuf(c->slot_in_elems);
+    for (int b = c->hist; b >= 1; --b) {
+      if ((uint64_t)b > next) continue;
+      const uint64_t s = next - (uint64_t)b;
+      TT_CK(cudaMemcpy(slotbuf.data(), c->d_in + (size_t)(s % (uint64_t)c->Q) * c->slot_in_elems,
+                       c->slot_in_elems * sizeof(int16_t), cudaMemcpyDeviceToHost));
+      for (uint32_t t = 0; t < c->cfg.n_tx; ++t)
+        for (uint32_t i = 0; i < D; ++i) {
+          const int64_t m = (int64_t)next * c->n - (int64_t)D + (int64_t)i;
+          if (m < (int64_t)s * c->n || m >= (int64_t)(s + 1) * c->n) continue;
+          const size_t w = (size_t)(m - (int64_t)s * c->n);
+          out[((size_t)t * D + i) * 2] = slotbuf[((size_t)t * c->n + w) * 2];
+          out[((size_t)t * D + i) * 2 + 1] = slotbuf[((size_t)t * c->n + w) * 2 + 1];
+        }
+    }
+  }
+  *len = need;
+  return TT_OK;
+}
+
+tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len) {
+  if (!valid_chan(c) || !buf) return fail(TT_ERR_INVALID, "tt_chan_set_state: bad argument");
+  StateHeader h{};
+  if (len < sizeof h) return fail(TT_ERR_STATE, "state blob too short");
+  std::memcpy(&h, buf, sizeof h);
+  const uint32_t D = c->cfg.max_delay;
+  if (h.magic != kStateMagic || h.version != 1 || h.n != (uint32_t)c->n || h.n_tx != c->cfg.n_tx ||
+      h.hist_samples != D || len < sizeof h + (size_t)h.n_tx * D * 2 * sizeof(int16_t))
+    return fail(TT_ERR_STATE, "state blob does not match this channel");
+  tt_engine *e = c->e;
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  cudaError_t q = update_completed(e);
+  if (q != cudaSuccess) return fail(TT_ERR_CUDA, "%s", cudaGetErrorString(q));
+  update_chan(c);
+  if (c->launched_end != c->pushed_end || c->completed_end != c->launched_end)
+    return fail(TT_ERR_STATE, "channel has pending or running slots");
+  TT_CK(cudaStreamSynchronize(e->stream));
+  const int16_t *in = reinterpret_cast<const int16_t *>(static_cast<const char *>(buf) + sizeof h);
+  const uint64_t next = h.next_slot;
+  // zero the history slots, then write the saved samples into them
+  for (int b = 1; b <= c->hist; ++b) {
+    if ((uint64_t)b > next) break;
+    const uint64_t s = next - (uint64_t)b;
+    TT_CK(cudaMemset(c->d_in + (size_t)(s % (uint64_t)c->Q) * c->slot_in_elems, 0,
+                     c->slot_in_elems * sizeof(int16_t)));
+  }
+  if (h.started) {
+    std::vector<int16_t> slotbuf(c->slot_in_elems);
+    for (int b = c->hist; b >= 1; --b) {
+      if ((uint64_t)b > next) continue;
+      const uint64_t s = next - (uint64_t)b;
+      std::fill(slotbuf.begin(), slotbuf.end(), 0);
+      for (uint32_t t = 0; t < c->cfg.n_tx; ++t)
+        for (uint32_t i = 0; i < D; ++i) {
+          const int64_t m = (int64_t)next * c->n - (int64_t)D + (int64_t)i;
+          if (m < (int64_t)s * c->n || m >= (int64_t)(s + 1) * c->n) continue;
+          const size_t w = (size_t)(m - (int64_t)s * c->n);
+          slotbuf[((size_t)t * c->n + w) * 2] = in[((size_t)t * D + i) * 2];
+          slotbuf[((size_t)t * c->n + w) * 2 + 1] = in[((size_t)t * D + i) * 2 + 1];
+        }
+      TT_CK(cudaMemcpy(c->d_in + (size_t)(s % (uint64_t)c->Q) * c->slot_in_elems, slotbuf.data(),
+                       c->slot_in_elems * sizeof(int16_t), cudaMemcpyHostToDevice));
+    }
+  }
+  c->cfg.seed = h.seed;
+  c->cfg.ue_id = h.ue_id;
+  c->desc.seed = h.seed;
+  c->desc.ue_id = h.ue_id;
+  c->started = h.started != 0;
+  c->pushed_end = c->launched_end = c->completed_end = c->pulled_end = next;
+  c->inflight.clear();
+  return upload_desc(c);
+}
+
+}  // extern "C"

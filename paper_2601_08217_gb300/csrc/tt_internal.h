@@ -1,0 +1,89 @@
+// Internal types shared by the engine (host C++) and the CUDA kernels.
+// Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define TT_MAX_SYM 32
+#define TT_MAX_ANT 4
+#define TT_MAX_TAPS 128
+#define TT_MAX_DELAY 1024
+#define TT_TPB 128  // threads per CTA of the tiled kernel
+
+// Delay classes of the tiled kernel: the staged window is sized at compile
+// time for delays up to these bounds.
+#define TT_DCLASS0 128
+#define TT_DCLASS1 512
+#define TT_DCLASS2 1024
+
+// Window geometry of the tiled kernel (samples per thread S, delay class DMAX):
+// delay padding DP (a multiple of S) and phase-plane pitch NP in float2 words.
+__host__ __device__ constexpr int tt_geo_dp(int S, int DMAX) { return (DMAX + S - 1) / S * S; }
+__host__ __device__ constexpr int tt_geo_np(int S, int DMAX) {
+  return (TT_TPB * S + tt_geo_dp(S, DMAX)) / S + 1;
+}
+__host__ __device__ constexpr int tt_dclass_max(int dclass) {
+  return dclass == 0 ? TT_DCLASS0 : (dclass == 1 ? TT_DCLASS1 : TT_DCLASS2);
+}
+
+// Device-resident description of one admitted UE link.  The engine keeps an
+// array of these on the device; work items index into it.
+struct TTUEDesc {
+  const int16_t *ring_in;  // [Q][n_tx][N][2]
+  void *ring_out;          // [Q][n_rx][N] x (int16 I,Q | float2)
+  const float2 *taps;      // [T][n_rx][n_tx][K]
+  const int32_t *delays;   // [K]
+  double step_samples;     // 0: one trace entry per symbol
+  uint64_t seed;
+  int32_t n;               // samples per slot
+  int32_t nsym;            // symbols per slot
+  int32_t n_tx, n_rx, n_taps;
+  int32_t d_max;           // largest delay of the loaded trace
+  int32_t ring_q;          // ring depth in slots
+  int32_t n_anchors;
+  int32_t loop;
+  uint32_t ue_id;
+  float noise_std;         // per I/Q component; 0 = AWGN off
+  int32_t out_f32;         // 1: write y as float2 (no packing)
+  int32_t spt;             // samples per thread of the tiled kernel for this UE
+  int32_t groups;          // groups of spt samples per slot
+  int32_t items_per_slot;  // CTAs (work items) per slot
+  int32_t sym_start[TT_MAX_SYM + 1];  // symbol starts, sym_start[nsym] = n
+  int32_t grp_start[TT_MAX_SYM + 1];  // first group of each symbol, grp_start[nsym] = groups
+};
+
+// A run of consecutive slots of one UE inside one launch.
+struct TTSeg {
+  uint64_t first_slot;
+  uint32_t ue;          // index into the UE table
+  uint32_t n_slots;
+  uint32_t item_begin;  // first global work-item index of this run
+  uint32_t items;       // n_slots * items_per_slot
+};
+
+struct TTLaunch {
+  const TTUEDesc *ues;
+  const TTSeg *segs;
+  int n_segs;
+  uint32_t total_items;
+  uint32_t *counter;    // persistent mode: device work counter (zeroed before launch); else null
+  int spt;              // 1, 2, 4, 8
+  int nrx;              // 1..4
+  int dclass;           // 0: d_max <= 256, 1: d_max <= 1024
+  int grid;             // CTAs (persistent) -- ignored otherwise
+  size_t smem;          // dynamic shared memory bytes
+};
+
+// Per-UE dynamic shared memory of the tiled kernel.
+size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int n_rx, int n_taps, int max_sym_touched);
+int tt_conv_max_sym_touched(int spt, const int32_t *sym_len, int nsym);
+cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s1(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s2(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s4(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s8(const TTLaunch &L, cudaStream_t st);
+
+// Plain comparison form: one launch per UE per slot.
+cudaError_t tt_launch_plain(const TTUEDesc *ue_dev, uint64_t slot, int n, cudaStream_t st);

@@ -1,0 +1,364 @@
+"""Thin ctypes binding of libttchan.so (the C ABI in include/tt_chan.h).
+
+Argument marshalling only: every step of the channel path runs in the CUDA
+library.  Functions keep the C names (``tt_engine_create`` ...); ``Engine`` and
+``Chan`` are small conveniences over them.  If the library has not been built
+the binding raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libttchan.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "tt_chan.h")
+
+TT_OK, TT_ERR_INVALID, TT_ERR_NO_MEMORY, TT_ERR_CUDA = 0, -1, -2, -3
+TT_ERR_TRACE, TT_ERR_AGAIN, TT_ERR_TIMEOUT, TT_ERR_STATE = -4, -5, -6, -7
+TT_FORM_BATCHED, TT_FORM_PLAIN = 0, 1
+TT_FP32, TT_BF16_TC, TT_FP16_TC = 0, 1, 2
+TT_OUT_INT16, TT_OUT_CF32 = 0, 1
+
+STATUS_NAMES = {0: "TT_OK", -1: "TT_ERR_INVALID", -2: "TT_ERR_NO_MEMORY", -3: "TT_ERR_CUDA",
+                -4: "TT_ERR_TRACE", -5: "TT_ERR_AGAIN", -6: "TT_ERR_TIMEOUT", -7: "TT_ERR_STATE"}
+
+
+class TTError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class EngineConfig(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("device", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
+                ("form", C.c_uint32), ("max_ues", C.c_uint32), ("samples_per_thread", C.c_uint32),
+                ("threads_per_block", C.c_uint32), ("persistent", C.c_uint32)]
+
+
+class ChanConfig(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("ue_id", C.c_uint32), ("samples_per_slot", C.c_uint32),
+                ("symbols_per_slot", C.c_uint32), ("symbol_len", C.POINTER(C.c_uint32)),
+                ("n_tx", C.c_uint32), ("n_rx", C.c_uint32), ("max_taps", C.c_uint32),
+                ("max_delay", C.c_uint32), ("ring_slots", C.c_uint32), ("seed", C.c_uint64),
+                ("noise_var", C.c_float), ("precision", C.c_uint32), ("output_format", C.c_uint32)]
+
+
+class TraceDesc(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("taps", C.POINTER(C.c_float)),
+                ("delays", C.POINTER(C.c_int32)), ("n_anchors", C.c_uint32), ("n_taps", C.c_uint32),
+                ("step_samples", C.c_double), ("loop", C.c_int32)]
+
+
+class EngineStats(C.Structure):
+    _fields_ = [("hbm_in_use", C.c_uint64), ("hbm_budget", C.c_uint64), ("n_chans", C.c_uint32),
+                ("pad", C.c_uint32), ("launches", C.c_uint64), ("slots_processed", C.c_uint64)]
+
+
+_VP = C.c_void_p
+_SIGS = {
+    "tt_engine_create": [C.POINTER(EngineConfig), C.POINTER(_VP)],
+    "tt_engine_destroy": [_VP],
+    "tt_engine_run": [_VP],
+    "tt_engine_sync": [_VP, C.c_int64],
+    "tt_engine_stream": [_VP, C.POINTER(_VP)],
+    "tt_engine_get_stats": [_VP, C.POINTER(EngineStats)],
+    "tt_chan_create": [_VP, C.POINTER(ChanConfig), C.POINTER(_VP)],
+    "tt_chan_destroy": [_VP],
+    "tt_chan_load_trace": [_VP, C.POINTER(TraceDesc)],
+    "tt_chan_push_slot": [_VP, C.c_uint64, _VP],
+    "tt_chan_push_slots": [_VP, C.c_uint64, C.c_uint32, _VP],
+    "tt_chan_push_slots_dev": [_VP, C.c_uint64, C.c_uint32, _VP, _VP],
+    "tt_chan_slot_input": [_VP, C.c_uint64, C.POINTER(_VP)],
+    "tt_chan_commit_slots": [_VP, C.c_uint64, C.c_uint32],
+    "tt_chan_pull_slot": [_VP, C.POINTER(C.c_uint64), _VP, C.c_int64],
+    "tt_chan_pull_slots": [_VP, C.c_uint64, C.c_uint32, _VP, C.c_int64],
+    "tt_chan_pull_slots_dev": [_VP, C.c_uint64, C.c_uint32, _VP, _VP],
+    "tt_chan_slot_output": [_VP, C.c_uint64, C.POINTER(_VP)],
+    "tt_chan_release_slots": [_VP, C.c_uint64, C.c_uint32],
+    "tt_chan_get_state": [_VP, _VP, C.POINTER(C.c_size_t)],
+    "tt_chan_set_state": [_VP, _VP, C.c_size_t],
+}
+
+_lib = None
+
+
+def header_functions(path: str = HEADER) -> list:
+    """Names of every function the public headers declare."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(tt_\w+)\s*\(", txt, flags=re.M)))
+
+
+def load(path: Optional[str] = None):
+    """Load libttchan.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libttchan.so is not built ({p}); run __graft_entry__.build()")
+    lib = C.CDLL(p)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int32
+    lib.tt_last_error.restype = C.c_char_p
+    lib.tt_last_error.argtypes = []
+    lib.tt_abi_version.restype = C.c_int32
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != TT_OK:
+        raise TTError(status, (_lib.tt_last_error() or b"").decode(errors="replace"))
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array or a torch tensor (host or device); 0 for None."""
+    if x is None:
+        return 0
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("buffer must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- C-named calls
+def tt_engine_create(device: int = 0, form: int = TT_FORM_BATCHED, hbm_budget_bytes: int = 0,
+                     max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False) -> int:
+    lib = load()
+    cfg = EngineConfig(C.sizeof(EngineConfig), device, hbm_budget_bytes, form, max_ues,
+                       samples_per_thread, 0, int(bool(persistent)))
+    h = _VP()
+    _check(lib.tt_engine_create(C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def tt_engine_destroy(e: int):
+    _check(load().tt_engine_destroy(e))
+
+
+def tt_engine_run(e: int):
+    _check(load().tt_engine_run(e))
+
+
+def tt_engine_sync(e: int, timeout_us: int = -1):
+    _check(load().tt_engine_sync(e, timeout_us))
+
+
+def tt_engine_stream(e: int) -> int:
+    s = _VP()
+    _check(load().tt_engine_stream(e, C.byref(s)))
+    return s.value or 0
+
+
+def tt_engine_get_stats(e: int) -> dict:
+    st = EngineStats()
+    _check(load().tt_engine_get_stats(e, C.byref(st)))
+    return {f: getattr(st, f) for f, _ in EngineStats._fields_ if f != "pad"}
+
+
+def tt_chan_create(e: int, samples_per_slot: int, symbol_len: Sequence[int], n_tx: int = 1, n_rx: int = 1,
+                   max_taps: int = 128, max_delay: int = 0, ring_slots: int = 0, seed: int = 0,
+                   noise_var: float = 0.0, ue_id: int = 0, precision: int = TT_FP32,
+                   output_format: int = TT_OUT_INT16) -> int:
+    lib = load()
+    L = (C.c_uint32 * len(symbol_len))(*[int(v) for v in symbol_len])
+    cfg = ChanConfig(C.sizeof(ChanConfig), ue_id, samples_per_slot, len(symbol_len), L, n_tx, n_rx,
+                     max_taps, max_delay, ring_slots, seed, noise_var, precision, output_format)
+    h = _VP()
+    _check(lib.tt_chan_create(e, C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def tt_chan_destroy(c: int):
+    _check(load().tt_chan_destroy(c))
+
+
+def tt_chan_load_trace(c: int, taps: np.ndarray, delays, step_samples: float = 0.0, loop: bool = False):
+    """taps: complex [n_anchors][n_rx][n_tx][K]; delays: int [K]."""
+    taps = np.asarray(taps)
+    if taps.ndim != 4 or not np.iscomplexobj(taps):
+        raise ValueError("taps must be complex [n_anchors][n_rx][n_tx][K]")
+    n_anchors = taps.shape[0]
+    t = np.ascontiguousarray(taps.astype(np.complex64)).view(np.float32).reshape(-1)
+    d = np.ascontiguousarray(delays, dtype=np.int32)
+    k = int(d.size)
+    desc = TraceDesc(C.sizeof(TraceDesc), t.ctypes.data_as(C.POINTER(C.c_float)),
+                     d.ctypes.data_as(C.POINTER(C.c_int32)), n_anchors, k, float(step_samples), int(bool(loop)))
+    _check(load().tt_chan_load_trace(c, C.byref(desc)))
+
+
+def tt_chan_push_slot(c: int, slot: int, iq_in):
+    _check(load().tt_chan_push_slot(c, slot, _ptr(iq_in)))
+
+
+def tt_chan_push_slots(c: int, first: int, n: int, iq_in):
+    _check(load().tt_chan_push_slots(c, first, n, _ptr(iq_in)))
+
+
+def tt_chan_push_slots_dev(c: int, first: int, n: int, d_iq_in, stream=None):
+    _check(load().tt_chan_push_slots_dev(c, first, n, _ptr(d_iq_in), _stream_ptr(stream)))
+
+
+def tt_chan_slot_input(c: int, slot: int) -> int:
+    p = _VP()
+    _check(load().tt_chan_slot_input(c, slot, C.byref(p)))
+    return p.value
+
+
+def tt_chan_commit_slots(c: int, first: int, n: int):
+    _check(load().tt_chan_commit_slots(c, first, n))
+
+
+def tt_chan_pull_slot(c: int, iq_out, timeout_us: int = -1) -> int:
+    s = C.c_uint64()
+    _check(load().tt_chan_pull_slot(c, C.byref(s), _ptr(iq_out), timeout_us))
+    return s.value
+
+
+def tt_chan_pull_slots(c: int, first: int, n: int, iq_out, timeout_us: int = -1):
+    _check(load().tt_chan_pull_slots(c, first, n, _ptr(iq_out), timeout_us))
+
+
+def tt_chan_pull_slots_dev(c: int, first: int, n: int, d_iq_out, stream=None):
+    _check(load().tt_chan_pull_slots_dev(c, first, n, _ptr(d_iq_out), _stream_ptr(stream)))
+
+
+def tt_chan_slot_output(c: int, slot: int) -> int:
+    p = _VP()
+    _check(load().tt_chan_slot_output(c, slot, C.byref(p)))
+    return p.value
+
+
+def tt_chan_release_slots(c: int, first: int, n: int):
+    _check(load().tt_chan_release_slots(c, first, n))
+
+
+def tt_chan_get_state(c: int) -> bytes:
+    lib = load()
+    n = C.c_size_t(0)
+    _check(lib.tt_chan_get_state(c, None, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(lib.tt_chan_get_state(c, buf, C.byref(n)))
+    return buf.raw[: n.value]
+
+
+def tt_chan_set_state(c: int, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load().tt_chan_set_state(c, buf, len(blob)))
+
+
+def tt_last_error() -> str:
+    return (load().tt_last_error() or b"").decode(errors="replace")
+
+
+def tt_abi_version() -> int:
+    return int(load().tt_abi_version())
+
+
+# ---------------------------------------------------------------- conveniences
+class Engine:
+    def __init__(self, device: int = 0, form: str = "batched", hbm_budget_bytes: int = 0,
+                 max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False):
+        f = {"batched": TT_FORM_BATCHED, "plain": TT_FORM_PLAIN}[form]
+        self.h = tt_engine_create(device, f, hbm_budget_bytes, max_ues, samples_per_thread, persistent)
+        self.chans = []
+
+    def run(self):
+        tt_engine_run(self.h)
+
+    def sync(self, timeout_us: int = -1):
+        tt_engine_sync(self.h, timeout_us)
+
+    @property
+    def stream(self) -> int:
+        return tt_engine_stream(self.h)
+
+    def stats(self) -> dict:
+        return tt_engine_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            tt_engine_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Chan:
+    """One UE link.  ``spec`` is an ``inputs.UESpec`` (or anything with its fields)."""
+
+    def __init__(self, engine: Engine, spec, ring_slots: int = 0, load: bool = True, cf32: bool = False):
+        self.engine = engine
+        self.spec = spec
+        self.cf32 = cf32
+        self.n = int(sum(spec.symbol_len))
+        self.h = tt_chan_create(engine.h, self.n, spec.symbol_len, spec.n_tx, spec.n_rx,
+                                max(int(len(spec.delays)), 1), int(max(spec.max_delay, max(spec.delays))),
+                                ring_slots, int(spec.seed), float(spec.noise_var), int(spec.ue_id),
+                                output_format=TT_OUT_CF32 if cf32 else TT_OUT_INT16)
+        engine.chans.append(self)
+        if load:
+            self.load_trace(spec.taps, spec.delays, spec.step_samples, spec.loop)
+
+    def load_trace(self, taps, delays, step_samples=0.0, loop=False):
+        tt_chan_load_trace(self.h, np.asarray(taps), delays, step_samples, loop)
+
+    def push(self, first: int, iq: np.ndarray):
+        """iq: int16 [n_slots][n_tx][N][2] (or [n_tx][n_slots*N][2], reordered here)."""
+        iq = np.asarray(iq, dtype=np.int16)
+        if iq.ndim == 3:
+            iq = slots_major(iq, self.n)
+        tt_chan_push_slots(self.h, first, iq.shape[0], np.ascontiguousarray(iq))
+
+    def pull(self, first: int, n_slots: int, timeout_us: int = -1) -> np.ndarray:
+        """int16 [n_slots][n_rx][N][2], or complex64 [n_slots][n_rx][N] for a TT_OUT_CF32 channel."""
+        if self.cf32:
+            out = np.empty((n_slots, self.spec.n_rx, self.n), dtype=np.complex64)
+        else:
+            out = np.empty((n_slots, self.spec.n_rx, self.n, 2), dtype=np.int16)
+        tt_chan_pull_slots(self.h, first, n_slots, out, timeout_us)
+        return out
+
+    def destroy(self):
+        if self.h:
+            tt_chan_destroy(self.h)
+            self.h = None
+
+
+def slots_major(x: np.ndarray, n: int) -> np.ndarray:
+    """[ant][n_slots*N][2] -> [n_slots][ant][N][2]."""
+    a, tot, _ = x.shape
+    return np.ascontiguousarray(x.reshape(a, tot // n, n, 2).transpose(1, 0, 2, 3))
+
+
+def antenna_major(y: np.ndarray) -> np.ndarray:
+    """[n_slots][ant][N](...) -> [ant][n_slots*N](...)."""
+    s, a, n = y.shape[:3]
+    return np.ascontiguousarray(np.moveaxis(y, 1, 0).reshape((a, s * n) + y.shape[3:]))
