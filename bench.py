@@ -265,6 +265,7 @@ def cpu_baseline(budget_s: float = 12.0):
 
 
 def main():
+    global N_SLOTS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -274,11 +275,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--slots", type=int, default=N_SLOTS,
+    ap.add_argument("--slots", type=int, default=1000,
                     help="slots per UE per step (smaller for profiling captures)")
     args = ap.parse_args()
 
-    global N_SLOTS
     N_SLOTS = args.slots
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
