@@ -121,7 +121,8 @@ def run_ours(args, rank, world, device):
 
     specs, iq = make_workload(rank)
     n = specs[0].n
-    eng = tc.Engine(device=device, form="batched", persistent=bool(args.persistent))
+    eng = tc.Engine(device=device, form="batched", persistent=bool(args.persistent),
+                    samples_per_thread=args.spt)
     q = N_SLOTS + 1
     chans = [tc.Chan(eng, s, ring_slots=q) for s in specs]
     stream = torch.cuda.ExternalStream(eng.stream)
@@ -272,6 +273,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--spt", type=int, default=0, help="cap on samples per thread (0 = largest that fits)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -39,6 +39,7 @@ cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st) {
     case 2: return tt_launch_conv_s2(L, st);
     case 4: return tt_launch_conv_s4(L, st);
     case 8: return tt_launch_conv_s8(L, st);
+    case 16: return tt_launch_conv_s16(L, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -27,6 +27,7 @@
 
 namespace tt {
 
+
 // Anchor value H[a] for flat tap index e in [0, per) = ((r*n_tx + t)*K + k).
 // step_samples == 0: trace entry a.  Otherwise: linear interpolation of the
 // trace in FP64 time at the symbol's first sample (trace entry i at i*step).
@@ -50,16 +51,61 @@ __device__ __forceinline__ float2 tt_anchor(const TTUEDesc *__restrict__ U, uint
                      (float)((double)h0.y + f * ((double)h1.y - (double)h0.y)));
 }
 
+// Stage the window x[ws, ws + wlen) of Tx antenna t into the phase planes.
+// Element e goes to plane (e mod S) row (e / S) + 1 and plane (e mod S) + S row e / S.
+template <int S, int NP>
+__device__ __forceinline__ void tt_stage_window(float2 *__restrict__ pl, const uint32_t *__restrict__ rin,
+                                                int ws, int wlen, int n, int n_tx, int t, int slot_pos, int Q,
+                                                int tid) {
+  if constexpr (S >= 4) {
+    // four consecutive samples per thread: one 16-byte load, never straddling a slot
+    for (int e = 4 * tid; e < wlen; e += 4 * TT_TPB) {
+      int w = ws + e;
+      int pos = slot_pos;
+      if (w < 0) {  // delay line: earlier slots of this UE
+        const int back = (-w + n - 1) / n;
+        w += back * n;
+        pos -= back;
+        while (pos < 0) pos += Q;
+      }
+      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rin + ((size_t)(pos * n_tx + t) * n + w)));
+      const int beta = e % S, i = e / S;
+      const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float2 xv = tt_unpack_iq(vv[c]);
+        pl[(beta + c) * NP + i + 1] = xv;
+        pl[(beta + c + S) * NP + i] = xv;
+      }
+    }
+  } else {
+    for (int e = tid; e < wlen; e += TT_TPB) {
+      int w = ws + e;
+      int pos = slot_pos;
+      if (w < 0) {
+        const int back = (-w + n - 1) / n;
+        w += back * n;
+        pos -= back;
+        while (pos < 0) pos += Q;
+      }
+      const float2 xv = tt_unpack_iq(__ldg(rin + ((size_t)(pos * n_tx + t) * n + w)));
+      const int beta = e % S, i = e / S;
+      pl[beta * NP + i + 1] = xv;
+      pl[(beta + S) * NP + i] = xv;
+    }
+  }
+}
+
 template <int S, int NRX, int DMAX>
 __global__ void __launch_bounds__(TT_TPB)
     tt_conv_fp32_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                         uint32_t total_items, uint32_t *__restrict__ counter) {
-  constexpr int DP = tt_geo_dp(S, DMAX);
   constexpr int NP = tt_geo_np(S, DMAX);
+  constexpr int KU = S >= 16 ? 1 : 2;  // tap-loop unroll
   extern __shared__ float4 dyn_smem[];
   __shared__ uint32_t s_item;
   __shared__ int s_ue, s_g0, s_gend, s_jfirst, s_nsymt;
-  __shared__ unsigned long long s_slot;
+  __shared__ unsigned long long s_slot, s_idx0;
   __shared__ int s_sym[TT_MAX_SYM + 1];
 
   const int tid = threadIdx.x;
@@ -72,7 +118,7 @@ __global__ void __launch_bounds__(TT_TPB)
     }
     if (item >= total_items) return;
 
-    // ---- locate the item: segment -> (UE, slot, first group) ----
+    // ---- locate the item: segment -> (UE, slot, first group); trace index of the first anchor ----
     if (tid == 0) {
       int lo = 0, hi = n_segs - 1;
       while (lo < hi) {
@@ -90,7 +136,11 @@ __global__ void __launch_bounds__(TT_TPB)
       while (j + 1 < U->nsym && U->sym_start[j + 1] <= w0) ++j;
       int jl = j;
       while (jl + 1 < U->nsym && U->sym_start[jl + 1] <= wl) ++jl;
-      s_slot = sg.first_slot + rel / ips;
+      const uint64_t slot = sg.first_slot + rel / ips;
+      const uint64_t a0 = slot * (uint64_t)U->nsym + (uint64_t)j;
+      const uint64_t T = (uint64_t)U->n_anchors;
+      s_idx0 = U->loop ? a0 % T : a0;
+      s_slot = slot;
       s_ue = (int)sg.ue;
       s_g0 = g0;
       s_gend = gend;
@@ -103,6 +153,7 @@ __global__ void __launch_bounds__(TT_TPB)
     const uint64_t slot = s_slot;
     const int g0 = s_g0, gend = s_gend, jf = s_jfirst, nst = s_nsymt;
     const int n = U->n, nsym = U->nsym, n_tx = U->n_tx, K = U->n_taps, Q = U->ring_q;
+    const int dpad = U->dpad;
     const int per = NRX * n_tx * K;
     if (tid <= nsym) s_sym[tid] = U->sym_start[tid];
 
@@ -112,41 +163,47 @@ __global__ void __launch_bounds__(TT_TPB)
     float2 *planes = reinterpret_cast<float2 *>(offk + ((K + 3) & ~3));
 
     // ---- taps of the touched symbols: (H[a], H[a+1] - H[a]) ----
-    for (int e = tid; e < ntap_e; e += TT_TPB) {
-      const int jl = e / per;
-      const int rem = e - jl * per;
-      const uint64_t a = slot * (uint64_t)nsym + (uint64_t)(jf + jl);
-      const float2 h0 = tt_anchor(U, a, rem, per);
-      const float2 h1 = tt_anchor(U, a + 1, rem, per);
-      tapsm[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
+    if (U->step_samples == 0.0) {
+      // one trace entry per symbol: entry index of anchor a0 + j without 64-bit division
+      const uint64_t T = (uint64_t)U->n_anchors;
+      const uint64_t idx0 = s_idx0;
+      for (int e = tid; e < ntap_e; e += TT_TPB) {
+        const int jl = e / per;
+        const int rem = e - jl * per;
+        uint64_t i0 = idx0 + (uint64_t)jl, i1 = i0 + 1;
+        if (U->loop) {
+          while (i0 >= T) i0 -= T;
+          while (i1 >= T) i1 -= T;
+        } else {
+          i0 = i0 < T ? i0 : T - 1;
+          i1 = i1 < T ? i1 : T - 1;
+        }
+        const float2 h0 = __ldg(U->taps + i0 * (uint64_t)per + (uint64_t)rem);
+        const float2 h1 = __ldg(U->taps + i1 * (uint64_t)per + (uint64_t)rem);
+        tapsm[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
+      }
+    } else {
+      for (int e = tid; e < ntap_e; e += TT_TPB) {
+        const int jl = e / per;
+        const int rem = e - jl * per;
+        const uint64_t a = slot * (uint64_t)nsym + (uint64_t)(jf + jl);
+        const float2 h0 = tt_anchor(U, a, rem, per);
+        const float2 h1 = tt_anchor(U, a + 1, rem, per);
+        tapsm[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
+      }
     }
     for (int k = tid; k < K; k += TT_TPB) {
       const int d = __ldg(U->delays + k);
       offk[k] = (S - d % S) * NP - d / S;
     }
 
-    // ---- input window x[w_first - DP, w_last + S) from the ring, int16 -> float ----
-    const int ws = g0 * S - DP;
-    const int wlen = (gend - g0) * S + DP;
+    // ---- input window x[w_first - dpad, w_last + S) from the ring, int16 -> float ----
+    const int ws = g0 * S - dpad;
+    const int wlen = (gend - g0) * S + dpad;
     const int slot_pos = (int)(slot % (uint64_t)Q);
     const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
-    for (int t = 0; t < n_tx; ++t) {
-      float2 *pl = planes + t * (2 * S * NP);
-      for (int e = tid; e < wlen; e += TT_TPB) {
-        int w = ws + e;
-        int pos = slot_pos;
-        if (w < 0) {  // delay line: earlier slots of this UE
-          const int back = (-w + n - 1) / n;
-          w += back * n;
-          pos -= back;
-          while (pos < 0) pos += Q;
-        }
-        const float2 xv = tt_unpack_iq(__ldg(rin + ((size_t)(pos * n_tx + t) * n + w)));
-        const int beta = e % S, i = e / S;
-        pl[beta * NP + i + 1] = xv;
-        pl[(beta + S) * NP + i] = xv;
-      }
-    }
+    for (int t = 0; t < n_tx; ++t)
+      tt_stage_window<S, NP>(planes + t * (2 * S * NP), rin, ws, wlen, n, n_tx, t, slot_pos, Q, tid);
     __syncthreads();
 
     // ---- S consecutive outputs per thread, all Rx antennas ----
@@ -156,10 +213,10 @@ __global__ void __launch_bounds__(TT_TPB)
       int j = jf;
       while (j + 1 < nsym && s_sym[j + 1] <= w_me) ++j;
       const int o = w_me - s_sym[j];
-      const float Lf = (float)(s_sym[j + 1] - s_sym[j]);
+      const float rL = 1.0f / (float)(s_sym[j + 1] - s_sym[j]);
       float tau[S];
 #pragma unroll
-      for (int jj = 0; jj < S; ++jj) tau[jj] = (float)(o + jj) / Lf;
+      for (int jj = 0; jj < S; ++jj) tau[jj] = (float)(o + jj) * rL;
 
       float2 acc[NRX][S];
 #pragma unroll
@@ -168,11 +225,11 @@ __global__ void __launch_bounds__(TT_TPB)
         for (int jj = 0; jj < S; ++jj) acc[r][jj] = make_float2(0.f, 0.f);
 
       const float4 *tb = tapsm + (j - jf) * per;
-      const int q0 = tid + DP / S;
+      const int q0 = tid + dpad / S;
       for (int t = 0; t < n_tx; ++t) {
         const float2 *pl = planes + t * (2 * S * NP) + q0;
         const float4 *tbt = tb + t * K;
-#pragma unroll 2
+#pragma unroll KU
         for (int k = 0; k < K; ++k) {
           const float2 *px = pl + offk[k];
           float2 xv[S];
@@ -201,19 +258,12 @@ __global__ void __launch_bounds__(TT_TPB)
       for (int r = 0; r < NRX; ++r) {
         if (nstd > 0.f) {
           if (S == 1) {
-            const float2 z = tt_awgn_one(U->seed, U->ue_id, (uint32_t)r, m0);
-            acc[r][0].x = fmaf(nstd, z.x, acc[r][0].x);
-            acc[r][0].y = fmaf(nstd, z.y, acc[r][0].y);
+            tt_awgn_add_one(U->seed, U->ue_id, (uint32_t)r, m0, nstd, acc[r][0]);
           } else {
 #pragma unroll
-            for (int jj = 0; jj < S; jj += 2) {
-              float2 z0, z1;
-              tt_awgn_pair(U->seed, U->ue_id, (uint32_t)r, m0 + (uint64_t)jj, z0, z1);
-              acc[r][jj].x = fmaf(nstd, z0.x, acc[r][jj].x);
-              acc[r][jj].y = fmaf(nstd, z0.y, acc[r][jj].y);
-              acc[r][jj + 1].x = fmaf(nstd, z1.x, acc[r][jj + 1].x);
-              acc[r][jj + 1].y = fmaf(nstd, z1.y, acc[r][jj + 1].y);
-            }
+            for (int jj = 0; jj < S; jj += 2)
+              tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, m0 + (uint64_t)jj, nstd, acc[r][jj],
+                               acc[r][jj + 1]);
           }
         }
         if (U->out_f32) {
@@ -292,8 +342,12 @@ cudaError_t tt_launch_spt(const TTLaunch &L, cudaStream_t st) {
   switch (L.nrx) {
     case 1: return tt_launch_dclass<S, 1>(L, st);
     case 2: return tt_launch_dclass<S, 2>(L, st);
-    case 3: return tt_launch_dclass<S, 3>(L, st);
-    case 4: return tt_launch_dclass<S, 4>(L, st);
+    case 3:
+      if constexpr (S <= 8) return tt_launch_dclass<S, 3>(L, st);
+      return cudaErrorInvalidValue;
+    case 4:
+      if constexpr (S <= 8) return tt_launch_dclass<S, 4>(L, st);
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

@@ -163,10 +163,11 @@ tt_status wait_seq(tt_engine *e, uint64_t seq, int64_t timeout_us, std::unique_l
   }
 }
 
-int pick_spt(const std::vector<uint32_t> &L, uint32_t override_spt) {
-  static const int cands[] = {8, 4, 2, 1};
+int pick_spt(const std::vector<uint32_t> &L, uint32_t override_spt, uint32_t n_rx) {
+  static const int cands[] = {16, 8, 4, 2, 1};
   for (int s : cands) {
     if (override_spt && (uint32_t)s > override_spt) continue;
+    if (s == 16 && n_rx > 2) continue;
     bool ok = true;
     for (uint32_t v : L) ok = ok && (v % (uint32_t)s == 0);
     if (ok) return s;
@@ -241,8 +242,8 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
     return fail(TT_ERR_INVALID, "tt_engine_create: bad config");
   if (cfg->form > TT_FORM_PLAIN) return fail(TT_ERR_INVALID, "unknown form %u", cfg->form);
   if (cfg->samples_per_thread && cfg->samples_per_thread != 1 && cfg->samples_per_thread != 2 &&
-      cfg->samples_per_thread != 4 && cfg->samples_per_thread != 8)
-    return fail(TT_ERR_INVALID, "samples_per_thread must be 0, 1, 2, 4 or 8");
+      cfg->samples_per_thread != 4 && cfg->samples_per_thread != 8 && cfg->samples_per_thread != 16)
+    return fail(TT_ERR_INVALID, "samples_per_thread must be 0, 1, 2, 4, 8 or 16");
   int ndev = 0;
   cudaError_t q = cudaGetDeviceCount(&ndev);
   if (q != cudaSuccess || ndev == 0) return fail(TT_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(q));
@@ -373,7 +374,7 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   }
   c->ring_bytes = bytes;
   e->in_use += bytes;
-  c->spt = pick_spt(c->sym_len, e->spt_override);
+  c->spt = pick_spt(c->sym_len, e->spt_override, cfg->n_rx);
   TTUEDesc &d = c->desc;
   d.ring_in = c->d_in;
   d.ring_out = c->d_out;
@@ -492,6 +493,7 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   d.step_samples = tr->step_samples;
   d.n_taps = (int)tr->n_taps;
   d.d_max = d_max;
+  d.dpad = (d_max + c->spt - 1) / c->spt * c->spt;
   d.n_anchors = (int)tr->n_anchors;
   d.loop = tr->loop ? 1 : 0;
   return upload_desc(c);

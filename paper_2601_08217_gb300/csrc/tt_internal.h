@@ -20,9 +20,15 @@
 
 // Window geometry of the tiled kernel (samples per thread S, delay class DMAX):
 // delay padding DP (a multiple of S) and phase-plane pitch NP in float2 words.
+// NP is padded so that NP = 16/S (mod 16): sixteen consecutive window
+// elements written by a half-warp then land in sixteen distinct 8-byte bank
+// pairs (element e goes to plane e mod S, row e / S).
 __host__ __device__ constexpr int tt_geo_dp(int S, int DMAX) { return (DMAX + S - 1) / S * S; }
-__host__ __device__ constexpr int tt_geo_np(int S, int DMAX) {
+__host__ __device__ constexpr int tt_geo_np_raw(int S, int DMAX) {
   return (TT_TPB * S + tt_geo_dp(S, DMAX)) / S + 1;
+}
+__host__ __device__ constexpr int tt_geo_np(int S, int DMAX) {
+  return tt_geo_np_raw(S, DMAX) + ((16 / (S < 16 ? S : 16)) % 16 - tt_geo_np_raw(S, DMAX) % 16 + 16) % 16;
 }
 __host__ __device__ constexpr int tt_dclass_max(int dclass) {
   return dclass == 0 ? TT_DCLASS0 : (dclass == 1 ? TT_DCLASS1 : TT_DCLASS2);
@@ -48,6 +54,7 @@ struct TTUEDesc {
   float noise_std;         // per I/Q component; 0 = AWGN off
   int32_t out_f32;         // 1: write y as float2 (no packing)
   int32_t spt;             // samples per thread of the tiled kernel for this UE
+  int32_t dpad;            // d_max rounded up to a multiple of spt: delay-line part of the window
   int32_t groups;          // groups of spt samples per slot
   int32_t items_per_slot;  // CTAs (work items) per slot
   int32_t sym_start[TT_MAX_SYM + 1];  // symbol starts, sym_start[nsym] = n
@@ -69,7 +76,7 @@ struct TTLaunch {
   int n_segs;
   uint32_t total_items;
   uint32_t *counter;    // persistent mode: device work counter (zeroed before launch); else null
-  int spt;              // 1, 2, 4, 8
+  int spt;              // 1, 2, 4, 8, 16
   int nrx;              // 1..4
   int dclass;           // 0: d_max <= 256, 1: d_max <= 1024
   int grid;             // CTAs (persistent) -- ignored otherwise
@@ -84,6 +91,7 @@ cudaError_t tt_launch_conv_s1(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s2(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s4(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s8(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s16(const TTLaunch &L, cudaStream_t st);
 
 // Plain comparison form: one launch per UE per slot.
 cudaError_t tt_launch_plain(const TTUEDesc *ue_dev, uint64_t slot, int n, cudaStream_t st);

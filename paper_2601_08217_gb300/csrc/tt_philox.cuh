@@ -31,14 +31,31 @@ __device__ __forceinline__ float tt_u01(uint32_t w) {
 }
 
 // Standard normal pair (r cos th, r sin th) with r = sqrt(-2 ln u0), th = 2 pi u1.
-// The angle is evaluated as th - pi = 2 pi (u1 - 0.5), inside the fast sine's
-// accurate range, and the signs flipped back.
+// The angle is evaluated as th - pi = 2 pi u1 - pi, inside the fast sine's
+// accurate range, and the signs flipped back.  The radius uses the hardware
+// square root (sqrt.approx.f32) of the clamped, non-negative argument.
+__device__ __forceinline__ float tt_sqrt_approx(float v) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
 __device__ __forceinline__ float2 tt_box_muller(uint32_t w0, uint32_t w1) {
   const float u0 = tt_u01(w0), u1 = tt_u01(w1);
-  const float r = sqrtf(fmaxf(-1.38629436111989061f * __log2f(u0), 0.0f));
+  const float r = tt_sqrt_approx(fmaxf(-1.38629436111989061f * __log2f(u0), 0.0f));
   float s, c;
-  __sincosf(6.28318530717958648f * (u1 - 0.5f), &s, &c);
+  __sincosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f), &s, &c);
   return make_float2(-r * c, -r * s);
+}
+
+// acc += sigma * (Gaussian pair) without forming the pair first.
+__device__ __forceinline__ void tt_box_muller_add(uint32_t w0, uint32_t w1, float sigma, float2 &acc) {
+  const float u0 = tt_u01(w0), u1 = tt_u01(w1);
+  const float r = tt_sqrt_approx(fmaxf(-1.38629436111989061f * __log2f(u0), 0.0f)) * (-sigma);
+  float s, c;
+  __sincosf(fmaf(6.28318530717958648f, u1, -3.14159265358979324f), &s, &c);
+  acc.x = fmaf(r, c, acc.x);
+  acc.y = fmaf(r, s, acc.y);
 }
 
 // AWGN for samples m and m+1 (m even) of (seed, ue, rx): one Philox block.
@@ -49,6 +66,24 @@ __device__ __forceinline__ void tt_awgn_pair(uint64_t seed, uint32_t ue, uint32_
                                    (uint32_t)seed, (uint32_t)(seed >> 32));
   n0 = tt_box_muller(w.x, w.y);
   n1 = tt_box_muller(w.z, w.w);
+}
+
+__device__ __forceinline__ void tt_awgn_add_pair(uint64_t seed, uint32_t ue, uint32_t rx, uint64_t m, float sigma,
+                                                 float2 &a0, float2 &a1) {
+  const uint64_t p = m >> 1;
+  const uint4 w = tt_philox4x32_10(make_uint4((uint32_t)p, (uint32_t)(p >> 32), ue, rx),
+                                   (uint32_t)seed, (uint32_t)(seed >> 32));
+  tt_box_muller_add(w.x, w.y, sigma, a0);
+  tt_box_muller_add(w.z, w.w, sigma, a1);
+}
+
+__device__ __forceinline__ void tt_awgn_add_one(uint64_t seed, uint32_t ue, uint32_t rx, uint64_t m, float sigma,
+                                                float2 &a) {
+  const uint64_t p = m >> 1;
+  const uint4 w = tt_philox4x32_10(make_uint4((uint32_t)p, (uint32_t)(p >> 32), ue, rx),
+                                   (uint32_t)seed, (uint32_t)(seed >> 32));
+  if (m & 1) tt_box_muller_add(w.z, w.w, sigma, a);
+  else tt_box_muller_add(w.x, w.y, sigma, a);
 }
 
 __device__ __forceinline__ float2 tt_awgn_one(uint64_t seed, uint32_t ue, uint32_t rx, uint64_t m) {
