@@ -5,21 +5,27 @@
 #include "tt_internal.h"
 #include "tt_philox.cuh"
 
-size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int n_rx, int n_taps, int max_sym_touched) {
-  const int np = tt_geo_np(spt, tt_dclass_max(dclass));
-  const size_t taps = (size_t)max_sym_touched * n_rx * n_tx * n_taps * sizeof(float4);
-  const size_t offk = (size_t)((n_taps + 3) & ~3) * sizeof(int);
+size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max) {
+  const int dmax = tt_dclass_max(dclass);
+  const int np = tt_geo_np(spt, dmax);
+  const int wmax = tt_geo_wmax(spt, dmax);
   const size_t planes = (size_t)n_tx * 2 * spt * np * sizeof(float2);
-  return taps + offk + planes;
+  const size_t raw = (size_t)((n_tx * wmax + 3) & ~3) * sizeof(uint32_t);
+  const size_t taps = 2 * (size_t)tap_max * sizeof(float4);
+  const size_t dly = 2 * (size_t)((k_max + 3) & ~3) * sizeof(int);
+  return planes + raw + taps + dly;
 }
 
-// Largest number of symbols one work item (TT_TPB groups of spt samples) can touch.
-int tt_conv_max_sym_touched(int spt, const int32_t *sym_len, int nsym) {
+// For each work item (TT_TPB groups of spt samples) of a slot: first symbol it
+// touches and how many symbols it touches, packed as jf | (nst << 16).
+int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, int max_out) {
   int n = 0;
   for (int j = 0; j < nsym; ++j) n += sym_len[j];
   const int groups = n / spt;
-  int best = 1;
-  for (int g0 = 0; g0 < groups; g0 += TT_TPB) {
+  const int items = (groups + TT_TPB - 1) / TT_TPB;
+  if (items > max_out) return -1;
+  for (int c = 0; c < items; ++c) {
+    const int g0 = c * TT_TPB;
     const int w0 = g0 * spt;
     const int wl = (g0 + TT_TPB < groups ? g0 + TT_TPB : groups) * spt - 1;
     int b = 0, j0 = -1, j1 = -1;
@@ -28,9 +34,9 @@ int tt_conv_max_sym_touched(int spt, const int32_t *sym_len, int nsym) {
       if (j1 < 0 && wl < b + sym_len[j]) j1 = j;
       b += sym_len[j];
     }
-    if (j1 - j0 + 1 > best) best = j1 - j0 + 1;
+    out[c] = j0 | ((j1 - j0 + 1) << 16);
   }
-  return best;
+  return items;
 }
 
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st) {

@@ -6,27 +6,33 @@
 // Work decomposition.  A slot of one UE is cut into groups of S consecutive
 // samples (S divides every symbol length, so a group never straddles a symbol
 // and shares one set of taps).  A work item is TT_TPB consecutive groups of
-// one (UE, slot): one CTA, one group per thread, all Rx antennas per thread so
-// every staged input sample is reused n_rx times.
+// one (UE, slot): one group per thread, all Rx antennas per thread so every
+// staged input sample is reused n_rx times.
 //
-// Shared memory per item:
-//   taps  float4 [symbols touched][NRX][n_tx][K] = (H[a], H[a+1] - H[a])  (interpolation endpoints)
-//   offk  int    [K]  plane offset of each delay
-//   planes float2 [n_tx][2S][NP]  the input window x[w_first - DP, w_last + S)
+// Persistent, software-pipelined CTAs.  While a CTA computes item i it has
+// already issued cp.async copies of item i+1's raw input window, raw trace
+// entries and delays into shared memory, so global-memory latency overlaps
+// the arithmetic; after a barrier the raw window is converted to float and
+// scattered into the phase planes.
+//
+// Shared memory:
+//   planes float2 [n_tx][2S][NP]  the input window x[w_first - dpad, w_last + S)
+//   raw    uint32 [n_tx][WMAX]    the same window as packed int16 I/Q (cp.async target)
+//   taps   float4 [2][tap_max]    (H[a], H[a+1] - H[a]) per touched symbol, double-buffered
+//   dly    int    [2][k_max]      raw delays (cp.async target), then plane offsets
 // The window is stored in 2S "phase planes": plane b holds the elements whose
 // index is b mod S (planes S..2S-1 repeat planes 0..S-1 shifted by one row).
-// Thread l needs x[S*l + j - d] for j = 0..S-1; in this layout those are
-// plane (j - d mod S + S), row (l - floor(d/S) - ...), so for one delay all
+// Thread l needs x[S*l + j - d] for j = 0..S-1; in this layout those sit in
+// plane (j - d mod S + S), row l - floor(d/S) + const, so for one delay all
 // lanes read consecutive 8-byte words (conflict-free), and the S samples of a
 // thread sit at a compile-time stride NP: one LDS with an immediate offset
-// per tap-sample, no per-sample index arithmetic.
+// per tap-sample and no per-sample index arithmetic.
 #pragma once
 
 #include "tt_internal.h"
 #include "tt_philox.cuh"
 
 namespace tt {
-
 
 // Anchor value H[a] for flat tap index e in [0, per) = ((r*n_tx + t)*K + k).
 // step_samples == 0: trace entry a.  Otherwise: linear interpolation of the
@@ -51,15 +57,87 @@ __device__ __forceinline__ float2 tt_anchor(const TTUEDesc *__restrict__ U, uint
                      (float)((double)h0.y + f * ((double)h1.y - (double)h0.y)));
 }
 
-// Stage the window x[ws, ws + wlen) of Tx antenna t into the phase planes.
-// Element e goes to plane (e mod S) row (e / S) + 1 and plane (e mod S) + S row e / S.
-template <int S, int NP>
-__device__ __forceinline__ void tt_stage_window(float2 *__restrict__ pl, const uint32_t *__restrict__ rin,
-                                                int ws, int wlen, int n, int n_tx, int t, int slot_pos, int Q,
-                                                int tid) {
-  if constexpr (S >= 4) {
-    // four consecutive samples per thread: one 16-byte load, never straddling a slot
-    for (int e = 4 * tid; e < wlen; e += 4 * TT_TPB) {
+// ---- small PTX helpers ----
+__device__ __forceinline__ uint32_t tt_smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void tt_cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(tt_smem_addr(dst)), "l"(src));
+}
+__device__ __forceinline__ void tt_cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(tt_smem_addr(dst)), "l"(src));
+}
+__device__ __forceinline__ void tt_cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(tt_smem_addr(dst)), "l"(src));
+}
+__device__ __forceinline__ void tt_cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void tt_cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Packed pair FMA (two independent single-rounding FMAs, one instruction): a*b + c.
+__device__ __forceinline__ float2 tt_fma2(float2 a, float2 b, float2 c) {
+  uint64_t ra, rb, rc, rd;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ra) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rb) : "f"(b.x), "f"(b.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(rc) : "f"(c.x), "f"(c.y));
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  float2 d;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(rd));
+  return d;
+}
+
+// Per-item description shared through smem.
+struct TTItem {
+  unsigned long long slot;
+  unsigned long long idx0;  // trace entry of the item's first anchor (per-symbol traces)
+  int ue, g0, gend, jf, nst, valid;
+};
+
+// Thread 0: item index -> (UE, slot, groups, first symbol, symbols touched).
+__device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs,
+                                          int n_segs, uint32_t item, uint32_t total_items, TTItem &it) {
+  if (item >= total_items) {
+    it.valid = 0;
+    return;
+  }
+  int lo = 0, hi = n_segs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+  }
+  const TTSeg sg = segs[lo];
+  const TTUEDesc *U = ues + sg.ue;
+  const uint32_t rel = item - sg.item_begin;
+  const uint32_t ips = (uint32_t)U->items_per_slot;
+  const uint32_t c = rel % ips;
+  const int ci = __ldg(U->chunk_info + c);
+  const int g0 = (int)c * TT_TPB;
+  const uint64_t slot = sg.first_slot + rel / ips;
+  const int jf = ci & 0xFFFF;
+  const uint64_t a0 = slot * (uint64_t)U->nsym + (uint64_t)jf;
+  it.slot = slot;
+  it.idx0 = U->loop ? a0 % (uint64_t)U->n_anchors : a0;
+  it.ue = (int)sg.ue;
+  it.g0 = g0;
+  it.gend = min(g0 + TT_TPB, U->groups);
+  it.jf = jf;
+  it.nst = ci >> 16;
+  it.valid = 1;
+}
+
+// All threads: start the asynchronous copies of one item's raw window, trace
+// entries, delays and symbol table into shared memory.
+template <int S, int NRX>
+__device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, const TTItem &it, uint32_t *raw,
+                                              int wmax, float4 *taps, int *dly, int *sym, int tid) {
+  const int n = U->n, n_tx = U->n_tx, Q = U->ring_q, K = U->n_taps, dpad = U->dpad;
+  const int ws = it.g0 * S - dpad;
+  const int wlen = (it.gend - it.g0) * S + dpad;
+  const int slot_pos = (int)(it.slot % (uint64_t)Q);
+  const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
+  constexpr int V = S >= 4 ? 4 : 1;  // samples per copy: 16-byte copies when windows are 4-aligned
+  for (int t = 0; t < n_tx; ++t) {
+    uint32_t *rt = raw + t * wmax;
+    for (int e = V * tid; e < wlen; e += V * TT_TPB) {
       int w = ws + e;
       int pos = slot_pos;
       if (w < 0) {  // delay line: earlier slots of this UE
@@ -68,30 +146,177 @@ __device__ __forceinline__ void tt_stage_window(float2 *__restrict__ pl, const u
         pos -= back;
         while (pos < 0) pos += Q;
       }
-      const uint4 v = __ldg(reinterpret_cast<const uint4 *>(rin + ((size_t)(pos * n_tx + t) * n + w)));
-      const int beta = e % S, i = e / S;
-      const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+      const uint32_t *src = rin + ((size_t)(pos * n_tx + t) * n + w);
+      if (V == 4) tt_cp_async16(rt + e, src); else tt_cp_async4(rt + e, src);
+    }
+  }
+  const int per = NRX * n_tx * K;
+  const int ntap_e = it.nst * per;
+  if (U->step_samples == 0.0) {
+    const uint64_t T = (uint64_t)U->n_anchors;
+    for (int e = tid; e < ntap_e; e += TT_TPB) {
+      const int jl = e / per;
+      const int rem = e - jl * per;
+      uint64_t i0 = it.idx0 + (uint64_t)jl, i1 = i0 + 1;
+      if (U->loop) {
+        while (i0 >= T) i0 -= T;
+        while (i1 >= T) i1 -= T;
+      } else {
+        i0 = i0 < T ? i0 : T - 1;
+        i1 = i1 < T ? i1 : T - 1;
+      }
+      tt_cp_async8(&taps[e].x, U->taps + i0 * (uint64_t)per + (uint64_t)rem);
+      tt_cp_async8(&taps[e].z, U->taps + i1 * (uint64_t)per + (uint64_t)rem);
+    }
+  }
+  for (int k = tid; k < K; k += TT_TPB) tt_cp_async4(dly + k, U->delays + k);
+  if (tid <= U->nsym) tt_cp_async4(sym + tid, U->sym_start + tid);
+  tt_cp_async_commit();
+}
+
+// All threads, after the copies landed: raw window -> phase planes, taps -> (H0, dH),
+// delays -> plane offsets.
+template <int S, int NRX, int NP>
+__device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, const TTItem &it,
+                                                const uint32_t *raw, int wmax, float2 *planes, float4 *taps,
+                                                int *dly, int tid) {
+  const int n_tx = U->n_tx, K = U->n_taps, dpad = U->dpad;
+  const int wlen = (it.gend - it.g0) * S + dpad;
+  for (int t = 0; t < n_tx; ++t) {
+    const uint32_t *rt = raw + t * wmax;
+    float2 *pl = planes + t * (2 * S * NP);
+    if constexpr (S >= 4) {
+      for (int e = 4 * tid; e < wlen; e += 4 * TT_TPB) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(rt + e);
+        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+        const int beta = e % S, i = e / S;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float2 xv = tt_unpack_iq(vv[c]);
-        pl[(beta + c) * NP + i + 1] = xv;
-        pl[(beta + c + S) * NP + i] = xv;
+        for (int c = 0; c < 4; ++c) {
+          const float2 xv = tt_unpack_iq(vv[c]);
+          pl[(beta + c) * NP + i + 1] = xv;
+          pl[(beta + c + S) * NP + i] = xv;
+        }
+      }
+    } else {
+      for (int e = tid; e < wlen; e += TT_TPB) {
+        const float2 xv = tt_unpack_iq(rt[e]);
+        const int beta = e % S, i = e / S;
+        pl[beta * NP + i + 1] = xv;
+        pl[(beta + S) * NP + i] = xv;
       }
     }
-  } else {
-    for (int e = tid; e < wlen; e += TT_TPB) {
-      int w = ws + e;
-      int pos = slot_pos;
-      if (w < 0) {
-        const int back = (-w + n - 1) / n;
-        w += back * n;
-        pos -= back;
-        while (pos < 0) pos += Q;
+  }
+  const int per = NRX * n_tx * K;
+  const int ntap_e = it.nst * per;
+  if (U->step_samples == 0.0) {
+    for (int e = tid; e < ntap_e; e += TT_TPB) {
+      float4 h = taps[e];
+      h.z -= h.x;
+      h.w -= h.y;
+      taps[e] = h;
+    }
+  } else {  // trace-time interpolation (FP64) straight from global memory
+    const int nsym = U->nsym;
+    for (int e = tid; e < ntap_e; e += TT_TPB) {
+      const int jl = e / per;
+      const int rem = e - jl * per;
+      const uint64_t a = it.slot * (uint64_t)nsym + (uint64_t)(it.jf + jl);
+      const float2 h0 = tt_anchor(U, a, rem, per);
+      const float2 h1 = tt_anchor(U, a + 1, rem, per);
+      taps[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
+    }
+  }
+  for (int k = tid; k < K; k += TT_TPB) {
+    const int d = dly[k];
+    dly[k] = (S - d % S) * NP - d / S;
+  }
+}
+
+// All threads: S consecutive outputs per thread of one item, all Rx antennas, fused epilogue.
+template <int S, int NRX, int NP>
+__device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, const TTItem &it,
+                                                const float2 *planes, const float4 *taps, const int *offk,
+                                                const int *sym, int tid) {
+  constexpr int KU = S >= 16 ? 1 : 2;  // tap-loop unroll
+  const int g = it.g0 + tid;
+  if (g >= it.gend) return;
+  const int n = U->n, nsym = U->nsym, n_tx = U->n_tx, K = U->n_taps;
+  const int per = NRX * n_tx * K;
+  const int w_me = g * S;
+  int j = it.jf;
+  while (j + 1 < nsym && sym[j + 1] <= w_me) ++j;
+  const int o = w_me - sym[j];
+  const float rL = 1.0f / (float)(sym[j + 1] - sym[j]);
+  float2 tau2[S];  // (tau, tau) per sample: operand of the packed interpolation
+#pragma unroll
+  for (int jj = 0; jj < S; ++jj) {
+    const float tv = (float)(o + jj) * rL;
+    tau2[jj] = make_float2(tv, tv);
+  }
+  float2 acc[NRX][S];
+#pragma unroll
+  for (int r = 0; r < NRX; ++r)
+#pragma unroll
+    for (int jj = 0; jj < S; ++jj) acc[r][jj] = make_float2(0.f, 0.f);
+
+  const float4 *tb = taps + (j - it.jf) * per;
+  const int q0 = tid + U->dpad / S;
+  for (int t = 0; t < n_tx; ++t) {
+    const float2 *pl = planes + t * (2 * S * NP) + q0;
+    const float4 *tbt = tb + t * K;
+#pragma unroll KU
+    for (int k = 0; k < K; ++k) {
+      const float2 *px = pl + offk[k];
+      float2 xv[S];
+#pragma unroll
+      for (int jj = 0; jj < S; ++jj) xv[jj] = px[jj * NP];
+#pragma unroll
+      for (int r = 0; r < NRX; ++r) {
+        const float4 h = tbt[r * n_tx * K + k];
+        const float2 h0 = make_float2(h.x, h.y), dh = make_float2(h.z, h.w);
+#pragma unroll
+        for (int jj = 0; jj < S; ++jj) {
+          const float2 hv = tt_fma2(tau2[jj], dh, h0);  // h(m) = H[a] + tau (H[a+1] - H[a])
+          acc[r][jj].x = fmaf(hv.x, xv[jj].x, acc[r][jj].x);
+          acc[r][jj].x = fmaf(-hv.y, xv[jj].y, acc[r][jj].x);
+          acc[r][jj].y = fmaf(hv.x, xv[jj].y, acc[r][jj].y);
+          acc[r][jj].y = fmaf(hv.y, xv[jj].x, acc[r][jj].y);
+        }
       }
-      const float2 xv = tt_unpack_iq(__ldg(rin + ((size_t)(pos * n_tx + t) * n + w)));
-      const int beta = e % S, i = e / S;
-      pl[beta * NP + i + 1] = xv;
-      pl[(beta + S) * NP + i] = xv;
+    }
+  }
+
+  const float nstd = U->noise_std;
+  const uint64_t m0 = it.slot * (uint64_t)n + (uint64_t)w_me;
+  const int slot_pos = (int)(it.slot % (uint64_t)U->ring_q);
+#pragma unroll
+  for (int r = 0; r < NRX; ++r) {
+    if (nstd > 0.f) {
+      if (S == 1) {
+        tt_awgn_add_one(U->seed, U->ue_id, (uint32_t)r, m0, nstd, acc[r][0]);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < S; jj += 2)
+          tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, m0 + (uint64_t)jj, nstd, acc[r][jj], acc[r][jj + 1]);
+      }
+    }
+    if (U->out_f32) {
+      float2 *dstf = reinterpret_cast<float2 *>(U->ring_out) + ((size_t)(slot_pos * NRX + r) * n + w_me);
+#pragma unroll
+      for (int jj = 0; jj < S; ++jj) dstf[jj] = acc[r][jj];
+      continue;
+    }
+    uint32_t pk[S];
+#pragma unroll
+    for (int jj = 0; jj < S; ++jj) pk[jj] = tt_pack_iq(acc[r][jj].x, acc[r][jj].y);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(U->ring_out) + ((size_t)(slot_pos * NRX + r) * n + w_me);
+    if (S >= 4 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+      for (int jj = 0; jj < S; jj += 4)
+        *reinterpret_cast<uint4 *>(dst + jj) = make_uint4(pk[jj], pk[jj + 1], pk[jj + 2], pk[jj + 3]);
+    } else {
+#pragma unroll
+      for (int jj = 0; jj < S; ++jj) dst[jj] = pk[jj];
     }
   }
 }
@@ -99,195 +324,67 @@ __device__ __forceinline__ void tt_stage_window(float2 *__restrict__ pl, const u
 template <int S, int NRX, int DMAX>
 __global__ void __launch_bounds__(TT_TPB)
     tt_conv_fp32_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
-                        uint32_t total_items, uint32_t *__restrict__ counter) {
+                        uint32_t total_items, uint32_t *__restrict__ counter, int ntx, int tap_max, int k_max) {
   constexpr int NP = tt_geo_np(S, DMAX);
-  constexpr int KU = S >= 16 ? 1 : 2;  // tap-loop unroll
+  constexpr int WMAX = tt_geo_wmax(S, DMAX);
   extern __shared__ float4 dyn_smem[];
-  __shared__ uint32_t s_item;
-  __shared__ int s_ue, s_g0, s_gend, s_jfirst, s_nsymt;
-  __shared__ unsigned long long s_slot, s_idx0;
-  __shared__ int s_sym[TT_MAX_SYM + 1];
+  __shared__ TTItem s_it[2];
+  __shared__ uint32_t s_claim;
+  __shared__ int s_sym[2][TT_MAX_SYM + 1];
 
   const int tid = threadIdx.x;
-  uint32_t item = blockIdx.x;
+  const int kpad = (k_max + 3) & ~3;
+  float2 *planes = reinterpret_cast<float2 *>(dyn_smem);
+  uint32_t *raw = reinterpret_cast<uint32_t *>(planes + ntx * 2 * S * NP);
+  float4 *taps0 = reinterpret_cast<float4 *>(raw + ((ntx * WMAX + 3) & ~3));
+  float4 *taps1 = taps0 + tap_max;
+  int *dly0 = reinterpret_cast<int *>(taps1 + tap_max);
+  int *dly1 = dly0 + kpad;
+
+  uint32_t next_static = blockIdx.x;
+  auto claim = [&]() -> uint32_t {
+    if (counter) return atomicAdd(counter, 1u);
+    const uint32_t v = next_static;
+    next_static += gridDim.x;
+    return v;
+  };
+
+  // ---- prologue: first item fully staged, second item located ----
+  if (tid == 0) {
+    tt_locate(ues, segs, n_segs, claim(), total_items, s_it[0]);
+    s_claim = claim();
+  }
+  __syncthreads();
+  if (!s_it[0].valid) return;
+  {
+    const TTItem it = s_it[0];
+    const TTUEDesc *U = ues + it.ue;
+    tt_issue_item<S, NRX>(U, it, raw, WMAX, taps0, dly0, s_sym[0], tid);
+    tt_cp_async_wait_all();
+    __syncthreads();
+    tt_convert_item<S, NRX, NP>(U, it, raw, WMAX, planes, taps0, dly0, tid);
+    if (tid == 0) tt_locate(ues, segs, n_segs, s_claim, total_items, s_it[1]);
+    __syncthreads();
+  }
+
+  int cb = 0;
   for (;;) {
-    if (counter) {
-      if (tid == 0) s_item = atomicAdd(counter, 1u);
-      __syncthreads();
-      item = s_item;
-    }
-    if (item >= total_items) return;
-
-    // ---- locate the item: segment -> (UE, slot, first group); trace index of the first anchor ----
-    if (tid == 0) {
-      int lo = 0, hi = n_segs - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
-      }
-      const TTSeg sg = segs[lo];
-      const TTUEDesc *U = ues + sg.ue;
-      const uint32_t rel = item - sg.item_begin;
-      const uint32_t ips = (uint32_t)U->items_per_slot;
-      const int g0 = (int)(rel % ips) * TT_TPB;
-      const int gend = min(g0 + TT_TPB, U->groups);
-      const int w0 = g0 * S, wl = (gend - 1) * S;
-      int j = 0;
-      while (j + 1 < U->nsym && U->sym_start[j + 1] <= w0) ++j;
-      int jl = j;
-      while (jl + 1 < U->nsym && U->sym_start[jl + 1] <= wl) ++jl;
-      const uint64_t slot = sg.first_slot + rel / ips;
-      const uint64_t a0 = slot * (uint64_t)U->nsym + (uint64_t)j;
-      const uint64_t T = (uint64_t)U->n_anchors;
-      s_idx0 = U->loop ? a0 % T : a0;
-      s_slot = slot;
-      s_ue = (int)sg.ue;
-      s_g0 = g0;
-      s_gend = gend;
-      s_jfirst = j;
-      s_nsymt = jl - j + 1;
-    }
+    const TTItem cur = s_it[cb];
+    const TTItem nxt = s_it[cb ^ 1];
+    float4 *tc = cb ? taps1 : taps0, *tn = cb ? taps0 : taps1;
+    int *dc = cb ? dly1 : dly0, *dn = cb ? dly0 : dly1;
+    const TTUEDesc *Un = ues + nxt.ue;
+    if (nxt.valid) tt_issue_item<S, NRX>(Un, nxt, raw, WMAX, tn, dn, s_sym[cb ^ 1], tid);
+    tt_compute_item<S, NRX, NP>(ues + cur.ue, cur, planes, tc, dc, s_sym[cb], tid);
+    uint32_t nn = 0;
+    if (tid == 0 && nxt.valid) nn = claim();
+    tt_cp_async_wait_all();
     __syncthreads();
-
-    const TTUEDesc *__restrict__ U = ues + s_ue;
-    const uint64_t slot = s_slot;
-    const int g0 = s_g0, gend = s_gend, jf = s_jfirst, nst = s_nsymt;
-    const int n = U->n, nsym = U->nsym, n_tx = U->n_tx, K = U->n_taps, Q = U->ring_q;
-    const int dpad = U->dpad;
-    const int per = NRX * n_tx * K;
-    if (tid <= nsym) s_sym[tid] = U->sym_start[tid];
-
-    float4 *tapsm = dyn_smem;
-    const int ntap_e = nst * per;
-    int *offk = reinterpret_cast<int *>(tapsm + ntap_e);
-    float2 *planes = reinterpret_cast<float2 *>(offk + ((K + 3) & ~3));
-
-    // ---- taps of the touched symbols: (H[a], H[a+1] - H[a]) ----
-    if (U->step_samples == 0.0) {
-      // one trace entry per symbol: entry index of anchor a0 + j without 64-bit division
-      const uint64_t T = (uint64_t)U->n_anchors;
-      const uint64_t idx0 = s_idx0;
-      for (int e = tid; e < ntap_e; e += TT_TPB) {
-        const int jl = e / per;
-        const int rem = e - jl * per;
-        uint64_t i0 = idx0 + (uint64_t)jl, i1 = i0 + 1;
-        if (U->loop) {
-          while (i0 >= T) i0 -= T;
-          while (i1 >= T) i1 -= T;
-        } else {
-          i0 = i0 < T ? i0 : T - 1;
-          i1 = i1 < T ? i1 : T - 1;
-        }
-        const float2 h0 = __ldg(U->taps + i0 * (uint64_t)per + (uint64_t)rem);
-        const float2 h1 = __ldg(U->taps + i1 * (uint64_t)per + (uint64_t)rem);
-        tapsm[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
-      }
-    } else {
-      for (int e = tid; e < ntap_e; e += TT_TPB) {
-        const int jl = e / per;
-        const int rem = e - jl * per;
-        const uint64_t a = slot * (uint64_t)nsym + (uint64_t)(jf + jl);
-        const float2 h0 = tt_anchor(U, a, rem, per);
-        const float2 h1 = tt_anchor(U, a + 1, rem, per);
-        tapsm[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
-      }
-    }
-    for (int k = tid; k < K; k += TT_TPB) {
-      const int d = __ldg(U->delays + k);
-      offk[k] = (S - d % S) * NP - d / S;
-    }
-
-    // ---- input window x[w_first - dpad, w_last + S) from the ring, int16 -> float ----
-    const int ws = g0 * S - dpad;
-    const int wlen = (gend - g0) * S + dpad;
-    const int slot_pos = (int)(slot % (uint64_t)Q);
-    const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
-    for (int t = 0; t < n_tx; ++t)
-      tt_stage_window<S, NP>(planes + t * (2 * S * NP), rin, ws, wlen, n, n_tx, t, slot_pos, Q, tid);
+    if (!nxt.valid) return;
+    tt_convert_item<S, NRX, NP>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
+    if (tid == 0) tt_locate(ues, segs, n_segs, nn, total_items, s_it[cb]);
     __syncthreads();
-
-    // ---- S consecutive outputs per thread, all Rx antennas ----
-    const int g = g0 + tid;
-    if (g < gend) {
-      const int w_me = g * S;
-      int j = jf;
-      while (j + 1 < nsym && s_sym[j + 1] <= w_me) ++j;
-      const int o = w_me - s_sym[j];
-      const float rL = 1.0f / (float)(s_sym[j + 1] - s_sym[j]);
-      float tau[S];
-#pragma unroll
-      for (int jj = 0; jj < S; ++jj) tau[jj] = (float)(o + jj) * rL;
-
-      float2 acc[NRX][S];
-#pragma unroll
-      for (int r = 0; r < NRX; ++r)
-#pragma unroll
-        for (int jj = 0; jj < S; ++jj) acc[r][jj] = make_float2(0.f, 0.f);
-
-      const float4 *tb = tapsm + (j - jf) * per;
-      const int q0 = tid + dpad / S;
-      for (int t = 0; t < n_tx; ++t) {
-        const float2 *pl = planes + t * (2 * S * NP) + q0;
-        const float4 *tbt = tb + t * K;
-#pragma unroll KU
-        for (int k = 0; k < K; ++k) {
-          const float2 *px = pl + offk[k];
-          float2 xv[S];
-#pragma unroll
-          for (int jj = 0; jj < S; ++jj) xv[jj] = px[jj * NP];
-#pragma unroll
-          for (int r = 0; r < NRX; ++r) {
-            const float4 h = tbt[r * n_tx * K + k];
-#pragma unroll
-            for (int jj = 0; jj < S; ++jj) {
-              const float hr = fmaf(tau[jj], h.z, h.x);
-              const float hi = fmaf(tau[jj], h.w, h.y);
-              acc[r][jj].x = fmaf(hr, xv[jj].x, acc[r][jj].x);
-              acc[r][jj].x = fmaf(-hi, xv[jj].y, acc[r][jj].x);
-              acc[r][jj].y = fmaf(hr, xv[jj].y, acc[r][jj].y);
-              acc[r][jj].y = fmaf(hi, xv[jj].x, acc[r][jj].y);
-            }
-          }
-        }
-      }
-
-      // ---- epilogue: AWGN, pack, store ----
-      const float nstd = U->noise_std;
-      const uint64_t m0 = slot * (uint64_t)n + (uint64_t)w_me;
-#pragma unroll
-      for (int r = 0; r < NRX; ++r) {
-        if (nstd > 0.f) {
-          if (S == 1) {
-            tt_awgn_add_one(U->seed, U->ue_id, (uint32_t)r, m0, nstd, acc[r][0]);
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < S; jj += 2)
-              tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, m0 + (uint64_t)jj, nstd, acc[r][jj],
-                               acc[r][jj + 1]);
-          }
-        }
-        if (U->out_f32) {
-          float2 *dstf = reinterpret_cast<float2 *>(U->ring_out) + ((size_t)(slot_pos * NRX + r) * n + w_me);
-#pragma unroll
-          for (int jj = 0; jj < S; ++jj) dstf[jj] = acc[r][jj];
-          continue;
-        }
-        uint32_t pk[S];
-#pragma unroll
-        for (int jj = 0; jj < S; ++jj) pk[jj] = tt_pack_iq(acc[r][jj].x, acc[r][jj].y);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(U->ring_out) + ((size_t)(slot_pos * NRX + r) * n + w_me);
-        if (S >= 4 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-#pragma unroll
-          for (int jj = 0; jj < S; jj += 4)
-            *reinterpret_cast<uint4 *>(dst + jj) = make_uint4(pk[jj], pk[jj + 1], pk[jj + 2], pk[jj + 3]);
-        } else {
-#pragma unroll
-          for (int jj = 0; jj < S; ++jj) dst[jj] = pk[jj];
-        }
-      }
-    }
-    if (!counter) return;
-    __syncthreads();
+    cb ^= 1;
   }
 }
 
@@ -296,43 +393,29 @@ cudaError_t tt_launch_variant(const TTLaunch &L, cudaStream_t st) {
   auto kern = tt_conv_fp32_kernel<S, NRX, DMAX>;
   static bool attr_done = false;  // benign race: the attribute call is idempotent
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  const unsigned grid = L.counter ? (unsigned)L.grid : L.total_items;
-  if (grid == 0) return cudaSuccess;
-  kern<<<grid, TT_TPB, L.smem, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter);
+  if (L.grid < 0) {  // occupancy query: blocks per SM returned through grid
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, TT_TPB, L.smem) != cudaSuccess) blocks = 1;
+    const_cast<TTLaunch &>(L).grid = -(blocks > 0 ? blocks : 1);
+    return cudaSuccess;
+  }
+  if (L.grid == 0 || L.total_items == 0) return cudaSuccess;
+  kern<<<L.grid, TT_TPB, L.smem, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter, L.ntx, L.tap_max,
+                                       L.k_max);
   return cudaGetLastError();
-}
-
-template <int S, int NRX, int DMAX>
-int tt_occupancy_variant(size_t smem) {
-  int blocks = 0;
-  auto kern = tt_conv_fp32_kernel<S, NRX, DMAX>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, TT_TPB, smem) != cudaSuccess) return 1;
-  return blocks > 0 ? blocks : 1;
 }
 
 template <int S, int NRX>
 cudaError_t tt_launch_dclass(const TTLaunch &L, cudaStream_t st) {
-  if (L.grid < 0) {  // occupancy query: blocks per SM returned through grid
-    int b = 1;
-    switch (L.dclass) {
-      case 0: b = tt_occupancy_variant<S, NRX, TT_DCLASS0>(L.smem); break;
-      case 1: b = tt_occupancy_variant<S, NRX, TT_DCLASS1>(L.smem); break;
-      case 2: b = tt_occupancy_variant<S, NRX, TT_DCLASS2>(L.smem); break;
-      default: return cudaErrorInvalidValue;
-    }
-    const_cast<TTLaunch &>(L).grid = -b;
-    return cudaSuccess;
-  }
   switch (L.dclass) {
     case 0: return tt_launch_variant<S, NRX, TT_DCLASS0>(L, st);
     case 1: return tt_launch_variant<S, NRX, TT_DCLASS1>(L, st);
     case 2: return tt_launch_variant<S, NRX, TT_DCLASS2>(L, st);
+    case 3: return tt_launch_variant<S, NRX, TT_DCLASS3>(L, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -91,6 +91,8 @@ struct tt_chan {
   uint64_t trace_bytes = 0;
   bool has_trace = false;
   int spt = 1, dclass = 0, max_sym_touched = 1;
+  int32_t *d_chunks = nullptr;  // per work item of a slot: first symbol | symbols touched << 16
+  int tap_need = 0;             // max symbols touched x n_rx x n_tx x K
   size_t smem = 0;
   TTUEDesc desc{};
   bool started = false;
@@ -178,7 +180,8 @@ int pick_spt(const std::vector<uint32_t> &L, uint32_t override_spt, uint32_t n_r
 int pick_dclass(int d_max) {
   if (d_max <= TT_DCLASS0) return 0;
   if (d_max <= TT_DCLASS1) return 1;
-  return 2;
+  if (d_max <= TT_DCLASS2) return 2;
+  return 3;
 }
 
 // Copy [first, first+n) slots between a linear buffer and the ring (<= 2 copies).
@@ -280,6 +283,7 @@ tt_status tt_engine_destroy(tt_engine *e) {
       cudaFree(c->d_out);
       cudaFree(c->d_taps);
       cudaFree(c->d_delays);
+      cudaFree(c->d_chunks);
       c->e = nullptr;
       delete c;
     }
@@ -400,7 +404,22 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   d.sym_start[d.nsym] = b;
   d.grp_start[d.nsym] = g;
   std::vector<int32_t> L32(c->sym_len.begin(), c->sym_len.end());
-  c->max_sym_touched = tt_conv_max_sym_touched(c->spt, L32.data(), d.nsym);
+  std::vector<int32_t> chunks(d.items_per_slot);
+  tt_conv_chunk_info(c->spt, L32.data(), d.nsym, chunks.data(), (int)chunks.size());
+  c->max_sym_touched = 1;
+  for (int32_t v : chunks) c->max_sym_touched = std::max(c->max_sym_touched, (int)(v >> 16));
+  err = cudaMalloc(&c->d_chunks, chunks.size() * sizeof(int32_t));
+  if (err == cudaSuccess)
+    err = cudaMemcpy(c->d_chunks, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    cudaFree(c->d_in);
+    cudaFree(c->d_out);
+    cudaFree(c->d_chunks);
+    e->in_use -= bytes;
+    delete c;
+    return fail(TT_ERR_CUDA, "chunk table: %s", cudaGetErrorString(err));
+  }
+  d.chunk_info = c->d_chunks;
   e->table[idx] = c;
   tt_status st = upload_desc(c);
   if (st != TT_OK) return st;
@@ -418,6 +437,7 @@ tt_status tt_chan_destroy(tt_chan *c) {
   cudaFree(c->d_out);
   cudaFree(c->d_taps);
   cudaFree(c->d_delays);
+  cudaFree(c->d_chunks);
   e->in_use -= c->ring_bytes + c->trace_bytes;
   e->table[c->index] = nullptr;
   c->e = nullptr;
@@ -448,8 +468,9 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   for (size_t i = 0; i < nval; ++i)
     if (!std::isfinite(tr->taps[i])) return fail(TT_ERR_TRACE, "non-finite tap value at %zu", i);
   const int dclass = pick_dclass(d_max);
-  int spt = c->spt;
-  size_t smem = tt_conv_smem_bytes(spt, dclass, c->cfg.n_tx, c->cfg.n_rx, tr->n_taps, c->max_sym_touched);
+  const int spt = c->spt;
+  const int tap_need = c->max_sym_touched * (int)(c->cfg.n_rx * c->cfg.n_tx * tr->n_taps);
+  size_t smem = tt_conv_smem_bytes(spt, dclass, c->cfg.n_tx, tap_need, tr->n_taps);
   if (smem > 200 * 1024) return fail(TT_ERR_INVALID, "channel too large for the tiled kernel (%zu B smem)", smem);
 
   std::lock_guard<std::mutex> lk(e->mu);
@@ -487,6 +508,7 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   c->has_trace = true;
   c->dclass = dclass;
   c->smem = smem;
+  c->tap_need = tap_need;
   TTUEDesc &d = c->desc;
   d.taps = taps;
   d.delays = delays;
@@ -587,7 +609,7 @@ tt_status tt_engine_run(tt_engine *e) {
     std::vector<std::vector<Entry>> groups;
     std::vector<int> keys;
     for (tt_chan *c : ready) {
-      const int key = (c->spt * 8 + c->cfg.n_rx) * 4 + c->dclass;
+      const int key = ((c->spt * 8 + (int)c->cfg.n_rx) * 8 + (int)c->cfg.n_tx) * 8 + c->dclass;
       size_t gi = std::find(keys.begin(), keys.end(), key) - keys.begin();
       if (gi == keys.size()) {
         keys.push_back(key);
@@ -606,11 +628,11 @@ tt_status tt_engine_run(tt_engine *e) {
     if ((int)groups.size() > e->counter_cap) return fail(TT_ERR_INVALID, "too many kernel variants");
     std::vector<TTSeg> segs;
     segs.reserve(nseg);
-    struct GL { size_t seg0; int nseg; uint32_t items; size_t smem; int spt, nrx, dclass; };
+    struct GL { size_t seg0; int nseg; uint32_t items; size_t smem; int spt, nrx, ntx, dclass, tap_max, k_max; };
     std::vector<GL> gls;
     for (auto &g : groups) {
       std::stable_sort(g.begin(), g.end(), [](const Entry &a, const Entry &b) { return a.cost > b.cost; });
-      GL gl{segs.size(), 0, 0, 0, g[0].c->spt, (int)g[0].c->cfg.n_rx, g[0].c->dclass};
+      GL gl{segs.size(), 0, 0, 0, g[0].c->spt, (int)g[0].c->cfg.n_rx, (int)g[0].c->cfg.n_tx, g[0].c->dclass, 1, 1};
       for (auto &en : g) {
         tt_chan *c = en.c;
         TTSeg s{};
@@ -620,10 +642,12 @@ tt_status tt_engine_run(tt_engine *e) {
         s.item_begin = gl.items;
         s.items = s.n_slots * (uint32_t)c->desc.items_per_slot;
         gl.items += s.items;
-        gl.smem = std::max(gl.smem, c->smem);
+        gl.tap_max = std::max(gl.tap_max, c->tap_need);
+        gl.k_max = std::max(gl.k_max, c->desc.n_taps);
         segs.push_back(s);
         ++gl.nseg;
       }
+      gl.smem = tt_conv_smem_bytes(gl.spt, gl.dclass, gl.ntx, gl.tap_max, gl.k_max);
       gls.push_back(gl);
     }
     TT_CK(cudaMemcpyAsync(e->d_segs, segs.data(), sizeof(TTSeg) * segs.size(), cudaMemcpyHostToDevice,
@@ -638,17 +662,18 @@ tt_status tt_engine_run(tt_engine *e) {
       L.total_items = gl.items;
       L.spt = gl.spt;
       L.nrx = gl.nrx;
+      L.ntx = gl.ntx;
       L.dclass = gl.dclass;
+      L.tap_max = gl.tap_max;
+      L.k_max = gl.k_max;
       L.smem = gl.smem;
-      L.counter = nullptr;
-      if (e->persistent) {
-        L.grid = -1;  // occupancy query
-        tt_launch_conv_fp32(L, e->stream);
-        const int per_sm = -L.grid;
-        L.counter = e->d_counters + gi;
-        L.grid = (int)std::min<uint64_t>((uint64_t)per_sm * e->num_sms, gl.items);
-      }
+      L.counter = e->persistent ? e->d_counters + gi : nullptr;
+      L.grid = -1;  // occupancy query
       cudaError_t err = tt_launch_conv_fp32(L, e->stream);
+      if (err != cudaSuccess) return fail(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(err));
+      const int per_sm = -L.grid;
+      L.grid = (int)std::min<uint64_t>((uint64_t)per_sm * e->num_sms, gl.items);
+      err = tt_launch_conv_fp32(L, e->stream);
       if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tiled launch: %s", cudaGetErrorString(err));
       ++e->launches;
     }

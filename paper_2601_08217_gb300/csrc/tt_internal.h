@@ -15,8 +15,9 @@
 // Delay classes of the tiled kernel: the staged window is sized at compile
 // time for delays up to these bounds.
 #define TT_DCLASS0 128
-#define TT_DCLASS1 512
-#define TT_DCLASS2 1024
+#define TT_DCLASS1 256
+#define TT_DCLASS2 512
+#define TT_DCLASS3 1024
 
 // Window geometry of the tiled kernel (samples per thread S, delay class DMAX):
 // delay padding DP (a multiple of S) and phase-plane pitch NP in float2 words.
@@ -31,8 +32,10 @@ __host__ __device__ constexpr int tt_geo_np(int S, int DMAX) {
   return tt_geo_np_raw(S, DMAX) + ((16 / (S < 16 ? S : 16)) % 16 - tt_geo_np_raw(S, DMAX) % 16 + 16) % 16;
 }
 __host__ __device__ constexpr int tt_dclass_max(int dclass) {
-  return dclass == 0 ? TT_DCLASS0 : (dclass == 1 ? TT_DCLASS1 : TT_DCLASS2);
+  return dclass == 0 ? TT_DCLASS0 : (dclass == 1 ? TT_DCLASS1 : (dclass == 2 ? TT_DCLASS2 : TT_DCLASS3));
 }
+// Longest input window of one work item (samples): the item's span plus the delay line.
+__host__ __device__ constexpr int tt_geo_wmax(int S, int DMAX) { return TT_TPB * S + tt_geo_dp(S, DMAX); }
 
 // Device-resident description of one admitted UE link.  The engine keeps an
 // array of these on the device; work items index into it.
@@ -41,6 +44,7 @@ struct TTUEDesc {
   void *ring_out;          // [Q][n_rx][N] x (int16 I,Q | float2)
   const float2 *taps;      // [T][n_rx][n_tx][K]
   const int32_t *delays;   // [K]
+  const int32_t *chunk_info;  // per work item of a slot: first symbol | (symbols touched << 16)
   double step_samples;     // 0: one trace entry per symbol
   uint64_t seed;
   int32_t n;               // samples per slot
@@ -75,17 +79,22 @@ struct TTLaunch {
   const TTSeg *segs;
   int n_segs;
   uint32_t total_items;
-  uint32_t *counter;    // persistent mode: device work counter (zeroed before launch); else null
+  uint32_t *counter;    // non-null: CTAs claim items from this device counter (zeroed before launch);
+                        // null: CTA b takes items b, b + grid, b + 2 grid, ...
   int spt;              // 1, 2, 4, 8, 16
-  int nrx;              // 1..4
-  int dclass;           // 0: d_max <= 256, 1: d_max <= 1024
-  int grid;             // CTAs (persistent) -- ignored otherwise
-  size_t smem;          // dynamic shared memory bytes
+  int nrx;              // 1..4 (every UE of the launch has this many Rx antennas)
+  int ntx;              // 1..4 (every UE of the launch has this many Tx antennas)
+  int dclass;           // delay class, see TT_DCLASS*
+  int tap_max;          // largest (symbols touched x n_rx x n_tx x K) of the launch's UEs
+  int k_max;            // largest tap count of the launch's UEs
+  int grid;             // CTAs; < 0 on input asks for the occupancy (returned as -blocks per SM)
+  size_t smem;          // dynamic shared memory bytes (tt_conv_smem_bytes)
 };
 
-// Per-UE dynamic shared memory of the tiled kernel.
-size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int n_rx, int n_taps, int max_sym_touched);
-int tt_conv_max_sym_touched(int spt, const int32_t *sym_len, int nsym);
+// Dynamic shared memory of the tiled kernel for a launch.
+size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max);
+// First symbol and number of symbols touched by each work item of a slot (packed jf | nst << 16).
+int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, int max_out);
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s1(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s2(const TTLaunch &L, cudaStream_t st);
