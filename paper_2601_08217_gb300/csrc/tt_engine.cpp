@@ -165,23 +165,37 @@ tt_status wait_seq(tt_engine *e, uint64_t seq, int64_t timeout_us, std::unique_l
   }
 }
 
-int pick_spt(const std::vector<uint32_t> &L, uint32_t override_spt, uint32_t n_rx) {
-  static const int cands[] = {16, 8, 4, 2, 1};
-  for (int s : cands) {
-    if (override_spt && (uint32_t)s > override_spt) continue;
-    if (s == 16 && n_rx > 2) continue;
-    bool ok = true;
-    for (uint32_t v : L) ok = ok && (v % (uint32_t)s == 0);
-    if (ok) return s;
-  }
-  return 1;
-}
-
 int pick_dclass(int d_max) {
   if (d_max <= TT_DCLASS0) return 0;
   if (d_max <= TT_DCLASS1) return 1;
   if (d_max <= TT_DCLASS2) return 2;
   return 3;
+}
+
+// Work-item geometry of a channel for samples-per-thread spt: (chunk table, largest symbols touched).
+std::vector<int32_t> chunk_table(const std::vector<uint32_t> &L, int spt, int *max_touched) {
+  int n = 0;
+  for (uint32_t v : L) n += (int)v;
+  const int items = (n / spt + TT_TPB - 1) / TT_TPB;
+  std::vector<int32_t> L32(L.begin(), L.end()), chunks(items);
+  tt_conv_chunk_info(spt, L32.data(), (int)L32.size(), chunks.data(), items);
+  *max_touched = 1;
+  for (int32_t v : chunks) *max_touched = std::max(*max_touched, (int)(v >> 16));
+  return chunks;
+}
+
+// Candidate samples-per-thread values of a channel, largest first: each divides every
+// symbol length; 16 only with at most 2 Rx antennas; none above the engine's cap.
+std::vector<int> spt_candidates(const std::vector<uint32_t> &L, uint32_t cap, uint32_t n_rx) {
+  std::vector<int> out;
+  for (int s : {16, 8, 4, 2, 1}) {
+    if (cap && (uint32_t)s > cap) continue;
+    if (s == 16 && n_rx > 2) continue;
+    bool ok = true;
+    for (uint32_t v : L) ok = ok && (v % (uint32_t)s == 0);
+    if (ok) out.push_back(s);
+  }
+  return out;
 }
 
 // Copy [first, first+n) slots between a linear buffer and the ring (<= 2 copies).
@@ -231,6 +245,40 @@ void mark_pushed(tt_chan *c, uint64_t first, uint32_t n) {
 }
 
 bool valid_chan(const tt_chan *c) { return c && c->e; }
+
+// Switch a channel's tiled-kernel geometry to spt samples per thread (engine lock held).
+tt_status set_spt(tt_chan *c, int spt) {
+  int touched = 1;
+  std::vector<int32_t> chunks = chunk_table(c->sym_len, spt, &touched);
+  int32_t *d_chunks = nullptr;
+  cudaError_t err = cudaMalloc(&d_chunks, chunks.size() * sizeof(int32_t));
+  if (err == cudaSuccess)
+    err = cudaMemcpy(d_chunks, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    cudaFree(d_chunks);
+    return fail(TT_ERR_CUDA, "chunk table: %s", cudaGetErrorString(err));
+  }
+  cudaFree(c->d_chunks);
+  c->d_chunks = d_chunks;
+  c->spt = spt;
+  c->max_sym_touched = touched;
+  TTUEDesc &d = c->desc;
+  d.chunk_info = d_chunks;
+  d.spt = spt;
+  d.groups = c->n / spt;
+  d.items_per_slot = (int)chunks.size();
+  int b = 0, g = 0;
+  for (int j = 0; j < d.nsym; ++j) {
+    d.sym_start[j] = b;
+    d.grp_start[j] = g;
+    b += (int)c->sym_len[j];
+    g += (int)c->sym_len[j] / spt;
+  }
+  d.sym_start[d.nsym] = b;
+  d.grp_start[d.nsym] = g;
+  d.dpad = (d.d_max + spt - 1) / spt * spt;
+  return TT_OK;
+}
 
 }  // namespace
 
@@ -378,7 +426,6 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   }
   c->ring_bytes = bytes;
   e->in_use += bytes;
-  c->spt = pick_spt(c->sym_len, e->spt_override, cfg->n_rx);
   TTUEDesc &d = c->desc;
   d.ring_in = c->d_in;
   d.ring_out = c->d_out;
@@ -391,35 +438,15 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   d.seed = cfg->seed;
   d.noise_std = cfg->noise_var > 0.f ? (float)std::sqrt((double)cfg->noise_var / 2.0) : 0.f;
   d.out_f32 = cfg->output_format == TT_OUT_CF32 ? 1 : 0;
-  d.spt = c->spt;
-  d.groups = (int)N / c->spt;
-  d.items_per_slot = (d.groups + TT_TPB - 1) / TT_TPB;
-  int b = 0, g = 0;
-  for (int j = 0; j < d.nsym; ++j) {
-    d.sym_start[j] = b;
-    d.grp_start[j] = g;
-    b += (int)c->sym_len[j];
-    g += (int)c->sym_len[j] / c->spt;
-  }
-  d.sym_start[d.nsym] = b;
-  d.grp_start[d.nsym] = g;
-  std::vector<int32_t> L32(c->sym_len.begin(), c->sym_len.end());
-  std::vector<int32_t> chunks(d.items_per_slot);
-  tt_conv_chunk_info(c->spt, L32.data(), d.nsym, chunks.data(), (int)chunks.size());
-  c->max_sym_touched = 1;
-  for (int32_t v : chunks) c->max_sym_touched = std::max(c->max_sym_touched, (int)(v >> 16));
-  err = cudaMalloc(&c->d_chunks, chunks.size() * sizeof(int32_t));
-  if (err == cudaSuccess)
-    err = cudaMemcpy(c->d_chunks, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
-  if (err != cudaSuccess) {
+  const std::vector<int> cands = spt_candidates(c->sym_len, e->spt_override, cfg->n_rx);
+  tt_status sst = set_spt(c, cands.empty() ? 1 : cands[0]);
+  if (sst != TT_OK) {
     cudaFree(c->d_in);
     cudaFree(c->d_out);
-    cudaFree(c->d_chunks);
     e->in_use -= bytes;
     delete c;
-    return fail(TT_ERR_CUDA, "chunk table: %s", cudaGetErrorString(err));
+    return sst;
   }
-  d.chunk_info = c->d_chunks;
   e->table[idx] = c;
   tt_status st = upload_desc(c);
   if (st != TT_OK) return st;
@@ -468,10 +495,24 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   for (size_t i = 0; i < nval; ++i)
     if (!std::isfinite(tr->taps[i])) return fail(TT_ERR_TRACE, "non-finite tap value at %zu", i);
   const int dclass = pick_dclass(d_max);
-  const int spt = c->spt;
-  const int tap_need = c->max_sym_touched * (int)(c->cfg.n_rx * c->cfg.n_tx * tr->n_taps);
-  size_t smem = tt_conv_smem_bytes(spt, dclass, c->cfg.n_tx, tap_need, tr->n_taps);
-  if (smem > 200 * 1024) return fail(TT_ERR_INVALID, "channel too large for the tiled kernel (%zu B smem)", smem);
+  // largest samples-per-thread whose shared-memory footprint fits
+  int spt = 0, tap_need = 0;
+  size_t smem = 0;
+  for (int s : spt_candidates(c->sym_len, c->e->spt_override, c->cfg.n_rx)) {
+    int touched = 1;
+    chunk_table(c->sym_len, s, &touched);
+    const int need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * tr->n_taps);
+    const size_t b = tt_conv_smem_bytes(s, dclass, c->cfg.n_tx, need, tr->n_taps);
+    if (b <= 200 * 1024) {
+      spt = s;
+      tap_need = need;
+      smem = b;
+      break;
+    }
+  }
+  if (spt == 0)
+    return fail(TT_ERR_INVALID, "channel too large for the tiled kernel: %u x %u antennas, %u taps, delay %d",
+                c->cfg.n_rx, c->cfg.n_tx, tr->n_taps, d_max);
 
   std::lock_guard<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
@@ -515,9 +556,10 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   d.step_samples = tr->step_samples;
   d.n_taps = (int)tr->n_taps;
   d.d_max = d_max;
-  d.dpad = (d_max + c->spt - 1) / c->spt * c->spt;
   d.n_anchors = (int)tr->n_anchors;
   d.loop = tr->loop ? 1 : 0;
+  tt_status sst = set_spt(c, spt);
+  if (sst != TT_OK) return sst;
   return upload_desc(c);
 }
 

