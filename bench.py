@@ -272,7 +272,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--persistent", type=int, default=1, help="1: CTAs claim work items from a device counter")
     ap.add_argument("--spt", type=int, default=0, help="cap on samples per thread (0 = largest that fits)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -346,7 +346,7 @@ def main():
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "ues_per_gpu": N_UES, "slots": N_SLOTS,
                    "samples_per_slot": SLOT_SAMPLES, "taps": N_TAPS, "max_delay": D_MAX,
-                   "form": "batched" + (" persistent" if args.persistent else ""),
+                   "form": "batched, persistent CTAs" + (" (device work counter)" if args.persistent else " (strided)"),
                    "iq": f"{DISTINCT_IQ_SLOTS} distinct synthetic slots per UE cycled",
                    "l2": "inputs larger than L2 (1.97 GB of IQ read per step per GPU)"},
         "gmac_per_s": gmac, "samples_per_s": N_UES * N_SLOTS * SLOT_SAMPLES * world / (ms_step / 1e3),
