@@ -352,7 +352,7 @@ def main():
         "gmac_per_s": gmac, "samples_per_s": N_UES * N_SLOTS * SLOT_SAMPLES * world / (ms_step / 1e3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
-                     "kernel": "tt_conv_fp32_kernel<8,1,512>", "kernel_ms": kms,
+                     "kernel": "tt_conv_fp32_kernel<8,1,256>", "kernel_ms": kms,
                      "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz ({pk['src']})"},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],

@@ -219,6 +219,58 @@ tt_status tt_chan_release_slots(tt_chan *c, uint64_t first, uint32_t n);
 tt_status tt_chan_get_state(const tt_chan *c, void *buf, size_t *len);
 tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len);
 
+/* --------------------------------------------------- no-allocation entry point
+ * The paper has no counterpart to this call.  It exists for callers that may
+ * not allocate device memory: code inside another framework's memory pool or
+ * a fixed-size real-time partition, or anything that must keep a constant
+ * footprint.  tt_conv_static runs the same tiled kernel as tt_engine_run on
+ * buffers the caller owns and calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Its scratch (descriptors, work list, chunk tables,
+ * delays, work counters) lives in one fixed __device__ array inside the
+ * library, about 200 KB, which every GPU that loads the library holds until
+ * the process exits.
+ *
+ * Limits, rejected with TT_ERR_INVALID: at most 64 channels per call,
+ * samples_per_slot <= 65536, at most 128 taps, delays <= 1024, and a
+ * channel must fit the kernel's shared memory.
+ *
+ * Layout and semantics follow the engine's rings: slot s of a channel sits at
+ * ring position s % ring_slots, input [ring_slots][n_tx][N][2] int16, output
+ * [ring_slots][n_rx][N] x (int16 I,Q | complex64).  The call computes slots
+ * [first_slot, first_slot + n_slots) and reads the delay line from the ring
+ * positions of earlier slots, so the caller keeps those filled (zeros before
+ * the first slot).  Asynchronous on `stream` (cudaStream_t, NULL = legacy).
+ *
+ * The first call on a device looks up the scratch array's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the array and leaves its contents behind; each call
+ * rewrites what it reads and zeroes its counters.  Calls that overlap on the
+ * GPU (different streams or threads) race on the array: order them on one
+ * stream. */
+typedef struct {
+  uint32_t struct_size;       /* sizeof(tt_static_chan) */
+  uint32_t ue_id;             /* keys the AWGN stream */
+  uint32_t samples_per_slot;  /* N */
+  uint32_t symbols_per_slot;
+  const uint32_t *symbol_len; /* host, [symbols_per_slot], summing to N */
+  uint32_t n_tx, n_rx;        /* 1 .. 4 */
+  uint32_t ring_slots;        /* ring depth Q of both rings: >= ceil(max delay / N) + 1 and >= n_slots */
+  const int16_t *d_ring_in;   /* device, caller-owned input ring */
+  void *d_ring_out;           /* device, caller-owned output ring */
+  const float *d_taps;        /* device, caller-owned complex64 [n_anchors][n_rx][n_tx][n_taps] */
+  const int32_t *delays;      /* host, [n_taps], non-decreasing, 0 .. 1024 */
+  uint32_t n_anchors, n_taps;
+  double step_samples;        /* as in tt_trace_desc */
+  int32_t loop;
+  uint64_t seed;
+  float noise_var;            /* sigma^2 per complex sample, 0 = off */
+  uint32_t output_format;     /* TT_OUT_INT16 or TT_OUT_CF32 */
+  uint64_t first_slot;        /* first slot to compute */
+  uint32_t n_slots;           /* number of slots to compute */
+} tt_static_chan;
+
+tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chans, void *stream);
+
 /* ---------------------------------------------------------------- misc */
 
 const char *tt_last_error(void);

@@ -283,6 +283,11 @@ tt_status set_spt(tt_chan *c, int spt) {
 
 }  // namespace
 
+int32_t tt_set_error(int32_t status, const char *msg) {
+  g_err = msg ? msg : "";
+  return status;
+}
+
 // =========================================================================
 extern "C" {
 

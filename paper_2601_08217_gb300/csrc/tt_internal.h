@@ -11,6 +11,8 @@
 #define TT_MAX_TAPS 128
 #define TT_MAX_DELAY 1024
 #define TT_TPB 128  // threads per CTA of the tiled kernel
+#define TT_STATIC_MAX_CHANS 64            // channels per tt_conv_static call
+#define TT_STATIC_MAX_ITEMS_PER_SLOT 512  // work items per slot in tt_conv_static (N <= 65536)
 
 // Delay classes of the tiled kernel: the staged window is sized at compile
 // time for delays up to these bounds.
@@ -101,6 +103,9 @@ cudaError_t tt_launch_conv_s2(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s4(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s8(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s16(const TTLaunch &L, cudaStream_t st);
+
+// Record a message for tt_last_error() (thread-local) and return the status.
+int32_t tt_set_error(int32_t status, const char *msg);
 
 // Plain comparison form: one launch per UE per slot.
 cudaError_t tt_launch_plain(const TTUEDesc *ue_dev, uint64_t slot, int n, cudaStream_t st);

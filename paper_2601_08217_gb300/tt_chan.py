@@ -59,6 +59,17 @@ class EngineStats(C.Structure):
                 ("pad", C.c_uint32), ("launches", C.c_uint64), ("slots_processed", C.c_uint64)]
 
 
+class StaticChan(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("ue_id", C.c_uint32), ("samples_per_slot", C.c_uint32),
+                ("symbols_per_slot", C.c_uint32), ("symbol_len", C.POINTER(C.c_uint32)),
+                ("n_tx", C.c_uint32), ("n_rx", C.c_uint32), ("ring_slots", C.c_uint32),
+                ("d_ring_in", C.c_void_p), ("d_ring_out", C.c_void_p), ("d_taps", C.c_void_p),
+                ("delays", C.POINTER(C.c_int32)), ("n_anchors", C.c_uint32), ("n_taps", C.c_uint32),
+                ("step_samples", C.c_double), ("loop", C.c_int32), ("seed", C.c_uint64),
+                ("noise_var", C.c_float), ("output_format", C.c_uint32), ("first_slot", C.c_uint64),
+                ("n_slots", C.c_uint32)]
+
+
 _VP = C.c_void_p
 _SIGS = {
     "tt_engine_create": [C.POINTER(EngineConfig), C.POINTER(_VP)],
@@ -82,6 +93,7 @@ _SIGS = {
     "tt_chan_release_slots": [_VP, C.c_uint64, C.c_uint32],
     "tt_chan_get_state": [_VP, _VP, C.POINTER(C.c_size_t)],
     "tt_chan_set_state": [_VP, _VP, C.c_size_t],
+    "tt_conv_static": [C.POINTER(StaticChan), C.c_uint32, _VP],
 }
 
 _lib = None
@@ -268,6 +280,26 @@ def tt_chan_get_state(c: int) -> bytes:
 def tt_chan_set_state(c: int, blob: bytes):
     buf = C.create_string_buffer(blob, len(blob))
     _check(load().tt_chan_set_state(c, buf, len(blob)))
+
+
+def tt_conv_static(chans, stream=None):
+    """chans: list of dicts with the tt_static_chan fields (device buffers as tensors or addresses,
+    symbol_len and delays as host sequences).  Runs on `stream` without allocating."""
+    arr = (StaticChan * max(len(chans), 1))()
+    keep = []
+    for i, c in enumerate(chans):
+        L = (C.c_uint32 * len(c["symbol_len"]))(*[int(v) for v in c["symbol_len"]])
+        d = np.ascontiguousarray(c["delays"], dtype=np.int32)
+        keep += [L, d]
+        arr[i] = StaticChan(C.sizeof(StaticChan), int(c.get("ue_id", 0)), int(sum(c["symbol_len"])),
+                            len(c["symbol_len"]), L, int(c["n_tx"]), int(c["n_rx"]), int(c["ring_slots"]),
+                            _ptr(c["d_ring_in"]), _ptr(c["d_ring_out"]), _ptr(c["d_taps"]),
+                            d.ctypes.data_as(C.POINTER(C.c_int32)), int(c["n_anchors"]), int(d.size),
+                            float(c.get("step_samples", 0.0)), int(bool(c.get("loop", False))),
+                            int(c.get("seed", 0)), float(c.get("noise_var", 0.0)),
+                            int(c.get("output_format", TT_OUT_INT16)), int(c["first_slot"]),
+                            int(c["n_slots"]))
+    _check(load().tt_conv_static(arr, len(chans), _stream_ptr(stream)))
 
 
 def tt_last_error() -> str:
