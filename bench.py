@@ -34,6 +34,10 @@ SLOT_SAMPLES = 30720
 FLOP_PER_TAP_SAMPLE = 12      # complex MAC (8) + tap interpolation h = H + tau*dH (2 FMA = 4)
 DISTINCT_IQ_SLOTS = 64        # synthetic IQ slots per UE, cycled through the replay
 METRIC = "UE-slots/s and GMAC/s at 1 GB300 vs plain form; p99 slot latency vs 0.5 ms"
+# DRAM traffic per full launch from the ncu capture summarised in
+# profiles/tt_conv_fp32_kernel_40mhz_16ue.md, valid only for the kernel source it was taken on.
+TRAFFIC_BYTES = 3.52e9
+TRAFFIC_KERNEL_SHA = "ddb7e2023d2e3c33"
 WORKLOAD = ("16 UEs SISO, 40 MHz (30720 samples/slot), 1000 slots each, 24 taps (delays <= 256), "
             "100 Hz Jakes, AWGN 20 dB, int16 IQ, FP32 accumulation")
 
@@ -331,6 +335,10 @@ def main():
     ts = tap_samples(r["specs"]) * N_SLOTS
     gmac = ts * world / (ms_step / 1e3) / 1e9
     pk = peaks()
+    import hashlib
+    ksrc = os.path.join(ROOT, "paper_2601_08217_gb300", "csrc", "tt_conv_kernel.cuh")
+    ksha = hashlib.sha256(open(ksrc, "rb").read()).hexdigest()[:16]
+    traffic = TRAFFIC_BYTES if (ksha == TRAFFIC_KERNEL_SHA and N_SLOTS == 1000) else None
     kms = statistics.mean(r["kern_ms"])
     peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     achieved = ts * FLOP_PER_TAP_SAMPLE / (kms / 1e3) / 1e12
@@ -351,7 +359,7 @@ def main():
                    "l2": "inputs larger than L2 (1.97 GB of IQ read per step per GPU)"},
         "gmac_per_s": gmac, "samples_per_s": N_UES * N_SLOTS * SLOT_SAMPLES * world / (ms_step / 1e3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
+                     "frac": achieved / peak_tflops, "traffic": traffic,
                      "kernel": "tt_conv_fp32_kernel<8,1,256>", "kernel_ms": kms,
                      "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz ({pk['src']})"},
         "gpu_launches": r["launches"],
