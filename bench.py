@@ -98,11 +98,11 @@ class ClockSampler:
 
 
 def make_workload(rank: int):
-    from paper_2601_08217_gb300 import inputs
+    from paper_2601_08217_gb300 import inputs, shard
     specs = inputs.workload_plain_16ue(n_slots=N_SLOTS, n_ues=N_UES)
-    for s in specs:
+    for s, uid in zip(specs, shard.shard_ue_ids(N_UES, rank)):
         s.loop = True            # repeated steps keep replaying the trace
-        s.ue_id += rank * N_UES
+        s.ue_id = uid
     iq = [inputs.make_iq(2, s, DISTINCT_IQ_SLOTS) for s in specs]
     return specs, iq
 
@@ -121,6 +121,7 @@ def tap_samples(specs):
 
 def run_ours(args, rank, world, device):
     import torch
+    from paper_2601_08217_gb300 import shard
     from paper_2601_08217_gb300 import tt_chan as tc
 
     specs, iq = make_workload(rank)
@@ -203,11 +204,7 @@ def run_ours(args, rank, world, device):
         ts = time.perf_counter()
         for _ in range(e2e_steps):
             e2e_step()
-        te = time.perf_counter() - ts
-        if world > 1:
-            t = torch.tensor([te], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = shard.max_over_ranks(time.perf_counter() - ts, device="cuda")
         bytes_in = sum(h.numel() * 2 for h in h_in)
         bytes_out = sum(h.numel() * 2 for h in h_out)
         e2e = {"value": N_UES * N_SLOTS * world * e2e_steps / te, "unit": "UE-slots/s",
@@ -325,11 +322,8 @@ def main():
     __graft_entry__.build()
 
     r = run_ours(args, rank, world, local)
-    ms_step = r["ms_total"] / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    from paper_2601_08217_gb300 import shard
+    ms_step = shard.max_over_ranks(r["ms_total"] / args.steps, device="cuda")
     ue_slots = N_UES * N_SLOTS * world
     value = ue_slots / (ms_step / 1e3)
     ts = tap_samples(r["specs"]) * N_SLOTS
