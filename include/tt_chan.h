@@ -91,7 +91,9 @@ typedef struct {
                                   (16 only for channels with at most 2 Rx antennas).
                                   Each channel uses the largest allowed value dividing all its symbol lengths. */
   uint32_t threads_per_block;  /* reserved: 0 (the tiled kernel runs 128 threads per CTA) */
-  uint32_t persistent;       /* 1: persistent CTAs claim work from a device counter; 0: one CTA per item */
+  uint32_t persistent;       /* 1: persistent CTAs claim work items from a device counter; 0: by stride */
+  uint32_t graphs;           /* 1: tt_engine_run captures its launches in a CUDA graph and replays it
+                                while the set of channels and slots per run stays the same */
 } tt_engine_config;
 
 typedef struct {
@@ -127,6 +129,8 @@ typedef struct {
   uint32_t pad;
   uint64_t launches;        /* kernel launches issued by tt_engine_run so far */
   uint64_t slots_processed; /* (UE, slot) pairs launched so far */
+  uint64_t graph_builds;    /* CUDA graphs captured (graphs mode) */
+  uint64_t graph_launches;  /* CUDA graph replays (graphs mode) */
 } tt_engine_stats;
 
 /* ---------------------------------------------------------------- engine */
@@ -151,6 +155,15 @@ tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us);
 tt_status tt_engine_stream(tt_engine *e, void **stream);
 
 tt_status tt_engine_get_stats(tt_engine *e, tt_engine_stats *out);
+
+/* Autotune the tiled kernel's samples-per-thread for every class of admitted,
+ * traced channels (same symbol lengths, antennas, tap count, delay class):
+ * each candidate that fits shared memory is timed `reps` times on one slot
+ * of every channel of the class that has a free ring position (written to
+ * that free position, so no queued or unpulled slot is touched), and the
+ * fastest is kept.  Waits for queued work first.  *classes_tuned (may be
+ * NULL) receives the number of classes that had a choice to make. */
+tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned);
 
 /* ---------------------------------------------------------------- channel */
 

@@ -93,8 +93,10 @@ struct TTItem {
 };
 
 // Thread 0: item index -> (UE, slot, groups, first symbol, symbols touched).
+// With device cursors (graph replay), a run's first slot is cursors[ue] instead of seg.first_slot.
 __device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs,
-                                          int n_segs, uint32_t item, uint32_t total_items, TTItem &it) {
+                                          int n_segs, uint32_t item, uint32_t total_items,
+                                          const unsigned long long *__restrict__ cursors, TTItem &it) {
   if (item >= total_items) {
     it.valid = 0;
     return;
@@ -111,7 +113,7 @@ __device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, cons
   const uint32_t c = rel % ips;
   const int ci = __ldg(U->chunk_info + c);
   const int g0 = (int)c * TT_TPB;
-  const uint64_t slot = sg.first_slot + rel / ips;
+  const uint64_t slot = (cursors ? cursors[sg.ue] : sg.first_slot) + rel / ips;
   const int jf = ci & 0xFFFF;
   const uint64_t a0 = slot * (uint64_t)U->nsym + (uint64_t)jf;
   it.slot = slot;
@@ -324,7 +326,8 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
 template <int S, int NRX, int DMAX>
 __global__ void __launch_bounds__(TT_TPB)
     tt_conv_fp32_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
-                        uint32_t total_items, uint32_t *__restrict__ counter, int ntx, int tap_max, int k_max) {
+                        uint32_t total_items, uint32_t *__restrict__ counter, int ntx, int tap_max, int k_max,
+                        const unsigned long long *__restrict__ cursors) {
   constexpr int NP = tt_geo_np(S, DMAX);
   constexpr int WMAX = tt_geo_wmax(S, DMAX);
   extern __shared__ float4 dyn_smem[];
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(TT_TPB)
 
   // ---- prologue: first item fully staged, second item located ----
   if (tid == 0) {
-    tt_locate(ues, segs, n_segs, claim(), total_items, s_it[0]);
+    tt_locate(ues, segs, n_segs, claim(), total_items, cursors, s_it[0]);
     s_claim = claim();
   }
   __syncthreads();
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(TT_TPB)
     tt_cp_async_wait_all();
     __syncthreads();
     tt_convert_item<S, NRX, NP>(U, it, raw, WMAX, planes, taps0, dly0, tid);
-    if (tid == 0) tt_locate(ues, segs, n_segs, s_claim, total_items, s_it[1]);
+    if (tid == 0) tt_locate(ues, segs, n_segs, s_claim, total_items, cursors, s_it[1]);
     __syncthreads();
   }
 
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(TT_TPB)
     __syncthreads();
     if (!nxt.valid) return;
     tt_convert_item<S, NRX, NP>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
-    if (tid == 0) tt_locate(ues, segs, n_segs, nn, total_items, s_it[cb]);
+    if (tid == 0) tt_locate(ues, segs, n_segs, nn, total_items, cursors, s_it[cb]);
     __syncthreads();
     cb ^= 1;
   }
@@ -405,7 +408,7 @@ cudaError_t tt_launch_variant(const TTLaunch &L, cudaStream_t st) {
   }
   if (L.grid == 0 || L.total_items == 0) return cudaSuccess;
   kern<<<L.grid, TT_TPB, L.smem, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter, L.ntx, L.tap_max,
-                                       L.k_max);
+                                       L.k_max, L.cursors);
   return cudaGetLastError();
 }
 

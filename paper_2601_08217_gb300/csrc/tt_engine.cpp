@@ -7,7 +7,9 @@
 // Convolution Computation") is kept by construction: every channel has its
 // own ring, trace and descriptor, and no kernel mixes data of two UEs.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -75,6 +77,14 @@ struct tt_engine {
   std::deque<std::pair<uint64_t, cudaEvent_t>> events;  // (seq, event) not yet known complete
   std::vector<cudaEvent_t> pool;
   uint64_t launches = 0, slots_processed = 0;
+  // CUDA-graph replay of the batched launch (tt_engine_config.graphs)
+  bool graphs = false;
+  unsigned long long *d_cursors = nullptr;  // device-resident next slot of every UE table entry
+  TTSeg *d_gsegs = nullptr;                 // work list owned by the cached graph
+  size_t gseg_cap = 0;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint64_t> gkey;               // shape of the cached graph
+  uint64_t graph_builds = 0, graph_launches = 0;
 };
 
 struct tt_chan {
@@ -97,6 +107,7 @@ struct tt_chan {
   TTUEDesc desc{};
   bool started = false;
   uint64_t pushed_end = 0, launched_end = 0, completed_end = 0, pulled_end = 0;
+  uint64_t dev_cursor = UINT64_MAX;  // what the engine's device cursor holds for this UE (after queued work)
   std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
 };
 
@@ -281,6 +292,207 @@ tt_status set_spt(tt_chan *c, int spt) {
   return TT_OK;
 }
 
+// Shared-memory need of a traced channel at spt samples per thread (0 if it does not fit).
+size_t smem_need(const tt_chan *c, int spt, int *tap_need) {
+  int touched = 1;
+  chunk_table(c->sym_len, spt, &touched);
+  *tap_need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * (uint32_t)c->desc.n_taps);
+  const size_t b = tt_conv_smem_bytes(spt, c->dclass, (int)c->cfg.n_tx, *tap_need, c->desc.n_taps);
+  return b <= 200 * 1024 ? b : 0;
+}
+
+// Switch a traced channel to spt and refresh its launch parameters (engine lock held).
+tt_status apply_spt(tt_chan *c, int spt) {
+  int need = 0;
+  const size_t b = smem_need(c, spt, &need);
+  if (!b) return fail(TT_ERR_INVALID, "samples per thread %d does not fit", spt);
+  tt_status st = set_spt(c, spt);
+  if (st != TT_OK) return st;
+  c->tap_need = need;
+  c->smem = b;
+  return TT_OK;
+}
+
+
+// ---- batched launch planning (engine lock held) ----
+struct PlanGroup {
+  size_t seg0 = 0;
+  int nseg = 0;
+  uint32_t items = 0;
+  size_t smem = 0;
+  int spt = 1, nrx = 1, ntx = 1, dclass = 0, tap_max = 1, k_max = 1, grid = 1;
+};
+struct Plan {
+  std::vector<TTSeg> segs;
+  std::vector<PlanGroup> groups;
+  std::vector<tt_chan *> chans;  // in segment order
+  std::vector<uint64_t> key;     // shape: (UE, slots, variant) per segment
+};
+
+// One segment per channel (slots [first[i], first[i] + count[i])), grouped by kernel variant,
+// heaviest channels first inside a group; grid sizes from the occupancy of each variant.
+tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const std::vector<uint64_t> &first,
+                     const std::vector<uint64_t> &count, Plan &p) {
+  std::vector<size_t> order(chans.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  auto vkey = [&](size_t i) {
+    const tt_chan *c = chans[i];
+    return ((c->spt * 8 + (int)c->cfg.n_rx) * 8 + (int)c->cfg.n_tx) * 8 + c->dclass;
+  };
+  auto cost = [&](size_t i) {
+    const tt_chan *c = chans[i];
+    return (double)c->desc.n_taps * c->cfg.n_tx * c->cfg.n_rx;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    if (vkey(a) != vkey(b)) return vkey(a) < vkey(b);
+    return cost(a) > cost(b);
+  });
+  int cur_key = -1;
+  for (size_t oi = 0; oi < order.size(); ++oi) {
+    const size_t i = order[oi];
+    tt_chan *c = chans[i];
+    if (count[i] == 0) continue;
+    if (p.groups.empty() || vkey(i) != cur_key) {
+      cur_key = vkey(i);
+      PlanGroup g;
+      g.seg0 = p.segs.size();
+      g.spt = c->spt;
+      g.nrx = (int)c->cfg.n_rx;
+      g.ntx = (int)c->cfg.n_tx;
+      g.dclass = c->dclass;
+      p.groups.push_back(g);
+    }
+    PlanGroup &g = p.groups.back();
+    TTSeg sg{};
+    sg.first_slot = first[i];
+    sg.ue = c->index;
+    sg.n_slots = (uint32_t)count[i];
+    sg.item_begin = g.items;
+    sg.items = sg.n_slots * (uint32_t)c->desc.items_per_slot;
+    g.items += sg.items;
+    g.tap_max = std::max(g.tap_max, c->tap_need);
+    g.k_max = std::max(g.k_max, c->desc.n_taps);
+    ++g.nseg;
+    p.segs.push_back(sg);
+    p.chans.push_back(c);
+    p.key.push_back(((uint64_t)c->index << 40) ^ ((uint64_t)count[i] << 8) ^ (uint64_t)vkey(i));
+  }
+  if ((int)p.groups.size() > e->counter_cap) return fail(TT_ERR_INVALID, "too many kernel variants in one run");
+  for (PlanGroup &g : p.groups) {
+    g.smem = tt_conv_smem_bytes(g.spt, g.dclass, g.ntx, g.tap_max, g.k_max);
+    TTLaunch L{};
+    L.spt = g.spt;
+    L.nrx = g.nrx;
+    L.ntx = g.ntx;
+    L.dclass = g.dclass;
+    L.smem = g.smem;
+    L.grid = -1;  // occupancy query
+    cudaError_t err = tt_launch_conv_fp32(L, e->stream);
+    if (err != cudaSuccess) return fail(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(err));
+    g.grid = (int)std::min<uint64_t>((uint64_t)(-L.grid) * e->num_sms, g.items);
+  }
+  return TT_OK;
+}
+
+cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const unsigned long long *cursors) {
+  if (e->persistent) {
+    cudaError_t err = cudaMemsetAsync(e->d_counters, 0, sizeof(uint32_t) * p.groups.size(), e->stream);
+    if (err != cudaSuccess) return err;
+  }
+  for (size_t gi = 0; gi < p.groups.size(); ++gi) {
+    const PlanGroup &g = p.groups[gi];
+    TTLaunch L{};
+    L.ues = e->d_ues;
+    L.segs = d_segs + g.seg0;
+    L.n_segs = g.nseg;
+    L.total_items = g.items;
+    L.counter = e->persistent ? e->d_counters + gi : nullptr;
+    L.spt = g.spt;
+    L.nrx = g.nrx;
+    L.ntx = g.ntx;
+    L.dclass = g.dclass;
+    L.tap_max = g.tap_max;
+    L.k_max = g.k_max;
+    L.smem = g.smem;
+    L.grid = g.grid;
+    L.cursors = cursors;
+    cudaError_t err = tt_launch_conv_fp32(L, e->stream);
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+// Direct launch: the work list is uploaded from the host and the device cursors are not used.
+tt_status launch_direct(tt_engine *e, const Plan &p) {
+  if (p.segs.size() > e->seg_cap) {
+    cudaFree(e->d_segs);
+    e->d_segs = nullptr;
+    e->seg_cap = 0;
+    TT_CK(cudaMalloc(&e->d_segs, sizeof(TTSeg) * p.segs.size() * 2));
+    e->seg_cap = p.segs.size() * 2;
+  }
+  TT_CK(cudaMemcpyAsync(e->d_segs, p.segs.data(), sizeof(TTSeg) * p.segs.size(), cudaMemcpyHostToDevice,
+                        e->stream));
+  cudaError_t err = enqueue_plan(e, p, e->d_segs, nullptr);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tiled launch: %s", cudaGetErrorString(err));
+  e->launches += p.groups.size();
+  for (tt_chan *c : p.chans) c->dev_cursor = UINT64_MAX;  // the device cursor did not follow
+  return TT_OK;
+}
+
+// Graph launch: a run of the same shape as the cached graph replays it; the slot each run
+// starts at comes from the device cursors, which the graph's last node advances.
+tt_status launch_graph(tt_engine *e, const Plan &p) {
+  if (!e->gexec || p.key != e->gkey) {
+    if (e->gexec) {
+      cudaGraphExecDestroy(e->gexec);
+      e->gexec = nullptr;
+    }
+    e->gkey.clear();
+    TT_CK(cudaStreamSynchronize(e->stream));  // the old graph may still read d_gsegs
+    if (p.segs.size() > e->gseg_cap) {
+      cudaFree(e->d_gsegs);
+      e->d_gsegs = nullptr;
+      e->gseg_cap = 0;
+      TT_CK(cudaMalloc(&e->d_gsegs, sizeof(TTSeg) * p.segs.size() * 2));
+      e->gseg_cap = p.segs.size() * 2;
+    }
+    TT_CK(cudaMemcpy(e->d_gsegs, p.segs.data(), sizeof(TTSeg) * p.segs.size(), cudaMemcpyHostToDevice));
+    cudaGraph_t graph = nullptr;
+    TT_CK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = enqueue_plan(e, p, e->d_gsegs, e->d_cursors);
+    if (err == cudaSuccess) err = tt_launch_advance(e->d_gsegs, (int)p.segs.size(), e->d_cursors, e->stream);
+    cudaError_t err2 = cudaStreamEndCapture(e->stream, &graph);
+    if (err == cudaSuccess) err = err2;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&e->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+      e->gexec = nullptr;
+      return fail(TT_ERR_CUDA, "graph build: %s", cudaGetErrorString(err));
+    }
+    e->gkey = p.key;
+    ++e->graph_builds;
+  }
+  // bring stale device cursors in line with the host's view
+  std::vector<unsigned long long> fix(p.chans.size());
+  bool any = false;
+  for (size_t i = 0; i < p.chans.size(); ++i) {
+    tt_chan *c = p.chans[i];
+    if (c->dev_cursor != p.segs[i].first_slot) {
+      fix[i] = p.segs[i].first_slot;
+      TT_CK(cudaMemcpyAsync(e->d_cursors + c->index, &fix[i], sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                            e->stream));
+      any = true;
+    }
+  }
+  if (any) TT_CK(cudaStreamSynchronize(e->stream));  // fix[] lives on this stack frame
+  TT_CK(cudaGraphLaunch(e->gexec, e->stream));
+  ++e->graph_launches;
+  e->launches += p.groups.size();
+  for (size_t i = 0; i < p.chans.size(); ++i) p.chans[i]->dev_cursor = p.segs[i].first_slot + p.segs[i].n_slots;
+  return TT_OK;
+}
+
 }  // namespace
 
 int32_t tt_set_error(int32_t status, const char *msg) {
@@ -313,12 +525,14 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   e->max_ues = cfg->max_ues ? cfg->max_ues : 1024;
   e->spt_override = cfg->samples_per_thread;
   e->persistent = cfg->persistent;
+  e->graphs = cfg->struct_size >= offsetof(tt_engine_config, graphs) + sizeof(uint32_t) && cfg->graphs != 0;
   cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
   e->table.assign(e->max_ues, nullptr);
   cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_ues, sizeof(TTUEDesc) * e->max_ues);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_counters, sizeof(uint32_t) * e->counter_cap);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_cursors, sizeof(unsigned long long) * e->max_ues);
   if (err != cudaSuccess) {
     tt_engine_destroy(e);
     return fail(TT_ERR_CUDA, "engine setup: %s", cudaGetErrorString(err));
@@ -343,9 +557,12 @@ tt_status tt_engine_destroy(tt_engine *e) {
     }
   for (auto &p : e->events) cudaEventDestroy(p.second);
   for (auto ev : e->pool) cudaEventDestroy(ev);
+  if (e->gexec) cudaGraphExecDestroy(e->gexec);
   cudaFree(e->d_ues);
   cudaFree(e->d_segs);
+  cudaFree(e->d_gsegs);
   cudaFree(e->d_counters);
+  cudaFree(e->d_cursors);
   if (e->stream) cudaStreamDestroy(e->stream);
   if (e->copy) cudaStreamDestroy(e->copy);
   delete e;
@@ -367,6 +584,8 @@ tt_status tt_engine_get_stats(tt_engine *e, tt_engine_stats *out) {
   for (tt_chan *c : e->table) s.n_chans += c ? 1 : 0;
   s.launches = e->launches;
   s.slots_processed = e->slots_processed;
+  s.graph_builds = e->graph_builds;
+  s.graph_launches = e->graph_launches;
   *out = s;
   return TT_OK;
 }
@@ -652,79 +871,16 @@ tt_status tt_engine_run(tt_engine *e) {
       }
     }
   } else {
-    // group by kernel variant; inside a group, heaviest items first
-    struct Entry { tt_chan *c; double cost; };
-    std::vector<std::vector<Entry>> groups;
-    std::vector<int> keys;
-    for (tt_chan *c : ready) {
-      const int key = ((c->spt * 8 + (int)c->cfg.n_rx) * 8 + (int)c->cfg.n_tx) * 8 + c->dclass;
-      size_t gi = std::find(keys.begin(), keys.end(), key) - keys.begin();
-      if (gi == keys.size()) {
-        keys.push_back(key);
-        groups.emplace_back();
-      }
-      groups[gi].push_back({c, (double)c->desc.n_taps * c->cfg.n_tx * c->cfg.n_rx});
+    std::vector<uint64_t> first(ready.size()), count(ready.size());
+    for (size_t i = 0; i < ready.size(); ++i) {
+      first[i] = ready[i]->launched_end;
+      count[i] = ready[i]->pushed_end - ready[i]->launched_end;
     }
-    size_t nseg = ready.size();
-    if (nseg > e->seg_cap) {
-      cudaFree(e->d_segs);
-      e->d_segs = nullptr;
-      e->seg_cap = 0;
-      TT_CK(cudaMalloc(&e->d_segs, sizeof(TTSeg) * nseg * 2));
-      e->seg_cap = nseg * 2;
-    }
-    if ((int)groups.size() > e->counter_cap) return fail(TT_ERR_INVALID, "too many kernel variants");
-    std::vector<TTSeg> segs;
-    segs.reserve(nseg);
-    struct GL { size_t seg0; int nseg; uint32_t items; size_t smem; int spt, nrx, ntx, dclass, tap_max, k_max; };
-    std::vector<GL> gls;
-    for (auto &g : groups) {
-      std::stable_sort(g.begin(), g.end(), [](const Entry &a, const Entry &b) { return a.cost > b.cost; });
-      GL gl{segs.size(), 0, 0, 0, g[0].c->spt, (int)g[0].c->cfg.n_rx, (int)g[0].c->cfg.n_tx, g[0].c->dclass, 1, 1};
-      for (auto &en : g) {
-        tt_chan *c = en.c;
-        TTSeg s{};
-        s.first_slot = c->launched_end;
-        s.ue = c->index;
-        s.n_slots = (uint32_t)(c->pushed_end - c->launched_end);
-        s.item_begin = gl.items;
-        s.items = s.n_slots * (uint32_t)c->desc.items_per_slot;
-        gl.items += s.items;
-        gl.tap_max = std::max(gl.tap_max, c->tap_need);
-        gl.k_max = std::max(gl.k_max, c->desc.n_taps);
-        segs.push_back(s);
-        ++gl.nseg;
-      }
-      gl.smem = tt_conv_smem_bytes(gl.spt, gl.dclass, gl.ntx, gl.tap_max, gl.k_max);
-      gls.push_back(gl);
-    }
-    TT_CK(cudaMemcpyAsync(e->d_segs, segs.data(), sizeof(TTSeg) * segs.size(), cudaMemcpyHostToDevice,
-                          e->stream));
-    if (e->persistent) TT_CK(cudaMemsetAsync(e->d_counters, 0, sizeof(uint32_t) * gls.size(), e->stream));
-    for (size_t gi = 0; gi < gls.size(); ++gi) {
-      const GL &gl = gls[gi];
-      TTLaunch L{};
-      L.ues = e->d_ues;
-      L.segs = e->d_segs + gl.seg0;
-      L.n_segs = gl.nseg;
-      L.total_items = gl.items;
-      L.spt = gl.spt;
-      L.nrx = gl.nrx;
-      L.ntx = gl.ntx;
-      L.dclass = gl.dclass;
-      L.tap_max = gl.tap_max;
-      L.k_max = gl.k_max;
-      L.smem = gl.smem;
-      L.counter = e->persistent ? e->d_counters + gi : nullptr;
-      L.grid = -1;  // occupancy query
-      cudaError_t err = tt_launch_conv_fp32(L, e->stream);
-      if (err != cudaSuccess) return fail(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(err));
-      const int per_sm = -L.grid;
-      L.grid = (int)std::min<uint64_t>((uint64_t)per_sm * e->num_sms, gl.items);
-      err = tt_launch_conv_fp32(L, e->stream);
-      if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tiled launch: %s", cudaGetErrorString(err));
-      ++e->launches;
-    }
+    Plan plan;
+    tt_status st = build_plan(e, ready, first, count, plan);
+    if (st != TT_OK) return st;
+    st = e->graphs ? launch_graph(e, plan) : launch_direct(e, plan);
+    if (st != TT_OK) return st;
   }
   cudaEvent_t ev = get_event(e);
   if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
@@ -737,6 +893,89 @@ tt_status tt_engine_run(tt_engine *e) {
     c->launched_end = c->pushed_end;
   }
   return TT_OK;
+}
+
+tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned) {
+  if (!e) return fail(TT_ERR_INVALID, "null engine");
+  if (reps < 1) reps = 3;
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  TT_CK(cudaStreamSynchronize(e->stream));
+  // classes: same numerology, antennas, taps and delay class tune alike
+  std::vector<std::pair<std::vector<int64_t>, std::vector<tt_chan *>>> classes;
+  for (tt_chan *c : e->table) {
+    if (!c || !c->has_trace) continue;
+    std::vector<int64_t> key(c->sym_len.begin(), c->sym_len.end());
+    key.insert(key.end(), {(int64_t)c->cfg.n_tx, (int64_t)c->cfg.n_rx, (int64_t)c->desc.n_taps,
+                           (int64_t)c->dclass, (int64_t)(c->desc.noise_std > 0.f), (int64_t)c->desc.out_f32});
+    auto it = std::find_if(classes.begin(), classes.end(), [&](const auto &p) { return p.first == key; });
+    if (it == classes.end()) classes.push_back({key, {c}});
+    else it->second.push_back(c);
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  TT_CK(cudaEventCreate(&a));
+  TT_CK(cudaEventCreate(&b));
+  uint32_t tuned = 0;
+  tt_status result = TT_OK;
+  for (auto &cls : classes) {
+    tt_chan *c0 = cls.second[0];
+    std::vector<int> cands;
+    for (int s : spt_candidates(c0->sym_len, e->spt_override ? e->spt_override : 16, c0->cfg.n_rx)) {
+      int need = 0;
+      if (smem_need(c0, s, &need)) cands.push_back(s);
+    }
+    if (cands.size() < 2) continue;
+    // time one slot of every channel of the class that has a free ring position
+    std::vector<tt_chan *> room;
+    std::vector<uint64_t> first, count;
+    for (tt_chan *c : cls.second) {
+      const uint64_t f = c->started ? c->pushed_end : 0, start = c->started ? c->pulled_end : 0;
+      if (f + 1 - start + (uint64_t)c->hist <= (uint64_t)c->Q) {
+        room.push_back(c);
+        first.push_back(f);
+        count.push_back(1);
+      }
+    }
+    if (room.empty()) continue;
+    int best = cands[0];
+    float best_ms = 1e30f;
+    for (int s : cands) {
+      for (tt_chan *c : cls.second) {
+        if ((result = apply_spt(c, s)) != TT_OK || (result = upload_desc(c)) != TT_OK) break;
+      }
+      if (result != TT_OK) break;
+      Plan plan;
+      if ((result = build_plan(e, room, first, count, plan)) != TT_OK) break;
+      if ((result = launch_direct(e, plan)) != TT_OK) break;  // warm-up
+      for (int r = 0; r < reps && result == TT_OK; ++r) {
+        cudaEventRecord(a, e->stream);
+        result = launch_direct(e, plan);
+        cudaEventRecord(b, e->stream);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = s;
+        }
+      }
+      if (result != TT_OK) break;
+    }
+    if (result != TT_OK) break;
+    for (tt_chan *c : cls.second)
+      if ((result = apply_spt(c, best)) != TT_OK || (result = upload_desc(c)) != TT_OK) break;
+    if (result != TT_OK) break;
+    ++tuned;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e->gexec) {  // tuned geometry invalidates the cached graph
+    cudaGraphExecDestroy(e->gexec);
+    e->gexec = nullptr;
+    e->gkey.clear();
+  }
+  if (result == TT_OK && classes_tuned) *classes_tuned = tuned;
+  return result;
 }
 
 tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us) {

@@ -91,7 +91,11 @@ struct TTLaunch {
   int k_max;            // largest tap count of the launch's UEs
   int grid;             // CTAs; < 0 on input asks for the occupancy (returned as -blocks per SM)
   size_t smem;          // dynamic shared memory bytes (tt_conv_smem_bytes)
+  const unsigned long long *cursors;  // non-null: first slot of each run = cursors[ue] (graph replay)
 };
+
+// cursors[segs[i].ue] += segs[i].n_slots for every segment (device-resident slot cursors).
+cudaError_t tt_launch_advance(const TTSeg *segs, int n_segs, unsigned long long *cursors, cudaStream_t st);
 
 // Dynamic shared memory of the tiled kernel for a launch.
 size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max);

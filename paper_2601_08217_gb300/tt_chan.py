@@ -37,7 +37,7 @@ class TTError(RuntimeError):
 class EngineConfig(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("device", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
                 ("form", C.c_uint32), ("max_ues", C.c_uint32), ("samples_per_thread", C.c_uint32),
-                ("threads_per_block", C.c_uint32), ("persistent", C.c_uint32)]
+                ("threads_per_block", C.c_uint32), ("persistent", C.c_uint32), ("graphs", C.c_uint32)]
 
 
 class ChanConfig(C.Structure):
@@ -56,7 +56,8 @@ class TraceDesc(C.Structure):
 
 class EngineStats(C.Structure):
     _fields_ = [("hbm_in_use", C.c_uint64), ("hbm_budget", C.c_uint64), ("n_chans", C.c_uint32),
-                ("pad", C.c_uint32), ("launches", C.c_uint64), ("slots_processed", C.c_uint64)]
+                ("pad", C.c_uint32), ("launches", C.c_uint64), ("slots_processed", C.c_uint64),
+                ("graph_builds", C.c_uint64), ("graph_launches", C.c_uint64)]
 
 
 class StaticChan(C.Structure):
@@ -78,6 +79,7 @@ _SIGS = {
     "tt_engine_sync": [_VP, C.c_int64],
     "tt_engine_stream": [_VP, C.POINTER(_VP)],
     "tt_engine_get_stats": [_VP, C.POINTER(EngineStats)],
+    "tt_engine_autotune": [_VP, C.c_int32, C.POINTER(C.c_uint32)],
     "tt_chan_create": [_VP, C.POINTER(ChanConfig), C.POINTER(_VP)],
     "tt_chan_destroy": [_VP],
     "tt_chan_load_trace": [_VP, C.POINTER(TraceDesc)],
@@ -158,10 +160,11 @@ def _stream_ptr(stream) -> int:
 
 # ---------------------------------------------------------------- C-named calls
 def tt_engine_create(device: int = 0, form: int = TT_FORM_BATCHED, hbm_budget_bytes: int = 0,
-                     max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False) -> int:
+                     max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False,
+                     graphs: bool = False) -> int:
     lib = load()
     cfg = EngineConfig(C.sizeof(EngineConfig), device, hbm_budget_bytes, form, max_ues,
-                       samples_per_thread, 0, int(bool(persistent)))
+                       samples_per_thread, 0, int(bool(persistent)), int(bool(graphs)))
     h = _VP()
     _check(lib.tt_engine_create(C.byref(cfg), C.byref(h)))
     return h.value
@@ -189,6 +192,12 @@ def tt_engine_get_stats(e: int) -> dict:
     st = EngineStats()
     _check(load().tt_engine_get_stats(e, C.byref(st)))
     return {f: getattr(st, f) for f, _ in EngineStats._fields_ if f != "pad"}
+
+
+def tt_engine_autotune(e: int, reps: int = 3) -> int:
+    n = C.c_uint32(0)
+    _check(load().tt_engine_autotune(e, reps, C.byref(n)))
+    return n.value
 
 
 def tt_chan_create(e: int, samples_per_slot: int, symbol_len: Sequence[int], n_tx: int = 1, n_rx: int = 1,
@@ -313,9 +322,9 @@ def tt_abi_version() -> int:
 # ---------------------------------------------------------------- conveniences
 class Engine:
     def __init__(self, device: int = 0, form: str = "batched", hbm_budget_bytes: int = 0,
-                 max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False):
+                 max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False, graphs: bool = False):
         f = {"batched": TT_FORM_BATCHED, "plain": TT_FORM_PLAIN}[form]
-        self.h = tt_engine_create(device, f, hbm_budget_bytes, max_ues, samples_per_thread, persistent)
+        self.h = tt_engine_create(device, f, hbm_budget_bytes, max_ues, samples_per_thread, persistent, graphs)
         self.chans = []
 
     def run(self):
@@ -330,6 +339,9 @@ class Engine:
 
     def stats(self) -> dict:
         return tt_engine_get_stats(self.h)
+
+    def autotune(self, reps: int = 3) -> int:
+        return tt_engine_autotune(self.h, reps)
 
     def close(self):
         if self.h:

@@ -1,0 +1,90 @@
+"""Batching form: CUDA-graph replay with device-resident slot cursors, and the autotuner.
+
+Each output sample is accumulated in the same order whatever the kernel
+geometry, so graph replay, direct launches and every samples-per-thread
+choice must agree bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_08217_gb300 import inputs
+from paper_2601_08217_gb300 import tt_chan as tc
+from tests.gpu_harness import hist_slots, run_gpu
+from tests.helpers import nrmse
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream(specs, xs, n_slots, engine_kw, per_run=1, autotune=False):
+    eng = tc.Engine(**engine_kw)
+    chans = [tc.Chan(eng, sp, ring_slots=hist_slots(sp) + 3 * per_run + 1) for sp in specs]
+    if autotune:
+        assert eng.autotune(reps=2) >= 0
+    outs = [[] for _ in specs]
+    s = 0
+    while s < n_slots:
+        k = min(per_run, n_slots - s)
+        for ch, x in zip(chans, xs):
+            ch.push(s, tc.slots_major(x, ch.n)[s:s + k])
+        eng.run()
+        for i, ch in enumerate(chans):
+            outs[i].append(ch.pull(s, k))
+        s += k
+    st = eng.stats()
+    eng.close()
+    return [tc.antenna_major(np.concatenate(o, 0)) for o in outs], st
+
+
+def test_graph_replay_equals_direct_launches():
+    specs = inputs.workload_batching(n_ues=10, n_slots_trace=2)
+    xs = [inputs.make_iq(3, sp, 6) for sp in specs]
+    direct, _ = _stream(specs, xs, 6, dict(persistent=True))
+    graph, st = _stream(specs, xs, 6, dict(persistent=True, graphs=True))
+    for a, b in zip(direct, graph):
+        assert np.array_equal(a, b)
+    assert st["graph_builds"] == 1 and st["graph_launches"] == 6
+    # a second shape (2 slots per run) rebuilds the graph once and stays correct
+    graph2, st2 = _stream(specs, xs, 6, dict(persistent=True, graphs=True), per_run=2)
+    for a, b in zip(direct, graph2):
+        assert np.array_equal(a, b)
+    assert st2["graph_builds"] == 1 and st2["graph_launches"] == 3
+
+
+def test_graph_replay_against_oracle_and_after_resume():
+    spec = inputs.make_ue(3, 4, 2048, 20, 400, 300.0, 8, snr_db=20.0, loop=True)
+    x = inputs.make_iq(3, spec, 8)
+    y_ref, q_ref = oracle.run_ue(oracle.OracleUE.from_spec(spec), x)
+    eng = tc.Engine(graphs=True, persistent=True)
+    ch = tc.Chan(eng, spec, ring_slots=4)
+    xs = tc.slots_major(x, spec.n)
+    got = []
+    for s in range(4):
+        ch.push(s, xs[s:s + 1])
+        eng.run()
+        got.append(ch.pull(s, 1))
+    eng.sync()
+    blob = tc.tt_chan_get_state(ch.h)
+    ch.destroy()
+    ch2 = tc.Chan(eng, spec, ring_slots=4)        # same engine: the cached graph's cursor is stale
+    tc.tt_chan_set_state(ch2.h, blob)
+    for s in range(4, 8):
+        ch2.push(s, xs[s:s + 1])
+        eng.run()
+        got.append(ch2.pull(s, 1))
+    eng.close()
+    q = tc.antenna_major(np.concatenate(got, 0))
+    d = np.abs(q.astype(np.int32) - q_ref.astype(np.int32))
+    assert d.max() <= 1 and np.count_nonzero(d) < 1e-4 * d.size
+
+
+def test_autotuner_keeps_results_bit_identical():
+    specs = inputs.workload_batching(n_ues=8, n_slots_trace=2)
+    xs = [inputs.make_iq(3, sp, 3) for sp in specs]
+    base, _ = _stream(specs, xs, 3, dict(persistent=True))
+    tuned, _ = _stream(specs, xs, 3, dict(persistent=True, graphs=True), autotune=True)
+    for a, b in zip(base, tuned):
+        assert np.array_equal(a, b)
+    for s in (1, 2, 4, 16):
+        other = run_gpu(specs[:3], xs[:3], 3, spt=s)
+        for a, b in zip(base[:3], other):
+            assert np.array_equal(a, b)
