@@ -238,6 +238,53 @@ def run_ours(args, rank, world, device):
                 plain=plain, specs=specs)
 
 
+def run_batching(args, device, n_ues=256, steps=400, warmup=20):
+    """256 UEs of mixed bandwidth (5/20/40/100 MHz, 1:2:4:1), 4-48 taps, delays <= 512, AWGN 20 dB:
+    one slot of every UE per step, one CUDA-graph replay of the persistent kernel per step,
+    samples-per-thread picked by the engine's autotuner."""
+    import torch
+    from paper_2601_08217_gb300 import inputs
+    from paper_2601_08217_gb300 import tt_chan as tc
+    specs = inputs.workload_batching(n_ues=n_ues, n_slots_trace=20)
+    eng = tc.Engine(device=device, graphs=True, persistent=True)
+    chans, xs = [], []
+    for sp in specs:
+        hist = -(-int(max(sp.max_delay, int(sp.delays.max()))) // sp.n)
+        chans.append(tc.Chan(eng, sp, ring_slots=hist + 9))
+        xs.append(tc.slots_major(inputs.make_iq(3, sp, 8), sp.n))
+    for ch, x in zip(chans, xs):                     # fill every ring position with synthetic IQ
+        ch.push(0, x[np.arange(9) % 8])
+    eng.run()
+    for ch in chans:
+        tc.tt_chan_release_slots(ch.h, 0, 9)
+    for ch, x in zip(chans, xs):
+        ch.push(9, x[1:2])
+    eng.run()
+    eng.sync()
+    tuned = eng.autotune(reps=3)
+    stream = torch.cuda.ExternalStream(eng.stream)
+    tc.tt_engine_replay(eng.h, warmup, 1)
+    eng.sync()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st0 = eng.stats()
+    t_host = time.perf_counter()
+    a.record(stream)
+    tc.tt_engine_replay(eng.h, steps, 1)
+    b.record(stream)
+    eng.sync()
+    t_host = time.perf_counter() - t_host
+    st1 = eng.stats()
+    ms = a.elapsed_time(b)
+    samples = sum(sp.n for sp in specs)
+    tap_s = sum(sp.n * len(sp.delays) * sp.n_tx * sp.n_rx for sp in specs)
+    eng.close()
+    return {"ues": n_ues, "steps": steps, "ms_per_step": ms / steps, "host_ms_per_step": t_host * 1e3 / steps,
+            "ue_slots_per_s": n_ues * steps / (ms / 1e3), "gmac_per_s": tap_s * steps / (ms / 1e3) / 1e9,
+            "samples_per_slot_step": samples, "realtime": (ms / steps) <= 0.5,
+            "graph_launches": st1["graph_launches"] - st0["graph_launches"],
+            "graph_builds": st1["graph_builds"], "autotuned_classes": tuned}
+
+
 def cpu_baseline(budget_s: float = 12.0):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload.
 
@@ -278,6 +325,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--slots", type=int, default=1000,
                     help="slots per UE per step (smaller for profiling captures)")
     args = ap.parse_args()
@@ -336,6 +384,9 @@ def main():
     kms = statistics.mean(r["kern_ms"])
     peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     achieved = ts * FLOP_PER_TAP_SAMPLE / (kms / 1e3) / 1e12
+    batching = None
+    if rank == 0 and world == 1 and not args.no_batching:
+        batching = run_batching(args, local)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -361,6 +412,7 @@ def main():
         "e2e": r["e2e"],
         "plain": r["plain"],
         "vs_plain": (value / r["plain"]["value"]) if r["plain"] else None,
+        "batching": batching,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))

@@ -147,6 +147,13 @@ tt_status tt_engine_destroy(tt_engine *e);
  * engine's stream.  Channels without a trace are skipped. */
 tt_status tt_engine_run(tt_engine *e);
 
+/* Slot-synchronous replay: n_steps times, every started, traced channel
+ * releases its launched outputs, commits its next slots_per_step slots in
+ * place (the input ring already holds their IQ: whatever the caller last
+ * wrote at those ring positions) and tt_engine_run launches them all.
+ * Asynchronous like tt_engine_run.  TT_ERR_AGAIN if a ring has no room. */
+tt_status tt_engine_replay(tt_engine *e, uint32_t n_steps, uint32_t slots_per_step);
+
 /* Block until all launched work is complete, at most timeout_us (< 0: no limit).
  * TT_ERR_TIMEOUT if it is still running. */
 tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us);

@@ -978,6 +978,26 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
   return result;
 }
 
+tt_status tt_engine_replay(tt_engine *e, uint32_t n_steps, uint32_t slots_per_step) {
+  if (!e || slots_per_step == 0) return fail(TT_ERR_INVALID, "tt_engine_replay: bad argument");
+  for (uint32_t step = 0; step < n_steps; ++step) {
+    {
+      std::lock_guard<std::mutex> lk(e->mu);
+      for (tt_chan *c : e->table) {
+        if (!c || !c->has_trace || !c->started) continue;
+        // release what the previous steps produced, then reuse the ring in place
+        c->pulled_end = std::max(c->pulled_end, std::min(c->launched_end, c->pushed_end));
+        tt_status st = check_room(c, c->pushed_end, slots_per_step);
+        if (st != TT_OK) return st;
+        mark_pushed(c, c->pushed_end, slots_per_step);
+      }
+    }
+    tt_status st = tt_engine_run(e);
+    if (st != TT_OK) return st;
+  }
+  return TT_OK;
+}
+
 tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us) {
   if (!e) return fail(TT_ERR_INVALID, "null engine");
   std::unique_lock<std::mutex> lk(e->mu);

@@ -80,6 +80,7 @@ _SIGS = {
     "tt_engine_stream": [_VP, C.POINTER(_VP)],
     "tt_engine_get_stats": [_VP, C.POINTER(EngineStats)],
     "tt_engine_autotune": [_VP, C.c_int32, C.POINTER(C.c_uint32)],
+    "tt_engine_replay": [_VP, C.c_uint32, C.c_uint32],
     "tt_chan_create": [_VP, C.POINTER(ChanConfig), C.POINTER(_VP)],
     "tt_chan_destroy": [_VP],
     "tt_chan_load_trace": [_VP, C.POINTER(TraceDesc)],
@@ -198,6 +199,10 @@ def tt_engine_autotune(e: int, reps: int = 3) -> int:
     n = C.c_uint32(0)
     _check(load().tt_engine_autotune(e, reps, C.byref(n)))
     return n.value
+
+
+def tt_engine_replay(e: int, n_steps: int, slots_per_step: int = 1):
+    _check(load().tt_engine_replay(e, n_steps, slots_per_step))
 
 
 def tt_chan_create(e: int, samples_per_slot: int, symbol_len: Sequence[int], n_tx: int = 1, n_rx: int = 1,
