@@ -285,6 +285,49 @@ def run_batching(args, device, n_ues=256, steps=400, warmup=20):
             "graph_builds": st1["graph_builds"], "autotuned_classes": tuned}
 
 
+def run_serving(args, device, n_ues=512, duration=2.0, warmup=0.2, plain_duration=0.3):
+    """512 UEs (20/40/100 MHz, SISO and 2x2, 6-48 taps, delays <= 512), Poisson slot pushes at the
+    0.5 ms slot rate with +-50 us jitter, device-resident IQ, 40 GB HBM admission budget,
+    continuous batching; the plain one-launch-per-UE-per-slot form served the same way beside it."""
+    from paper_2601_08217_gb300 import inputs
+    from paper_2601_08217_gb300 import tt_chan as tc
+    specs = inputs.workload_serving(n_ues=n_ues, n_slots_trace=10)
+    out = {}
+    for form, dur in (("batched", duration), ("plain", plain_duration)):
+        eng = tc.Engine(device=device, form=form, persistent=True, hbm_budget_bytes=40 << 30)
+        admitted = refused = 0
+        chans = []
+        for sp in specs:
+            hist = -(-int(max(sp.max_delay, int(sp.delays.max()))) // sp.n)
+            try:
+                ch = tc.Chan(eng, sp, ring_slots=hist + 12)
+            except tc.TTError as ex:
+                if ex.status != tc.TT_ERR_NO_MEMORY:
+                    raise
+                refused += 1
+                continue
+            admitted += 1
+            x = tc.slots_major(inputs.make_iq(5, sp, 4), sp.n)
+            ch.push(0, x[np.arange(12) % 4])
+            chans.append(ch)
+        eng.run()
+        for ch in chans:
+            tc.tt_chan_release_slots(ch.h, 0, 12)
+        eng.sync()
+        rep = tc.tt_engine_serve(eng.h, duration_s=dur, warmup_s=warmup, slot_period_us=500.0, jitter_us=50.0,
+                                 deadline_us=500.0, seed=11, release_outputs=True)
+        st = eng.stats()
+        eng.close()
+        out[form] = {"ues_admitted": admitted, "ues_refused": refused, "hbm_gb": st["hbm_in_use"] / 1e9,
+                     "duration_s": dur, "requests": rep["requests"], "completed": rep["completed"],
+                     "refused_requests": rep["refused"], "ue_slots_per_s": rep["throughput"],
+                     "p50_us": rep["p50_us"], "p99_us": rep["p99_us"], "p999_us": rep["p999_us"],
+                     "max_us": rep["max_us"], "deadline_misses": rep["deadline_misses"],
+                     "mean_batch": rep["mean_batch"], "batches": rep["batches"]}
+    out["p99_under_deadline"] = out["batched"]["p99_us"] < 500.0
+    return out
+
+
 def cpu_baseline(budget_s: float = 12.0):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload.
 
@@ -326,6 +369,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--slots", type=int, default=1000,
                     help="slots per UE per step (smaller for profiling captures)")
     args = ap.parse_args()
@@ -387,6 +431,9 @@ def main():
     batching = None
     if rank == 0 and world == 1 and not args.no_batching:
         batching = run_batching(args, local)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = run_serving(args, local)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -413,6 +460,7 @@ def main():
         "plain": r["plain"],
         "vs_plain": (value / r["plain"]["value"]) if r["plain"] else None,
         "batching": batching,
+        "serving": serving,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))

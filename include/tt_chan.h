@@ -172,6 +172,40 @@ tt_status tt_engine_get_stats(tt_engine *e, tt_engine_stats *out);
  * NULL) receives the number of classes that had a choice to make. */
 tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned);
 
+/* Serving form.  Runs a request loop on the calling thread for warmup_s +
+ * duration_s seconds: every channel with a trace receives slot-push requests
+ * at Poisson times (mean inter-arrival slot_period_us, plus uniform
+ * +-jitter_us, kept increasing).  A request commits the UE's next slot in
+ * place: the IQ the caller left at that ring position (device-resident input).
+ * A request that finds the UE's ring full is refused (counted, not queued).
+ * Continuous batching: whenever requests are pending and fewer than
+ * max_inflight_batches batches run, everything pending is launched as one
+ * batch (any UEs, several slots of one UE allowed); requests that arrive
+ * meanwhile join the next batch.  Latency = completion seen by the host
+ * (event polled) minus arrival, for requests that arrived after the warm-up.
+ * release_outputs = 1 frees each output ring position as soon as it is
+ * complete; 0 keeps the outputs for tt_chan_pull_* (rings then fill up). */
+typedef struct {
+  uint32_t struct_size;           /* sizeof(tt_serve_config) */
+  uint32_t max_slots_per_ue;      /* 0 = no limit; else each UE stops after this many requests */
+  double warmup_s, duration_s;    /* arrivals before the measured window, and its length */
+  double slot_period_us;          /* mean inter-arrival per UE (500 = one 30 kHz slot) */
+  double jitter_us;               /* uniform +- jitter added to each inter-arrival */
+  double deadline_us;             /* latency bound counted as a miss (0 = 500) */
+  uint64_t seed;                  /* arrival-process seed */
+  uint32_t release_outputs;
+  uint32_t max_inflight_batches;  /* 0 = 2 (one running, one forming) */
+} tt_serve_config;
+
+typedef struct {
+  uint64_t requests, refused, completed, batches, deadline_misses;
+  double mean_batch;              /* requests per batch */
+  double throughput;              /* completed requests (UE-slots) per second of the measured window */
+  double p50_us, p99_us, p999_us, max_us, mean_us;
+} tt_serve_report;
+
+tt_status tt_engine_serve(tt_engine *e, const tt_serve_config *cfg, tt_serve_report *out);
+
 /* ---------------------------------------------------------------- channel */
 
 /* Admit a channel: allocates its slot rings if they fit in the budget

@@ -16,6 +16,9 @@
 #include <chrono>
 #include <deque>
 #include <mutex>
+#include <queue>
+#include <random>
+#include <unordered_map>
 #include <string>
 #include <thread>
 #include <utility>
@@ -84,7 +87,12 @@ struct tt_engine {
   size_t gseg_cap = 0;
   cudaGraphExec_t gexec = nullptr;
   std::vector<uint64_t> gkey;               // shape of the cached graph
+  std::vector<tt_chan *> gchans;            // channels of the cached graph, in table order
+  std::vector<uint64_t> gcounts;            // their slots per run
+  std::vector<tt_chan *> gplan_chans;       // the same channels in the graph's segment order
   uint64_t graph_builds = 0, graph_launches = 0;
+  uint64_t graph_nodes = 0;                 // tiled-kernel launches inside the cached graph
+  std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
 };
 
 struct tt_chan {
@@ -440,6 +448,21 @@ tt_status launch_direct(tt_engine *e, const Plan &p) {
   return TT_OK;
 }
 
+tt_status launch_cached_graph(tt_engine *e, const std::vector<tt_chan *> &chans, const std::vector<TTSeg> &segs);
+
+// Forget the cached graph (channel set or geometry changed).  Engine lock held.
+void drop_graph(tt_engine *e) {
+  if (e->gexec) {
+    cudaStreamSynchronize(e->stream);
+    cudaGraphExecDestroy(e->gexec);
+    e->gexec = nullptr;
+  }
+  e->gkey.clear();
+  e->gchans.clear();
+  e->gcounts.clear();
+  e->gplan_chans.clear();
+}
+
 // Graph launch: a run of the same shape as the cached graph replays it; the slot each run
 // starts at comes from the device cursors, which the graph's last node advances.
 tt_status launch_graph(tt_engine *e, const Plan &p) {
@@ -471,15 +494,22 @@ tt_status launch_graph(tt_engine *e, const Plan &p) {
       return fail(TT_ERR_CUDA, "graph build: %s", cudaGetErrorString(err));
     }
     e->gkey = p.key;
+    e->graph_nodes = p.groups.size();
+    e->gsegs_host = p.segs;
     ++e->graph_builds;
   }
+  return launch_cached_graph(e, p.chans, p.segs);
+}
+
+// Replay the cached graph for channels `chans` (segment order) starting at the given slots.
+tt_status launch_cached_graph(tt_engine *e, const std::vector<tt_chan *> &chans, const std::vector<TTSeg> &segs) {
   // bring stale device cursors in line with the host's view
-  std::vector<unsigned long long> fix(p.chans.size());
+  std::vector<unsigned long long> fix(chans.size());
   bool any = false;
-  for (size_t i = 0; i < p.chans.size(); ++i) {
-    tt_chan *c = p.chans[i];
-    if (c->dev_cursor != p.segs[i].first_slot) {
-      fix[i] = p.segs[i].first_slot;
+  for (size_t i = 0; i < chans.size(); ++i) {
+    tt_chan *c = chans[i];
+    if (c->dev_cursor != segs[i].first_slot) {
+      fix[i] = segs[i].first_slot;
       TT_CK(cudaMemcpyAsync(e->d_cursors + c->index, &fix[i], sizeof(unsigned long long), cudaMemcpyHostToDevice,
                             e->stream));
       any = true;
@@ -488,8 +518,8 @@ tt_status launch_graph(tt_engine *e, const Plan &p) {
   if (any) TT_CK(cudaStreamSynchronize(e->stream));  // fix[] lives on this stack frame
   TT_CK(cudaGraphLaunch(e->gexec, e->stream));
   ++e->graph_launches;
-  e->launches += p.groups.size();
-  for (size_t i = 0; i < p.chans.size(); ++i) p.chans[i]->dev_cursor = p.segs[i].first_slot + p.segs[i].n_slots;
+  e->launches += e->graph_nodes;
+  for (size_t i = 0; i < chans.size(); ++i) chans[i]->dev_cursor = segs[i].first_slot + segs[i].n_slots;
   return TT_OK;
 }
 
@@ -692,6 +722,7 @@ tt_status tt_chan_destroy(tt_chan *c) {
   cudaFree(c->d_chunks);
   e->in_use -= c->ring_bytes + c->trace_bytes;
   e->table[c->index] = nullptr;
+  drop_graph(e);
   c->e = nullptr;
   delete c;
   return TT_OK;
@@ -775,6 +806,7 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   c->dclass = dclass;
   c->smem = smem;
   c->tap_need = tap_need;
+  drop_graph(e);
   TTUEDesc &d = c->desc;
   d.taps = taps;
   d.delays = delays;
@@ -876,11 +908,24 @@ tt_status tt_engine_run(tt_engine *e) {
       first[i] = ready[i]->launched_end;
       count[i] = ready[i]->pushed_end - ready[i]->launched_end;
     }
-    Plan plan;
-    tt_status st = build_plan(e, ready, first, count, plan);
-    if (st != TT_OK) return st;
-    st = e->graphs ? launch_graph(e, plan) : launch_direct(e, plan);
-    if (st != TT_OK) return st;
+    if (e->graphs && e->gexec && ready == e->gchans && count == e->gcounts) {
+      // same channels, same slots per run: replay without re-planning
+      std::vector<tt_chan *> &seg_chans = e->gplan_chans;
+      for (size_t i = 0; i < seg_chans.size(); ++i) e->gsegs_host[i].first_slot = seg_chans[i]->launched_end;
+      tt_status st = launch_cached_graph(e, seg_chans, e->gsegs_host);
+      if (st != TT_OK) return st;
+    } else {
+      Plan plan;
+      tt_status st = build_plan(e, ready, first, count, plan);
+      if (st != TT_OK) return st;
+      st = e->graphs ? launch_graph(e, plan) : launch_direct(e, plan);
+      if (st != TT_OK) return st;
+      if (e->graphs) {
+        e->gchans = ready;
+        e->gcounts = count;
+        e->gplan_chans = plan.chans;
+      }
+    }
   }
   cudaEvent_t ev = get_event(e);
   if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
@@ -969,11 +1014,7 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  if (e->gexec) {  // tuned geometry invalidates the cached graph
-    cudaGraphExecDestroy(e->gexec);
-    e->gexec = nullptr;
-    e->gkey.clear();
-  }
+  drop_graph(e);  // tuned geometry invalidates the cached graph
   if (result == TT_OK && classes_tuned) *classes_tuned = tuned;
   return result;
 }
@@ -1207,6 +1248,156 @@ tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len) {
   c->pushed_end = c->launched_end = c->completed_end = c->pulled_end = next;
   c->inflight.clear();
   return upload_desc(c);
+}
+
+
+// ---------------------------------------------------------------- serving form
+namespace {
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+struct Pending {
+  uint64_t slot;
+  int64_t t_arrival;
+  bool counted;
+};
+}  // namespace
+
+tt_status tt_engine_serve(tt_engine *e, const tt_serve_config *cfg, tt_serve_report *out) {
+  if (!e || !cfg || !out || cfg->struct_size < sizeof(tt_serve_config))
+    return fail(TT_ERR_INVALID, "tt_engine_serve: bad argument");
+  if (!(cfg->duration_s > 0.0) || !(cfg->slot_period_us > 0.0) || cfg->warmup_s < 0.0 || cfg->jitter_us < 0.0)
+    return fail(TT_ERR_INVALID, "tt_engine_serve: bad timing parameters");
+  std::vector<tt_chan *> chans;
+  {
+    std::lock_guard<std::mutex> lk(e->mu);
+    for (tt_chan *c : e->table)
+      if (c && c->has_trace) chans.push_back(c);
+  }
+  if (chans.empty()) return fail(TT_ERR_STATE, "tt_engine_serve: no channel with a trace");
+  const int64_t period = (int64_t)(cfg->slot_period_us * 1e3), jitter = (int64_t)(cfg->jitter_us * 1e3);
+  std::mt19937_64 rng(cfg->seed);
+  std::exponential_distribution<double> expo(1.0 / (double)period);
+  std::uniform_int_distribution<int64_t> jit(-jitter, jitter), phase(0, period);
+  auto gap = [&]() -> int64_t { return std::max<int64_t>(expo(rng) + (double)jit(rng), 1000); };
+
+  const int64_t t0 = now_ns();
+  const int64_t t_warm = t0 + (int64_t)(cfg->warmup_s * 1e9), t_end = t_warm + (int64_t)(cfg->duration_s * 1e9);
+  using Ev = std::pair<int64_t, uint32_t>;
+  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> heap;
+  for (uint32_t u = 0; u < chans.size(); ++u) heap.push({t0 + phase(rng), u});
+  std::vector<std::deque<Pending>> pend(chans.size());
+  std::vector<uint32_t> pushed(chans.size(), 0);
+  std::unordered_map<tt_chan *, uint32_t> idx;
+  for (uint32_t u = 0; u < chans.size(); ++u) idx[chans[u]] = u;
+  struct Batch { uint64_t seq; std::vector<std::pair<uint32_t, uint64_t>> ends; uint32_t reqs; };
+  std::deque<Batch> inflight;
+  std::vector<double> lat;
+  lat.reserve(1 << 20);
+  uint64_t requests = 0, refused = 0, batches = 0, batched_reqs = 0, misses = 0, completed = 0;
+  uint32_t unlaunched = 0;
+  const uint32_t max_inflight = cfg->max_inflight_batches ? cfg->max_inflight_batches : 2;
+  const double deadline_ns = (cfg->deadline_us > 0 ? cfg->deadline_us : 500.0) * 1e3;
+
+  for (;;) {
+    int64_t now = now_ns();
+    bool did = false;
+    // 1. arrivals due now: commit the UE's next slot in place (its IQ is already in the ring)
+    while (!heap.empty() && heap.top().first <= now && heap.top().first < t_end) {
+      const Ev ev = heap.top();
+      heap.pop();
+      const uint32_t u = ev.second;
+      if (cfg->max_slots_per_ue && pushed[u] >= cfg->max_slots_per_ue) continue;
+      tt_chan *c = chans[u];
+      {
+        std::lock_guard<std::mutex> lk(e->mu);
+        const uint64_t slot = c->started ? c->pushed_end : 0;
+        ++requests;
+        if (check_room(c, slot, 1) == TT_OK) {
+          mark_pushed(c, slot, 1);
+          pend[u].push_back({slot, ev.first, ev.first >= t_warm});
+          ++pushed[u];
+          ++unlaunched;
+        } else {
+          ++refused;  // ring full: the engine is behind this UE
+        }
+      }
+      heap.push({ev.first + gap(), u});
+      did = true;
+    }
+    // 2. continuous batching: launch everything pending while fewer than max_inflight batches run
+    if (unlaunched > 0 && inflight.size() < max_inflight) {
+      Batch b;
+      b.reqs = unlaunched;
+      {
+        std::lock_guard<std::mutex> lk(e->mu);
+        for (uint32_t u = 0; u < chans.size(); ++u)
+          if (chans[u]->started && chans[u]->pushed_end > chans[u]->launched_end)
+            b.ends.push_back({u, chans[u]->pushed_end});
+      }
+      tt_status st = tt_engine_run(e);
+      if (st != TT_OK) return st;
+      {
+        std::lock_guard<std::mutex> lk(e->mu);
+        b.seq = e->launch_seq;
+      }
+      unlaunched = 0;
+      ++batches;
+      batched_reqs += b.reqs;
+      inflight.push_back(std::move(b));
+      did = true;
+    }
+    // 3. completions: stamp every request of every finished batch
+    if (!inflight.empty()) {
+      std::lock_guard<std::mutex> lk(e->mu);
+      cudaError_t q = update_completed(e);
+      if (q != cudaSuccess) return fail(TT_ERR_CUDA, "kernel failed: %s", cudaGetErrorString(q));
+      const int64_t t_done = now_ns();
+      while (!inflight.empty() && inflight.front().seq <= e->completed_seq) {
+        for (auto &pe : inflight.front().ends) {
+          tt_chan *c = chans[pe.first];
+          auto &dq = pend[pe.first];
+          while (!dq.empty() && dq.front().slot < pe.second) {
+            const double l = (double)(t_done - dq.front().t_arrival);
+            if (dq.front().counted) {
+              lat.push_back(l);
+              if (l > deadline_ns) ++misses;
+              ++completed;
+            }
+            dq.pop_front();
+          }
+          update_chan(c);
+          if (cfg->release_outputs) c->pulled_end = std::max(c->pulled_end, std::min(pe.second, c->completed_end));
+        }
+        inflight.pop_front();
+        did = true;
+      }
+    }
+    if (now >= t_end && inflight.empty() && unlaunched == 0) break;
+    if (!did) std::this_thread::yield();
+  }
+  tt_serve_report r{};
+  r.requests = requests;
+  r.refused = refused;
+  r.completed = completed;
+  r.batches = batches;
+  r.mean_batch = batches ? (double)batched_reqs / (double)batches : 0.0;
+  r.deadline_misses = misses;
+  r.throughput = (double)completed / cfg->duration_s;
+  if (!lat.empty()) {
+    std::sort(lat.begin(), lat.end());
+    auto pct = [&](double p) { return lat[std::min(lat.size() - 1, (size_t)(p * (double)(lat.size() - 1) + 0.5))] / 1e3; };
+    r.p50_us = pct(0.50);
+    r.p99_us = pct(0.99);
+    r.p999_us = pct(0.999);
+    r.max_us = lat.back() / 1e3;
+    double s = 0;
+    for (double v : lat) s += v;
+    r.mean_us = s / (double)lat.size() / 1e3;
+  }
+  *out = r;
+  return TT_OK;
 }
 
 }  // extern "C"

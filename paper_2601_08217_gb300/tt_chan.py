@@ -60,6 +60,20 @@ class EngineStats(C.Structure):
                 ("graph_builds", C.c_uint64), ("graph_launches", C.c_uint64)]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("max_slots_per_ue", C.c_uint32), ("warmup_s", C.c_double),
+                ("duration_s", C.c_double), ("slot_period_us", C.c_double), ("jitter_us", C.c_double),
+                ("deadline_us", C.c_double), ("seed", C.c_uint64), ("release_outputs", C.c_uint32),
+                ("max_inflight_batches", C.c_uint32)]
+
+
+class ServeReport(C.Structure):
+    _fields_ = [("requests", C.c_uint64), ("refused", C.c_uint64), ("completed", C.c_uint64),
+                ("batches", C.c_uint64), ("deadline_misses", C.c_uint64), ("mean_batch", C.c_double),
+                ("throughput", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double),
+                ("p999_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double)]
+
+
 class StaticChan(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("ue_id", C.c_uint32), ("samples_per_slot", C.c_uint32),
                 ("symbols_per_slot", C.c_uint32), ("symbol_len", C.POINTER(C.c_uint32)),
@@ -81,6 +95,7 @@ _SIGS = {
     "tt_engine_get_stats": [_VP, C.POINTER(EngineStats)],
     "tt_engine_autotune": [_VP, C.c_int32, C.POINTER(C.c_uint32)],
     "tt_engine_replay": [_VP, C.c_uint32, C.c_uint32],
+    "tt_engine_serve": [_VP, C.POINTER(ServeConfig), C.POINTER(ServeReport)],
     "tt_chan_create": [_VP, C.POINTER(ChanConfig), C.POINTER(_VP)],
     "tt_chan_destroy": [_VP],
     "tt_chan_load_trace": [_VP, C.POINTER(TraceDesc)],
@@ -203,6 +218,16 @@ def tt_engine_autotune(e: int, reps: int = 3) -> int:
 
 def tt_engine_replay(e: int, n_steps: int, slots_per_step: int = 1):
     _check(load().tt_engine_replay(e, n_steps, slots_per_step))
+
+
+def tt_engine_serve(e: int, duration_s: float, warmup_s: float = 0.0, slot_period_us: float = 500.0,
+                    jitter_us: float = 50.0, deadline_us: float = 500.0, seed: int = 0,
+                    max_slots_per_ue: int = 0, release_outputs: bool = True, max_inflight_batches: int = 0) -> dict:
+    cfg = ServeConfig(C.sizeof(ServeConfig), max_slots_per_ue, warmup_s, duration_s, slot_period_us, jitter_us,
+                      deadline_us, seed, int(bool(release_outputs)), max_inflight_batches)
+    rep = ServeReport()
+    _check(load().tt_engine_serve(e, C.byref(cfg), C.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in ServeReport._fields_}
 
 
 def tt_chan_create(e: int, samples_per_slot: int, symbol_len: Sequence[int], n_tx: int = 1, n_rx: int = 1,
