@@ -15,15 +15,15 @@ pytestmark = pytest.mark.gpu
 PREFILL = 8
 
 
-def _prefill(eng, specs, ring_extra):
+def _prefill(eng, specs, ring_extra, n=PREFILL):
     chans = []
     for i, sp in enumerate(specs):
         ch = tc.Chan(eng, sp, ring_slots=hist_slots(sp) + ring_extra)
-        ch.push(0, tc.slots_major(inputs.make_iq(5, sp, PREFILL), sp.n))
+        ch.push(0, tc.slots_major(inputs.make_iq(5, sp, n), sp.n))
         chans.append(ch)
     eng.run()
     for ch in chans:
-        ch.pull(0, PREFILL)
+        ch.pull(0, n)
     return chans
 
 
@@ -51,7 +51,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 def test_full_ring_refuses_requests():
     specs = inputs.workload_serving(n_ues=4, n_slots_trace=2)
     eng = tc.Engine()
-    _prefill(eng, specs, 3)
+    _prefill(eng, specs, 3, n=2)
     rep = tc.tt_engine_serve(eng.h, duration_s=0.02, slot_period_us=200.0, jitter_us=0.0, seed=1,
                              release_outputs=False)
     assert rep["refused"] > 0 and rep["completed"] == rep["requests"] - rep["refused"]
