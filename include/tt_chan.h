@@ -108,7 +108,8 @@ typedef struct {
   uint32_t ring_slots;        /* slot ring depth Q (>= 2 + ceil(max_delay/N)); 0 = that minimum + 2 */
   uint64_t seed;              /* AWGN key */
   float noise_var;            /* sigma^2 per complex sample; 0 disables AWGN */
-  uint32_t precision;         /* TT_FP32 (tensor-core forms use their own entry points) */
+  uint32_t precision;         /* TT_FP32: CUDA-core FP32 path.  TT_BF16_TC / TT_FP16_TC: block-Toeplitz
+                                 tensor-core path (tcgen05, FP32 accumulation), delays <= 127 */
   uint32_t output_format;     /* TT_OUT_INT16 (packed IQ) or TT_OUT_CF32 (complex64 before packing) */
 } tt_chan_config;
 
@@ -155,7 +156,8 @@ tt_status tt_engine_run(tt_engine *e);
 tt_status tt_engine_replay(tt_engine *e, uint32_t n_steps, uint32_t slots_per_step);
 
 /* Block until all launched work is complete, at most timeout_us (< 0: no limit).
- * TT_ERR_TIMEOUT if it is still running. */
+ * TT_ERR_TIMEOUT if it is still running, or if a tensor-core kernel reported
+ * that one of its bounded waits expired (the affected slots are invalid). */
 tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us);
 
 /* The engine's CUDA stream (a cudaStream_t) for ordering caller work. */

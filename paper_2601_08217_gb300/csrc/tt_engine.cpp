@@ -92,6 +92,9 @@ struct tt_engine {
   std::vector<tt_chan *> gplan_chans;       // the same channels in the graph's segment order
   uint64_t graph_builds = 0, graph_launches = 0;
   uint64_t graph_nodes = 0;                 // tiled-kernel launches inside the cached graph
+  TTSeg *d_tcsegs = nullptr;                // work list of the tensor-core channels
+  size_t tcseg_cap = 0;
+  int *d_status = nullptr;                  // set by a kernel whose bounded wait expired
   std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
 };
 
@@ -523,6 +526,61 @@ tt_status launch_cached_graph(tt_engine *e, const std::vector<tt_chan *> &chans,
   return TT_OK;
 }
 
+
+// Tensor-core channels: one item per (UE, slot, symbol), BF16 and FP16 channels in separate launches.
+tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
+  std::vector<TTSeg> segs;
+  int n16 = 0;
+  for (int pass = 0; pass < 2; ++pass)  // BF16 channels first, then FP16
+    for (tt_chan *c : chans) {
+      const bool fp16 = c->cfg.precision == TT_FP16_TC;
+      if ((int)fp16 != pass) continue;
+      TTSeg sg{};
+      sg.first_slot = c->launched_end;
+      sg.ue = c->index;
+      sg.n_slots = (uint32_t)(c->pushed_end - c->launched_end);
+      sg.items = sg.n_slots * (uint32_t)c->desc.nsym;
+      segs.push_back(sg);
+      n16 += fp16;
+    }
+  if (segs.size() > e->tcseg_cap) {
+    cudaFree(e->d_tcsegs);
+    e->d_tcsegs = nullptr;
+    e->tcseg_cap = 0;
+    TT_CK(cudaMalloc(&e->d_tcsegs, sizeof(TTSeg) * segs.size() * 2));
+    e->tcseg_cap = segs.size() * 2;
+  }
+  const size_t nbf = segs.size() - (size_t)n16;
+  uint32_t acc = 0;
+  for (size_t i = 0; i < segs.size(); ++i) {
+    if (i == nbf) acc = 0;  // item numbering restarts for the FP16 launch
+    segs[i].item_begin = acc;
+    acc += segs[i].items;
+  }
+  TT_CK(cudaMemcpyAsync(e->d_tcsegs, segs.data(), sizeof(TTSeg) * segs.size(), cudaMemcpyHostToDevice,
+                        e->stream));
+  for (int pass = 0; pass < 2; ++pass) {
+    const size_t s0 = pass ? nbf : 0, s1 = pass ? segs.size() : nbf;
+    if (s0 == s1) continue;
+    uint32_t items = 0;
+    for (size_t i = s0; i < s1; ++i) items += segs[i].items;
+    TTLaunch L{};
+    L.ues = e->d_ues;
+    L.segs = e->d_tcsegs + s0;
+    L.n_segs = (int)(s1 - s0);
+    L.total_items = items;
+    L.counter = nullptr;
+    L.grid = -1;
+    cudaError_t err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->stream);
+    if (err != cudaSuccess) return fail(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(err));
+    L.grid = (int)std::min<uint64_t>((uint64_t)(-L.grid) * e->num_sms, items);
+    err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->stream);
+    if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tensor-core launch: %s", cudaGetErrorString(err));
+    ++e->launches;
+  }
+  return TT_OK;
+}
+
 }  // namespace
 
 int32_t tt_set_error(int32_t status, const char *msg) {
@@ -563,6 +621,8 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   if (err == cudaSuccess) err = cudaMalloc(&e->d_ues, sizeof(TTUEDesc) * e->max_ues);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_counters, sizeof(uint32_t) * e->counter_cap);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_cursors, sizeof(unsigned long long) * e->max_ues);
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_status, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemset(e->d_status, 0, sizeof(int));
   if (err != cudaSuccess) {
     tt_engine_destroy(e);
     return fail(TT_ERR_CUDA, "engine setup: %s", cudaGetErrorString(err));
@@ -593,6 +653,8 @@ tt_status tt_engine_destroy(tt_engine *e) {
   cudaFree(e->d_gsegs);
   cudaFree(e->d_counters);
   cudaFree(e->d_cursors);
+  cudaFree(e->d_tcsegs);
+  cudaFree(e->d_status);
   if (e->stream) cudaStreamDestroy(e->stream);
   if (e->copy) cudaStreamDestroy(e->copy);
   delete e;
@@ -632,7 +694,7 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   if (cfg->max_taps < 1 || cfg->max_taps > TT_MAX_TAPS)
     return fail(TT_ERR_INVALID, "max_taps must be 1..%d", TT_MAX_TAPS);
   if (cfg->max_delay > TT_MAX_DELAY) return fail(TT_ERR_INVALID, "max_delay must be <= %d", TT_MAX_DELAY);
-  if (cfg->precision != TT_FP32) return fail(TT_ERR_INVALID, "only TT_FP32 channels run through the engine");
+  if (cfg->precision > TT_FP16_TC) return fail(TT_ERR_INVALID, "unknown precision");
   if (cfg->output_format > TT_OUT_CF32) return fail(TT_ERR_INVALID, "unknown output_format");
   if (!(cfg->noise_var >= 0.0f) || !std::isfinite(cfg->noise_var)) return fail(TT_ERR_INVALID, "bad noise_var");
   uint64_t sum = 0;
@@ -751,10 +813,17 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   for (size_t i = 0; i < nval; ++i)
     if (!std::isfinite(tr->taps[i])) return fail(TT_ERR_TRACE, "non-finite tap value at %zu", i);
   const int dclass = pick_dclass(d_max);
+  const bool tc = c->cfg.precision != TT_FP32;
+  if (tc && d_max > tt_tc_max_delay())
+    return fail(TT_ERR_TRACE, "tensor-core channels take delays up to %d (got %d)", tt_tc_max_delay(), d_max);
   // largest samples-per-thread whose shared-memory footprint fits
   int spt = 0, tap_need = 0;
   size_t smem = 0;
   for (int s : spt_candidates(c->sym_len, c->e->spt_override, c->cfg.n_rx)) {
+    if (tc) {  // the tiled geometry is unused; keep the smallest valid one
+      spt = 1;
+      break;
+    }
     int touched = 1;
     chunk_table(c->sym_len, s, &touched);
     const int need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * tr->n_taps);
@@ -889,10 +958,13 @@ tt_status tt_engine_run(tt_engine *e) {
   if (!e) return fail(TT_ERR_INVALID, "null engine");
   std::lock_guard<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
-  std::vector<tt_chan *> ready;
+  std::vector<tt_chan *> ready, tc_ready;
   for (tt_chan *c : e->table)
-    if (c && c->has_trace && c->started && c->pushed_end > c->launched_end) ready.push_back(c);
-  if (ready.empty()) return TT_OK;
+    if (c && c->has_trace && c->started && c->pushed_end > c->launched_end) {
+      if (c->cfg.precision != TT_FP32 && e->form != TT_FORM_PLAIN) tc_ready.push_back(c);
+      else ready.push_back(c);
+    }
+  if (ready.empty() && tc_ready.empty()) return TT_OK;
 
   if (e->form == TT_FORM_PLAIN) {
     for (tt_chan *c : ready) {
@@ -902,7 +974,7 @@ tt_status tt_engine_run(tt_engine *e) {
         ++e->launches;
       }
     }
-  } else {
+  } else if (!ready.empty()) {
     std::vector<uint64_t> first(ready.size()), count(ready.size());
     for (size_t i = 0; i < ready.size(); ++i) {
       first[i] = ready[i]->launched_end;
@@ -926,6 +998,11 @@ tt_status tt_engine_run(tt_engine *e) {
         e->gplan_chans = plan.chans;
       }
     }
+  }
+  if (!tc_ready.empty()) {
+    tt_status st = launch_tc(e, tc_ready);
+    if (st != TT_OK) return st;
+    ready.insert(ready.end(), tc_ready.begin(), tc_ready.end());
   }
   cudaEvent_t ev = get_event(e);
   if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
@@ -1046,6 +1123,12 @@ tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us) {
   tt_status s = wait_seq(e, e->launch_seq, timeout_us, lk);
   if (s != TT_OK) return s;
   if (timeout_us < 0) TT_CK(cudaStreamSynchronize(e->stream));
+  int kst = 0;
+  TT_CK(cudaMemcpy(&kst, e->d_status, sizeof kst, cudaMemcpyDeviceToHost));
+  if (kst) {
+    cudaMemset(e->d_status, 0, sizeof(int));
+    return fail(TT_ERR_TIMEOUT, "a kernel's bounded wait on the tensor core expired; its slots are invalid");
+  }
   for (tt_chan *c : e->table)
     if (c) update_chan(c);
   return TT_OK;

@@ -108,6 +108,12 @@ cudaError_t tt_launch_conv_s4(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s8(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s16(const TTLaunch &L, cudaStream_t st);
 
+// Block-Toeplitz tensor-core kernel (tcgen05, BF16 or FP16 operands): one work item per
+// (UE, slot, symbol); status is set to 1 if a bounded wait on the tensor core expires.
+size_t tt_tc_smem_bytes();
+int tt_tc_max_delay();
+cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, cudaStream_t st);
+
 // Record a message for tt_last_error() (thread-local) and return the status.
 int32_t tt_set_error(int32_t status, const char *msg);
 

@@ -388,7 +388,8 @@ class Engine:
 class Chan:
     """One UE link.  ``spec`` is an ``inputs.UESpec`` (or anything with its fields)."""
 
-    def __init__(self, engine: Engine, spec, ring_slots: int = 0, load: bool = True, cf32: bool = False):
+    def __init__(self, engine: Engine, spec, ring_slots: int = 0, load: bool = True, cf32: bool = False,
+                 precision: int = TT_FP32):
         self.engine = engine
         self.spec = spec
         self.cf32 = cf32
@@ -396,7 +397,7 @@ class Chan:
         self.h = tt_chan_create(engine.h, self.n, spec.symbol_len, spec.n_tx, spec.n_rx,
                                 max(int(len(spec.delays)), 1), int(max(spec.max_delay, max(spec.delays))),
                                 ring_slots, int(spec.seed), float(spec.noise_var), int(spec.ue_id),
-                                output_format=TT_OUT_CF32 if cf32 else TT_OUT_INT16)
+                                precision=precision, output_format=TT_OUT_CF32 if cf32 else TT_OUT_INT16)
         engine.chans.append(self)
         if load:
             self.load_trace(spec.taps, spec.delays, spec.step_samples, spec.loop)
