@@ -44,10 +44,10 @@ WORKLOAD = ("16 UEs SISO, 40 MHz (30720 samples/slot), 1000 slots each, 24 taps 
 
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    out = {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0, "src": "fallback"}
+    out = {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
     if os.path.exists(p):
         d = json.load(open(p))
-        out.update({k: d[k] for k in ("sm_max_mhz", "hbm_gbs") if k in d})
+        out.update({k: d[k] for k in ("sm_max_mhz", "hbm_gbs", "bf16_tflops") if k in d})
         out["src"] = "measured"
     return out
 
@@ -328,6 +328,60 @@ def run_serving(args, device, n_ues=512, duration=2.0, warmup=0.2, plain_duratio
     return out
 
 
+def run_precision(args, device, n_ues=64, n_slots=20, warmup=3):
+    """64 UEs at 100 MHz (61440 samples/slot), 4x4 MIMO, 96 contiguous taps (delays 0..95), 100 Hz:
+    block-Toeplitz tensor-core form (BF16 and FP16 operands, FP32 accumulation) beside the FP32
+    CUDA-core form on the same inputs; EVM against the FP64 oracle on one UE-slot."""
+    import torch
+    import oracle
+    from paper_2601_08217_gb300 import inputs
+    from paper_2601_08217_gb300 import tt_chan as tc
+    pk = peaks()
+    specs = inputs.workload_precision(n_ues=n_ues, n_slots_trace=4)
+    iq = [tc.slots_major(inputs.make_iq(4, sp, 4), sp.n) for sp in specs]
+    x0 = inputs.make_iq(4, specs[0], 1)
+    y_ref, _ = oracle.run_ue(oracle.OracleUE.from_spec(specs[0]), x0)
+    out = {}
+    n = specs[0].n
+    tiles = sum(-(-L // 128) for L in specs[0].symbol_len)
+    exec_flop = n_ues * tiles * 64 * 128 * 16 * 16 * 2          # MMAs issued per slot
+    useful_flop = n_ues * n * 16 * 96 * 8                        # complex MACs per slot
+    for name, prec in (("bf16_tc", tc.TT_BF16_TC), ("fp16_tc", tc.TT_FP16_TC), ("fp32", tc.TT_FP32)):
+        eng = tc.Engine(device=device, persistent=True, graphs=(prec == tc.TT_FP32))
+        chans = [tc.Chan(eng, sp, ring_slots=n_slots + 2, precision=prec) for sp in specs]
+        for ch, x in zip(chans, iq):
+            ch.push(0, x[np.arange(n_slots + 1) % 4])
+        eng.run()
+        for ch in chans:
+            tc.tt_chan_release_slots(ch.h, 0, n_slots + 1)
+        eng.sync()
+        stream = torch.cuda.ExternalStream(eng.stream)
+        tc.tt_engine_replay(eng.h, warmup, 1)
+        eng.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tc.tt_engine_replay(eng.h, n_slots, 1)
+        b.record(stream)
+        eng.sync()
+        ms = a.elapsed_time(b) / n_slots
+        # EVM of UE 0's first slot against the oracle
+        e1 = tc.Engine(device=device)
+        c1 = tc.Chan(e1, specs[0], ring_slots=3, cf32=True, precision=prec)
+        c1.push(0, x0)
+        e1.run()
+        y = tc.antenna_major(c1.pull(0, 1))
+        e1.close()
+        evm = 20 * np.log10(np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref))
+        rec = {"ms_per_slot_64ue": ms, "realtime": ms <= 0.5, "ue_slots_per_s": n_ues / (ms / 1e3),
+               "useful_tflops": useful_flop / (ms / 1e3) / 1e12, "evm_db_vs_oracle": evm}
+        if prec != tc.TT_FP32:
+            rec["executed_tflops"] = exec_flop / (ms / 1e3) / 1e12
+            rec["tensor_frac_of_measured_bf16_peak"] = rec["executed_tflops"] / pk.get("bf16_tflops", 1918.0)
+        out[name] = rec
+        eng.close()
+    return out
+
+
 def cpu_baseline(budget_s: float = 12.0):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload.
 
@@ -370,6 +424,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--slots", type=int, default=1000,
                     help="slots per UE per step (smaller for profiling captures)")
     args = ap.parse_args()
@@ -431,6 +486,9 @@ def main():
     batching = None
     if rank == 0 and world == 1 and not args.no_batching:
         batching = run_batching(args, local)
+    precision = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        precision = run_precision(args, local)
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(args, local)
@@ -461,6 +519,7 @@ def main():
         "vs_plain": (value / r["plain"]["value"]) if r["plain"] else None,
         "batching": batching,
         "serving": serving,
+        "precision": precision,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
