@@ -328,7 +328,7 @@ def run_serving(args, device, n_ues=512, duration=2.0, warmup=0.2, plain_duratio
     return out
 
 
-def run_precision(args, device, n_ues=64, n_slots=20, warmup=3):
+def run_precision(args, device, n_ues=64, n_slots=20, warmup=3, forms=("bf16_tc", "fp16_tc", "fp32")):
     """64 UEs at 100 MHz (61440 samples/slot), 4x4 MIMO, 96 contiguous taps (delays 0..95), 100 Hz:
     block-Toeplitz tensor-core form (BF16 and FP16 operands, FP32 accumulation) beside the FP32
     CUDA-core form on the same inputs; EVM against the FP64 oracle on one UE-slot."""
@@ -347,6 +347,8 @@ def run_precision(args, device, n_ues=64, n_slots=20, warmup=3):
     exec_flop = n_ues * tiles * 64 * 128 * 16 * 16 * 2          # MMAs issued per slot
     useful_flop = n_ues * n * 16 * 96 * 8                        # complex MACs per slot
     for name, prec in (("bf16_tc", tc.TT_BF16_TC), ("fp16_tc", tc.TT_FP16_TC), ("fp32", tc.TT_FP32)):
+        if name not in forms:
+            continue
         eng = tc.Engine(device=device, persistent=True, graphs=(prec == tc.TT_FP32))
         chans = [tc.Chan(eng, sp, ring_slots=n_slots + 2, precision=prec) for sp in specs]
         for ch, x in zip(chans, iq):
@@ -425,6 +427,9 @@ def main():
     ap.add_argument("--no-batching", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--only-precision", default="", help="profiling: run only these precision forms "
+                    "(comma list of bf16_tc,fp16_tc,fp32) with --prec-ues UEs and print their record")
+    ap.add_argument("--prec-ues", type=int, default=64)
     ap.add_argument("--slots", type=int, default=1000,
                     help="slots per UE per step (smaller for profiling captures)")
     args = ap.parse_args()
@@ -458,6 +463,12 @@ def main():
         return
 
     import torch
+    if args.only_precision:
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(run_precision(args, local, n_ues=args.prec_ues, n_slots=4, warmup=1,
+                                       forms=tuple(args.only_precision.split(",")))))
+        return
     if world > 1:
         torch.distributed.init_process_group("nccl")
     torch.cuda.set_device(local)
