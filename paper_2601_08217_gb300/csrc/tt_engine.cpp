@@ -539,7 +539,7 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
       sg.first_slot = c->launched_end;
       sg.ue = c->index;
       sg.n_slots = (uint32_t)(c->pushed_end - c->launched_end);
-      sg.items = sg.n_slots * (uint32_t)c->desc.nsym;
+      sg.items = sg.n_slots * (uint32_t)c->desc.items_per_slot;
       segs.push_back(sg);
       n16 += fp16;
     }
@@ -816,6 +816,9 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   const bool tc = c->cfg.precision != TT_FP32;
   if (tc && d_max > tt_tc_max_delay())
     return fail(TT_ERR_TRACE, "tensor-core channels take delays up to %d (got %d)", tt_tc_max_delay(), d_max);
+  if (tc)
+    for (uint32_t v : c->sym_len)
+      if (v % 8) return fail(TT_ERR_INVALID, "tensor-core channels need symbol lengths divisible by 8");
   // largest samples-per-thread whose shared-memory footprint fits
   int spt = 0, tap_need = 0;
   size_t smem = 0;
@@ -886,6 +889,10 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   d.loop = tr->loop ? 1 : 0;
   tt_status sst = set_spt(c, spt);
   if (sst != TT_OK) return sst;
+  if (tc) {  // the tensor-core kernel's work items: up to 4096 samples of one symbol
+    std::vector<int32_t> L32(c->sym_len.begin(), c->sym_len.end());
+    d.items_per_slot = tt_tc_items_per_slot(L32.data(), (int)L32.size());
+  }
   return upload_desc(c);
 }
 

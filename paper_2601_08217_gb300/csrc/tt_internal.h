@@ -109,9 +109,11 @@ cudaError_t tt_launch_conv_s8(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s16(const TTLaunch &L, cudaStream_t st);
 
 // Block-Toeplitz tensor-core kernel (tcgen05, BF16 or FP16 operands): one work item per
-// (UE, slot, symbol); status is set to 1 if a bounded wait on the tensor core expires.
+// (UE, slot, up to 4096 samples of one symbol); status is set to 1 if a bounded wait on the
+// tensor core expires.
 size_t tt_tc_smem_bytes();
 int tt_tc_max_delay();
+int tt_tc_items_per_slot(const int32_t *sym_len, int nsym);  // work items per slot of a channel
 cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, cudaStream_t st);
 
 // Record a message for tt_last_error() (thread-local) and return the status.

@@ -9,19 +9,19 @@
 // with H = the symbol's anchor and dH = next anchor - anchor: two static
 // convolutions whose sum over delays is a matrix product.
 //
-// Polyphase form (delay d = 8q + s, q = 0..15, s = 0..7, so d < 128):
-//     D[m][n] = sum_{t, p, s, q'} X_{t,p,s}[m][q'] * W[n][(t,p,s,q')]
-//     X_{t,p,s}[m][q'] = x_{t,p}[m - s - 120 + 8 q']          (q' = 15 - q; p = re/im part of x)
-//     n = (r, output part, A or B): 16 rows for up to 4 Rx antennas
-// For a fixed (t, p, s) the signal operand X is a Hankel-like view of one
-// contiguous run of samples: element (m, q') sits at byte 2 m + 16 q' of a
-// buffer holding x shifted by s.  That is exactly an MN-major shared-memory
-// matrix descriptor with 8-element core matrices 16 bytes apart along M and
-// 128 bytes apart along K, so the expanded Toeplitz operand is never stored:
-// the tensor core reads the window itself.  Eight phase-shifted copies keep
-// every descriptor start 16-byte aligned.  The tap operand W (16 x 1024) is
-// built once per (UE, symbol) and reused by all of the symbol's 128-sample
-// tiles.  One MMA per (t, p, s): M = 128 samples, N = 16, K = 16.
+// Block form (blocks of 8 output samples, delays d < 128):
+//     D[c][(i, n)] = sum_{t, p, j} X_{t,p}[c][j] * W[(i, n)][(t, p, j)]
+//     X_{t,p}[c][j] = x_{t,p}[8 c + j - 127],     W[(i, n)][(t, p, j)] = tap of delay i + 127 - j
+//     c = block row (M), i = sample in the block, n = (r, output part, A or B), p = re/im part of x
+// so output sample 8 c + i of (r, part) is D[c][(i, n)].  X is a Hankel-like
+// view of one contiguous run of 16-bit samples: element (c, j) sits at byte
+// 16 c + 2 j.  That is a K-major shared-memory matrix descriptor whose 8-row
+// core matrices are 128 bytes apart along M and only 16 bytes apart along K,
+// so the Toeplitz-expanded operand is never stored: the tensor core reads the
+// staged window itself.  The tap operand W (128 x 1152 for 4 Tx) is too big to
+// keep, so it streams in 4 KB K-chunks built in shared memory while the tensor
+// core consumes the previous chunk; each chunk feeds up to four 128x128x16 MMAs
+// (1024 samples each) whose accumulators fill the 512 tensor-memory columns.
 //
 // Every wait on the MMA-completion barrier is bounded; on expiry the kernel
 // sets the status word to 1, frees its tensor memory and exits.
@@ -37,23 +37,26 @@
 namespace {
 
 constexpr int kTPB = 128;
-constexpr int kTile = 128;            // output samples per MMA tile (M)
-constexpr int kPhases = 8;            // s
-constexpr int kQ = 16;                // q' (delays < 8 * 16 = 128)
-constexpr int kMaxDelayTC = kPhases * kQ - 1;
-constexpr int kBufElems = 256;        // phase buffer: j = (m - m0) + 8 q' < 128 + 120
-constexpr int kWin = kBufElems + 8;   // raw window samples per tile: phase buffer s reads raw[7 - s + j]
-constexpr int kN = 16;                // D columns: (r, part, A|B)
-constexpr int kKTot = 4 * 2 * kPhases * kQ;  // 1024: (t, p, s, q')
-constexpr uint32_t kTmemCols = 32;
+constexpr int kB = 8;                 // output samples per block row (16-byte rows of the signal view)
+constexpr int kRows = 128;            // block rows per MMA tile (M): 1024 samples
+constexpr int kTilesMax = 4;          // tiles accumulating at once: 4 x 128 TMEM columns
+constexpr int kGroup = kRows * kB * kTilesMax;  // samples per work item (4096)
+constexpr int kMaxDelayTC = 127;
+constexpr int kW = 144;               // window per (t, p): j in [0, 135) used, padded to 9 K-chunks of 16
+constexpr int kKC = kW / 16;          // K-chunks per (t, p)
+constexpr int kN = 128;               // D columns: (i, r, part, A|B)
+constexpr int kSig = kGroup + kW;     // staged samples per (t, p)
+constexpr uint32_t kTmemCols = 512;
 constexpr long long kSpinLimit = 1ll << 26;
 
 // shared memory layout (bytes)
-constexpr int kOffA = 0;                                          // [4 tx][2 parts][8 phases][256] x 2 B
-constexpr int kOffW = kOffA + 4 * 2 * kPhases * kBufElems * 2;   // 32 KB: [2 n-groups][128 k-groups][8][8] x 2 B
-constexpr int kOffTap = kOffW + kN * kKTot * 2;                  // [16 links][128 delays] float4
-constexpr int kOffRaw = kOffTap + 16 * 128 * 16;                 // [4 tx][2 parts][kWin] float
-constexpr int kSmemBytes = kOffRaw + 4 * 2 * kWin * 4;
+constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
+constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // 2 x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
+constexpr int kOffTap = kOffW + 2 * kN * 16 * 2;         // [16 links][128 delays] float4 (H, dH)
+constexpr int kSmemUsed = kOffTap + 16 * 128 * 16;
+// More than half an SM's shared memory: one CTA per SM, so no two CTAs ever compete for the
+// 512 tensor-memory columns each one allocates.
+constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -110,27 +113,40 @@ __device__ __forceinline__ uint16_t to_op(float v) {
 
 struct TCItem {
   unsigned long long slot;
-  int ue, sym, valid;
+  int ue, sym, m_start, m_end, valid;
 };
+
+// Bounded wait on an MMA-completion barrier: lane 0 polls, the warp follows its verdict.
+__device__ __forceinline__ int warp_wait(uint32_t mbar, uint32_t phase, int *status, int *abort_flag) {
+  int done = 0;
+  if ((threadIdx.x & 31) == 0) {
+    long long spins = 0;
+    while (!(done = mbar_try_wait(mbar, phase)) && ++spins < kSpinLimit) {
+    }
+    if (!done) {
+      atomicExch(status, 1);
+      *abort_flag = 1;
+    }
+  }
+  return __shfl_sync(0xFFFFFFFFu, done, 0);
+}
 
 }  // namespace
 
 template <bool FP16>
-__global__ void __launch_bounds__(kTPB)
+__global__ void __launch_bounds__(kTPB, 1)
     tt_toeplitz_tc_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                           uint32_t total_items, uint32_t *__restrict__ counter, int *__restrict__ status) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) unsigned long long s_mbar;
+  __shared__ __align__(8) unsigned long long s_mbar[2];
   __shared__ uint32_t s_tmem;
   __shared__ TCItem s_it;
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint16_t *Abuf = reinterpret_cast<uint16_t *>(sm + kOffA);
-  uint16_t *Wbuf = reinterpret_cast<uint16_t *>(sm + kOffW);
+  uint16_t *sig = reinterpret_cast<uint16_t *>(sm + kOffSig);
+  uint16_t *wbuf = reinterpret_cast<uint16_t *>(sm + kOffW);
   float4 *tapd = reinterpret_cast<float4 *>(sm + kOffTap);
-  float *raw = reinterpret_cast<float *>(sm + kOffRaw);
-  const uint32_t mbar = smem_u32(&s_mbar);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
@@ -138,7 +154,8 @@ __global__ void __launch_bounds__(kTPB)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_mbar[1])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     s_abort = 0;
@@ -147,12 +164,19 @@ __global__ void __launch_bounds__(kTPB)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = s_tmem;
-  uint32_t phase = 0;
+  uint32_t ph[2] = {0u, 0u};
+  int pending[2] = {0, 0};
+  auto wait_buf = [&](int b) {
+    if (!pending[b]) return;
+    warp_wait(smem_u32(&s_mbar[b]), ph[b], status, &s_abort);
+    ph[b] ^= 1u;
+    pending[b] = 0;
+  };
 
-  // idesc: D = F32, A/B = F16 (0) or BF16 (1), A MN-major, B K-major, N = 16, M = 128
+  // idesc: D = F32, A/B = F16 (0) or BF16 (1), both K-major, N = 128, M = 128
   const uint32_t fmt = FP16 ? 0u : 1u;
-  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (1u << 15) | ((uint32_t)(kN >> 3) << 17) |
-                         ((uint32_t)(kTile >> 4) << 24);
+  const uint32_t idesc =
+      (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 
   uint32_t next_static = blockIdx.x;
   for (;;) {
@@ -167,11 +191,22 @@ __global__ void __launch_bounds__(kTPB)
           if (segs[mid].item_begin <= item) lo = mid; else hi = mid - 1;
         }
         const TTSeg sg = segs[lo];
+        const TTUEDesc *U = ues + sg.ue;
         const uint32_t rel = item - sg.item_begin;
-        const uint32_t nsym = (uint32_t)ues[sg.ue].nsym;
-        it.slot = sg.first_slot + rel / nsym;
-        it.sym = (int)(rel % nsym);
+        const uint32_t ips = (uint32_t)U->items_per_slot;  // sum over symbols of ceil(L / 4096)
+        uint32_t c = rel % ips;
+        int j = 0;
+        for (;; ++j) {
+          const int L = U->sym_start[j + 1] - U->sym_start[j];
+          const uint32_t groups = (uint32_t)((L + kGroup - 1) / kGroup);
+          if (c < groups) break;
+          c -= groups;
+        }
+        it.slot = sg.first_slot + rel / ips;
         it.ue = (int)sg.ue;
+        it.sym = j;
+        it.m_start = U->sym_start[j] + (int)c * kGroup;
+        it.m_end = min(it.m_start + kGroup, U->sym_start[j + 1]);
         it.valid = 1;
       }
       s_it = it;
@@ -186,6 +221,9 @@ __global__ void __launch_bounds__(kTPB)
     const int per = n_rx * n_tx * K;
     const int slot_pos = (int)(it.slot % (uint64_t)Q);
     const uint64_t a = it.slot * (uint64_t)nsym + (uint64_t)it.sym;
+    const int blocks = (it.m_end - it.m_start + kB - 1) / kB;
+    const int n_tiles = (blocks + kRows - 1) / kRows;
+    const int nk = n_tx * 2 * kKC;  // K-chunks
 
     // ---- dense delay table of this symbol: tapd[r*4+t][d] = (H, dH) ----
     for (int e = tid; e < 16 * 128; e += kTPB) tapd[e] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -201,33 +239,13 @@ __global__ void __launch_bounds__(kTPB)
       atomicAdd(v + 2, h1.x - h0.x);
       atomicAdd(v + 3, h1.y - h0.y);
     }
-    __syncthreads();
-    // ---- tap operand W[n][k], K-major, core matrices 8x8 (16 B rows): k-groups 128 B apart,
-    //      n-groups 16 KB apart.  n = (r, out part, A|B), k = (t, p, s, q') ----
-    for (int e = tid; e < kN * kKTot; e += kTPB) {
-      const int nrow = e / kKTot, k = e % kKTot;
-      const int r = nrow >> 2, op = (nrow >> 1) & 1, ab = nrow & 1;
-      const int t = k >> 8, p = (k >> 7) & 1, s = (k >> 4) & 7, qp = k & 15;
-      const int d = 8 * (15 - qp) + s;
-      float v = 0.f;
-      if (r < n_rx && t < n_tx) {
-        const float4 h = tapd[(r * 4 + t) * 128 + d];
-        const float hr = ab ? h.z : h.x, hi = ab ? h.w : h.y;
-        // out re: re(x)*hr - im(x)*hi ; out im: re(x)*hi + im(x)*hr
-        v = op == 0 ? (p == 0 ? hr : -hi) : (p == 0 ? hi : hr);
-      }
-      const int off = (nrow >> 3) * 16384 + (k >> 3) * 128 + (nrow & 7) * 16 + (k & 7) * 2;
-      Wbuf[off >> 1] = to_op<FP16>(v);
-    }
-
-    // ---- 128-sample tiles of the symbol ----
-    for (int m0 = sym0; m0 < sym1; m0 += kTile) {
-      // raw window x_t[w], w in [m0 - 127, m0 - 127 + kWin), converted to float; zero beyond the slot
-      const int wbase = m0 - 127;
+    // ---- signal: sig[t][p][u] = x_{t,p}[m_start - 127 + u], 16-bit operands, zero past the slot end ----
+    {
       const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
-      for (int e = tid; e < n_tx * kWin; e += kTPB) {
-        const int t = e / kWin, j = e % kWin;
-        int w = wbase + j, pos = slot_pos;
+      const int ulen = n_tiles * kRows * kB + kW;
+      for (int e = tid; e < n_tx * ulen; e += kTPB) {
+        const int t = e / ulen, u = e - t * ulen;
+        int w = it.m_start - 127 + u, pos = slot_pos;
         float2 xv = make_float2(0.f, 0.f);
         if (w < n) {
           if (w < 0) {
@@ -238,54 +256,82 @@ __global__ void __launch_bounds__(kTPB)
           }
           xv = tt_unpack_iq(__ldg(rin + ((size_t)(pos * n_tx + t) * n + w)));
         }
-        raw[(t * 2 + 0) * kWin + j] = xv.x;
-        raw[(t * 2 + 1) * kWin + j] = xv.y;
+        sig[(t * 2 + 0) * kSig + u] = to_op<FP16>(xv.x);
+        sig[(t * 2 + 1) * kSig + u] = to_op<FP16>(xv.y);
       }
-      __syncthreads();
-      // phase buffers: A_{t,p,s}[j] = x_{t,p}[m0 - s - 120 + j] = raw[(t,p)][7 - s + j]
-      for (int e = tid; e < n_tx * 2 * kPhases * (kBufElems / 8); e += kTPB) {
-        const int chunk = e % (kBufElems / 8), tps = e / (kBufElems / 8);
-        const int s = tps % kPhases, tp = tps / kPhases;
-        const float *src = raw + tp * kWin + (7 - s) + chunk * 8;
+    }
+    __syncthreads();
+    // ---- tap chunk kc -> buffer b: rows (i, r, part, A|B), 16 K-elements (t, p, j in [16 jc, 16 jc + 16)).
+    //      Value: tap of delay d = i + 127 - j for link (r, t), part/sign from the complex product. ----
+    auto build_chunk = [&](int kc, int b) {
+      const int tp = kc / kKC, jc = kc % kKC, t = tp >> 1, p = tp & 1;
+      uint16_t *wb = wbuf + b * (kN * 16);
+      for (int e = tid; e < kN * 2; e += kTPB) {  // one 8-element (16-byte) row segment each
+        const int row = e >> 1, kg = e & 1;
+        const int i = row >> 4, nn = row & 15, r = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
         uint32_t pk[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          pk[i] = (uint32_t)to_op<FP16>(src[2 * i]) | ((uint32_t)to_op<FP16>(src[2 * i + 1]) << 16);
-        *reinterpret_cast<uint4 *>(Abuf + tps * kBufElems + chunk * 8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        for (int q = 0; q < 4; ++q) {
+          uint16_t hv[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = jc * 16 + kg * 8 + q * 2 + h;
+            const int d = i + 127 - j;
+            float v = 0.f;
+            if (r < n_rx && d >= 0 && d <= 127) {
+              const float4 tv = tapd[(r * 4 + t) * 128 + d];
+              const float hr = ab ? tv.z : tv.x, hi = ab ? tv.w : tv.y;
+              v = op == 0 ? (p == 0 ? hr : -hi) : (p == 0 ? hi : hr);
+            }
+            hv[h] = to_op<FP16>(v);
+          }
+          pk[q] = (uint32_t)hv[0] | ((uint32_t)hv[1] << 16);
+        }
+        // canonical K-major, no swizzle: row group (row / 8) every 256 B, k-group every 128 B, row every 16 B
+        *reinterpret_cast<uint4 *>(wb + ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
       }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      __syncthreads();
+    };
+
+    build_chunk(0, 0);
+    __syncthreads();
+    const uint32_t sig_base = smem_u32(sig), w_base = smem_u32(wbuf);
+    for (int kc = 0; kc < nk; ++kc) {
+      const int b = kc & 1;
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        const uint32_t a_base = smem_u32(Abuf), w_base = smem_u32(Wbuf);
-        const int nmma = n_tx * 2 * kPhases;
-        for (int i = 0; i < nmma; ++i) {
-          const uint64_t ad = umma_desc(a_base + (uint32_t)i * kBufElems * 2, /*lbo K*/ 128, /*sbo M*/ 16);
-          const uint64_t bd = umma_desc(w_base + (uint32_t)i * 2 * 128, /*lbo K*/ 128, /*sbo N*/ 16384);
-          umma_f16(tmem, ad, bd, idesc, i > 0 ? 1u : 0u);
+        const int tp = kc / kKC, jc = kc % kKC;
+        const uint64_t bd = umma_desc(w_base + (uint32_t)b * kN * 16 * 2, /*lbo K*/ 128, /*sbo N*/ 256);
+        for (int mt = 0; mt < n_tiles; ++mt) {
+          // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
+          const uint32_t a_start = sig_base + (uint32_t)(tp * kSig + mt * kRows * kB + jc * 16) * 2;
+          const uint64_t ad = umma_desc(a_start, /*lbo K*/ 16, /*sbo M*/ 128);
+          umma_f16(tmem + (uint32_t)mt * kN, ad, bd, idesc, kc > 0 ? 1u : 0u);
         }
-        umma_commit(mbar);
+        umma_commit(smem_u32(&s_mbar[b]));
       }
-      // wait for the tile's MMAs (bounded); lane 0 of each warp polls, the warp follows its verdict
-      int done = 0;
-      if (lane == 0) {
-        long long spins = 0;
-        while (!(done = mbar_try_wait(mbar, phase)) && ++spins < kSpinLimit) {
-        }
-        if (!done) {
-          atomicExch(status, 1);
-          s_abort = 1;
-        }
+      pending[b] = 1;
+      if (kc + 1 < nk) {
+        wait_buf(b ^ 1);  // MMAs of chunk kc - 1 are done with buffer b ^ 1
+        build_chunk(kc + 1, b ^ 1);
       }
-      done = __shfl_sync(0xFFFFFFFFu, done, 0);
-      phase ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-      if (done) {
-        // epilogue: lane = sample m0 + 32 warp + lane; 16 accumulator columns
+      __syncthreads();
+      if (s_abort) break;
+    }
+    wait_buf(0);
+    wait_buf(1);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    __syncthreads();
+    if (s_abort) break;
+    // ---- epilogue: lane = block row c of tile mt; 8 samples x (r, part, A|B) ----
+    for (int mt = 0; mt < n_tiles; ++mt) {
+      const int c = mt * kRows + warp * 32 + lane;
+      for (int i = 0; i < kB; ++i) {
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
-        const int m = m0 + warp * 32 + lane;
-        if (m < sym1) {
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * kN + i * 16), v);
+        const int m = it.m_start + c * kB + i;
+        if (m < it.m_end) {
           const float tau = (float)(m - sym0) / (float)(sym1 - sym0);
           const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
           for (int r = 0; r < n_rx; ++r) {
@@ -297,26 +343,26 @@ __global__ void __launch_bounds__(kTPB)
           }
         }
       }
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-      __syncthreads();
-      if (s_abort) break;
     }
-    if (s_abort) break;
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
   }
   __syncthreads();
-  if (s_abort && tid == 0) {  // one more bounded wait for anything still in flight
-    long long spins = 0;
-    while (!mbar_try_wait(mbar, phase) && ++spins < kSpinLimit) {
-    }
-  }
-  __syncthreads();
+  wait_buf(0);
+  wait_buf(1);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
 size_t tt_tc_smem_bytes() { return (size_t)kSmemBytes; }
 int tt_tc_max_delay() { return kMaxDelayTC; }
+int tt_tc_items_per_slot(const int32_t *sym_len, int nsym) {
+  int items = 0;
+  for (int j = 0; j < nsym; ++j) items += (sym_len[j] + kGroup - 1) / kGroup;
+  return items;
+}
 
 cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, cudaStream_t st) {
   auto kern = fp16 ? tt_toeplitz_tc_kernel<true> : tt_toeplitz_tc_kernel<false>;

@@ -38,10 +38,10 @@ def evm_db(y, ref):
 
 
 @pytest.mark.parametrize("prec", [tc.TT_BF16_TC, tc.TT_FP16_TC])
-@pytest.mark.parametrize("n_ant,K", [(4, 96), (1, 24), (2, 128)])
-def test_exactly_representable_inputs_give_exact_output(prec, n_ant, K):
+@pytest.mark.parametrize("n_ant,K,n_fft", [(4, 96, 1024), (1, 24, 1024), (2, 128, 1024), (3, 40, 4096)])
+def test_exactly_representable_inputs_give_exact_output(prec, n_ant, K, n_fft):
     rng = np.random.default_rng(40 + K)
-    L = inputs.nr_symbol_lengths(1024)                    # 20 MHz numerology (symbols 1112/1096)
+    L = inputs.nr_symbol_lengths(n_fft)                   # 20 MHz: one tile group; 100 MHz: two per symbol
     d = np.arange(K) if K <= 96 else np.sort(rng.choice(np.arange(128), K, replace=False))
     h = (rng.integers(-8, 9, size=(1, n_ant, n_ant, K)) + 1j * rng.integers(-8, 9, size=(1, n_ant, n_ant, K))) / 8
     taps = np.repeat(h, 3, axis=0).astype(np.complex64)  # static: H[a+1] - H[a] = 0
