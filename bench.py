@@ -343,8 +343,10 @@ def run_precision(args, device, n_ues=64, n_slots=20, warmup=3, forms=("bf16_tc"
     y_ref, _ = oracle.run_ue(oracle.OracleUE.from_spec(specs[0]), x0)
     out = {}
     n = specs[0].n
-    tiles = sum(-(-L // 128) for L in specs[0].symbol_len)
-    exec_flop = n_ues * tiles * 64 * 128 * 16 * 16 * 2          # MMAs issued per slot
+    # tensor-core MMAs issued per slot: per symbol, groups of <= 4096 samples in tiles of 1024
+    # samples (128 block rows of 8), each tile 2 x 4 x 9 K-chunks of a 128x128x16 MMA
+    tiles = sum(-(-min(4096, L - g) // 1024) for L in specs[0].symbol_len for g in range(0, L, 4096))
+    exec_flop = n_ues * tiles * (4 * 2 * 9) * 128 * 128 * 16 * 2
     useful_flop = n_ues * n * 16 * 96 * 8                        # complex MACs per slot
     for name, prec in (("bf16_tc", tc.TT_BF16_TC), ("fp16_tc", tc.TT_FP16_TC), ("fp32", tc.TT_FP32)):
         if name not in forms:

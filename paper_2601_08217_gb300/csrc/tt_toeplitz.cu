@@ -11,7 +11,7 @@
 //
 // Block form (blocks of 8 output samples, delays d < 128):
 //     D[c][(i, n)] = sum_{t, p, j} X_{t,p}[c][j] * W[(i, n)][(t, p, j)]
-//     X_{t,p}[c][j] = x_{t,p}[8 c + j - 127],     W[(i, n)][(t, p, j)] = tap of delay i + 127 - j
+//     X_{t,p}[c][j] = x_{t,p}[8 c + j - 128],     W[(i, n)][(t, p, j)] = tap of delay i + 128 - j
 //     c = block row (M), i = sample in the block, n = (r, output part, A or B), p = re/im part of x
 // so output sample 8 c + i of (r, part) is D[c][(i, n)].  X is a Hankel-like
 // view of one contiguous run of 16-bit samples: element (c, j) sits at byte
@@ -36,7 +36,7 @@
 
 namespace {
 
-constexpr int kTPB = 128;
+constexpr int kTPB = 256;
 constexpr int kB = 8;                 // output samples per block row (16-byte rows of the signal view)
 constexpr int kRows = 128;            // block rows per MMA tile (M): 1024 samples
 constexpr int kTilesMax = 4;          // tiles accumulating at once: 4 x 128 TMEM columns
@@ -49,11 +49,14 @@ constexpr int kSig = kGroup + kW;     // staged samples per (t, p)
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kSpinLimit = 1ll << 26;
 
+constexpr int kQL = 160;             // component-table length: q = j - i + 8 in [1, 151]
+
 // shared memory layout (bytes)
 constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
 constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // 2 x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
 constexpr int kOffTap = kOffW + 2 * kN * 16 * 2;         // [16 links][128 delays] float4 (H, dH)
-constexpr int kSmemUsed = kOffTap + 16 * 128 * 16;
+constexpr int kOffComp = kOffTap + 16 * 128 * 16;        // [16 links][6 comps][2 parities][kQL] 16-bit
+constexpr int kSmemUsed = kOffComp + 16 * 6 * 2 * kQL * 2;
 // More than half an SM's shared memory: one CTA per SM, so no two CTAs ever compete for the
 // 512 tensor-memory columns each one allocates.
 constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
@@ -113,6 +116,7 @@ __device__ __forceinline__ uint16_t to_op(float v) {
 
 struct TCItem {
   unsigned long long slot;
+  unsigned long long idx0, idx1;  // trace entries of the symbol's anchor and the next one
   int ue, sym, m_start, m_end, valid;
 };
 
@@ -147,6 +151,7 @@ __global__ void __launch_bounds__(kTPB, 1)
   uint16_t *sig = reinterpret_cast<uint16_t *>(sm + kOffSig);
   uint16_t *wbuf = reinterpret_cast<uint16_t *>(sm + kOffW);
   float4 *tapd = reinterpret_cast<float4 *>(sm + kOffTap);
+  uint16_t *comp = reinterpret_cast<uint16_t *>(sm + kOffComp);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
@@ -207,6 +212,9 @@ __global__ void __launch_bounds__(kTPB, 1)
         it.sym = j;
         it.m_start = U->sym_start[j] + (int)c * kGroup;
         it.m_end = min(it.m_start + kGroup, U->sym_start[j + 1]);
+        const uint64_t a0 = it.slot * (uint64_t)U->nsym + (uint64_t)j, T = (uint64_t)U->n_anchors;
+        it.idx0 = U->loop ? a0 % T : (a0 < T ? a0 : T - 1);
+        it.idx1 = U->loop ? (a0 + 1) % T : (a0 + 1 < T ? a0 + 1 : T - 1);
         it.valid = 1;
       }
       s_it = it;
@@ -231,22 +239,30 @@ __global__ void __launch_bounds__(kTPB, 1)
     for (int e = tid; e < per; e += kTPB) {  // delays may repeat: accumulate
       const int k = e % K, rt = e / K, r = rt / n_tx, t = rt % n_tx;
       const int d = __ldg(U->delays + k);
-      const float2 h0 = tt::tt_anchor(U, a, e, per);
-      const float2 h1 = tt::tt_anchor(U, a + 1, e, per);
+      float2 h0, h1;
+      if (U->step_samples == 0.0) {
+        h0 = __ldg(U->taps + it.idx0 * (uint64_t)per + (uint64_t)e);
+        h1 = __ldg(U->taps + it.idx1 * (uint64_t)per + (uint64_t)e);
+      } else {
+        h0 = tt::tt_anchor(U, a, e, per);
+        h1 = tt::tt_anchor(U, a + 1, e, per);
+      }
       float *v = reinterpret_cast<float *>(&tapd[(r * 4 + t) * 128 + d]);
       atomicAdd(v + 0, h0.x);
       atomicAdd(v + 1, h0.y);
       atomicAdd(v + 2, h1.x - h0.x);
       atomicAdd(v + 3, h1.y - h0.y);
     }
-    // ---- signal: sig[t][p][u] = x_{t,p}[m_start - 127 + u], 16-bit operands, zero past the slot end ----
+    // ---- signal: sig[t][p][u] = x_{t,p}[m_start - 128 + u], 16-bit operands, zero past the slot end.
+    //      Four samples per thread and load: the window start is 8-aligned and N is a multiple of 8. ----
     {
       const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
       const int ulen = n_tiles * kRows * kB + kW;
-      for (int e = tid; e < n_tx * ulen; e += kTPB) {
-        const int t = e / ulen, u = e - t * ulen;
-        int w = it.m_start - 127 + u, pos = slot_pos;
-        float2 xv = make_float2(0.f, 0.f);
+      const int quads = ulen / 4;
+      for (int e = tid; e < n_tx * quads; e += kTPB) {
+        const int t = e / quads, u = (e - t * quads) * 4;
+        int w = it.m_start - 128 + u, pos = slot_pos;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (w < n) {
           if (w < 0) {
             const int back = (-w + n - 1) / n;
@@ -254,42 +270,57 @@ __global__ void __launch_bounds__(kTPB, 1)
             pos -= back;
             while (pos < 0) pos += Q;
           }
-          xv = tt_unpack_iq(__ldg(rin + ((size_t)(pos * n_tx + t) * n + w)));
+          v = __ldg(reinterpret_cast<const uint4 *>(rin + ((size_t)(pos * n_tx + t) * n + w)));
         }
-        sig[(t * 2 + 0) * kSig + u] = to_op<FP16>(xv.x);
-        sig[(t * 2 + 1) * kSig + u] = to_op<FP16>(xv.y);
+        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+        uint32_t re2[2], im2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float2 x0 = tt_unpack_iq(vv[2 * h]), x1 = tt_unpack_iq(vv[2 * h + 1]);
+          re2[h] = (uint32_t)to_op<FP16>(x0.x) | ((uint32_t)to_op<FP16>(x1.x) << 16);
+          im2[h] = (uint32_t)to_op<FP16>(x0.y) | ((uint32_t)to_op<FP16>(x1.y) << 16);
+        }
+        *reinterpret_cast<uint2 *>(sig + (t * 2 + 0) * kSig + u) = make_uint2(re2[0], re2[1]);
+        *reinterpret_cast<uint2 *>(sig + (t * 2 + 1) * kSig + u) = make_uint2(im2[0], im2[1]);
       }
     }
     __syncthreads();
+    // ---- component tables: comp[link][c][par][q] = component c of the tap of delay 136 - q
+    //      (zero outside 0..127), par 1 shifted by one element so any 8-run starts 4-byte aligned.
+    //      c: 0 hr(H) 1 hi(H) 2 -hi(H) 3 hr(dH) 4 hi(dH) 5 -hi(dH) ----
+    for (int e = tid; e < 16 * 6 * 2 * kQL; e += kTPB) {
+      const int q = e % kQL, rest = e / kQL, par = rest & 1, c = (rest >> 1) % 6, link = rest / 12;
+      const int d = 136 - (q + par);
+      float v = 0.f;
+      if (d >= 0 && d <= 127) {
+        const float4 tv = tapd[link * 128 + d];
+        const float hr = c < 3 ? tv.x : tv.z, hi = c < 3 ? tv.y : tv.w;
+        const int cc = c % 3;
+        v = cc == 0 ? hr : (cc == 1 ? hi : -hi);
+      }
+      comp[e] = to_op<FP16>(v);
+    }
+    __syncthreads();
     // ---- tap chunk kc -> buffer b: rows (i, r, part, A|B), 16 K-elements (t, p, j in [16 jc, 16 jc + 16)).
-    //      Value: tap of delay d = i + 127 - j for link (r, t), part/sign from the complex product. ----
+    //      Value: tap of delay d = i + 128 - j for link (r, t) = comp[.][q = j - i + 8]. ----
     auto build_chunk = [&](int kc, int b) {
       const int tp = kc / kKC, jc = kc % kKC, t = tp >> 1, p = tp & 1;
       uint16_t *wb = wbuf + b * (kN * 16);
       for (int e = tid; e < kN * 2; e += kTPB) {  // one 8-element (16-byte) row segment each
         const int row = e >> 1, kg = e & 1;
         const int i = row >> 4, nn = row & 15, r = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
-        uint32_t pk[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          uint16_t hv[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int j = jc * 16 + kg * 8 + q * 2 + h;
-            const int d = i + 127 - j;
-            float v = 0.f;
-            if (r < n_rx && d >= 0 && d <= 127) {
-              const float4 tv = tapd[(r * 4 + t) * 128 + d];
-              const float hr = ab ? tv.z : tv.x, hi = ab ? tv.w : tv.y;
-              v = op == 0 ? (p == 0 ? hr : -hi) : (p == 0 ? hi : hr);
-            }
-            hv[h] = to_op<FP16>(v);
-          }
-          pk[q] = (uint32_t)hv[0] | ((uint32_t)hv[1] << 16);
+        uint4 seg = make_uint4(0u, 0u, 0u, 0u);
+        if (r < n_rx) {
+          // (op, p): (0,0) hr  (0,1) -hi  (1,0) hi  (1,1) hr
+          const int c = ab * 3 + ((op ^ p) == 0 ? 0 : (op == 0 ? 2 : 1));
+          const int q0 = jc * 16 + kg * 8 - i + 8;
+          const int par = q0 & 1;
+          const uint32_t *src =
+              reinterpret_cast<const uint32_t *>(comp + (((r * 4 + t) * 6 + c) * 2 + par) * kQL + (q0 - par));
+          seg = make_uint4(src[0], src[1], src[2], src[3]);
         }
         // canonical K-major, no swizzle: row group (row / 8) every 256 B, k-group every 128 B, row every 16 B
-        *reinterpret_cast<uint4 *>(wb + ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2) =
-            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4 *>(wb + ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2) = seg;
       }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     };
@@ -324,22 +355,35 @@ __global__ void __launch_bounds__(kTPB, 1)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     __syncthreads();
     if (s_abort) break;
-    // ---- epilogue: lane = block row c of tile mt; 8 samples x (r, part, A|B) ----
-    for (int mt = 0; mt < n_tiles; ++mt) {
-      const int c = mt * kRows + warp * 32 + lane;
-      for (int i = 0; i < kB; ++i) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * kN + i * 16), v);
-        const int m = it.m_start + c * kB + i;
-        if (m < it.m_end) {
-          const float tau = (float)(m - sym0) / (float)(sym1 - sym0);
-          const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
-          for (int r = 0; r < n_rx; ++r) {
-            float2 y = make_float2(fmaf(tau, v[r * 4 + 1], v[r * 4 + 0]), fmaf(tau, v[r * 4 + 3], v[r * 4 + 2]));
-            if (U->noise_std > 0.f) tt_awgn_add_one(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y);
-            const size_t o = (size_t)(slot_pos * n_rx + r) * n + m;
-            if (U->out_f32) reinterpret_cast<float2 *>(U->ring_out)[o] = y;
-            else reinterpret_cast<uint32_t *>(U->ring_out)[o] = tt_pack_iq(y.x, y.y);
+    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (block rows) and samples
+    //      i in [4 (w / 4), 4 (w / 4) + 4) of each block; AWGN per pair of samples (one Philox block) ----
+    {
+      const int quad = warp & 3, ihalf = warp >> 2;
+      for (int mt = 0; mt < n_tiles; ++mt) {
+        const int c = mt * kRows + quad * 32 + lane;
+        for (int i = ihalf * 4; i < ihalf * 4 + 4; i += 2) {
+          float v0[16], v1[16];
+          const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + i * 16);
+          tmem_ld16(tbase, v0);
+          tmem_ld16(tbase + 16, v1);
+          const int m = it.m_start + c * kB + i;  // even: pairs (m, m + 1) share a Philox block
+          if (m < it.m_end) {
+            const float rl = 1.0f / (float)(sym1 - sym0);
+            const float tau0 = (float)(m - sym0) * rl, tau1 = (float)(m + 1 - sym0) * rl;
+            const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
+            for (int r = 0; r < n_rx; ++r) {
+              float2 y0 = make_float2(fmaf(tau0, v0[r * 4 + 1], v0[r * 4 + 0]), fmaf(tau0, v0[r * 4 + 3], v0[r * 4 + 2]));
+              float2 y1 = make_float2(fmaf(tau1, v1[r * 4 + 1], v1[r * 4 + 0]), fmaf(tau1, v1[r * 4 + 3], v1[r * 4 + 2]));
+              if (U->noise_std > 0.f) tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y0, y1);
+              const size_t o = (size_t)(slot_pos * n_rx + r) * n + m;
+              if (U->out_f32) {
+                *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(U->ring_out) + o) =
+                    make_float4(y0.x, y0.y, y1.x, y1.y);
+              } else {
+                *reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(U->ring_out) + o) =
+                    make_uint2(tt_pack_iq(y0.x, y0.y), tt_pack_iq(y1.x, y1.y));
+              }
+            }
           }
         }
       }
