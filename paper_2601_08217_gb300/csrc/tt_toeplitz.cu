@@ -50,11 +50,12 @@ constexpr uint32_t kTmemCols = 512;
 constexpr long long kSpinLimit = 1ll << 26;
 
 constexpr int kQL = 160;             // component-table length: q = j - i + 8 in [1, 151]
+constexpr int kStages = 8;            // tap-chunk ring: chunks queued ahead of the tensor core
 
 // shared memory layout (bytes)
 constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
-constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // 2 x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
-constexpr int kOffTap = kOffW + 2 * kN * 16 * 2;         // [16 links][128 delays] float4 (H, dH)
+constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // kStages x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
+constexpr int kOffTap = kOffW + kStages * kN * 16 * 2;   // [16 links][128 delays] float4 (H, dH)
 constexpr int kOffComp = kOffTap + 16 * 128 * 16;        // [16 links][6 comps][2 parities][kQL] 16-bit
 constexpr int kSmemUsed = kOffComp + 16 * 6 * 2 * kQL * 2;
 // More than half an SM's shared memory: one CTA per SM, so no two CTAs ever compete for the
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(kTPB, 1)
     tt_toeplitz_tc_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                           uint32_t total_items, uint32_t *__restrict__ counter, int *__restrict__ status) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) unsigned long long s_mbar[2];
+  __shared__ __align__(8) unsigned long long s_mbar[kStages];
   __shared__ uint32_t s_tmem;
   __shared__ TCItem s_it;
   __shared__ int s_abort;
@@ -159,8 +160,8 @@ __global__ void __launch_bounds__(kTPB, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_mbar[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_mbar[1])));
+    for (int b = 0; b < kStages; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_mbar[b])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     s_abort = 0;
@@ -169,8 +170,12 @@ __global__ void __launch_bounds__(kTPB, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = s_tmem;
-  uint32_t ph[2] = {0u, 0u};
-  int pending[2] = {0, 0};
+  uint32_t ph[kStages];
+  int pending[kStages];
+  for (int b = 0; b < kStages; ++b) {
+    ph[b] = 0u;
+    pending[b] = 0;
+  }
   auto wait_buf = [&](int b) {
     if (!pending[b]) return;
     warp_wait(smem_u32(&s_mbar[b]), ph[b], status, &s_abort);
@@ -325,11 +330,13 @@ __global__ void __launch_bounds__(kTPB, 1)
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     };
 
+    // chunk kc + 1 is built while the tensor core works through the queued chunks; its ring
+    // slot was last read by chunk kc + 1 - kStages, issued kStages - 1 iterations earlier
     build_chunk(0, 0);
     __syncthreads();
     const uint32_t sig_base = smem_u32(sig), w_base = smem_u32(wbuf);
     for (int kc = 0; kc < nk; ++kc) {
-      const int b = kc & 1;
+      const int b = kc % kStages;
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         const int tp = kc / kKC, jc = kc % kKC;
@@ -343,15 +350,16 @@ __global__ void __launch_bounds__(kTPB, 1)
         umma_commit(smem_u32(&s_mbar[b]));
       }
       pending[b] = 1;
-      if (kc + 1 < nk) {
-        wait_buf(b ^ 1);  // MMAs of chunk kc - 1 are done with buffer b ^ 1
-        build_chunk(kc + 1, b ^ 1);
+      const int nxt = kc + 1;
+      if (nxt < nk) {
+        const int nb = nxt % kStages;
+        wait_buf(nb);  // the MMAs of chunk nxt - kStages are done with this slot
+        build_chunk(nxt, nb);
       }
       __syncthreads();
       if (s_abort) break;
     }
-    wait_buf(0);
-    wait_buf(1);
+    for (int b = 0; b < kStages; ++b) wait_buf(b);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     __syncthreads();
     if (s_abort) break;
@@ -392,8 +400,7 @@ __global__ void __launch_bounds__(kTPB, 1)
     __syncthreads();
   }
   __syncthreads();
-  wait_buf(0);
-  wait_buf(1);
+  for (int b = 0; b < kStages; ++b) wait_buf(b);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   __syncthreads();
   if (warp == 0)
