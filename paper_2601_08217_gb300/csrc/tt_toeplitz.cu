@@ -49,15 +49,23 @@ constexpr int kSig = kGroup + kW;     // staged samples per (t, p)
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kSpinLimit = 1ll << 26;
 
-constexpr int kQL = 160;             // component-table length: q = j - i + 8 in [1, 151]
-constexpr int kStages = 8;            // tap-chunk ring: chunks queued ahead of the tensor core
+constexpr int kQW = 128;              // words per component table (q = j - i + 8 in [1, 151] needs 76, plus shift)
+constexpr int kStages = 4;            // tap-chunk ring: chunks queued ahead of the tensor core
 
 // shared memory layout (bytes)
 constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
 constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // kStages x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
 constexpr int kOffTap = kOffW + kStages * kN * 16 * 2;   // [16 links][128 delays] float4 (H, dH)
-constexpr int kOffComp = kOffTap + 16 * 128 * 16;        // [16 links][6 comps][2 parities][kQL] 16-bit
-constexpr int kSmemUsed = kOffComp + 16 * 6 * 2 * kQL * 2;
+constexpr int kOffComp = kOffTap + 16 * 128 * 16;        // [16 links][6 comps][2 parities][kQW words]
+constexpr int kSmemUsed = kOffComp + 16 * 6 * 2 * kQW * 4;
+
+// Word shift of component table (r, c) inside its slot.  A warp building one tap chunk reads,
+// for fixed (t, p), the 16 tables of (r, output part, A|B), one 16-byte run each at the same q
+// (and q + 8 for the second K-group).  Shift 8 r + g(c) with g a bijection of the four tables
+// of either input part puts those 32 runs on 32 distinct banks.
+__host__ __device__ constexpr int comp_shift(int r, int c) {
+  return 8 * r + (c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 1 : c == 3 ? 2 : c == 4 ? 3 : 3);
+}
 // More than half an SM's shared memory: one CTA per SM, so no two CTAs ever compete for the
 // 512 tensor-memory columns each one allocates.
 constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
@@ -170,17 +178,12 @@ __global__ void __launch_bounds__(kTPB, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = s_tmem;
-  uint32_t ph[kStages];
-  int pending[kStages];
-  for (int b = 0; b < kStages; ++b) {
-    ph[b] = 0u;
-    pending[b] = 0;
-  }
+  uint32_t ph_bits = 0u, pend_bits = 0u;  // per ring slot: barrier phase, commit not yet waited for
   auto wait_buf = [&](int b) {
-    if (!pending[b]) return;
-    warp_wait(smem_u32(&s_mbar[b]), ph[b], status, &s_abort);
-    ph[b] ^= 1u;
-    pending[b] = 0;
+    if (!((pend_bits >> b) & 1u)) return;
+    warp_wait(smem_u32(&s_mbar[b]), (ph_bits >> b) & 1u, status, &s_abort);
+    ph_bits ^= 1u << b;
+    pend_bits &= ~(1u << b);
   };
 
   // idesc: D = F32, A/B = F16 (0) or BF16 (1), both K-major, N = 128, M = 128
@@ -293,8 +296,8 @@ __global__ void __launch_bounds__(kTPB, 1)
     // ---- component tables: comp[link][c][par][q] = component c of the tap of delay 136 - q
     //      (zero outside 0..127), par 1 shifted by one element so any 8-run starts 4-byte aligned.
     //      c: 0 hr(H) 1 hi(H) 2 -hi(H) 3 hr(dH) 4 hi(dH) 5 -hi(dH) ----
-    for (int e = tid; e < 16 * 6 * 2 * kQL; e += kTPB) {
-      const int q = e % kQL, rest = e / kQL, par = rest & 1, c = (rest >> 1) % 6, link = rest / 12;
+    for (int e = tid; e < 16 * 6 * 2 * 152; e += kTPB) {
+      const int q = e % 152, rest = e / 152, par = rest & 1, c = (rest >> 1) % 6, link = rest / 12;
       const int d = 136 - (q + par);
       float v = 0.f;
       if (d >= 0 && d <= 127) {
@@ -303,30 +306,40 @@ __global__ void __launch_bounds__(kTPB, 1)
         const int cc = c % 3;
         v = cc == 0 ? hr : (cc == 1 ? hi : -hi);
       }
-      comp[e] = to_op<FP16>(v);
+      comp[((link * 6 + c) * 2 + par) * (kQW * 2) + comp_shift(link >> 2, c) * 2 + q] = to_op<FP16>(v);
     }
     __syncthreads();
     // ---- tap chunk kc -> buffer b: rows (i, r, part, A|B), 16 K-elements (t, p, j in [16 jc, 16 jc + 16)).
     //      Value: tap of delay d = i + 128 - j for link (r, t) = comp[.][q = j - i + 8]. ----
+    // Each thread always writes the same (row, k-group) segment of a chunk: precompute the word
+    // address of its component table for every (t, p); a chunk then costs 4 LDS + 1 STS.
+    const int row = tid >> 1, kg = tid & 1;
+    const int ii = row >> 4, nn = row & 15, rr = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
+    const int qoff = kg * 8 - ii + 8, par = qoff & 1;
+    const uint32_t *comp_w = reinterpret_cast<const uint32_t *>(comp);
+    int tbase[8];
+#pragma unroll
+    for (int tp = 0; tp < 8; ++tp) {
+      const int t = tp >> 1, p = tp & 1;
+      // (op, p): (0,0) hr  (0,1) -hi  (1,0) hi  (1,1) hr
+      const int c = ab * 3 + ((op ^ p) == 0 ? 0 : (op == 0 ? 2 : 1));
+      tbase[tp] = (rr < n_rx && t < n_tx)
+                      ? ((rr * 4 + t) * 6 + c) * 2 * kQW + par * kQW + comp_shift(rr, c) + (qoff - par) / 2
+                      : -1;
+    }
+    const int w_off = ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2;
     auto build_chunk = [&](int kc, int b) {
-      const int tp = kc / kKC, jc = kc % kKC, t = tp >> 1, p = tp & 1;
-      uint16_t *wb = wbuf + b * (kN * 16);
-      for (int e = tid; e < kN * 2; e += kTPB) {  // one 8-element (16-byte) row segment each
-        const int row = e >> 1, kg = e & 1;
-        const int i = row >> 4, nn = row & 15, r = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
-        uint4 seg = make_uint4(0u, 0u, 0u, 0u);
-        if (r < n_rx) {
-          // (op, p): (0,0) hr  (0,1) -hi  (1,0) hi  (1,1) hr
-          const int c = ab * 3 + ((op ^ p) == 0 ? 0 : (op == 0 ? 2 : 1));
-          const int q0 = jc * 16 + kg * 8 - i + 8;
-          const int par = q0 & 1;
-          const uint32_t *src =
-              reinterpret_cast<const uint32_t *>(comp + (((r * 4 + t) * 6 + c) * 2 + par) * kQL + (q0 - par));
-          seg = make_uint4(src[0], src[1], src[2], src[3]);
-        }
-        // canonical K-major, no swizzle: row group (row / 8) every 256 B, k-group every 128 B, row every 16 B
-        *reinterpret_cast<uint4 *>(wb + ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2) = seg;
+      const int tp = kc / kKC, jc = kc % kKC;
+      int base = -1;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q == tp) base = tbase[q];
+      uint4 seg = make_uint4(0u, 0u, 0u, 0u);
+      if (base >= 0) {
+        const uint32_t *src = comp_w + base + jc * 8;
+        seg = make_uint4(src[0], src[1], src[2], src[3]);
       }
+      *reinterpret_cast<uint4 *>(wbuf + b * (kN * 16) + w_off) = seg;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     };
 
@@ -349,7 +362,7 @@ __global__ void __launch_bounds__(kTPB, 1)
         }
         umma_commit(smem_u32(&s_mbar[b]));
       }
-      pending[b] = 1;
+      pend_bits |= 1u << b;
       const int nxt = kc + 1;
       if (nxt < nk) {
         const int nb = nxt % kStages;
@@ -379,7 +392,9 @@ __global__ void __launch_bounds__(kTPB, 1)
             const float rl = 1.0f / (float)(sym1 - sym0);
             const float tau0 = (float)(m - sym0) * rl, tau1 = (float)(m + 1 - sym0) * rl;
             const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
-            for (int r = 0; r < n_rx; ++r) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              if (r >= n_rx) break;
               float2 y0 = make_float2(fmaf(tau0, v0[r * 4 + 1], v0[r * 4 + 0]), fmaf(tau0, v0[r * 4 + 3], v0[r * 4 + 2]));
               float2 y1 = make_float2(fmaf(tau1, v1[r * 4 + 1], v1[r * 4 + 0]), fmaf(tau1, v1[r * 4 + 3], v1[r * 4 + 2]));
               if (U->noise_std > 0.f) tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y0, y1);
