@@ -126,7 +126,7 @@ __device__ __forceinline__ uint16_t to_op(float v) {
 struct TCItem {
   unsigned long long slot;
   unsigned long long idx0, idx1;  // trace entries of the symbol's anchor and the next one
-  int ue, sym, m_start, m_end, valid;
+  int ue, sym, valid;
 };
 
 // Bounded wait on an MMA-completion barrier: lane 0 polls, the warp follows its verdict.
@@ -190,6 +190,16 @@ __global__ void __launch_bounds__(kTPB, 1)
   const uint32_t fmt = FP16 ? 0u : 1u;
   const uint32_t idesc =
       (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+  const uint32_t sig_base = smem_u32(sig), w_base = smem_u32(wbuf);
+
+  // this thread's fixed segment of every tap chunk: row (i, r, part, A|B), k-group kg
+  const int row = tid >> 1, kg = tid & 1;
+  const int ii = row >> 4, nn = row & 15, rr = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
+  const int qoff = kg * 8 - ii + 8, par = qoff & 1;
+  // (op, p): (0,0) hr  (0,1) -hi  (1,0) hi  (1,1) hr
+  const int c_p0 = ab * 3 + (op == 0 ? 0 : 1), c_p1 = ab * 3 + (op == 0 ? 2 : 0);
+  const int w_off = ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2;
+  const uint32_t *comp_w = reinterpret_cast<const uint32_t *>(comp);
 
   uint32_t next_static = blockIdx.x;
   for (;;) {
@@ -206,21 +216,11 @@ __global__ void __launch_bounds__(kTPB, 1)
         const TTSeg sg = segs[lo];
         const TTUEDesc *U = ues + sg.ue;
         const uint32_t rel = item - sg.item_begin;
-        const uint32_t ips = (uint32_t)U->items_per_slot;  // sum over symbols of ceil(L / 4096)
-        uint32_t c = rel % ips;
-        int j = 0;
-        for (;; ++j) {
-          const int L = U->sym_start[j + 1] - U->sym_start[j];
-          const uint32_t groups = (uint32_t)((L + kGroup - 1) / kGroup);
-          if (c < groups) break;
-          c -= groups;
-        }
-        it.slot = sg.first_slot + rel / ips;
+        const uint32_t nsym = (uint32_t)U->nsym;
+        it.slot = sg.first_slot + rel / nsym;
         it.ue = (int)sg.ue;
-        it.sym = j;
-        it.m_start = U->sym_start[j] + (int)c * kGroup;
-        it.m_end = min(it.m_start + kGroup, U->sym_start[j + 1]);
-        const uint64_t a0 = it.slot * (uint64_t)U->nsym + (uint64_t)j, T = (uint64_t)U->n_anchors;
+        it.sym = (int)(rel % nsym);
+        const uint64_t a0 = it.slot * (uint64_t)nsym + (uint64_t)it.sym, T = (uint64_t)U->n_anchors;
         it.idx0 = U->loop ? a0 % T : (a0 < T ? a0 : T - 1);
         it.idx1 = U->loop ? (a0 + 1) % T : (a0 + 1 < T ? a0 + 1 : T - 1);
         it.valid = 1;
@@ -237,182 +237,182 @@ __global__ void __launch_bounds__(kTPB, 1)
     const int per = n_rx * n_tx * K;
     const int slot_pos = (int)(it.slot % (uint64_t)Q);
     const uint64_t a = it.slot * (uint64_t)nsym + (uint64_t)it.sym;
-    const int blocks = (it.m_end - it.m_start + kB - 1) / kB;
-    const int n_tiles = (blocks + kRows - 1) / kRows;
-    const int nk = n_tx * 2 * kKC;  // K-chunks
 
     // ---- dense delay table of this symbol: tapd[r*4+t][d] = (H, dH) ----
     for (int e = tid; e < 16 * 128; e += kTPB) tapd[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    for (int e = tid; e < per; e += kTPB) {  // delays may repeat: accumulate
-      const int k = e % K, rt = e / K, r = rt / n_tx, t = rt % n_tx;
-      const int d = __ldg(U->delays + k);
-      float2 h0, h1;
-      if (U->step_samples == 0.0) {
-        h0 = __ldg(U->taps + it.idx0 * (uint64_t)per + (uint64_t)e);
-        h1 = __ldg(U->taps + it.idx1 * (uint64_t)per + (uint64_t)e);
-      } else {
-        h0 = tt::tt_anchor(U, a, e, per);
-        h1 = tt::tt_anchor(U, a + 1, e, per);
-      }
-      float *v = reinterpret_cast<float *>(&tapd[(r * 4 + t) * 128 + d]);
-      atomicAdd(v + 0, h0.x);
-      atomicAdd(v + 1, h0.y);
-      atomicAdd(v + 2, h1.x - h0.x);
-      atomicAdd(v + 3, h1.y - h0.y);
-    }
-    // ---- signal: sig[t][p][u] = x_{t,p}[m_start - 128 + u], 16-bit operands, zero past the slot end.
-    //      Four samples per thread and load: the window start is 8-aligned and N is a multiple of 8. ----
-    {
-      const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
-      const int ulen = n_tiles * kRows * kB + kW;
-      const int quads = ulen / 4;
-      for (int e = tid; e < n_tx * quads; e += kTPB) {
-        const int t = e / quads, u = (e - t * quads) * 4;
-        int w = it.m_start - 128 + u, pos = slot_pos;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (w < n) {
-          if (w < 0) {
-            const int back = (-w + n - 1) / n;
-            w += back * n;
-            pos -= back;
-            while (pos < 0) pos += Q;
-          }
-          v = __ldg(reinterpret_cast<const uint4 *>(rin + ((size_t)(pos * n_tx + t) * n + w)));
+    for (int rt = warp; rt < n_rx * n_tx; rt += kTPB / 32) {
+      const int r = rt / n_tx, t = rt - r * n_tx;
+      for (int k = lane; k < K; k += 32) {  // delays may repeat: accumulate
+        const int e = rt * K + k;
+        const int d = __ldg(U->delays + k);
+        float2 h0, h1;
+        if (U->step_samples == 0.0) {
+          h0 = __ldg(U->taps + it.idx0 * (uint64_t)per + (uint64_t)e);
+          h1 = __ldg(U->taps + it.idx1 * (uint64_t)per + (uint64_t)e);
+        } else {
+          h0 = tt::tt_anchor(U, a, e, per);
+          h1 = tt::tt_anchor(U, a + 1, e, per);
         }
-        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-        uint32_t re2[2], im2[2];
+        float *v = reinterpret_cast<float *>(&tapd[(r * 4 + t) * 128 + d]);
+        atomicAdd(v + 0, h0.x);
+        atomicAdd(v + 1, h0.y);
+        atomicAdd(v + 2, h1.x - h0.x);
+        atomicAdd(v + 3, h1.y - h0.y);
+      }
+    }
+    __syncthreads();
+    // ---- component tables: 16-bit c-component of the tap of delay 136 - (q + par), per
+    //      (link, c, par) slot of kQW words at shift comp_shift(r, c); two q per 32-bit store ----
+    for (int slot = warp; slot < 16 * 6 * 2; slot += kTPB / 32) {
+      const int tpar = slot & 1, c = (slot >> 1) % 6, link = slot / 12;
+      const int cc = c % 3;
+      uint32_t *dst = reinterpret_cast<uint32_t *>(comp) + slot * kQW + comp_shift(link >> 2, c);
+      for (int qh = lane; qh < 76; qh += 32) {
+        uint32_t pk = 0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const float2 x0 = tt_unpack_iq(vv[2 * h]), x1 = tt_unpack_iq(vv[2 * h + 1]);
-          re2[h] = (uint32_t)to_op<FP16>(x0.x) | ((uint32_t)to_op<FP16>(x1.x) << 16);
-          im2[h] = (uint32_t)to_op<FP16>(x0.y) | ((uint32_t)to_op<FP16>(x1.y) << 16);
+          const int d = 136 - (2 * qh + h + tpar);
+          float v = 0.f;
+          if (d >= 0 && d <= 127) {
+            const float4 tv = tapd[link * 128 + d];
+            const float hr = c < 3 ? tv.x : tv.z, hi = c < 3 ? tv.y : tv.w;
+            v = cc == 0 ? hr : (cc == 1 ? hi : -hi);
+          }
+          pk |= (uint32_t)to_op<FP16>(v) << (16 * h);
         }
-        *reinterpret_cast<uint2 *>(sig + (t * 2 + 0) * kSig + u) = make_uint2(re2[0], re2[1]);
-        *reinterpret_cast<uint2 *>(sig + (t * 2 + 1) * kSig + u) = make_uint2(im2[0], im2[1]);
+        dst[qh] = pk;
       }
     }
     __syncthreads();
-    // ---- component tables: comp[link][c][par][q] = component c of the tap of delay 136 - q
-    //      (zero outside 0..127), par 1 shifted by one element so any 8-run starts 4-byte aligned.
-    //      c: 0 hr(H) 1 hi(H) 2 -hi(H) 3 hr(dH) 4 hi(dH) 5 -hi(dH) ----
-    for (int e = tid; e < 16 * 6 * 2 * 152; e += kTPB) {
-      const int q = e % 152, rest = e / 152, par = rest & 1, c = (rest >> 1) % 6, link = rest / 12;
-      const int d = 136 - (q + par);
-      float v = 0.f;
-      if (d >= 0 && d <= 127) {
-        const float4 tv = tapd[link * 128 + d];
-        const float hr = c < 3 ? tv.x : tv.z, hi = c < 3 ? tv.y : tv.w;
-        const int cc = c % 3;
-        v = cc == 0 ? hr : (cc == 1 ? hi : -hi);
-      }
-      comp[((link * 6 + c) * 2 + par) * (kQW * 2) + comp_shift(link >> 2, c) * 2 + q] = to_op<FP16>(v);
-    }
-    __syncthreads();
-    // ---- tap chunk kc -> buffer b: rows (i, r, part, A|B), 16 K-elements (t, p, j in [16 jc, 16 jc + 16)).
-    //      Value: tap of delay d = i + 128 - j for link (r, t) = comp[.][q = j - i + 8]. ----
-    // Each thread always writes the same (row, k-group) segment of a chunk: precompute the word
-    // address of its component table for every (t, p); a chunk then costs 4 LDS + 1 STS.
-    const int row = tid >> 1, kg = tid & 1;
-    const int ii = row >> 4, nn = row & 15, rr = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
-    const int qoff = kg * 8 - ii + 8, par = qoff & 1;
-    const uint32_t *comp_w = reinterpret_cast<const uint32_t *>(comp);
-    int tbase[8];
-#pragma unroll
-    for (int tp = 0; tp < 8; ++tp) {
-      const int t = tp >> 1, p = tp & 1;
-      // (op, p): (0,0) hr  (0,1) -hi  (1,0) hi  (1,1) hr
-      const int c = ab * 3 + ((op ^ p) == 0 ? 0 : (op == 0 ? 2 : 1));
-      tbase[tp] = (rr < n_rx && t < n_tx)
-                      ? ((rr * 4 + t) * 6 + c) * 2 * kQW + par * kQW + comp_shift(rr, c) + (qoff - par) / 2
-                      : -1;
-    }
-    const int w_off = ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2;
+    // table word bases of this thread's segment for input part p (Tx antenna added per chunk)
+    const int tb0 = rr < n_rx ? ((rr * 4) * 6 + c_p0) * 2 * kQW + par * kQW + comp_shift(rr, c_p0) + (qoff - par) / 2
+                              : -1;
+    const int tb1 = rr < n_rx ? ((rr * 4) * 6 + c_p1) * 2 * kQW + par * kQW + comp_shift(rr, c_p1) + (qoff - par) / 2
+                              : -1;
     auto build_chunk = [&](int kc, int b) {
-      const int tp = kc / kKC, jc = kc % kKC;
-      int base = -1;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q == tp) base = tbase[q];
+      const int tp = kc / kKC, jc = kc - tp * kKC, t = tp >> 1, p = tp & 1;
+      const int base = p ? tb1 : tb0;
       uint4 seg = make_uint4(0u, 0u, 0u, 0u);
       if (base >= 0) {
-        const uint32_t *src = comp_w + base + jc * 8;
+        const uint32_t *src = comp_w + base + t * 12 * kQW + jc * 8;
         seg = make_uint4(src[0], src[1], src[2], src[3]);
       }
       *reinterpret_cast<uint4 *>(wbuf + b * (kN * 16) + w_off) = seg;
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     };
 
-    // chunk kc + 1 is built while the tensor core works through the queued chunks; its ring
-    // slot was last read by chunk kc + 1 - kStages, issued kStages - 1 iterations earlier
-    build_chunk(0, 0);
-    __syncthreads();
-    const uint32_t sig_base = smem_u32(sig), w_base = smem_u32(wbuf);
-    for (int kc = 0; kc < nk; ++kc) {
-      const int b = kc % kStages;
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-        const int tp = kc / kKC, jc = kc % kKC;
-        const uint64_t bd = umma_desc(w_base + (uint32_t)b * kN * 16 * 2, /*lbo K*/ 128, /*sbo N*/ 256);
-        for (int mt = 0; mt < n_tiles; ++mt) {
-          // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
-          const uint32_t a_start = sig_base + (uint32_t)(tp * kSig + mt * kRows * kB + jc * 16) * 2;
-          const uint64_t ad = umma_desc(a_start, /*lbo K*/ 16, /*sbo M*/ 128);
-          umma_f16(tmem + (uint32_t)mt * kN, ad, bd, idesc, kc > 0 ? 1u : 0u);
+    // ---- the symbol in groups of up to 4096 samples (4 tensor-memory tiles each) ----
+    for (int gs = sym0; gs < sym1; gs += kGroup) {
+      const int ge = min(gs + kGroup, sym1);
+      const int blocks = (ge - gs + kB - 1) / kB;
+      const int n_tiles = (blocks + kRows - 1) / kRows;
+      const int nk = n_tx * 2 * kKC;  // K-chunks
+      // signal: sig[t][p][u] = x_{t,p}[gs - 128 + u], 16-bit operands, zero past the slot end;
+      // four samples per load (the window start is 8-aligned and N is a multiple of 8)
+      {
+        const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
+        const int quads = (n_tiles * kRows * kB + kW) / 4;
+        for (int t = 0; t < n_tx; ++t) {
+          for (int qd = tid; qd < quads; qd += kTPB) {
+            const int u = qd * 4;
+            int w = gs - 128 + u, pos = slot_pos;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (w < n) {
+              if (w < 0) {
+                const int back = (-w + n - 1) / n;
+                w += back * n;
+                pos -= back;
+                while (pos < 0) pos += Q;
+              }
+              v = __ldg(reinterpret_cast<const uint4 *>(rin + ((size_t)(pos * n_tx + t) * n + w)));
+            }
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+            uint32_t re2[2], im2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float2 x0 = tt_unpack_iq(vv[2 * h]), x1 = tt_unpack_iq(vv[2 * h + 1]);
+              re2[h] = (uint32_t)to_op<FP16>(x0.x) | ((uint32_t)to_op<FP16>(x1.x) << 16);
+              im2[h] = (uint32_t)to_op<FP16>(x0.y) | ((uint32_t)to_op<FP16>(x1.y) << 16);
+            }
+            *reinterpret_cast<uint2 *>(sig + (t * 2 + 0) * kSig + u) = make_uint2(re2[0], re2[1]);
+            *reinterpret_cast<uint2 *>(sig + (t * 2 + 1) * kSig + u) = make_uint2(im2[0], im2[1]);
+          }
         }
-        umma_commit(smem_u32(&s_mbar[b]));
       }
-      pend_bits |= 1u << b;
-      const int nxt = kc + 1;
-      if (nxt < nk) {
-        const int nb = nxt % kStages;
-        wait_buf(nb);  // the MMAs of chunk nxt - kStages are done with this slot
-        build_chunk(nxt, nb);
+      // tap chunks 0 and 1 into the ring, then two chunks per iteration: issue kc, kc + 1;
+      // build kc + 2, kc + 3 into slots last read by chunks issued kStages - 2 chunks earlier
+      build_chunk(0, 0);
+      if (nk > 1) build_chunk(1, 1);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      __syncthreads();
+      for (int kc = 0; kc < nk; kc += 2) {
+        if (tid == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+          for (int kk = kc; kk < kc + 2 && kk < nk; ++kk) {
+            const int b = kk % kStages, tp = kk / kKC, jc = kk - tp * kKC;
+            const uint64_t bd = umma_desc(w_base + (uint32_t)b * kN * 16 * 2, /*lbo K*/ 128, /*sbo N*/ 256);
+            for (int mt = 0; mt < n_tiles; ++mt) {
+              // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
+              const uint32_t a_start = sig_base + (uint32_t)(tp * kSig + mt * kRows * kB + jc * 16) * 2;
+              const uint64_t ad = umma_desc(a_start, /*lbo K*/ 16, /*sbo M*/ 128);
+              umma_f16(tmem + (uint32_t)mt * kN, ad, bd, idesc, kk > 0 ? 1u : 0u);
+            }
+            umma_commit(smem_u32(&s_mbar[b]));
+          }
+        }
+        for (int kk = kc; kk < kc + 2 && kk < nk; ++kk) pend_bits |= 1u << (kk % kStages);
+        for (int kk = kc + 2; kk < kc + 4 && kk < nk; ++kk) {
+          const int nb = kk % kStages;
+          wait_buf(nb);  // the MMAs of chunk kk - kStages are done with this slot
+          build_chunk(kk, nb);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (s_abort) break;
       }
+      for (int b = 0; b < kStages; ++b) wait_buf(b);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
       __syncthreads();
       if (s_abort) break;
-    }
-    for (int b = 0; b < kStages; ++b) wait_buf(b);
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    __syncthreads();
-    if (s_abort) break;
-    // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (block rows) and samples
-    //      i in [4 (w / 4), 4 (w / 4) + 4) of each block; AWGN per pair of samples (one Philox block) ----
-    {
-      const int quad = warp & 3, ihalf = warp >> 2;
-      for (int mt = 0; mt < n_tiles; ++mt) {
-        const int c = mt * kRows + quad * 32 + lane;
-        for (int i = ihalf * 4; i < ihalf * 4 + 4; i += 2) {
-          float v0[16], v1[16];
-          const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + i * 16);
-          tmem_ld16(tbase, v0);
-          tmem_ld16(tbase + 16, v1);
-          const int m = it.m_start + c * kB + i;  // even: pairs (m, m + 1) share a Philox block
-          if (m < it.m_end) {
-            const float rl = 1.0f / (float)(sym1 - sym0);
-            const float tau0 = (float)(m - sym0) * rl, tau1 = (float)(m + 1 - sym0) * rl;
-            const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
+      // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (block rows) and samples
+      //      i in [4 (w / 4), 4 (w / 4) + 4) of each block; AWGN per pair of samples (one Philox block) ----
+      {
+        const int quad = warp & 3, ihalf = warp >> 2;
+        const float rl = 1.0f / (float)(sym1 - sym0);
+        for (int mt = 0; mt < n_tiles; ++mt) {
+          const int c = mt * kRows + quad * 32 + lane;
+          for (int i = ihalf * 4; i < ihalf * 4 + 4; i += 2) {
+            float v0[16], v1[16];
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + i * 16);
+            tmem_ld16(tbase, v0);
+            tmem_ld16(tbase + 16, v1);
+            const int m = gs + c * kB + i;  // even: pairs (m, m + 1) share a Philox block
+            if (m < ge) {
+              const float tau0 = (float)(m - sym0) * rl, tau1 = (float)(m + 1 - sym0) * rl;
+              const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              if (r >= n_rx) break;
-              float2 y0 = make_float2(fmaf(tau0, v0[r * 4 + 1], v0[r * 4 + 0]), fmaf(tau0, v0[r * 4 + 3], v0[r * 4 + 2]));
-              float2 y1 = make_float2(fmaf(tau1, v1[r * 4 + 1], v1[r * 4 + 0]), fmaf(tau1, v1[r * 4 + 3], v1[r * 4 + 2]));
-              if (U->noise_std > 0.f) tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y0, y1);
-              const size_t o = (size_t)(slot_pos * n_rx + r) * n + m;
-              if (U->out_f32) {
-                *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(U->ring_out) + o) =
-                    make_float4(y0.x, y0.y, y1.x, y1.y);
-              } else {
-                *reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(U->ring_out) + o) =
-                    make_uint2(tt_pack_iq(y0.x, y0.y), tt_pack_iq(y1.x, y1.y));
+              for (int r = 0; r < 4; ++r) {
+                if (r >= n_rx) break;
+                float2 y0 = make_float2(fmaf(tau0, v0[r * 4 + 1], v0[r * 4 + 0]), fmaf(tau0, v0[r * 4 + 3], v0[r * 4 + 2]));
+                float2 y1 = make_float2(fmaf(tau1, v1[r * 4 + 1], v1[r * 4 + 0]), fmaf(tau1, v1[r * 4 + 3], v1[r * 4 + 2]));
+                if (U->noise_std > 0.f) tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y0, y1);
+                const size_t o = (size_t)(slot_pos * n_rx + r) * n + m;
+                if (U->out_f32) {
+                  *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(U->ring_out) + o) =
+                      make_float4(y0.x, y0.y, y1.x, y1.y);
+                } else {
+                  *reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(U->ring_out) + o) =
+                      make_uint2(tt_pack_iq(y0.x, y0.y), tt_pack_iq(y1.x, y1.y));
+                }
               }
             }
           }
         }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+      __syncthreads();
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-    __syncthreads();
+    if (s_abort) break;
   }
   __syncthreads();
   for (int b = 0; b < kStages; ++b) wait_buf(b);
@@ -425,9 +425,8 @@ __global__ void __launch_bounds__(kTPB, 1)
 size_t tt_tc_smem_bytes() { return (size_t)kSmemBytes; }
 int tt_tc_max_delay() { return kMaxDelayTC; }
 int tt_tc_items_per_slot(const int32_t *sym_len, int nsym) {
-  int items = 0;
-  for (int j = 0; j < nsym; ++j) items += (sym_len[j] + kGroup - 1) / kGroup;
-  return items;
+  (void)sym_len;
+  return nsym;  // one work item per symbol; its samples run in groups of up to 4096
 }
 
 cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, cudaStream_t st) {
