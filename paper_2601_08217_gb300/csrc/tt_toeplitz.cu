@@ -105,17 +105,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
   return ok != 0;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
+// 16 consecutive accumulator columns of this thread's lane; completes at tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 template <bool FP16>
 __device__ __forceinline__ uint16_t to_op(float v) {
@@ -243,6 +241,7 @@ __global__ void __launch_bounds__(kTPB, 1)
     __syncthreads();
     for (int rt = warp; rt < n_rx * n_tx; rt += kTPB / 32) {
       const int r = rt / n_tx, t = rt - r * n_tx;
+#pragma unroll 4
       for (int k = lane; k < K; k += 32) {  // delays may repeat: accumulate
         const int e = rt * K + k;
         const int d = __ldg(U->delays + k);
@@ -313,6 +312,7 @@ __global__ void __launch_bounds__(kTPB, 1)
         const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
         const int quads = (n_tiles * kRows * kB + kW) / 4;
         for (int t = 0; t < n_tx; ++t) {
+#pragma unroll 4
           for (int qd = tid; qd < quads; qd += kTPB) {
             const int u = qd * 4;
             int w = gs - 128 + u, pos = slot_pos;
@@ -381,11 +381,14 @@ __global__ void __launch_bounds__(kTPB, 1)
         const float rl = 1.0f / (float)(sym1 - sym0);
         for (int mt = 0; mt < n_tiles; ++mt) {
           const int c = mt * kRows + quad * 32 + lane;
-          for (int i = ihalf * 4; i < ihalf * 4 + 4; i += 2) {
-            float v0[16], v1[16];
-            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + i * 16);
-            tmem_ld16(tbase, v0);
-            tmem_ld16(tbase + 16, v1);
+          uint32_t raw4[4][16];  // this warp's four samples of the block, 16 columns each
+          const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + ihalf * 4 * 16);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) tmem_ld16(tbase + (uint32_t)q * 16, raw4[q]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int q = 0; q < 4; q += 2) {
+            const int i = ihalf * 4 + q;
             const int m = gs + c * kB + i;  // even: pairs (m, m + 1) share a Philox block
             if (m < ge) {
               const float tau0 = (float)(m - sym0) * rl, tau1 = (float)(m + 1 - sym0) * rl;
@@ -393,8 +396,11 @@ __global__ void __launch_bounds__(kTPB, 1)
 #pragma unroll
               for (int r = 0; r < 4; ++r) {
                 if (r >= n_rx) break;
-                float2 y0 = make_float2(fmaf(tau0, v0[r * 4 + 1], v0[r * 4 + 0]), fmaf(tau0, v0[r * 4 + 3], v0[r * 4 + 2]));
-                float2 y1 = make_float2(fmaf(tau1, v1[r * 4 + 1], v1[r * 4 + 0]), fmaf(tau1, v1[r * 4 + 3], v1[r * 4 + 2]));
+                const uint32_t *v0 = raw4[q], *v1 = raw4[q + 1];
+                float2 y0 = make_float2(fmaf(tau0, __uint_as_float(v0[r * 4 + 1]), __uint_as_float(v0[r * 4 + 0])),
+                                        fmaf(tau0, __uint_as_float(v0[r * 4 + 3]), __uint_as_float(v0[r * 4 + 2])));
+                float2 y1 = make_float2(fmaf(tau1, __uint_as_float(v1[r * 4 + 1]), __uint_as_float(v1[r * 4 + 0])),
+                                        fmaf(tau1, __uint_as_float(v1[r * 4 + 3]), __uint_as_float(v1[r * 4 + 2])));
                 if (U->noise_std > 0.f) tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y0, y1);
                 const size_t o = (size_t)(slot_pos * n_rx + r) * n + m;
                 if (U->out_f32) {
