@@ -37,7 +37,7 @@ METRIC = "UE-slots/s and GMAC/s at 1 GB300 vs plain form; p99 slot latency vs 0.
 # DRAM traffic per full launch from the ncu capture summarised in
 # profiles/tt_conv_fp32_kernel_40mhz_16ue.md, valid only for the kernel source it was taken on.
 TRAFFIC_BYTES = 3.52e9
-TRAFFIC_KERNEL_SHA = "ddb7e2023d2e3c33"
+TRAFFIC_KERNEL_SHA = "e147f011d762eb67"
 WORKLOAD = ("16 UEs SISO, 40 MHz (30720 samples/slot), 1000 slots each, 24 taps (delays <= 256), "
             "100 Hz Jakes, AWGN 20 dB, int16 IQ, FP32 accumulation")
 
@@ -53,26 +53,31 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons, sampled every 20 ms from before the warm-up
+    until after the timed region; the summary keeps the samples stamped inside the region."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device: int):
         self.device = device
         self.proc = None
+        self.rows = []
+        self.window = None
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
-    def __exit__(self, *a):
-        self.rows = []
+    def region(self, t_begin: float, t_end: float):
+        self.window = (t_begin, t_end)
+
+    def stop(self):
         if self.proc is None:
             return
         self.proc.terminate()
@@ -81,20 +86,32 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        import datetime
         for line in out.splitlines():
             f = [v.strip() for v in line.split(",")]
-            if len(f) >= 9:
-                self.rows.append(f)
+            if len(f) < 10:
+                continue
+            try:
+                t = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            self.rows.append((t, f[1:]))
 
     def summary(self):
-        if not getattr(self, "rows", None):
+        rows = self.rows
+        if rows and self.window:
+            a, b = self.window
+            inside = [r for r in rows if a - 0.02 <= r[0] <= b + 0.02]
+            rows = inside or sorted(rows, key=lambda r: abs(r[0] - 0.5 * (a + b)))[:1]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        f = [r[1] for r in rows]
+        sm = [float(x[1]) for x in f if x[1].replace(".", "").isdigit()]
+        mx = [float(x[2]) for x in f if x[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        reasons = sorted({n for x in f for n, v in zip(names, x[5:9]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 def make_workload(rank: int):
@@ -158,24 +175,30 @@ def run_ours(args, rank, world, device):
             tc.tt_chan_release_slots(ch.h, s0, N_SLOTS)
         next_slot[0] = s0 + N_SLOTS
 
-    for _ in range(args.warmup):
-        step()
-    eng.sync()
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    launches0 = eng.stats()["launches"]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(device) as clk:
+    clk = ClockSampler(device).start()
+    try:
+        for _ in range(args.warmup):
+            step()
+        eng.sync()
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        launches0 = eng.stats()["launches"]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        w0 = time.time()
         t0.record(stream)
         for i in range(args.steps):
             step(kev[i])
         t1.record(stream)
         eng.sync()
         torch.cuda.synchronize()
+        clk.region(w0, time.time())
+        time.sleep(0.05)
+    finally:
+        clk.stop()
     if world > 1:
         torch.distributed.barrier()
     launches = eng.stats()["launches"] - launches0
@@ -418,7 +441,7 @@ def main():
     global N_SLOTS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--persistent", type=int, default=1, help="1: CTAs claim work items from a device counter")
