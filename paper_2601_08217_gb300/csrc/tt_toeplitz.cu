@@ -50,14 +50,18 @@ constexpr uint32_t kTmemCols = 512;
 constexpr long long kSpinLimit = 1ll << 26;
 
 constexpr int kQW = 128;              // words per component table (q = j - i + 8 in [1, 151] needs 76, plus shift)
-constexpr int kStages = 4;            // tap-chunk ring: chunks queued ahead of the tensor core
+constexpr int kStages = 12;           // tap-chunk ring: chunks queued ahead of the tensor core
+constexpr int kPer = 4;               // chunks issued (and built) per step; waits reach back two steps
 
-// shared memory layout (bytes)
+// shared memory layout (bytes).  The dense delay table is only read while the component tables
+// are built, before any signal is staged for the item, so it shares the signal's space.
 constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
+constexpr int kOffTap = 0;                               // [16 links][128 delays] float4 (H, dH)
 constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // kStages x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
-constexpr int kOffTap = kOffW + kStages * kN * 16 * 2;   // [16 links][128 delays] float4 (H, dH)
-constexpr int kOffComp = kOffTap + 16 * 128 * 16;        // [16 links][6 comps][2 parities][kQW words]
+constexpr int kOffComp = kOffW + kStages * kN * 16 * 2;  // [16 links][6 comps][2 parities][kQW words]
 constexpr int kSmemUsed = kOffComp + 16 * 6 * 2 * kQW * 4;
+static_assert(16 * 128 * 16 <= 4 * 2 * kSig * 2, "delay table must fit in the signal area");
+static_assert(kStages % kPer == 0 && kStages >= 3 * kPer, "ring holds the chunks of three steps");
 
 // Word shift of component table (r, c) inside its slot.  A warp building one tap chunk reads,
 // for fixed (t, p), the 16 tables of (r, output part, A|B), one 16-byte run each at the same q
@@ -289,8 +293,10 @@ __global__ void __launch_bounds__(kTPB, 1)
                               : -1;
     const int tb1 = rr < n_rx ? ((rr * 4) * 6 + c_p1) * 2 * kQW + par * kQW + comp_shift(rr, c_p1) + (qoff - par) / 2
                               : -1;
+    // K-chunks jc < jlo of every (t, p) window hold no tap: j = i + 128 - d >= 128 - d_max
+    const int jlo = (128 - U->d_max) >> 4, kpc = kKC - jlo;
     auto build_chunk = [&](int kc, int b) {
-      const int tp = kc / kKC, jc = kc - tp * kKC, t = tp >> 1, p = tp & 1;
+      const int tp = kc / kpc, jc = jlo + (kc - tp * kpc), t = tp >> 1, p = tp & 1;
       const int base = p ? tb1 : tb0;
       uint4 seg = make_uint4(0u, 0u, 0u, 0u);
       if (base >= 0) {
@@ -305,28 +311,32 @@ __global__ void __launch_bounds__(kTPB, 1)
       const int ge = min(gs + kGroup, sym1);
       const int blocks = (ge - gs + kB - 1) / kB;
       const int n_tiles = (blocks + kRows - 1) / kRows;
-      const int nk = n_tx * 2 * kKC;  // K-chunks
+      const int nk = n_tx * 2 * kpc;  // K-chunks
       // signal: sig[t][p][u] = x_{t,p}[gs - 128 + u], 16-bit operands, zero past the slot end;
       // four samples per load (the window start is 8-aligned and N is a multiple of 8)
       {
         const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
         const int quads = (n_tiles * kRows * kB + kW) / 4;
-        for (int t = 0; t < n_tx; ++t) {
-#pragma unroll 4
-          for (int qd = tid; qd < quads; qd += kTPB) {
-            const int u = qd * 4;
-            int w = gs - 128 + u, pos = slot_pos;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (w < n) {
-              if (w < 0) {
-                const int back = (-w + n - 1) / n;
-                w += back * n;
-                pos -= back;
-                while (pos < 0) pos += Q;
-              }
-              v = __ldg(reinterpret_cast<const uint4 *>(rin + ((size_t)(pos * n_tx + t) * n + w)));
-            }
-            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll 2
+        for (int qd = tid; qd < quads; qd += kTPB) {
+          const int u = qd * 4;
+          int w = gs - 128 + u, pos = slot_pos;
+          const bool live = w < n;
+          if (live && w < 0) {
+            const int back = (-w + n - 1) / n;
+            w += back * n;
+            pos -= back;
+            while (pos < 0) pos += Q;
+          }
+          const uint4 *src = reinterpret_cast<const uint4 *>(rin + ((size_t)pos * n_tx * n + w));
+          uint4 v[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            v[t] = (live && t < n_tx) ? __ldg(src + (size_t)t * (n / 4)) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (t >= n_tx) break;
+            const uint32_t vv[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
             uint32_t re2[2], im2[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -339,33 +349,43 @@ __global__ void __launch_bounds__(kTPB, 1)
           }
         }
       }
-      // tap chunks 0 and 1 into the ring, then two chunks per iteration: issue kc, kc + 1;
-      // build kc + 2, kc + 3 into slots last read by chunks issued kStages - 2 chunks earlier
-      build_chunk(0, 0);
-      if (nk > 1) build_chunk(1, 1);
+      // the first kPer tap chunks into the ring; then per step: issue chunks [kc, kc + kPer) and
+      // build [kc + kPer, kc + 2 kPer) into the slots last read by the chunks issued two steps before
+      for (int kk = 0; kk < kPer && kk < nk; ++kk) build_chunk(kk, kk);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       __syncthreads();
-      for (int kc = 0; kc < nk; kc += 2) {
+      int bi = 0;  // ring slot of chunk kc
+      for (int kc = 0; kc < nk; kc += kPer) {
         if (tid == 0) {
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-          for (int kk = kc; kk < kc + 2 && kk < nk; ++kk) {
-            const int b = kk % kStages, tp = kk / kKC, jc = kk - tp * kKC;
+          int tp = kc / kpc, jc = jlo + (kc - tp * kpc), b = bi;
+          for (int kk = kc; kk < kc + kPer && kk < nk; ++kk) {
             const uint64_t bd = umma_desc(w_base + (uint32_t)b * kN * 16 * 2, /*lbo K*/ 128, /*sbo N*/ 256);
+            // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
+            const uint32_t a0 = sig_base + (uint32_t)(tp * kSig + jc * 16) * 2;
             for (int mt = 0; mt < n_tiles; ++mt) {
-              // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
-              const uint32_t a_start = sig_base + (uint32_t)(tp * kSig + mt * kRows * kB + jc * 16) * 2;
-              const uint64_t ad = umma_desc(a_start, /*lbo K*/ 16, /*sbo M*/ 128);
+              const uint64_t ad = umma_desc(a0 + (uint32_t)(mt * kRows * kB * 2), /*lbo K*/ 16, /*sbo M*/ 128);
               umma_f16(tmem + (uint32_t)mt * kN, ad, bd, idesc, kk > 0 ? 1u : 0u);
             }
             umma_commit(smem_u32(&s_mbar[b]));
+            if (++jc == kKC) { jc = jlo; ++tp; }
+            if (++b == kStages) b = 0;
           }
         }
-        for (int kk = kc; kk < kc + 2 && kk < nk; ++kk) pend_bits |= 1u << (kk % kStages);
-        for (int kk = kc + 2; kk < kc + 4 && kk < nk; ++kk) {
-          const int nb = kk % kStages;
-          wait_buf(nb);  // the MMAs of chunk kk - kStages are done with this slot
-          build_chunk(kk, nb);
+        {
+          int b = bi;
+          for (int kk = kc; kk < kc + kPer && kk < nk; ++kk) {
+            pend_bits |= 1u << b;
+            if (++b == kStages) b = 0;
+          }
+          for (int kk = kc + kPer; kk < kc + 2 * kPer && kk < nk; ++kk) {
+            wait_buf(b);  // the MMAs of chunk kk - kStages are done with this slot
+            build_chunk(kk, b);
+            if (++b == kStages) b = 0;
+          }
         }
+        bi += kPer;
+        if (bi >= kStages) bi -= kStages;
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (s_abort) break;
