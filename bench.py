@@ -367,9 +367,11 @@ def run_precision(args, device, n_ues=64, n_slots=20, warmup=3, forms=("bf16_tc"
     out = {}
     n = specs[0].n
     # tensor-core MMAs issued per slot: per symbol, groups of <= 4096 samples in tiles of 1024
-    # samples (128 block rows of 8), each tile 2 x 4 x 9 K-chunks of a 128x128x16 MMA
+    # samples (128 block rows of 8), each tile 2 x 4 x kc K-chunks of a 128x128x16 MMA, where the
+    # 144-wide window per (Tx, part) skips the 16-wide chunks no delay reaches: kc = 9 - (128 - d_max) // 16
     tiles = sum(-(-min(4096, L - g) // 1024) for L in specs[0].symbol_len for g in range(0, L, 4096))
-    exec_flop = n_ues * tiles * (4 * 2 * 9) * 128 * 128 * 16 * 2
+    kc = 9 - (128 - int(np.max(specs[0].delays))) // 16
+    exec_flop = n_ues * tiles * (4 * 2 * kc) * 128 * 128 * 16 * 2
     useful_flop = n_ues * n * 16 * 96 * 8                        # complex MACs per slot
     for name, prec in (("bf16_tc", tc.TT_BF16_TC), ("fp16_tc", tc.TT_FP16_TC), ("fp32", tc.TT_FP32)):
         if name not in forms:

@@ -36,47 +36,50 @@
 
 namespace {
 
-constexpr int kTPB = 256;
+constexpr int kBuildWarps = 8;                  // stage, build tap chunks, epilogue
+constexpr int kTPB = (kBuildWarps + 1) * 32;    // + one warp that issues the MMAs
+constexpr int kBuilders = kBuildWarps * 32;
 constexpr int kB = 8;                 // output samples per block row (16-byte rows of the signal view)
 constexpr int kRows = 128;            // block rows per MMA tile (M): 1024 samples
 constexpr int kTilesMax = 4;          // tiles accumulating at once: 4 x 128 TMEM columns
-constexpr int kGroup = kRows * kB * kTilesMax;  // samples per work item (4096)
+constexpr int kGroup = kRows * kB * kTilesMax;  // samples per group (4096)
 constexpr int kMaxDelayTC = 127;
 constexpr int kW = 144;               // window per (t, p): j in [0, 135) used, padded to 9 K-chunks of 16
 constexpr int kKC = kW / 16;          // K-chunks per (t, p)
 constexpr int kN = 128;               // D columns: (i, r, part, A|B)
 constexpr int kSig = kGroup + kW;     // staged samples per (t, p)
 constexpr uint32_t kTmemCols = 512;
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr long long kSpinLimit = 1ll << 24;
 
 constexpr int kQW = 128;              // words per component table (q = j - i + 8 in [1, 151] needs 76, plus shift)
-constexpr int kStages = 12;           // tap-chunk ring: chunks queued ahead of the tensor core
-constexpr int kPer = 4;               // chunks issued (and built) per step; waits reach back two steps
+constexpr int kComps = 4;             // hr, hi of H and of dH; -hi is hi with the sign bits flipped
+constexpr int kPer = 4;               // tap chunks per pipeline step
+constexpr int kSteps = 3;             // steps in the ring: builders run up to two steps ahead of the MMAs
+constexpr int kStages = kPer * kSteps;
+constexpr int kChunkBytes = kN * 16 * 2;
 
 // shared memory layout (bytes).  The dense delay table is only read while the component tables
 // are built, before any signal is staged for the item, so it shares the signal's space.
 constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
 constexpr int kOffTap = 0;                               // [16 links][128 delays] float4 (H, dH)
 constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // kStages x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
-constexpr int kOffComp = kOffW + kStages * kN * 16 * 2;  // [16 links][6 comps][2 parities][kQW words]
-constexpr int kSmemUsed = kOffComp + 16 * 6 * 2 * kQW * 4;
+constexpr int kOffComp = kOffW + kStages * kChunkBytes;  // [16 links][kComps][2 parities][kQW words]
+constexpr int kSmemUsed = kOffComp + 16 * kComps * 2 * kQW * 4;
 static_assert(16 * 128 * 16 <= 4 * 2 * kSig * 2, "delay table must fit in the signal area");
-static_assert(kStages % kPer == 0 && kStages >= 3 * kPer, "ring holds the chunks of three steps");
 
-// Word shift of component table (r, c) inside its slot.  A warp building one tap chunk reads,
-// for fixed (t, p), the 16 tables of (r, output part, A|B), one 16-byte run each at the same q
-// (and q + 8 for the second K-group).  Shift 8 r + g(c) with g a bijection of the four tables
-// of either input part puts those 32 runs on 32 distinct banks.
-__host__ __device__ constexpr int comp_shift(int r, int c) {
-  return 8 * r + (c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 1 : c == 3 ? 2 : c == 4 ? 3 : 3);
-}
+// Word shift of component table (r, c) inside its slot.  A builder warp handles one sample i of the
+// block and all 16 rows (r, output part, A|B) for both K-groups; for either input part the four
+// tables of one r are a permutation of c = 0..3, so shift 8 r + c puts the warp's 32 words of
+// every 32-bit load on 32 distinct banks.
+__host__ __device__ constexpr int comp_shift(int r, int c) { return 8 * r + c; }
 // More than half an SM's shared memory: one CTA per SM, so no two CTAs ever compete for the
 // 512 tensor-memory columns each one allocates.
 constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: start, leading/stride byte offsets, no swizzle.
+// Shared-memory matrix descriptor: start, leading/stride byte offsets, no swizzle.  The start
+// address sits in the low 14 bits (16-byte units), so adding (bytes >> 4) moves the start.
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
@@ -99,6 +102,10 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
@@ -108,6 +115,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
       : "memory");
   return ok != 0;
 }
+
+// builder-warp barrier (named barrier 1): the MMA warp is not stopped
+__device__ __forceinline__ void builders_sync() { asm volatile("bar.sync 1, %0;\n" ::"n"(kBuilders) : "memory"); }
 
 // 16 consecutive accumulator columns of this thread's lane; completes at tmem_wait_ld().
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
@@ -131,19 +141,21 @@ struct TCItem {
   int ue, sym, valid;
 };
 
-// Bounded wait on an MMA-completion barrier: lane 0 polls, the warp follows its verdict.
-__device__ __forceinline__ int warp_wait(uint32_t mbar, uint32_t phase, int *status, int *abort_flag) {
-  int done = 0;
+// Bounded wait on an mbarrier phase by the whole warp: lane 0 polls, the warp follows its verdict.
+// Once any wait of the CTA has expired (abort flag), every later wait returns at once, so each
+// role runs through its remaining steps without blocking and the CTA reaches its exit.
+__device__ __forceinline__ void warp_wait(uint32_t mbar, uint32_t phase, int *status, volatile int *abort_flag) {
   if ((threadIdx.x & 31) == 0) {
     long long spins = 0;
-    while (!(done = mbar_try_wait(mbar, phase)) && ++spins < kSpinLimit) {
+    bool done = false;
+    while (!(done = mbar_try_wait(mbar, phase)) && !*abort_flag && ++spins < kSpinLimit) {
     }
-    if (!done) {
+    if (!done && !*abort_flag) {
       atomicExch(status, 1);
       *abort_flag = 1;
     }
   }
-  return __shfl_sync(0xFFFFFFFFu, done, 0);
+  __syncwarp();
 }
 
 }  // namespace
@@ -153,7 +165,10 @@ __global__ void __launch_bounds__(kTPB, 1)
     tt_toeplitz_tc_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                           uint32_t total_items, uint32_t *__restrict__ counter, int *__restrict__ status) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) unsigned long long s_mbar[kStages];
+  __shared__ __align__(8) unsigned long long s_full[kSteps];   // builders -> MMA warp: step's chunks written
+  __shared__ __align__(8) unsigned long long s_empty[kSteps];  // MMA completion -> builders: step's slots free
+  __shared__ __align__(8) unsigned long long s_acc;            // MMA completion of a group -> epilogue
+  __shared__ __align__(8) unsigned long long s_tfree;          // epilogue done with the accumulators -> MMA warp
   __shared__ uint32_t s_tmem;
   __shared__ TCItem s_it;
   __shared__ int s_abort;
@@ -162,7 +177,8 @@ __global__ void __launch_bounds__(kTPB, 1)
   uint16_t *sig = reinterpret_cast<uint16_t *>(sm + kOffSig);
   uint16_t *wbuf = reinterpret_cast<uint16_t *>(sm + kOffW);
   float4 *tapd = reinterpret_cast<float4 *>(sm + kOffTap);
-  uint16_t *comp = reinterpret_cast<uint16_t *>(sm + kOffComp);
+  uint32_t *comp_w = reinterpret_cast<uint32_t *>(sm + kOffComp);
+  volatile int *abort_flag = &s_abort;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
@@ -170,8 +186,12 @@ __global__ void __launch_bounds__(kTPB, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   if (tid == 0) {
-    for (int b = 0; b < kStages; ++b)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_mbar[b])));
+    for (int b = 0; b < kSteps; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&s_full[b])), "n"(kBuildWarps));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_empty[b])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_acc)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&s_tfree)), "n"(kBuildWarps));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     s_abort = 0;
@@ -180,13 +200,6 @@ __global__ void __launch_bounds__(kTPB, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = s_tmem;
-  uint32_t ph_bits = 0u, pend_bits = 0u;  // per ring slot: barrier phase, commit not yet waited for
-  auto wait_buf = [&](int b) {
-    if (!((pend_bits >> b) & 1u)) return;
-    warp_wait(smem_u32(&s_mbar[b]), (ph_bits >> b) & 1u, status, &s_abort);
-    ph_bits ^= 1u << b;
-    pend_bits &= ~(1u << b);
-  };
 
   // idesc: D = F32, A/B = F16 (0) or BF16 (1), both K-major, N = 128, M = 128
   const uint32_t fmt = FP16 ? 0u : 1u;
@@ -194,19 +207,21 @@ __global__ void __launch_bounds__(kTPB, 1)
       (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
   const uint32_t sig_base = smem_u32(sig), w_base = smem_u32(wbuf);
 
-  // this thread's fixed segment of every tap chunk: row (i, r, part, A|B), k-group kg
+  // this builder thread's fixed segment of every tap chunk: row (i, r, part, A|B), k-group kg
   const int row = tid >> 1, kg = tid & 1;
   const int ii = row >> 4, nn = row & 15, rr = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
   const int qoff = kg * 8 - ii + 8, par = qoff & 1;
-  // (op, p): (0,0) hr  (0,1) -hi  (1,0) hi  (1,1) hr
-  const int c_p0 = ab * 3 + (op == 0 ? 0 : 1), c_p1 = ab * 3 + (op == 0 ? 2 : 0);
+  // (op, p) -> component: (0,0) hr, (0,1) -hi, (1,0) hi, (1,1) hr
+  const int c_p0 = ab * 2 + (op == 0 ? 0 : 1), c_p1 = ab * 2 + (op == 0 ? 1 : 0);
+  const uint32_t neg_p1 = op == 0 ? 0x80008000u : 0u;
   const int w_off = ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2;
-  const uint32_t *comp_w = reinterpret_cast<const uint32_t *>(comp);
 
+  uint32_t gstep = 0;  // pipeline steps since launch (both roles count them alike)
+  uint32_t ggroup = 0; // accumulator groups since launch
   uint32_t next_static = blockIdx.x;
   for (;;) {
     if (tid == 0) {
-      const uint32_t item = counter ? atomicAdd(counter, 1u) : next_static;
+      const uint32_t item = *abort_flag ? total_items : (counter ? atomicAdd(counter, 1u) : next_static);
       TCItem it{};
       it.valid = 0;
       if (item < total_items) {
@@ -232,218 +247,236 @@ __global__ void __launch_bounds__(kTPB, 1)
     next_static += gridDim.x;
     __syncthreads();
     const TCItem it = s_it;
-    if (!it.valid || s_abort) break;
+    if (!it.valid) break;
     const TTUEDesc *__restrict__ U = ues + it.ue;
-    const int n = U->n, n_tx = U->n_tx, n_rx = U->n_rx, K = U->n_taps, Q = U->ring_q, nsym = U->nsym;
+    const int n = U->n, n_tx = U->n_tx, n_rx = U->n_rx, Q = U->ring_q;
     const int sym0 = U->sym_start[it.sym], sym1 = U->sym_start[it.sym + 1];
-    const int per = n_rx * n_tx * K;
     const int slot_pos = (int)(it.slot % (uint64_t)Q);
-    const uint64_t a = it.slot * (uint64_t)nsym + (uint64_t)it.sym;
-
-    // ---- dense delay table of this symbol: tapd[r*4+t][d] = (H, dH) ----
-    for (int e = tid; e < 16 * 128; e += kTPB) tapd[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
-    for (int rt = warp; rt < n_rx * n_tx; rt += kTPB / 32) {
-      const int r = rt / n_tx, t = rt - r * n_tx;
-#pragma unroll 4
-      for (int k = lane; k < K; k += 32) {  // delays may repeat: accumulate
-        const int e = rt * K + k;
-        const int d = __ldg(U->delays + k);
-        float2 h0, h1;
-        if (U->step_samples == 0.0) {
-          h0 = __ldg(U->taps + it.idx0 * (uint64_t)per + (uint64_t)e);
-          h1 = __ldg(U->taps + it.idx1 * (uint64_t)per + (uint64_t)e);
-        } else {
-          h0 = tt::tt_anchor(U, a, e, per);
-          h1 = tt::tt_anchor(U, a + 1, e, per);
-        }
-        float *v = reinterpret_cast<float *>(&tapd[(r * 4 + t) * 128 + d]);
-        atomicAdd(v + 0, h0.x);
-        atomicAdd(v + 1, h0.y);
-        atomicAdd(v + 2, h1.x - h0.x);
-        atomicAdd(v + 3, h1.y - h0.y);
-      }
-    }
-    __syncthreads();
-    // ---- component tables: 16-bit c-component of the tap of delay 136 - (q + par), per
-    //      (link, c, par) slot of kQW words at shift comp_shift(r, c); two q per 32-bit store ----
-    for (int slot = warp; slot < 16 * 6 * 2; slot += kTPB / 32) {
-      const int tpar = slot & 1, c = (slot >> 1) % 6, link = slot / 12;
-      const int cc = c % 3;
-      uint32_t *dst = reinterpret_cast<uint32_t *>(comp) + slot * kQW + comp_shift(link >> 2, c);
-      for (int qh = lane; qh < 76; qh += 32) {
-        uint32_t pk = 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int d = 136 - (2 * qh + h + tpar);
-          float v = 0.f;
-          if (d >= 0 && d <= 127) {
-            const float4 tv = tapd[link * 128 + d];
-            const float hr = c < 3 ? tv.x : tv.z, hi = c < 3 ? tv.y : tv.w;
-            v = cc == 0 ? hr : (cc == 1 ? hi : -hi);
-          }
-          pk |= (uint32_t)to_op<FP16>(v) << (16 * h);
-        }
-        dst[qh] = pk;
-      }
-    }
-    __syncthreads();
-    // table word bases of this thread's segment for input part p (Tx antenna added per chunk)
-    const int tb0 = rr < n_rx ? ((rr * 4) * 6 + c_p0) * 2 * kQW + par * kQW + comp_shift(rr, c_p0) + (qoff - par) / 2
-                              : -1;
-    const int tb1 = rr < n_rx ? ((rr * 4) * 6 + c_p1) * 2 * kQW + par * kQW + comp_shift(rr, c_p1) + (qoff - par) / 2
-                              : -1;
     // K-chunks jc < jlo of every (t, p) window hold no tap: j = i + 128 - d >= 128 - d_max
     const int jlo = (128 - U->d_max) >> 4, kpc = kKC - jlo;
-    auto build_chunk = [&](int kc, int b) {
-      const int tp = kc / kpc, jc = jlo + (kc - tp * kpc), t = tp >> 1, p = tp & 1;
-      const int base = p ? tb1 : tb0;
-      uint4 seg = make_uint4(0u, 0u, 0u, 0u);
-      if (base >= 0) {
-        const uint32_t *src = comp_w + base + t * 12 * kQW + jc * 8;
-        seg = make_uint4(src[0], src[1], src[2], src[3]);
-      }
-      *reinterpret_cast<uint4 *>(wbuf + b * (kN * 16) + w_off) = seg;
-    };
+    const int nk = n_tx * 2 * kpc;  // K-chunks per group
+    const int steps = (nk + kPer - 1) / kPer;
 
-    // ---- the symbol in groups of up to 4096 samples (4 tensor-memory tiles each) ----
-    for (int gs = sym0; gs < sym1; gs += kGroup) {
-      const int ge = min(gs + kGroup, sym1);
-      const int blocks = (ge - gs + kB - 1) / kB;
-      const int n_tiles = (blocks + kRows - 1) / kRows;
-      const int nk = n_tx * 2 * kpc;  // K-chunks
-      // signal: sig[t][p][u] = x_{t,p}[gs - 128 + u], 16-bit operands, zero past the slot end;
-      // four samples per load (the window start is 8-aligned and N is a multiple of 8)
-      {
-        const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
-        const int quads = (n_tiles * kRows * kB + kW) / 4;
-#pragma unroll 2
-        for (int qd = tid; qd < quads; qd += kTPB) {
-          const int u = qd * 4;
-          int w = gs - 128 + u, pos = slot_pos;
-          const bool live = w < n;
-          if (live && w < 0) {
-            const int back = (-w + n - 1) / n;
-            w += back * n;
-            pos -= back;
-            while (pos < 0) pos += Q;
+    if (warp == kBuildWarps) {
+      // ================= MMA warp: lane 0 issues, the warp waits =================
+      const uint64_t bdesc0 = umma_desc(w_base, /*lbo K*/ 128, /*sbo N*/ 256);
+      const uint64_t adesc0 = umma_desc(sig_base, /*lbo K*/ 16, /*sbo M*/ 128);
+      for (int gs = sym0; gs < sym1; gs += kGroup) {
+        const int blocks = (min(gs + kGroup, sym1) - gs + kB - 1) / kB;
+        const int n_tiles = (blocks + kRows - 1) / kRows;
+        if (ggroup > 0) warp_wait(smem_u32(&s_tfree), (ggroup - 1) & 1u, status, abort_flag);
+        int tp = 0, jc = jlo;
+        for (int s = 0; s < steps; ++s, ++gstep) {
+          const uint32_t ss = gstep % kSteps;
+          warp_wait(smem_u32(&s_full[ss]), (gstep / kSteps) & 1u, status, abort_flag);
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+          if (lane == 0) {
+            const int kk0 = s * kPer, kend = min(kk0 + kPer, nk);
+            uint64_t bd = bdesc0 + (uint64_t)((ss * kPer * kChunkBytes) >> 4);
+            for (int kk = kk0; kk < kend; ++kk) {
+              // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
+              const uint64_t ad = adesc0 + (uint64_t)(((tp * kSig + jc * 16) * 2) >> 4);
+              const uint32_t acc = kk > 0 ? 1u : 0u;
+              switch (n_tiles) {  // tiles are 2048 bytes of signal apart
+                case 4: umma_f16(tmem + 3 * kN, ad + 3 * 128, bd, idesc, acc);  // fallthrough
+                case 3: umma_f16(tmem + 2 * kN, ad + 2 * 128, bd, idesc, acc);  // fallthrough
+                case 2: umma_f16(tmem + 1 * kN, ad + 1 * 128, bd, idesc, acc);  // fallthrough
+                default: umma_f16(tmem, ad, bd, idesc, acc);
+              }
+              bd += kChunkBytes >> 4;
+              if (++jc == kKC) { jc = jlo; ++tp; }
+            }
+            umma_commit(smem_u32(&s_empty[ss]));
+            if (s == steps - 1) umma_commit(smem_u32(&s_acc));
           }
-          const uint4 *src = reinterpret_cast<const uint4 *>(rin + ((size_t)pos * n_tx * n + w));
-          uint4 v[4];
+          __syncwarp();
+        }
+        ++ggroup;
+      }
+    } else {
+      // ================= builder warps =================
+      const int per = n_rx * n_tx * U->n_taps, K = U->n_taps;
+      const uint64_t a = it.slot * (uint64_t)U->nsym + (uint64_t)it.sym;
+      // ---- dense delay table of this symbol: tapd[r*4+t][d] = (H, dH) ----
+      for (int e = tid; e < 16 * 128; e += kBuilders) tapd[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+      builders_sync();
+      for (int rt = warp; rt < n_rx * n_tx; rt += kBuildWarps) {
+        const int r = rt / n_tx, t = rt - r * n_tx;
+#pragma unroll 4
+        for (int k = lane; k < K; k += 32) {  // delays may repeat: accumulate
+          const int e = rt * K + k;
+          const int d = __ldg(U->delays + k);
+          float2 h0, h1;
+          if (U->step_samples == 0.0) {
+            h0 = __ldg(U->taps + it.idx0 * (uint64_t)per + (uint64_t)e);
+            h1 = __ldg(U->taps + it.idx1 * (uint64_t)per + (uint64_t)e);
+          } else {
+            h0 = tt::tt_anchor(U, a, e, per);
+            h1 = tt::tt_anchor(U, a + 1, e, per);
+          }
+          float *v = reinterpret_cast<float *>(&tapd[(r * 4 + t) * 128 + d]);
+          atomicAdd(v + 0, h0.x);
+          atomicAdd(v + 1, h0.y);
+          atomicAdd(v + 2, h1.x - h0.x);
+          atomicAdd(v + 3, h1.y - h0.y);
+        }
+      }
+      builders_sync();
+      // ---- component tables: 16-bit c-component of the tap of delay 136 - (q + par), per
+      //      (link, c, par) slot of kQW words at shift comp_shift(r, c); two q per 32-bit store ----
+      for (int slot = warp; slot < 16 * kComps * 2; slot += kBuildWarps) {
+        const int tpar = slot & 1, c = (slot >> 1) & (kComps - 1), link = slot >> 3;
+        uint32_t *dst = comp_w + slot * kQW + comp_shift(link >> 2, c);
+        const float4 *tl = tapd + link * 128;
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
-            v[t] = (live && t < n_tx) ? __ldg(src + (size_t)t * (n / 4)) : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            if (t >= n_tx) break;
-            const uint32_t vv[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
-            uint32_t re2[2], im2[2];
+        for (int j = 0; j < 3; ++j) {
+          const int qh = lane + 32 * j;
+          if (qh < 76) {
+            uint32_t pk = 0;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const float2 x0 = tt_unpack_iq(vv[2 * h]), x1 = tt_unpack_iq(vv[2 * h + 1]);
-              re2[h] = (uint32_t)to_op<FP16>(x0.x) | ((uint32_t)to_op<FP16>(x1.x) << 16);
-              im2[h] = (uint32_t)to_op<FP16>(x0.y) | ((uint32_t)to_op<FP16>(x1.y) << 16);
+              const int d = 136 - (2 * qh + h + tpar);
+              float v = 0.f;
+              if (d >= 0 && d <= 127) {
+                const float2 hv = (c & 2) ? make_float2(tl[d].z, tl[d].w) : make_float2(tl[d].x, tl[d].y);
+                v = (c & 1) ? hv.y : hv.x;
+              }
+              pk |= (uint32_t)to_op<FP16>(v) << (16 * h);
             }
-            *reinterpret_cast<uint2 *>(sig + (t * 2 + 0) * kSig + u) = make_uint2(re2[0], re2[1]);
-            *reinterpret_cast<uint2 *>(sig + (t * 2 + 1) * kSig + u) = make_uint2(im2[0], im2[1]);
+            dst[qh] = pk;
           }
         }
       }
-      // the first kPer tap chunks into the ring; then per step: issue chunks [kc, kc + kPer) and
-      // build [kc + kPer, kc + 2 kPer) into the slots last read by the chunks issued two steps before
-      for (int kk = 0; kk < kPer && kk < nk; ++kk) build_chunk(kk, kk);
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      __syncthreads();
-      int bi = 0;  // ring slot of chunk kc
-      for (int kc = 0; kc < nk; kc += kPer) {
-        if (tid == 0) {
-          asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-          int tp = kc / kpc, jc = jlo + (kc - tp * kpc), b = bi;
-          for (int kk = kc; kk < kc + kPer && kk < nk; ++kk) {
-            const uint64_t bd = umma_desc(w_base + (uint32_t)b * kN * 16 * 2, /*lbo K*/ 128, /*sbo N*/ 256);
-            // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
-            const uint32_t a0 = sig_base + (uint32_t)(tp * kSig + jc * 16) * 2;
-            for (int mt = 0; mt < n_tiles; ++mt) {
-              const uint64_t ad = umma_desc(a0 + (uint32_t)(mt * kRows * kB * 2), /*lbo K*/ 16, /*sbo M*/ 128);
-              umma_f16(tmem + (uint32_t)mt * kN, ad, bd, idesc, kk > 0 ? 1u : 0u);
-            }
-            umma_commit(smem_u32(&s_mbar[b]));
-            if (++jc == kKC) { jc = jlo; ++tp; }
-            if (++b == kStages) b = 0;
-          }
-        }
+      builders_sync();
+      // table word bases of this thread's segment for input part p (Tx antenna added per chunk)
+      const int tb0 = rr < n_rx ? ((rr * 4) * kComps + c_p0) * 2 * kQW + par * kQW + comp_shift(rr, c_p0) + (qoff - par) / 2
+                                : -1;
+      const int tb1 = rr < n_rx ? ((rr * 4) * kComps + c_p1) * 2 * kQW + par * kQW + comp_shift(rr, c_p1) + (qoff - par) / 2
+                                : -1;
+
+      // ---- the symbol in groups of up to 4096 samples (4 tensor-memory tiles each) ----
+      for (int gs = sym0; gs < sym1; gs += kGroup) {
+        const int ge = min(gs + kGroup, sym1);
+        const int blocks = (ge - gs + kB - 1) / kB;
+        const int n_tiles = (blocks + kRows - 1) / kRows;
+        // signal: sig[t][p][u] = x_{t,p}[gs - 128 + u], 16-bit operands, zero past the slot end;
+        // four samples per load (the window start is 8-aligned and N is a multiple of 8).  The
+        // accumulators of the previous group are complete, so nothing reads the old signal.
         {
-          int b = bi;
-          for (int kk = kc; kk < kc + kPer && kk < nk; ++kk) {
-            pend_bits |= 1u << b;
-            if (++b == kStages) b = 0;
-          }
-          for (int kk = kc + kPer; kk < kc + 2 * kPer && kk < nk; ++kk) {
-            wait_buf(b);  // the MMAs of chunk kk - kStages are done with this slot
-            build_chunk(kk, b);
-            if (++b == kStages) b = 0;
+          const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
+          const int quads = (n_tiles * kRows * kB + kW) / 4;
+#pragma unroll 2
+          for (int qd = tid; qd < quads; qd += kBuilders) {
+            const int u = qd * 4;
+            int w = gs - 128 + u, pos = slot_pos;
+            const bool live = w < n;
+            if (live && w < 0) {
+              const int back = (-w + n - 1) / n;
+              w += back * n;
+              pos -= back;
+              while (pos < 0) pos += Q;
+            }
+            const uint4 *src = reinterpret_cast<const uint4 *>(rin + ((size_t)pos * n_tx * n + w));
+            uint4 v[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              v[t] = (live && t < n_tx) ? __ldg(src + (size_t)t * (n / 4)) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              if (t >= n_tx) break;
+              const uint32_t vv[4] = {v[t].x, v[t].y, v[t].z, v[t].w};
+              uint32_t re2[2], im2[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const float2 x0 = tt_unpack_iq(vv[2 * h]), x1 = tt_unpack_iq(vv[2 * h + 1]);
+                re2[h] = (uint32_t)to_op<FP16>(x0.x) | ((uint32_t)to_op<FP16>(x1.x) << 16);
+                im2[h] = (uint32_t)to_op<FP16>(x0.y) | ((uint32_t)to_op<FP16>(x1.y) << 16);
+              }
+              *reinterpret_cast<uint2 *>(sig + (t * 2 + 0) * kSig + u) = make_uint2(re2[0], re2[1]);
+              *reinterpret_cast<uint2 *>(sig + (t * 2 + 1) * kSig + u) = make_uint2(im2[0], im2[1]);
+            }
           }
         }
-        bi += kPer;
-        if (bi >= kStages) bi -= kStages;
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (s_abort) break;
-      }
-      for (int b = 0; b < kStages; ++b) wait_buf(b);
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-      __syncthreads();
-      if (s_abort) break;
-      // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (block rows) and samples
-      //      i in [4 (w / 4), 4 (w / 4) + 4) of each block; AWGN per pair of samples (one Philox block) ----
-      {
-        const int quad = warp & 3, ihalf = warp >> 2;
-        const float rl = 1.0f / (float)(sym1 - sym0);
-        for (int mt = 0; mt < n_tiles; ++mt) {
-          const int c = mt * kRows + quad * 32 + lane;
-          uint32_t raw4[4][16];  // this warp's four samples of the block, 16 columns each
-          const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + ihalf * 4 * 16);
+        // tap chunks, kPer per step, into the step's ring slots once the MMAs of the step that
+        // last used them are done; each warp then arrives on the step's full barrier
+        int tp = 0, jc = jlo;
+        for (int s = 0; s < steps; ++s, ++gstep) {
+          const uint32_t ss = gstep % kSteps;
+          if (gstep >= kSteps) warp_wait(smem_u32(&s_empty[ss]), (gstep / kSteps - 1) & 1u, status, abort_flag);
+          const int kk0 = s * kPer, kend = min(kk0 + kPer, nk);
+          uint16_t *wdst = wbuf + ss * kPer * (kN * 16) + w_off;
+          for (int kk = kk0; kk < kend; ++kk) {
+            const int t = tp >> 1, p = tp & 1;
+            const int base = p ? tb1 : tb0;
+            uint4 seg = make_uint4(0u, 0u, 0u, 0u);
+            if (base >= 0) {
+              const uint32_t *src = comp_w + base + t * 2 * kComps * kQW + jc * 8;
+              const uint32_t ng = p ? neg_p1 : 0u;
+              seg = make_uint4(src[0] ^ ng, src[1] ^ ng, src[2] ^ ng, src[3] ^ ng);
+            }
+            *reinterpret_cast<uint4 *>(wdst) = seg;
+            wdst += kN * 16;
+            if (++jc == kKC) { jc = jlo; ++tp; }
+          }
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&s_full[ss]));
+        }
+        // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (block rows) and samples
+        //      i in [4 (w / 4), 4 (w / 4) + 4) of each block; AWGN per pair of samples (one Philox block) ----
+        warp_wait(smem_u32(&s_acc), ggroup & 1u, status, abort_flag);
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+        {
+          const int quad = warp & 3, ihalf = warp >> 2;
+          const float rl = 1.0f / (float)(sym1 - sym0);
+          for (int mt = 0; mt < n_tiles; ++mt) {
+            const int c = mt * kRows + quad * 32 + lane;
+            uint32_t raw4[4][16];  // this warp's four samples of the block, 16 columns each
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + ihalf * 4 * 16);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) tmem_ld16(tbase + (uint32_t)q * 16, raw4[q]);
-          tmem_wait_ld();
+            for (int q = 0; q < 4; ++q) tmem_ld16(tbase + (uint32_t)q * 16, raw4[q]);
+            tmem_wait_ld();
 #pragma unroll
-          for (int q = 0; q < 4; q += 2) {
-            const int i = ihalf * 4 + q;
-            const int m = gs + c * kB + i;  // even: pairs (m, m + 1) share a Philox block
-            if (m < ge) {
-              const float tau0 = (float)(m - sym0) * rl, tau1 = (float)(m + 1 - sym0) * rl;
-              const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
+            for (int q = 0; q < 4; q += 2) {
+              const int i = ihalf * 4 + q;
+              const int m = gs + c * kB + i;  // even: pairs (m, m + 1) share a Philox block
+              if (m < ge) {
+                const float tau0 = (float)(m - sym0) * rl, tau1 = (float)(m + 1 - sym0) * rl;
+                const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
 #pragma unroll
-              for (int r = 0; r < 4; ++r) {
-                if (r >= n_rx) break;
-                const uint32_t *v0 = raw4[q], *v1 = raw4[q + 1];
-                float2 y0 = make_float2(fmaf(tau0, __uint_as_float(v0[r * 4 + 1]), __uint_as_float(v0[r * 4 + 0])),
-                                        fmaf(tau0, __uint_as_float(v0[r * 4 + 3]), __uint_as_float(v0[r * 4 + 2])));
-                float2 y1 = make_float2(fmaf(tau1, __uint_as_float(v1[r * 4 + 1]), __uint_as_float(v1[r * 4 + 0])),
-                                        fmaf(tau1, __uint_as_float(v1[r * 4 + 3]), __uint_as_float(v1[r * 4 + 2])));
-                if (U->noise_std > 0.f) tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y0, y1);
-                const size_t o = (size_t)(slot_pos * n_rx + r) * n + m;
-                if (U->out_f32) {
-                  *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(U->ring_out) + o) =
-                      make_float4(y0.x, y0.y, y1.x, y1.y);
-                } else {
-                  *reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(U->ring_out) + o) =
-                      make_uint2(tt_pack_iq(y0.x, y0.y), tt_pack_iq(y1.x, y1.y));
+                for (int r = 0; r < 4; ++r) {
+                  if (r >= n_rx) break;
+                  const uint32_t *v0 = raw4[q], *v1 = raw4[q + 1];
+                  float2 y0 = make_float2(fmaf(tau0, __uint_as_float(v0[r * 4 + 1]), __uint_as_float(v0[r * 4 + 0])),
+                                          fmaf(tau0, __uint_as_float(v0[r * 4 + 3]), __uint_as_float(v0[r * 4 + 2])));
+                  float2 y1 = make_float2(fmaf(tau1, __uint_as_float(v1[r * 4 + 1]), __uint_as_float(v1[r * 4 + 0])),
+                                          fmaf(tau1, __uint_as_float(v1[r * 4 + 3]), __uint_as_float(v1[r * 4 + 2])));
+                  if (U->noise_std > 0.f)
+                    tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y0, y1);
+                  const size_t o = (size_t)(slot_pos * n_rx + r) * n + m;
+                  if (U->out_f32) {
+                    *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(U->ring_out) + o) =
+                        make_float4(y0.x, y0.y, y1.x, y1.y);
+                  } else {
+                    *reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(U->ring_out) + o) =
+                        make_uint2(tt_pack_iq(y0.x, y0.y), tt_pack_iq(y1.x, y1.y));
+                  }
                 }
               }
             }
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&s_tfree));
+        ++ggroup;
       }
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-      __syncthreads();
     }
-    if (s_abort) break;
   }
+  // every MMA was waited for by the epilogue of its group (or a wait expired: nothing more to wait for)
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
-  for (int b = 0; b < kStages; ++b) wait_buf(b);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-  __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
