@@ -41,20 +41,20 @@ constexpr int kTPB = (kBuildWarps + 1) * 32;    // + one warp that issues the MM
 constexpr int kBuilders = kBuildWarps * 32;
 constexpr int kB = 8;                 // output samples per block row (16-byte rows of the signal view)
 constexpr int kRows = 128;            // block rows per MMA tile (M): 1024 samples
-constexpr int kTilesMax = 4;          // tiles accumulating at once: 4 x 128 TMEM columns
-constexpr int kGroup = kRows * kB * kTilesMax;  // samples per group (4096)
+constexpr int kTilesMax = 2;          // tiles accumulating at once: 2 x 128 TMEM columns
+constexpr int kGroup = kRows * kB * kTilesMax;  // samples per group (2048)
 constexpr int kMaxDelayTC = 127;
 constexpr int kW = 144;               // window per (t, p): j in [0, 135) used, padded to 9 K-chunks of 16
 constexpr int kKC = kW / 16;          // K-chunks per (t, p)
 constexpr int kN = 128;               // D columns: (i, r, part, A|B)
 constexpr int kSig = kGroup + kW;     // staged samples per (t, p)
-constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTmemCols = kTilesMax * kN;  // two CTAs per SM share the 512 columns
 constexpr long long kSpinLimit = 1ll << 24;
 
-constexpr int kQW = 128;              // words per component table (q = j - i + 8 in [1, 151] needs 76, plus shift)
+constexpr int kQW = 88;               // words per component table: q = j - i + 8 in [1, 151] needs 76, plus shift <= 3
 constexpr int kComps = 4;             // hr, hi of H and of dH; -hi is hi with the sign bits flipped
 constexpr int kPer = 4;               // tap chunks per pipeline step
-constexpr int kSteps = 3;             // steps in the ring: builders run up to two steps ahead of the MMAs
+constexpr int kSteps = 2;             // steps in the ring: builders run up to one step ahead of the MMAs
 constexpr int kStages = kPer * kSteps;
 constexpr int kChunkBytes = kN * 16 * 2;
 
@@ -63,18 +63,25 @@ constexpr int kChunkBytes = kN * 16 * 2;
 constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
 constexpr int kOffTap = 0;                               // [16 links][128 delays] float4 (H, dH)
 constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // kStages x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
-constexpr int kOffComp = kOffW + kStages * kChunkBytes;  // [16 links][kComps][2 parities][kQW words]
+constexpr int kOffComp = kOffW + kStages * kChunkBytes;  // [4 tx][2 parities][kComps][4 rx][kQW words]
 constexpr int kSmemUsed = kOffComp + 16 * kComps * 2 * kQW * 4;
 static_assert(16 * 128 * 16 <= 4 * 2 * kSig * 2, "delay table must fit in the signal area");
 
-// Word shift of component table (r, c) inside its slot.  A builder warp handles one sample i of the
-// block and all 16 rows (r, output part, A|B) for both K-groups; for either input part the four
-// tables of one r are a permutation of c = 0..3, so shift 8 r + c puts the warp's 32 words of
-// every 32-bit load on 32 distinct banks.
-__host__ __device__ constexpr int comp_shift(int r, int c) { return 8 * r + c; }
-// More than half an SM's shared memory: one CTA per SM, so no two CTAs ever compete for the
-// 512 tensor-memory columns each one allocates.
-constexpr int kSmemBytes = kSmemUsed > 120 * 1024 ? kSmemUsed : 120 * 1024;
+// Component tables, one per (t, parity, c, r), kQW words each.  A builder warp handles one sample i
+// of the block and all 16 rows (r, output part, A|B) for both K-groups (4 words apart); for either
+// input part it reads, at one (t, parity), the four tables c of every r.  Table (t, par, c, r) starts
+// at word ((t * 2 + par) * 4 + c) * 4 + r) * kQW, whose bank is 24 r (mod 32) because kQW = 88 is
+// 24 mod 32; shifting its data by c words puts the warp's 32 words of every 32-bit load on 32
+// distinct banks.
+__host__ __device__ constexpr int comp_slot(int t, int par, int c, int r) { return ((t * 2 + par) * kComps + c) * 4 + r; }
+static_assert(kQW % 32 == 24 && 76 + (kComps - 1) <= kQW, "component table stride and shift");
+// Two CTAs per SM (each with half the tensor-memory columns): one stages, builds tables or drains
+// its accumulators while the other keeps the tensor core busy.  A third never fits.
+constexpr int kSmemBytes = kSmemUsed;
+constexpr int kCtasPerSm = 2;
+static_assert(kCtasPerSm * (int)kTmemCols <= 512, "tensor-memory columns of the co-resident CTAs");
+static_assert(3 * (kSmemBytes + 2048) > 228 * 1024 && 2 * (kSmemBytes + 2048) <= 228 * 1024,
+              "exactly two CTAs per SM");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -161,7 +168,7 @@ __device__ __forceinline__ void warp_wait(uint32_t mbar, uint32_t phase, int *st
 }  // namespace
 
 template <bool FP16>
-__global__ void __launch_bounds__(kTPB, 1)
+__global__ void __launch_bounds__(kTPB, 2)
     tt_toeplitz_tc_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                           uint32_t total_items, uint32_t *__restrict__ counter, int *__restrict__ status) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -277,12 +284,9 @@ __global__ void __launch_bounds__(kTPB, 1)
               // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
               const uint64_t ad = adesc0 + (uint64_t)(((tp * kSig + jc * 16) * 2) >> 4);
               const uint32_t acc = kk > 0 ? 1u : 0u;
-              switch (n_tiles) {  // tiles are 2048 bytes of signal apart
-                case 4: umma_f16(tmem + 3 * kN, ad + 3 * 128, bd, idesc, acc);  // fallthrough
-                case 3: umma_f16(tmem + 2 * kN, ad + 2 * 128, bd, idesc, acc);  // fallthrough
-                case 2: umma_f16(tmem + 1 * kN, ad + 1 * 128, bd, idesc, acc);  // fallthrough
-                default: umma_f16(tmem, ad, bd, idesc, acc);
-              }
+              // tiles are 2048 bytes of signal apart
+              if (n_tiles > 1) umma_f16(tmem + kN, ad + 128, bd, idesc, acc);
+              umma_f16(tmem, ad, bd, idesc, acc);
               bd += kChunkBytes >> 4;
               if (++jc == kKC) { jc = jlo; ++tp; }
             }
@@ -323,11 +327,11 @@ __global__ void __launch_bounds__(kTPB, 1)
       }
       builders_sync();
       // ---- component tables: 16-bit c-component of the tap of delay 136 - (q + par), per
-      //      (link, c, par) slot of kQW words at shift comp_shift(r, c); two q per 32-bit store ----
+      //      (t, par, c, r) slot of kQW words at shift c; two q per 32-bit store ----
       for (int slot = warp; slot < 16 * kComps * 2; slot += kBuildWarps) {
-        const int tpar = slot & 1, c = (slot >> 1) & (kComps - 1), link = slot >> 3;
-        uint32_t *dst = comp_w + slot * kQW + comp_shift(link >> 2, c);
-        const float4 *tl = tapd + link * 128;
+        const int r = slot & 3, c = (slot >> 2) & (kComps - 1), tpar = (slot >> 4) & 1, t = slot >> 5;
+        uint32_t *dst = comp_w + slot * kQW + c;
+        const float4 *tl = tapd + (r * 4 + t) * 128;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
           const int qh = lane + 32 * j;
@@ -349,10 +353,11 @@ __global__ void __launch_bounds__(kTPB, 1)
       }
       builders_sync();
       // table word bases of this thread's segment for input part p (Tx antenna added per chunk)
-      const int tb0 = rr < n_rx ? ((rr * 4) * kComps + c_p0) * 2 * kQW + par * kQW + comp_shift(rr, c_p0) + (qoff - par) / 2
-                                : -1;
-      const int tb1 = rr < n_rx ? ((rr * 4) * kComps + c_p1) * 2 * kQW + par * kQW + comp_shift(rr, c_p1) + (qoff - par) / 2
-                                : -1;
+      // (rows of absent Rx antennas read table r = 0 and write zeros)
+      const int rq = rr < n_rx ? rr : 0;
+      const uint32_t keep = rr < n_rx ? 0xFFFFFFFFu : 0u;
+      const int tb0 = comp_slot(0, par, c_p0, rq) * kQW + c_p0 + (qoff - par) / 2;
+      const int tb1 = comp_slot(0, par, c_p1, rq) * kQW + c_p1 + (qoff - par) / 2;
 
       // ---- the symbol in groups of up to 4096 samples (4 tensor-memory tiles each) ----
       for (int gs = sym0; gs < sym1; gs += kGroup) {
@@ -405,18 +410,16 @@ __global__ void __launch_bounds__(kTPB, 1)
           if (gstep >= kSteps) warp_wait(smem_u32(&s_empty[ss]), (gstep / kSteps - 1) & 1u, status, abort_flag);
           const int kk0 = s * kPer, kend = min(kk0 + kPer, nk);
           uint16_t *wdst = wbuf + ss * kPer * (kN * 16) + w_off;
-          for (int kk = kk0; kk < kend; ++kk) {
-            const int t = tp >> 1, p = tp & 1;
-            const int base = p ? tb1 : tb0;
-            uint4 seg = make_uint4(0u, 0u, 0u, 0u);
-            if (base >= 0) {
-              const uint32_t *src = comp_w + base + t * 2 * kComps * kQW + jc * 8;
+#pragma unroll
+          for (int e = 0; e < kPer; ++e) {
+            if (kk0 + e < kend) {
+              const int t = tp >> 1, p = tp & 1;
+              const uint32_t *src = comp_w + (p ? tb1 : tb0) + t * (2 * kComps * 4 * kQW) + jc * 8;
               const uint32_t ng = p ? neg_p1 : 0u;
-              seg = make_uint4(src[0] ^ ng, src[1] ^ ng, src[2] ^ ng, src[3] ^ ng);
+              *reinterpret_cast<uint4 *>(wdst + e * (kN * 16)) =
+                  make_uint4((src[0] ^ ng) & keep, (src[1] ^ ng) & keep, (src[2] ^ ng) & keep, (src[3] ^ ng) & keep);
+              if (++jc == kKC) { jc = jlo; ++tp; }
             }
-            *reinterpret_cast<uint4 *>(wdst) = seg;
-            wdst += kN * 16;
-            if (++jc == kKC) { jc = jlo; ++tp; }
           }
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
           __syncwarp();
@@ -431,13 +434,13 @@ __global__ void __launch_bounds__(kTPB, 1)
           const float rl = 1.0f / (float)(sym1 - sym0);
           for (int mt = 0; mt < n_tiles; ++mt) {
             const int c = mt * kRows + quad * 32 + lane;
-            uint32_t raw4[4][16];  // this warp's four samples of the block, 16 columns each
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + ihalf * 4 * 16);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) tmem_ld16(tbase + (uint32_t)q * 16, raw4[q]);
-            tmem_wait_ld();
-#pragma unroll
             for (int q = 0; q < 4; q += 2) {
+              uint32_t v0[16], v1[16];  // samples i and i + 1 of this lane's block row: 16 columns each
+              tmem_ld16(tbase + (uint32_t)q * 16, v0);
+              tmem_ld16(tbase + (uint32_t)(q + 1) * 16, v1);
+              tmem_wait_ld();
               const int i = ihalf * 4 + q;
               const int m = gs + c * kB + i;  // even: pairs (m, m + 1) share a Philox block
               if (m < ge) {
@@ -446,7 +449,6 @@ __global__ void __launch_bounds__(kTPB, 1)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                   if (r >= n_rx) break;
-                  const uint32_t *v0 = raw4[q], *v1 = raw4[q + 1];
                   float2 y0 = make_float2(fmaf(tau0, __uint_as_float(v0[r * 4 + 1]), __uint_as_float(v0[r * 4 + 0])),
                                           fmaf(tau0, __uint_as_float(v0[r * 4 + 3]), __uint_as_float(v0[r * 4 + 2])));
                   float2 y1 = make_float2(fmaf(tau1, __uint_as_float(v1[r * 4 + 1]), __uint_as_float(v1[r * 4 + 0])),
@@ -497,9 +499,10 @@ cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, cud
     attr[fp16] = true;
   }
   if (L.grid < 0) {
-    int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kTPB, kSmemBytes) != cudaSuccess) blocks = 1;
-    const_cast<TTLaunch &>(L).grid = -(blocks > 0 ? blocks : 1);
+    // The occupancy calculator reports one CTA per SM for any kernel that allocates tensor memory.
+    // Shared memory admits exactly two of these CTAs per SM (static_assert above) and each takes
+    // half of the 512 columns, so two run side by side.
+    const_cast<TTLaunch &>(L).grid = -kCtasPerSm;
     return cudaSuccess;
   }
   if (L.grid == 0 || L.total_items == 0) return cudaSuccess;
