@@ -166,12 +166,14 @@ tt_status tt_engine_stream(tt_engine *e, void **stream);
 tt_status tt_engine_get_stats(tt_engine *e, tt_engine_stats *out);
 
 /* Autotune the tiled kernel's samples-per-thread for every class of admitted,
- * traced channels (same symbol lengths, antennas, tap count, delay class):
- * each candidate that fits shared memory is timed `reps` times on one slot
- * of every channel of the class that has a free ring position (written to
- * that free position, so no queued or unpulled slot is touched), and the
- * fastest is kept.  Waits for queued work first.  *classes_tuned (may be
- * NULL) receives the number of classes that had a choice to make. */
+ * traced FP32 channels (same symbol lengths, antennas, tap count, delay
+ * class).  The objective is the whole batch: one slot of every channel that
+ * has a free ring position (written to that free position, so no queued or
+ * unpulled slot is touched), launched as tt_engine_run launches it, best of
+ * `reps` timings.  Classes are visited largest first; each candidate that
+ * fits shared memory replaces the class's current choice only if the batch
+ * gets at least 1% faster.  Waits for queued work first.  *classes_tuned
+ * (may be NULL) receives the number of classes that had a choice to make. */
 tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned);
 
 /* Serving form.  Runs a request loop on the calling thread for warmup_s +

@@ -68,6 +68,11 @@ struct tt_engine {
   int num_sms = 1;
   cudaStream_t stream = nullptr;  // all compute and device copies, in order
   cudaStream_t copy = nullptr;    // host pulls
+  // Kernel variants of one run go on parallel branches (side streams forked from and joined
+  // back to `stream`), so each variant's tail overlaps the others' work.
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
   std::mutex mu;
   std::vector<tt_chan *> table;   // UE table slot -> channel
   TTUEDesc *d_ues = nullptr;
@@ -410,7 +415,21 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
     cudaError_t err = cudaMemsetAsync(e->d_counters, 0, sizeof(uint32_t) * p.groups.size(), e->stream);
     if (err != cudaSuccess) return err;
   }
-  for (size_t gi = 0; gi < p.groups.size(); ++gi) {
+  // largest variant on the engine stream, the others on side branches that start with it
+  std::vector<size_t> order(p.groups.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+    return (double)p.groups[a].items * p.groups[a].k_max * p.groups[a].nrx * p.groups[a].spt >
+           (double)p.groups[b].items * p.groups[b].k_max * p.groups[b].nrx * p.groups[b].spt;
+  });
+  const int n_side = (int)std::min<size_t>(order.size() > 0 ? order.size() - 1 : 0, tt_engine::kSide);
+  if (n_side > 0) {
+    cudaError_t err = cudaEventRecord(e->fork, e->stream);
+    for (int i = 0; i < n_side && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(e->side[i], e->fork, 0);
+    if (err != cudaSuccess) return err;
+  }
+  for (size_t oi = 0; oi < order.size(); ++oi) {
+    const size_t gi = order[oi];
     const PlanGroup &g = p.groups[gi];
     TTLaunch L{};
     L.ues = e->d_ues;
@@ -427,7 +446,13 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
     L.smem = g.smem;
     L.grid = g.grid;
     L.cursors = cursors;
-    cudaError_t err = tt_launch_conv_fp32(L, e->stream);
+    cudaStream_t st = oi == 0 || n_side == 0 ? e->stream : e->side[(oi - 1) % n_side];
+    cudaError_t err = tt_launch_conv_fp32(L, st);
+    if (err != cudaSuccess) return err;
+  }
+  for (int i = 0; i < n_side; ++i) {
+    cudaError_t err = cudaEventRecord(e->join[i], e->side[i]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, e->join[i], 0);
     if (err != cudaSuccess) return err;
   }
   return cudaSuccess;
@@ -618,6 +643,11 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   e->table.assign(e->max_ues, nullptr);
   cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking);
+  for (int i = 0; i < tt_engine::kSide && err == cudaSuccess; ++i) {
+    err = cudaStreamCreateWithFlags(&e->side[i], cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->join[i], cudaEventDisableTiming);
+  }
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_ues, sizeof(TTUEDesc) * e->max_ues);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_counters, sizeof(uint32_t) * e->counter_cap);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_cursors, sizeof(unsigned long long) * e->max_ues);
@@ -657,6 +687,11 @@ tt_status tt_engine_destroy(tt_engine *e) {
   cudaFree(e->d_status);
   if (e->stream) cudaStreamDestroy(e->stream);
   if (e->copy) cudaStreamDestroy(e->copy);
+  for (int i = 0; i < tt_engine::kSide; ++i) {
+    if (e->side[i]) cudaStreamDestroy(e->side[i]);
+    if (e->join[i]) cudaEventDestroy(e->join[i]);
+  }
+  if (e->fork) cudaEventDestroy(e->fork);
   delete e;
   return TT_OK;
 }
@@ -1033,7 +1068,7 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
   // classes: same numerology, antennas, taps and delay class tune alike
   std::vector<std::pair<std::vector<int64_t>, std::vector<tt_chan *>>> classes;
   for (tt_chan *c : e->table) {
-    if (!c || !c->has_trace) continue;
+    if (!c || !c->has_trace || c->cfg.precision != TT_FP32) continue;
     std::vector<int64_t> key(c->sym_len.begin(), c->sym_len.end());
     key.insert(key.end(), {(int64_t)c->cfg.n_tx, (int64_t)c->cfg.n_rx, (int64_t)c->desc.n_taps,
                            (int64_t)c->dclass, (int64_t)(c->desc.noise_std > 0.f), (int64_t)c->desc.out_f32});
@@ -1041,22 +1076,13 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
     if (it == classes.end()) classes.push_back({key, {c}});
     else it->second.push_back(c);
   }
-  cudaEvent_t a = nullptr, b = nullptr;
-  TT_CK(cudaEventCreate(&a));
-  TT_CK(cudaEventCreate(&b));
-  uint32_t tuned = 0;
-  tt_status result = TT_OK;
-  for (auto &cls : classes) {
-    tt_chan *c0 = cls.second[0];
-    std::vector<int> cands;
-    for (int s : spt_candidates(c0->sym_len, e->spt_override ? e->spt_override : 16, c0->cfg.n_rx)) {
-      int need = 0;
-      if (smem_need(c0, s, &need)) cands.push_back(s);
-    }
-    if (cands.size() < 2) continue;
-    // time one slot of every channel of the class that has a free ring position
-    std::vector<tt_chan *> room;
-    std::vector<uint64_t> first, count;
+  // The objective is the whole batch: one slot of every channel that has a free ring position,
+  // launched as the engine launches it.  A class's samples-per-thread is changed only when the
+  // batch gets faster, so the tuner never splits the launch into more kernel variants for a
+  // class-local gain.
+  std::vector<tt_chan *> room;
+  std::vector<uint64_t> first, count;
+  for (auto &cls : classes)
     for (tt_chan *c : cls.second) {
       const uint64_t f = c->started ? c->pushed_end : 0, start = c->started ? c->pulled_end : 0;
       if (f + 1 - start + (uint64_t)c->hist <= (uint64_t)c->Q) {
@@ -1065,35 +1091,69 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
         count.push_back(1);
       }
     }
-    if (room.empty()) continue;
-    int best = cands[0];
-    float best_ms = 1e30f;
+  if (room.empty()) {
+    if (classes_tuned) *classes_tuned = 0;
+    return TT_OK;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  TT_CK(cudaEventCreate(&a));
+  TT_CK(cudaEventCreate(&b));
+  tt_status result = TT_OK;
+  auto time_batch = [&](float *best_ms) -> tt_status {
+    Plan plan;
+    tt_status st = build_plan(e, room, first, count, plan);
+    if (st != TT_OK) return st;
+    if ((st = launch_direct(e, plan)) != TT_OK) return st;  // warm-up
+    *best_ms = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      cudaEventRecord(a, e->stream);
+      if ((st = launch_direct(e, plan)) != TT_OK) return st;
+      cudaEventRecord(b, e->stream);
+      if (cudaEventSynchronize(b) != cudaSuccess) return fail(TT_ERR_CUDA, "autotune: timing failed");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      *best_ms = std::min(*best_ms, ms);
+    }
+    return TT_OK;
+  };
+  // largest classes first: their choice moves the batch most
+  std::stable_sort(classes.begin(), classes.end(), [](const auto &x, const auto &y) {
+    auto work = [](const std::vector<tt_chan *> &v) {
+      double w = 0;
+      for (const tt_chan *c : v) w += (double)c->n * c->desc.n_taps * c->cfg.n_tx * c->cfg.n_rx;
+      return w;
+    };
+    return work(x.second) > work(y.second);
+  });
+  float cur_ms = 0.f;
+  uint32_t tuned = 0;
+  result = time_batch(&cur_ms);
+  for (size_t ci = 0; ci < classes.size() && result == TT_OK; ++ci) {
+    auto &cls = classes[ci];
+    tt_chan *c0 = cls.second[0];
+    std::vector<int> cands;
+    for (int s : spt_candidates(c0->sym_len, e->spt_override ? e->spt_override : 16, c0->cfg.n_rx)) {
+      int need = 0;
+      if (smem_need(c0, s, &need)) cands.push_back(s);
+    }
+    if (cands.size() < 2) continue;
+    const int start_spt = c0->spt;
+    int best = start_spt;
     for (int s : cands) {
-      for (tt_chan *c : cls.second) {
+      if (s == start_spt) continue;
+      for (tt_chan *c : cls.second)
         if ((result = apply_spt(c, s)) != TT_OK || (result = upload_desc(c)) != TT_OK) break;
-      }
       if (result != TT_OK) break;
-      Plan plan;
-      if ((result = build_plan(e, room, first, count, plan)) != TT_OK) break;
-      if ((result = launch_direct(e, plan)) != TT_OK) break;  // warm-up
-      for (int r = 0; r < reps && result == TT_OK; ++r) {
-        cudaEventRecord(a, e->stream);
-        result = launch_direct(e, plan);
-        cudaEventRecord(b, e->stream);
-        cudaEventSynchronize(b);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = s;
-        }
+      float ms = 0.f;
+      if ((result = time_batch(&ms)) != TT_OK) break;
+      if (ms < 0.99f * cur_ms) {
+        cur_ms = ms;
+        best = s;
       }
-      if (result != TT_OK) break;
     }
     if (result != TT_OK) break;
     for (tt_chan *c : cls.second)
       if ((result = apply_spt(c, best)) != TT_OK || (result = upload_desc(c)) != TT_OK) break;
-    if (result != TT_OK) break;
     ++tuned;
   }
   cudaEventDestroy(a);
