@@ -323,8 +323,12 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
   }
 }
 
+// Single-antenna variants with up to 8 samples per thread fit 64 registers, so eight CTAs share an
+// SM and hide each other's staging barriers; the wider variants keep the compiler's choice.
+constexpr int tt_min_blocks(int S, int NRX) { return (NRX == 1 && S <= 8) ? 8 : 1; }
+
 template <int S, int NRX, int DMAX>
-__global__ void __launch_bounds__(TT_TPB)
+__global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     tt_conv_fp32_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                         uint32_t total_items, uint32_t *__restrict__ counter, int ntx, int tap_max, int k_max,
                         const unsigned long long *__restrict__ cursors) {
