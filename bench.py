@@ -18,6 +18,8 @@ from __future__ import annotations
 
 import argparse
 import json
+import queue
+import threading
 import os
 import statistics
 import subprocess
@@ -211,14 +213,45 @@ def run_ours(args, rank, world, device):
         h_in = [torch.from_numpy(cycled_slots(x, n, N_SLOTS)).pin_memory() for x in iq]
         h_out = [torch.empty((N_SLOTS, 1, n, 2), dtype=torch.int16).pin_memory() for _ in chans]
         e2e_steps = max(1, min(args.steps, 5))
+        # slots per push/run/pull round: the copies of one chunk overlap the kernels of the next
+        chunk = 125 if N_SLOTS % 125 == 0 else N_SLOTS
+        slot_bytes = n * 2 * 2
+        hs = [ch.h for ch in chans]
 
         def e2e_step():
+            # a producer thread pushes chunk after chunk (all UEs in one call) and launches it; this
+            # thread pulls each launched chunk, so host-to-device and device-to-host copies overlap
+            # each other and the kernels
             s0 = next_slot[0]
-            for ch, hi in zip(chans, h_in):
-                tc.tt_chan_push_slots(ch.h, s0, N_SLOTS, hi.data_ptr())
-            eng.run()
-            for ch, ho in zip(chans, h_out):
-                tc.tt_chan_pull_slots(ch.h, s0, N_SLOTS, ho.data_ptr(), -1)
+            launched = queue.Queue()
+            err = []
+
+            def producer():
+                try:
+                    prev = None
+                    for c0 in range(0, N_SLOTS, chunk):
+                        tc.tt_engine_push_slots(eng.h, hs, [s0 + c0] * len(hs), [chunk] * len(hs),
+                                                [hi.data_ptr() + c0 * slot_bytes for hi in h_in])
+                        eng.run()
+                        if prev is not None:   # hand over a chunk once the next one is pushed:
+                            launched.put(prev)  # its kernels have finished by then
+                        prev = c0
+                    launched.put(prev)
+                except Exception as ex:  # surfaced below
+                    err.append(ex)
+                    launched.put(None)
+
+            th = threading.Thread(target=producer)
+            th.start()
+            for _ in range(0, N_SLOTS, chunk):
+                c0 = launched.get()
+                if c0 is None:
+                    break
+                tc.tt_engine_pull_slots(eng.h, hs, [s0 + c0] * len(hs), [chunk] * len(hs),
+                                        [ho.data_ptr() + c0 * slot_bytes for ho in h_out], -1)
+            th.join()
+            if err:
+                raise err[0]
             next_slot[0] = s0 + N_SLOTS
 
         e2e_step()

@@ -32,8 +32,12 @@
  * buffers (host or device) are borrowed only for the duration of the call,
  * except where a function says it works asynchronously on the caller's stream.
  * Handles are not thread-safe individually: use one tt_chan from one thread
- * at a time; an engine serialises its own state, so different channels of one
- * engine may be used from different threads.
+ * at a time, with one exception: one producer thread may push to a channel
+ * (tt_chan_push_slot(s)) while one consumer thread pulls from it
+ * (tt_chan_pull_slot(s)).  An engine serialises its own state, so different
+ * channels of one engine may be used from different threads; push and pull
+ * wait for their copies with the engine unlocked, so host-to-device and
+ * device-to-host copies of different threads overlap.
  *
  * Errors.  Every function returns a tt_status.  On error no out-parameter is
  * written, and tt_last_error() returns a thread-local message.  There is no CPU
@@ -266,6 +270,21 @@ tt_status tt_chan_pull_slots_dev(tt_chan *c, uint64_t first, uint32_t n, void *d
  * oldest not-yet-pulled slots. */
 tt_status tt_chan_slot_output(tt_chan *c, uint64_t slot, const void **d_ptr);
 tt_status tt_chan_release_slots(tt_chan *c, uint64_t first, uint32_t n);
+
+/* Many channels in one call.  Entry i pushes slots [first[i], first[i]+n[i])
+ * of chans[i] from the host buffer iq_in[i] (layout as tt_chan_push_slots),
+ * or pulls them into iq_out[i] (layout as tt_chan_pull_slots).  Every entry is
+ * checked before any copy starts (the first failing entry's status is
+ * returned and nothing is copied); the copies are then queued back to back on
+ * one copy stream and the call waits once, with the engine unlocked, for all
+ * of them: per-channel calls would leave the copy engine idle between
+ * channels.  Pull waits for the entries' slots to complete as
+ * tt_chan_pull_slots does (timeout_us); a channel may appear at most once.
+ * No counterpart in the paper, whose UE processes each move their own IQ. */
+tt_status tt_engine_push_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *chans, const uint64_t *first,
+                               const uint32_t *n, const int16_t *const *iq_in);
+tt_status tt_engine_pull_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *chans, const uint64_t *first,
+                               const uint32_t *n, void *const *iq_out, int64_t timeout_us);
 
 /* Checkpoint / resume.  The state is the next slot index, the last
  * max_delay input samples per Tx antenna and the AWGN key; outputs that have

@@ -68,6 +68,7 @@ struct tt_engine {
   int num_sms = 1;
   cudaStream_t stream = nullptr;  // all compute and device copies, in order
   cudaStream_t copy = nullptr;    // host pulls
+  cudaStream_t h2d = nullptr;     // host pushes: wait only for kernels that still read the overwritten ring slots
   // Kernel variants of one run go on parallel branches (side streams forked from and joined
   // back to `stream`), so each variant's tail overlaps the others' work.
   static constexpr int kSide = 3;
@@ -643,6 +644,7 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   e->table.assign(e->max_ues, nullptr);
   cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking);
+  if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->h2d, cudaStreamNonBlocking);
   for (int i = 0; i < tt_engine::kSide && err == cudaSuccess; ++i) {
     err = cudaStreamCreateWithFlags(&e->side[i], cudaStreamNonBlocking);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->join[i], cudaEventDisableTiming);
@@ -687,6 +689,7 @@ tt_status tt_engine_destroy(tt_engine *e) {
   cudaFree(e->d_status);
   if (e->stream) cudaStreamDestroy(e->stream);
   if (e->copy) cudaStreamDestroy(e->copy);
+  if (e->h2d) cudaStreamDestroy(e->h2d);
   for (int i = 0; i < tt_engine::kSide; ++i) {
     if (e->side[i]) cudaStreamDestroy(e->side[i]);
     if (e->join[i]) cudaEventDestroy(e->join[i]);
@@ -935,21 +938,88 @@ tt_status tt_chan_push_slot(tt_chan *c, uint64_t slot, const int16_t *iq_in) {
   return tt_chan_push_slots(c, slot, 1, iq_in);
 }
 
+// Make stream `st` wait for every queued batch that may still read the input-ring positions that
+// slots [first, first + n) overwrite: they held slots [first - Q, first + n - Q), which batches
+// processing up to slot first + n - Q - 1 + hist read (the delay line).  Batches complete in order,
+// so waiting for the batch holding that slot covers all of them.  Engine lock held.
+static cudaError_t wait_ring_readers(tt_chan *c, uint64_t first, uint32_t n, cudaStream_t st) {
+  tt_engine *e = c->e;
+  if (!c->started || first + n <= (uint64_t)c->Q) return cudaSuccess;
+  cudaError_t q = update_completed(e);
+  if (q != cudaSuccess) return q;
+  update_chan(c);
+  const uint64_t last_reader_slot = first + n - (uint64_t)c->Q - 1 + (uint64_t)c->hist;
+  for (const auto &p : c->inflight)
+    if (p.first > last_reader_slot) {
+      cudaEvent_t ev = event_of(e, p.second);
+      return ev ? cudaStreamWaitEvent(st, ev, 0) : cudaSuccess;
+    }
+  return cudaSuccess;
+}
+
 tt_status tt_chan_push_slots(tt_chan *c, uint64_t first, uint32_t n, const int16_t *iq_in) {
   if (!valid_chan(c) || (!iq_in && n)) return fail(TT_ERR_INVALID, "tt_chan_push_slots: bad argument");
   if (n == 0) return TT_OK;
   tt_engine *e = c->e;
-  std::lock_guard<std::mutex> lk(e->mu);
+  std::unique_lock<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
   tt_status s = check_room(c, first, n);
   if (s != TT_OK) return s;
-  // In stream order after every queued kernel (they may still read the ring
-  // positions being overwritten), then wait so the caller's buffer is free.
-  cudaError_t err = ring_copy(c->d_in, c->slot_in_elems, c->Q, first, n, iq_in, nullptr,
-                              cudaMemcpyHostToDevice, e->stream, true);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+  // On the push stream, after any queued kernel that still reads the ring positions being
+  // overwritten (others keep running), then wait, with the engine unlocked, so the caller's
+  // buffer is free.  The slots count as pushed only once the copy is complete, so no kernel
+  // reads them earlier.
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  cudaError_t err = wait_ring_readers(c, first, n, e->h2d);
+  if (err == cudaSuccess)
+    err = ring_copy(c->d_in, c->slot_in_elems, c->Q, first, n, iq_in, nullptr, cudaMemcpyHostToDevice, e->h2d, true);
+  if (err == cudaSuccess) err = cudaEventRecord(ev, e->h2d);
+  if (err == cudaSuccess) {
+    lk.unlock();
+    err = cudaEventSynchronize(ev);
+    lk.lock();
+  }
+  e->pool.push_back(ev);
   if (err != cudaSuccess) return fail(TT_ERR_CUDA, "push copy: %s", cudaGetErrorString(err));
   mark_pushed(c, first, n);
+  return TT_OK;
+}
+
+tt_status tt_engine_push_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *chans, const uint64_t *first,
+                               const uint32_t *n, const int16_t *const *iq_in) {
+  if (!e || (n_chans && (!chans || !first || !n || !iq_in))) return fail(TT_ERR_INVALID, "tt_engine_push_slots: bad argument");
+  std::unique_lock<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  for (uint32_t i = 0; i < n_chans; ++i) {
+    tt_chan *c = chans[i];
+    if (!valid_chan(c) || c->e != e || (n[i] && !iq_in[i])) return fail(TT_ERR_INVALID, "push entry %u: bad channel or buffer", i);
+    for (uint32_t j = 0; j < i; ++j)
+      if (chans[j] == c) return fail(TT_ERR_INVALID, "push entry %u: channel repeated", i);
+    tt_status s = check_room(c, first[i], n[i]);
+    if (s != TT_OK) return s;
+  }
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  cudaError_t err = cudaSuccess;
+  for (uint32_t i = 0; i < n_chans && err == cudaSuccess; ++i) {
+    if (!n[i]) continue;
+    tt_chan *c = chans[i];
+    err = wait_ring_readers(c, first[i], n[i], e->h2d);
+    if (err == cudaSuccess)
+      err = ring_copy(c->d_in, c->slot_in_elems, c->Q, first[i], n[i], iq_in[i], nullptr, cudaMemcpyHostToDevice,
+                      e->h2d, true);
+  }
+  if (err == cudaSuccess) err = cudaEventRecord(ev, e->h2d);
+  if (err == cudaSuccess) {
+    lk.unlock();
+    err = cudaEventSynchronize(ev);
+    lk.lock();
+  }
+  e->pool.push_back(ev);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "push copy: %s", cudaGetErrorString(err));
+  for (uint32_t i = 0; i < n_chans; ++i)
+    if (n[i]) mark_pushed(chans[i], first[i], n[i]);
   return TT_OK;
 }
 
@@ -1217,11 +1287,64 @@ static tt_status pull_common(tt_chan *c, uint64_t first, uint32_t n, void *out, 
     if (s != TT_OK) return s;
     update_chan(c);
   }
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
   cudaError_t err = ring_copy(c->d_out, c->slot_out_elems, c->Q, first, n, nullptr, out,
                               cudaMemcpyDeviceToHost, e->copy, false);
-  if (err == cudaSuccess) err = cudaStreamSynchronize(e->copy);
+  if (err == cudaSuccess) err = cudaEventRecord(ev, e->copy);
+  if (err == cudaSuccess) {  // wait for the copy with the engine unlocked (a pusher may run meanwhile)
+    lk.unlock();
+    err = cudaEventSynchronize(ev);
+    lk.lock();
+  }
+  e->pool.push_back(ev);
   if (err != cudaSuccess) return fail(TT_ERR_CUDA, "pull copy: %s", cudaGetErrorString(err));
   c->pulled_end = first + n;
+  return TT_OK;
+}
+
+tt_status tt_engine_pull_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *chans, const uint64_t *first,
+                               const uint32_t *n, void *const *iq_out, int64_t timeout_us) {
+  if (!e || (n_chans && (!chans || !first || !n || !iq_out))) return fail(TT_ERR_INVALID, "tt_engine_pull_slots: bad argument");
+  std::unique_lock<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  uint64_t need = 0;  // the batch that completes the last requested slot of every entry
+  for (uint32_t i = 0; i < n_chans; ++i) {
+    tt_chan *c = chans[i];
+    if (!valid_chan(c) || c->e != e || (n[i] && !iq_out[i])) return fail(TT_ERR_INVALID, "pull entry %u: bad channel or buffer", i);
+    for (uint32_t j = 0; j < i; ++j)
+      if (chans[j] == c) return fail(TT_ERR_INVALID, "pull entry %u: channel repeated", i);
+    if (!n[i]) continue;
+    if (!c->started || first[i] != c->pulled_end)
+      return fail(TT_ERR_STATE, "pull entry %u must start at the oldest unpulled slot %llu", i,
+                  (unsigned long long)c->pulled_end);
+    if (first[i] + n[i] > c->launched_end) return fail(TT_ERR_AGAIN, "pull entry %u: slot not launched yet", i);
+    update_chan(c);
+    if (first[i] + n[i] > c->completed_end)
+      for (auto &p : c->inflight)
+        if (p.first >= first[i] + n[i]) { need = std::max(need, p.second); break; }
+  }
+  if (need) {
+    tt_status s = wait_seq(e, need, timeout_us, lk);
+    if (s != TT_OK) return s;
+  }
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  cudaError_t err = cudaSuccess;
+  for (uint32_t i = 0; i < n_chans && err == cudaSuccess; ++i)
+    if (n[i])
+      err = ring_copy(chans[i]->d_out, chans[i]->slot_out_elems, chans[i]->Q, first[i], n[i], nullptr, iq_out[i],
+                      cudaMemcpyDeviceToHost, e->copy, false);
+  if (err == cudaSuccess) err = cudaEventRecord(ev, e->copy);
+  if (err == cudaSuccess) {
+    lk.unlock();
+    err = cudaEventSynchronize(ev);
+    lk.lock();
+  }
+  e->pool.push_back(ev);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "pull copy: %s", cudaGetErrorString(err));
+  for (uint32_t i = 0; i < n_chans; ++i)
+    if (n[i]) chans[i]->pulled_end = first[i] + n[i];
   return TT_OK;
 }
 

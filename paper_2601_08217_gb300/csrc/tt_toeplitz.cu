@@ -61,7 +61,7 @@ constexpr int kChunkBytes = kN * 16 * 2;
 // shared memory layout (bytes).  The dense delay table is only read while the component tables
 // are built, before any signal is staged for the item, so it shares the signal's space.
 constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
-constexpr int kOffTap = 0;                               // [16 links][128 delays] float4 (H, dH)
+constexpr int kOffTap = 0;                               // [16 links][128 delays] float4 (H, dH), by tap_pos(d)
 constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // kStages x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
 constexpr int kOffComp = kOffW + kStages * kChunkBytes;  // [4 tx][2 parities][kComps][4 rx][kQW words]
 constexpr int kSmemUsed = kOffComp + 16 * kComps * 2 * kQW * 4;
@@ -84,6 +84,10 @@ static_assert(3 * (kSmemBytes + 2048) > 228 * 1024 && 2 * (kSmemBytes + 2048) <=
               "exactly two CTAs per SM");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Position of delay d in a link's row of the dense delay table: even delays first, then odd ones,
+// so the table build, which reads delays two apart across a warp, reads consecutive entries.
+__device__ __forceinline__ int tap_pos(int d) { return (d >> 1) | ((d & 1) << 6); }
 
 // Shared-memory matrix descriptor: start, leading/stride byte offsets, no swizzle.  The start
 // address sits in the low 14 bits (16-byte units), so adding (bytes >> 4) moves the start.
@@ -214,8 +218,10 @@ __global__ void __launch_bounds__(kTPB, 2)
       (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
   const uint32_t sig_base = smem_u32(sig), w_base = smem_u32(wbuf);
 
-  // this builder thread's fixed segment of every tap chunk: row (i, r, part, A|B), k-group kg
-  const int row = tid >> 1, kg = tid & 1;
+  // this builder thread's fixed segment of every tap chunk: row (i, r, part, A|B), k-group kg.
+  // Lanes 8h .. 8h + 7 of a warp take rows 8 (h >> 1) .. + 7 of its 16 and k-group h & 1, so each
+  // quarter-warp stores one contiguous 128-byte run of the chunk.
+  const int row = warp * 16 + ((lane >> 4) << 3) + (lane & 7), kg = (lane >> 3) & 1;
   const int ii = row >> 4, nn = row & 15, rr = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
   const int qoff = kg * 8 - ii + 8, par = qoff & 1;
   // (op, p) -> component: (0,0) hr, (0,1) -hi, (1,0) hi, (1,1) hr
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(kTPB, 2)
             h0 = tt::tt_anchor(U, a, e, per);
             h1 = tt::tt_anchor(U, a + 1, e, per);
           }
-          float *v = reinterpret_cast<float *>(&tapd[(r * 4 + t) * 128 + d]);
+          float *v = reinterpret_cast<float *>(&tapd[(r * 4 + t) * 128 + tap_pos(d)]);
           atomicAdd(v + 0, h0.x);
           atomicAdd(v + 1, h0.y);
           atomicAdd(v + 2, h1.x - h0.x);
@@ -342,7 +348,8 @@ __global__ void __launch_bounds__(kTPB, 2)
               const int d = 136 - (2 * qh + h + tpar);
               float v = 0.f;
               if (d >= 0 && d <= 127) {
-                const float2 hv = (c & 2) ? make_float2(tl[d].z, tl[d].w) : make_float2(tl[d].x, tl[d].y);
+                const float4 tv = tl[tap_pos(d)];
+                const float2 hv = (c & 2) ? make_float2(tv.z, tv.w) : make_float2(tv.x, tv.y);
                 v = (c & 1) ? hv.y : hv.x;
               }
               pk |= (uint32_t)to_op<FP16>(v) << (16 * h);

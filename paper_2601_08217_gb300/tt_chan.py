@@ -107,6 +107,8 @@ _SIGS = {
     "tt_chan_pull_slot": [_VP, C.POINTER(C.c_uint64), _VP, C.c_int64],
     "tt_chan_pull_slots": [_VP, C.c_uint64, C.c_uint32, _VP, C.c_int64],
     "tt_chan_pull_slots_dev": [_VP, C.c_uint64, C.c_uint32, _VP, _VP],
+    "tt_engine_push_slots": [_VP, C.c_uint32, _VP, _VP, _VP, _VP],
+    "tt_engine_pull_slots": [_VP, C.c_uint32, _VP, _VP, _VP, _VP, C.c_int64],
     "tt_chan_slot_output": [_VP, C.c_uint64, C.POINTER(_VP)],
     "tt_chan_release_slots": [_VP, C.c_uint64, C.c_uint32],
     "tt_chan_get_state": [_VP, _VP, C.POINTER(C.c_size_t)],
@@ -291,6 +293,29 @@ def tt_chan_pull_slot(c: int, iq_out, timeout_us: int = -1) -> int:
 
 def tt_chan_pull_slots(c: int, first: int, n: int, iq_out, timeout_us: int = -1):
     _check(load().tt_chan_pull_slots(c, first, n, _ptr(iq_out), timeout_us))
+
+
+def _many(chans, first, n, bufs):
+    k = len(chans)
+    hs = (C.c_void_p * k)(*chans)
+    fs = (C.c_uint64 * k)(*first)
+    ns = (C.c_uint32 * k)(*n)
+    ps = (C.c_void_p * k)(*[_ptr(b) for b in bufs])
+    return k, hs, fs, ns, ps
+
+
+def tt_engine_push_slots(e: int, chans, first, n, iq_in):
+    """Push slots of many channels in one call: entry i is (chans[i], first[i], n[i], iq_in[i])."""
+    k, hs, fs, ns, ps = _many(chans, first, n, iq_in)
+    _check(load().tt_engine_push_slots(e, k, C.cast(hs, C.c_void_p), C.cast(fs, C.c_void_p),
+                                       C.cast(ns, C.c_void_p), C.cast(ps, C.c_void_p)))
+
+
+def tt_engine_pull_slots(e: int, chans, first, n, iq_out, timeout_us: int = -1):
+    """Pull slots of many channels in one call: entry i is (chans[i], first[i], n[i], iq_out[i])."""
+    k, hs, fs, ns, ps = _many(chans, first, n, iq_out)
+    _check(load().tt_engine_pull_slots(e, k, C.cast(hs, C.c_void_p), C.cast(fs, C.c_void_p),
+                                       C.cast(ns, C.c_void_p), C.cast(ps, C.c_void_p), timeout_us))
 
 
 def tt_chan_pull_slots_dev(c: int, first: int, n: int, d_iq_out, stream=None):

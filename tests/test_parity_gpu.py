@@ -318,3 +318,94 @@ def test_device_buffers_and_zero_copy_paths():
     got = torch.cat([out, last], 0).cpu().numpy()
     assert np.array_equal(tc.antenna_major(got), ref)
     eng.close()
+
+
+def test_producer_and_consumer_threads_on_one_channel_equal_bulk():
+    """One thread pushes and launches slot after slot while another pulls them, on the same
+    channels, through a ring only a few slots deep: the output equals the bulk run bit for bit,
+    and the ring-full refusal (TT_ERR_AGAIN) is the producer's only back-pressure."""
+    import threading
+    import time
+    specs = inputs.workload_plain_16ue(n_slots=12, n_ues=3)
+    xs = [inputs.make_iq(2, sp, 12) for sp in specs]
+    bulk = run_gpu(specs, xs, 12)
+    eng = tc.Engine(persistent=True)
+    try:
+        from tests.gpu_harness import hist_slots
+        chans = [tc.Chan(eng, sp, ring_slots=hist_slots(sp) + 3) for sp in specs]
+        outs = [[None] * 12 for _ in specs]
+        launched = []
+        lock = threading.Condition()
+        err = []
+
+        def producer():
+            try:
+                for s in range(12):
+                    for ch, x in zip(chans, xs):
+                        while True:
+                            try:
+                                ch.push(s, tc.slots_major(x, ch.n)[s:s + 1])
+                                break
+                            except tc.TTError as ex:
+                                if ex.status != tc.TT_ERR_AGAIN:
+                                    raise
+                                time.sleep(1e-4)
+                    eng.run()
+                    with lock:
+                        launched.append(s)
+                        lock.notify()
+            except Exception as ex:
+                err.append(ex)
+                with lock:
+                    launched.append(None)
+                    lock.notify()
+
+        th = threading.Thread(target=producer)
+        th.start()
+        for s in range(12):
+            with lock:
+                lock.wait_for(lambda: len(launched) > s)
+                if launched[s] is None:
+                    break
+            for i, ch in enumerate(chans):
+                outs[i][s] = ch.pull(s, 1)
+        th.join()
+        assert not err, err
+        for i in range(len(specs)):
+            got = tc.antenna_major(np.concatenate(outs[i], axis=0))
+            assert np.array_equal(got, bulk[i])
+    finally:
+        eng.close()
+
+
+def test_many_channel_push_and_pull_equal_per_channel_calls():
+    """tt_engine_push_slots / tt_engine_pull_slots move every channel's slots in one call and give
+    the same bits as per-channel calls; a repeated channel or an out-of-order slot is refused
+    before anything is copied."""
+    specs = inputs.workload_plain_16ue(n_slots=6, n_ues=3)
+    xs = [tc.slots_major(inputs.make_iq(2, sp, 6), sp.n) for sp in specs]
+    bulk = run_gpu(specs, [inputs.make_iq(2, sp, 6) for sp in specs], 6)
+    eng = tc.Engine(persistent=True)
+    try:
+        chans = [tc.Chan(eng, sp, ring_slots=10) for sp in specs]
+        hs = [ch.h for ch in chans]
+        with pytest.raises(tc.TTError) as ex:
+            tc.tt_engine_push_slots(eng.h, [hs[0], hs[0]], [0, 0], [3, 3], [xs[0], xs[0]])
+        assert ex.value.status == tc.TT_ERR_INVALID
+        outs = [np.zeros((6, 1, sp.n, 2), dtype=np.int16) for sp in specs]
+        for s0 in (0, 3):
+            bufs = [np.ascontiguousarray(x[s0:s0 + 3]) for x in xs]
+            tc.tt_engine_push_slots(eng.h, hs, [s0] * 3, [3] * 3, bufs)
+            eng.run()
+        with pytest.raises(tc.TTError) as ex:
+            tc.tt_engine_pull_slots(eng.h, hs, [3] * 3, [3] * 3, [o[3:] for o in outs])
+        assert ex.value.status == tc.TT_ERR_STATE
+        for s0 in (0, 3):
+            part = [np.zeros((3, 1, sp.n, 2), dtype=np.int16) for sp in specs]
+            tc.tt_engine_pull_slots(eng.h, hs, [s0] * 3, [3] * 3, part)
+            for o, p in zip(outs, part):
+                o[s0:s0 + 3] = p
+        for i in range(3):
+            assert np.array_equal(tc.antenna_major(outs[i]), bulk[i])
+    finally:
+        eng.close()
