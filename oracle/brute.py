@@ -53,11 +53,46 @@ def anchor_exact(taps: np.ndarray, a_start: int, a: int, step_samples, loop: boo
     return out
 
 
+def round_f32(v: Fraction) -> Fraction:
+    """v rounded to the nearest binary32 value (ties to even), as an exact Fraction."""
+    if v == 0:
+        return Fraction(0)
+    sign = -1 if v < 0 else 1
+    a = abs(v)
+    e = a.numerator.bit_length() - a.denominator.bit_length()   # 2^(e-1) <= a < 2^(e+1)
+    if Fraction(2) ** e > a:
+        e -= 1                                                   # now 2^e <= a < 2^(e+1)
+    e = max(e, -126)                                             # subnormals share the last exponent
+    scale = Fraction(2) ** (e - 23)                              # spacing of binary32 values at a
+    return sign * round(a / scale) * scale                      # round(): ties to even
+
+
+def keep_top_n(H, top_n: int):
+    """Sparse convolution (Sec. III-C): per link, the top_n taps of |H[a]|^2, ties to the lower
+    index.  The powers are taken as the kernel takes them: components rounded to binary32 and
+    p = fma(re, re, im * im) in binary32 (each operation rounded once)."""
+    n_rx, n_tx, K = len(H), len(H[0]), len(H[0][0])
+    keep = [[[True] * K for _ in range(n_tx)] for _ in range(n_rx)]
+    if not top_n or top_n >= K:
+        return keep
+    for r in range(n_rx):
+        for t in range(n_tx):
+            p = []
+            for k in range(K):
+                re, im = round_f32(H[r][t][k][0]), round_f32(H[r][t][k][1])
+                p.append(round_f32(re * re + round_f32(im * im)))
+            for k in range(K):
+                beat = sum(1 for j in range(K) if p[j] > p[k] or (p[j] == p[k] and j < k))
+                keep[r][t][k] = beat < top_n
+    return keep
+
+
 def run_exact(symbol_len: Sequence[int], delays: Sequence[int], taps: np.ndarray, x: np.ndarray,
-              s_first: int = 0, step_samples=0, loop: bool = False):
+              s_first: int = 0, step_samples=0, loop: bool = False, top_n: int = 0):
     """Exact y (lists of Fraction pairs) and packed q for slots s_first.. of one UE.
 
-    x: int16 [n_tx][n_slots*N][2]; taps: complex [T][n_rx][n_tx][K].
+    x: int16 [n_tx][n_slots*N][2]; taps: complex [T][n_rx][n_tx][K].  top_n > 0 keeps, for each
+    symbol and link, only the top_n taps of the symbol's anchor (Sec. III-C sparse convolution).
     Returns (y, q) with y[r][i] = (re, im) Fractions and q int16 [n_rx][n_slots*N][2].
     """
     L = list(symbol_len)
@@ -76,6 +111,7 @@ def run_exact(symbol_len: Sequence[int], delays: Sequence[int], taps: np.ndarray
             nxt_abs = b_abs + Lj                     # first sample of anchor a+1
             H0 = anchor_exact(taps, b_abs, a, step_samples, loop)
             H1 = anchor_exact(taps, nxt_abs, a + 1, step_samples, loop)
+            keep = keep_top_n(H0, top_n)
             for off in range(Lj):
                 i = sl * n + b_local + off           # index inside the processed block
                 tau = Fraction(off, Lj)
@@ -85,7 +121,7 @@ def run_exact(symbol_len: Sequence[int], delays: Sequence[int], taps: np.ndarray
                     for t in range(n_tx):
                         for k, d in enumerate(delays):
                             src = i - int(d)
-                            if src < 0:
+                            if src < 0 or not keep[r][t][k]:
                                 continue
                             h0, h1 = H0[r][t][k], H1[r][t][k]
                             hr = h0[0] + tau * (h1[0] - h0[0])

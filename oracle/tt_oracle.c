@@ -136,7 +136,17 @@ void tto_anchor(const tto_ue *u, uint64_t a, double *out) {
     out[e] = (double)h0[e] + f * ((double)h1[e] - (double)h0[e]);
 }
 
-/* keep[(r*n_tx+t)*n_taps+k] = 1 for the top_n taps of |H[a]|^2 per link (ties: lower k) */
+/* Sparse convolution (Sec. III-C): keep[(r*n_tx+t)*n_taps+k] = 1 for the top_n taps of |H[a]|^2
+ * per link (ties: lower k).  The selection is a decision taken from floating-point values, so it
+ * is taken in the precision of the GPU kernel that also takes it: the anchor rounded to FP32 and
+ * p = fma(re, re, im * im) in FP32.  The selection of anchor a holds for the whole symbol
+ * [b_a, b_{a+1}); each kept tap is interpolated toward its own H[a+1]. */
+static float tap_power_f32(const double *h) {
+  const float re = (float)h[0], im = (float)h[1];
+  const float im2 = im * im;
+  return fmaf(re, re, im2);
+}
+
 static void top_n_mask(const tto_ue *u, const double *H, unsigned char *keep) {
   for (uint32_t r = 0; r < u->n_rx; ++r)
     for (uint32_t t = 0; t < u->n_tx; ++t) {
@@ -144,10 +154,10 @@ static void top_n_mask(const tto_ue *u, const double *H, unsigned char *keep) {
       for (uint32_t k = 0; k < u->n_taps; ++k) {
         if (u->top_n == 0 || u->top_n >= u->n_taps) { keep[base + k] = 1; continue; }
         /* rank = number of taps that beat tap k */
-        double pk = H[2 * (base + k)] * H[2 * (base + k)] + H[2 * (base + k) + 1] * H[2 * (base + k) + 1];
+        const float pk = tap_power_f32(H + 2 * (base + k));
         uint32_t rank = 0;
         for (uint32_t j = 0; j < u->n_taps; ++j) {
-          double pj = H[2 * (base + j)] * H[2 * (base + j)] + H[2 * (base + j) + 1] * H[2 * (base + j) + 1];
+          const float pj = tap_power_f32(H + 2 * (base + j));
           if (pj > pk || (pj == pk && j < k)) ++rank;
         }
         keep[base + k] = rank < u->top_n;

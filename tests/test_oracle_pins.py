@@ -346,3 +346,57 @@ def test_top_n_selects_dominant_taps():
     ref = np.zeros_like(xc)
     ref[5:] = (3 - 1j) * xc[:-5]
     assert np.allclose(y1[0], ref, rtol=0, atol=1e-9)
+
+
+TOPN_CASES = [
+    # symbol_len, n_tx, n_rx, delays, n_slots, step_samples, top_n
+    ([6, 5, 5], 1, 1, [0, 2, 5, 9, 11], 2, 0, 2),
+    ([5, 4, 4, 4], 2, 2, [0, 1, 3, 7, 8, 20], 2, 0, 3),
+    ([4, 4], 1, 2, [0, 3, 9, 10], 3, 5.5, 1),           # selection from trace-time anchors
+]
+
+
+@pytest.mark.parametrize("case", range(len(TOPN_CASES)))
+def test_top_n_equals_exact_brute_force(case):
+    """The per-symbol, per-link selection (Sec. III-C) and the convolution with only the kept taps
+    agree with the exact rational brute force, whose selection rounds each power to binary32 as
+    the kernel does; the selection changes from symbol to symbol here (taps drawn per anchor)."""
+    L, n_tx, n_rx, d, n_slots, step, top_n = TOPN_CASES[case]
+    rng = np.random.default_rng(300 + case)
+    n = sum(L)
+    T = int(np.ceil(n_slots * n / step)) + 3 if step else len(L) * n_slots + 1
+    taps = _rand_taps(rng, T, n_rx, n_tx, len(d))
+    x = rng.integers(-3000, 3000, size=(n_tx, n_slots * n, 2)).astype(np.int16)
+    ue = oracle.OracleUE(L, n_tx, n_rx, d, taps, step_samples=step, top_n=top_n)
+    y, q = oracle.run_ue(ue, x)
+    ye, qe = brute.run_exact(L, d, taps, x, step_samples=step, top_n=top_n)
+    ye = brute.to_complex(ye)
+    assert nrmse(y, ye) < 1e-13
+    assert np.array_equal(q, qe)
+    full, _ = oracle.run_ue(oracle.OracleUE(L, n_tx, n_rx, d, taps, step_samples=step), x)
+    assert nrmse(y, full) > 1e-3                          # the sparse result really differs
+
+
+def test_top_n_ties_keep_the_lower_tap_and_follow_each_anchor():
+    """Equal powers: the lower tap index wins.  A static profile whose dominant tap moves from
+    index 1 (anchor 0) to index 3 (anchor 1) makes top-1 switch taps at the symbol boundary."""
+    L = [4, 4]
+    d = np.array([0, 1, 2, 3], dtype=np.int32)
+    x = np.zeros((1, 8, 2), dtype=np.int16)
+    x[0, 0, 0] = 1000                                     # unit impulse of height 1000 at sample 0
+    # anchors: tap powers equal (1, 1j, -1, 0.5 - 0.5j has 0.5) -> top-1 keeps tap 0
+    eq = np.array([1.0, 1j, -1.0, 0.5 - 0.5j], dtype=np.complex64).reshape(1, 1, 1, 4)
+    y, _ = oracle.run_ue(oracle.OracleUE(L, 1, 1, d, np.tile(eq, (3, 1, 1, 1)), top_n=1), x)
+    assert np.allclose(y[0, :4], [1000, 0, 0, 0], atol=1e-9)
+    # anchor 0 favours tap 1, anchor 1 tap 3 (taps interpolate toward the next anchor)
+    a0 = np.array([0.1, 2.0, 0.1, 0.1], dtype=np.complex64)
+    a1 = np.array([0.1, 0.1, 0.1, 3.0], dtype=np.complex64)
+    taps = np.stack([a0, a1, a1]).reshape(3, 1, 1, 4)
+    x2 = np.zeros((1, 8, 2), dtype=np.int16)
+    x2[0, :, 0] = 100                                     # constant input: y = sum of kept taps
+    y2, _ = oracle.run_ue(oracle.OracleUE(L, 1, 1, d, taps, top_n=1), x2)
+    for m in range(4):                                    # symbol 0 keeps tap 1 (delay 1)
+        h = a0[1] + (m / 4) * (a1[1] - a0[1])
+        assert abs(y2[0, m] - (100 * h if m >= 1 else 0)) < 1e-4
+    for m in range(4, 8):                                 # symbol 1 keeps tap 3 (delay 3)
+        assert abs(y2[0, m] - 100 * a1[3]) < 1e-4
