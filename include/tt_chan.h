@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define TT_CHAN_ABI_VERSION 1
+#define TT_CHAN_ABI_VERSION 2
 
 typedef struct tt_engine tt_engine; /* one per GPU: stream, HBM budget, form, UE table */
 typedef struct tt_chan tt_chan;     /* one per UE link: config, trace, delay line, rings */
@@ -115,6 +115,11 @@ typedef struct {
   uint32_t precision;         /* TT_FP32: CUDA-core FP32 path.  TT_BF16_TC / TT_FP16_TC: block-Toeplitz
                                  tensor-core path (tcgen05, FP32 accumulation), delays <= 127 */
   uint32_t output_format;     /* TT_OUT_INT16 (packed IQ) or TT_OUT_CF32 (complex64 before packing) */
+  uint32_t top_n;             /* sparse convolution (Sec. III-C): 0 = every tap; n > 0 = for each OFDM
+                                 symbol and (r, t) link only the n taps of largest |H[a]|^2 at the
+                                 symbol's anchor a (ties: lower tap index), each interpolated toward
+                                 its H[a+1].  The powers are binary32, p = fma(re, re, im * im).
+                                 TT_FP32 batched form only (TT_ERR_INVALID otherwise) */
 } tt_chan_config;
 
 typedef struct {

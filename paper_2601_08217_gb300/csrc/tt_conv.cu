@@ -40,6 +40,16 @@ int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, 
 }
 
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st) {
+  if (L.topn) {
+    switch (L.spt) {
+      case 1: return tt_launch_conv_s1_topn(L, st);
+      case 2: return tt_launch_conv_s2_topn(L, st);
+      case 4: return tt_launch_conv_s4_topn(L, st);
+      case 8: return tt_launch_conv_s8_topn(L, st);
+      case 16: return tt_launch_conv_s16_topn(L, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (L.spt) {
     case 1: return tt_launch_conv_s1(L, st);
     case 2: return tt_launch_conv_s2(L, st);

@@ -178,7 +178,54 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
 
 // All threads, after the copies landed: raw window -> phase planes, taps -> (H0, dH),
 // delays -> plane offsets.
+// Sparse convolution (Sec. III-C): for every touched symbol jl and link (r, t), keep the top_n taps
+// of largest |H[a]|^2 at the symbol's anchor (ties: lower tap index) and compact them, in tap
+// order, to the front of the tap table: entry ((jl * NRX + r) * n_tx + t) * top_n + i holds
+// (H, dH) of the i-th kept tap and its plane offset.  The powers are binary32,
+// p = fma(re, re, im * im), the precision the oracle takes the same decision in.  The raw window
+// has been converted to planes, so its storage holds the powers, keep flags and compacted lists.
 template <int S, int NRX, int NP>
+__device__ __forceinline__ void tt_select_top_n(const TTUEDesc *__restrict__ U, const TTItem &it, uint32_t *raw,
+                                                float4 *taps, int *dly, int tid) {
+  const int n_tx = U->n_tx, K = U->n_taps, nsel = U->top_n;
+  const int ntap_e = it.nst * NRX * n_tx * K;
+  const int nseg = it.nst * NRX * n_tx;
+  float *pw = reinterpret_cast<float *>(raw);
+  int *keep = reinterpret_cast<int *>(raw) + ((ntap_e + 3) & ~3);
+  float4 *ctap = reinterpret_cast<float4 *>(keep + ((ntap_e + 3) & ~3));
+  int *coff = reinterpret_cast<int *>(ctap + nseg * nsel);
+  __syncthreads();  // every thread is done with the raw window and the (H, dH) conversion
+  for (int e = tid; e < ntap_e; e += TT_TPB) {
+    const float4 h = taps[e];
+    pw[e] = __fmaf_rn(h.x, h.x, __fmul_rn(h.y, h.y));
+  }
+  __syncthreads();
+  for (int e = tid; e < ntap_e; e += TT_TPB) {
+    const int seg = e / K, k = e - seg * K;
+    const float *ps = pw + seg * K;
+    const float pk = ps[k];
+    int beat = 0;
+    for (int j = 0; j < K; ++j) beat += (ps[j] > pk) || (ps[j] == pk && j < k);
+    keep[e] = beat < nsel;
+  }
+  __syncthreads();
+  for (int e = tid; e < ntap_e; e += TT_TPB) {
+    if (!keep[e]) continue;
+    const int seg = e / K, k = e - seg * K;
+    int pos = 0;
+    for (int j = 0; j < k; ++j) pos += keep[seg * K + j];
+    ctap[seg * nsel + pos] = taps[e];
+    const int d = dly[k];  // the trace's delay, not yet an offset
+    coff[seg * nsel + pos] = (S - d % S) * NP - d / S;
+  }
+  __syncthreads();
+  for (int e = tid; e < nseg * nsel; e += TT_TPB) {
+    taps[e] = ctap[e];
+    dly[e] = coff[e];
+  }
+}
+
+template <int S, int NRX, int NP, bool TOPN>
 __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, const TTItem &it,
                                                 const uint32_t *raw, int wmax, float2 *planes, float4 *taps,
                                                 int *dly, int tid) {
@@ -228,14 +275,18 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
       taps[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
     }
   }
-  for (int k = tid; k < K; k += TT_TPB) {
-    const int d = dly[k];
-    dly[k] = (S - d % S) * NP - d / S;
+  if constexpr (TOPN) {  // every UE of a TOPN launch keeps fewer taps than it has
+    tt_select_top_n<S, NRX, NP>(U, it, const_cast<uint32_t *>(raw), taps, dly, tid);
+  } else {
+    for (int k = tid; k < K; k += TT_TPB) {
+      const int d = dly[k];
+      dly[k] = (S - d % S) * NP - d / S;
+    }
   }
 }
 
 // All threads: S consecutive outputs per thread of one item, all Rx antennas, fused epilogue.
-template <int S, int NRX, int NP>
+template <int S, int NRX, int NP, bool TOPN>
 __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, const TTItem &it,
                                                 const float2 *planes, const float4 *taps, const int *offk,
                                                 const int *sym, int tid) {
@@ -261,8 +312,37 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
 #pragma unroll
     for (int jj = 0; jj < S; ++jj) acc[r][jj] = make_float2(0.f, 0.f);
 
-  const float4 *tb = taps + (j - it.jf) * per;
   const int q0 = tid + U->dpad / S;
+  if constexpr (TOPN) {
+    // sparse convolution: the compacted top-n list of this symbol, per link, with its own offsets
+    const int nsel = U->top_n;
+    const float4 *tb = taps + (j - it.jf) * NRX * n_tx * nsel;
+    const int *ob = offk + (j - it.jf) * NRX * n_tx * nsel;
+    for (int t = 0; t < n_tx; ++t) {
+      const float2 *pl = planes + t * (2 * S * NP) + q0;
+#pragma unroll
+      for (int r = 0; r < NRX; ++r) {
+        const float4 *tl = tb + (r * n_tx + t) * nsel;
+        const int *ol = ob + (r * n_tx + t) * nsel;
+#pragma unroll KU
+        for (int k = 0; k < nsel; ++k) {
+          const float2 *px = pl + ol[k];
+          const float4 h = tl[k];
+          const float2 h0 = make_float2(h.x, h.y), dh = make_float2(h.z, h.w);
+#pragma unroll
+          for (int jj = 0; jj < S; ++jj) {
+            const float2 xv = px[jj * NP];
+            const float2 hv = tt_fma2(tau2[jj], dh, h0);
+            acc[r][jj].x = fmaf(hv.x, xv.x, acc[r][jj].x);
+            acc[r][jj].x = fmaf(-hv.y, xv.y, acc[r][jj].x);
+            acc[r][jj].y = fmaf(hv.x, xv.y, acc[r][jj].y);
+            acc[r][jj].y = fmaf(hv.y, xv.x, acc[r][jj].y);
+          }
+        }
+      }
+    }
+  } else {
+  const float4 *tb = taps + (j - it.jf) * per;
   for (int t = 0; t < n_tx; ++t) {
     const float2 *pl = planes + t * (2 * S * NP) + q0;
     const float4 *tbt = tb + t * K;
@@ -286,6 +366,7 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
         }
       }
     }
+  }
   }
 
   const float nstd = U->noise_std;
@@ -327,7 +408,7 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
 // SM and hide each other's staging barriers; the wider variants keep the compiler's choice.
 constexpr int tt_min_blocks(int S, int NRX) { return (NRX == 1 && S <= 8) ? 8 : 1; }
 
-template <int S, int NRX, int DMAX>
+template <int S, int NRX, int DMAX, bool TOPN>
 __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     tt_conv_fp32_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                         uint32_t total_items, uint32_t *__restrict__ counter, int ntx, int tap_max, int k_max,
@@ -369,7 +450,7 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     tt_issue_item<S, NRX>(U, it, raw, WMAX, taps0, dly0, s_sym[0], tid);
     tt_cp_async_wait_all();
     __syncthreads();
-    tt_convert_item<S, NRX, NP>(U, it, raw, WMAX, planes, taps0, dly0, tid);
+    tt_convert_item<S, NRX, NP, TOPN>(U, it, raw, WMAX, planes, taps0, dly0, tid);
     if (tid == 0) tt_locate(ues, segs, n_segs, s_claim, total_items, cursors, s_it[1]);
     __syncthreads();
   }
@@ -382,22 +463,22 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     int *dc = cb ? dly1 : dly0, *dn = cb ? dly0 : dly1;
     const TTUEDesc *Un = ues + nxt.ue;
     if (nxt.valid) tt_issue_item<S, NRX>(Un, nxt, raw, WMAX, tn, dn, s_sym[cb ^ 1], tid);
-    tt_compute_item<S, NRX, NP>(ues + cur.ue, cur, planes, tc, dc, s_sym[cb], tid);
+    tt_compute_item<S, NRX, NP, TOPN>(ues + cur.ue, cur, planes, tc, dc, s_sym[cb], tid);
     uint32_t nn = 0;
     if (tid == 0 && nxt.valid) nn = claim();
     tt_cp_async_wait_all();
     __syncthreads();
     if (!nxt.valid) return;
-    tt_convert_item<S, NRX, NP>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
+    tt_convert_item<S, NRX, NP, TOPN>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
     if (tid == 0) tt_locate(ues, segs, n_segs, nn, total_items, cursors, s_it[cb]);
     __syncthreads();
     cb ^= 1;
   }
 }
 
-template <int S, int NRX, int DMAX>
+template <int S, int NRX, int DMAX, bool TOPN>
 cudaError_t tt_launch_variant(const TTLaunch &L, cudaStream_t st) {
-  auto kern = tt_conv_fp32_kernel<S, NRX, DMAX>;
+  auto kern = tt_conv_fp32_kernel<S, NRX, DMAX, TOPN>;
   static bool attr_done = false;  // benign race: the attribute call is idempotent
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -416,27 +497,27 @@ cudaError_t tt_launch_variant(const TTLaunch &L, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int S, int NRX>
+template <int S, int NRX, bool TOPN>
 cudaError_t tt_launch_dclass(const TTLaunch &L, cudaStream_t st) {
   switch (L.dclass) {
-    case 0: return tt_launch_variant<S, NRX, TT_DCLASS0>(L, st);
-    case 1: return tt_launch_variant<S, NRX, TT_DCLASS1>(L, st);
-    case 2: return tt_launch_variant<S, NRX, TT_DCLASS2>(L, st);
-    case 3: return tt_launch_variant<S, NRX, TT_DCLASS3>(L, st);
+    case 0: return tt_launch_variant<S, NRX, TT_DCLASS0, TOPN>(L, st);
+    case 1: return tt_launch_variant<S, NRX, TT_DCLASS1, TOPN>(L, st);
+    case 2: return tt_launch_variant<S, NRX, TT_DCLASS2, TOPN>(L, st);
+    case 3: return tt_launch_variant<S, NRX, TT_DCLASS3, TOPN>(L, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int S>
+template <int S, bool TOPN>
 cudaError_t tt_launch_spt(const TTLaunch &L, cudaStream_t st) {
   switch (L.nrx) {
-    case 1: return tt_launch_dclass<S, 1>(L, st);
-    case 2: return tt_launch_dclass<S, 2>(L, st);
+    case 1: return tt_launch_dclass<S, 1, TOPN>(L, st);
+    case 2: return tt_launch_dclass<S, 2, TOPN>(L, st);
     case 3:
-      if constexpr (S <= 8) return tt_launch_dclass<S, 3>(L, st);
+      if constexpr (S <= 8) return tt_launch_dclass<S, 3, TOPN>(L, st);
       return cudaErrorInvalidValue;
     case 4:
-      if constexpr (S <= 8) return tt_launch_dclass<S, 4>(L, st);
+      if constexpr (S <= 8) return tt_launch_dclass<S, 4, TOPN>(L, st);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

@@ -309,12 +309,26 @@ tt_status set_spt(tt_chan *c, int spt) {
   return TT_OK;
 }
 
-// Shared-memory need of a traced channel at spt samples per thread (0 if it does not fit).
+// Sparse convolution is active when top_n keeps fewer taps than the trace has.
+bool sparse(const tt_chan *c) { return c->desc.top_n > 0 && c->desc.top_n < c->desc.n_taps; }
+
+// Length of the kernel's per-item delay-offset array: the trace's taps, or with sparse convolution
+// the compacted lists of every touched symbol and link (at most tap_need entries).
+int k_need(const tt_chan *c, int tap_need) { return sparse(c) ? std::max(c->desc.n_taps, tap_need) : c->desc.n_taps; }
+
+// Shared-memory need of a traced channel at spt samples per thread (0 if it does not fit).  With
+// sparse convolution the kernel selects taps in its raw staging area (powers, keep flags,
+// compacted taps and offsets), which must hold them.
 size_t smem_need(const tt_chan *c, int spt, int *tap_need) {
   int touched = 1;
   chunk_table(c->sym_len, spt, &touched);
   *tap_need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * (uint32_t)c->desc.n_taps);
-  const size_t b = tt_conv_smem_bytes(spt, c->dclass, (int)c->cfg.n_tx, *tap_need, c->desc.n_taps);
+  if (sparse(c)) {
+    const size_t raw = (size_t)(((int)c->cfg.n_tx * tt_geo_wmax(spt, tt_dclass_max(c->dclass)) + 3) & ~3) * 4;
+    const size_t scratch = (size_t)((*tap_need + 3) & ~3) * 4 * 2 + (size_t)*tap_need * (16 + 4);
+    if (scratch > raw) return 0;
+  }
+  const size_t b = tt_conv_smem_bytes(spt, c->dclass, (int)c->cfg.n_tx, *tap_need, k_need(c, *tap_need));
   return b <= 200 * 1024 ? b : 0;
 }
 
@@ -338,6 +352,7 @@ struct PlanGroup {
   uint32_t items = 0;
   size_t smem = 0;
   int spt = 1, nrx = 1, ntx = 1, dclass = 0, tap_max = 1, k_max = 1, grid = 1;
+  int topn = 0;  // the group's UEs use sparse convolution
 };
 struct Plan {
   std::vector<TTSeg> segs;
@@ -354,7 +369,7 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
   auto vkey = [&](size_t i) {
     const tt_chan *c = chans[i];
-    return ((c->spt * 8 + (int)c->cfg.n_rx) * 8 + (int)c->cfg.n_tx) * 8 + c->dclass;
+    return (((c->spt * 8 + (int)c->cfg.n_rx) * 8 + (int)c->cfg.n_tx) * 8 + c->dclass) * 2 + (sparse(c) ? 1 : 0);
   };
   auto cost = [&](size_t i) {
     const tt_chan *c = chans[i];
@@ -377,6 +392,7 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
       g.nrx = (int)c->cfg.n_rx;
       g.ntx = (int)c->cfg.n_tx;
       g.dclass = c->dclass;
+      g.topn = sparse(c) ? 1 : 0;
       p.groups.push_back(g);
     }
     PlanGroup &g = p.groups.back();
@@ -388,7 +404,7 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
     sg.items = sg.n_slots * (uint32_t)c->desc.items_per_slot;
     g.items += sg.items;
     g.tap_max = std::max(g.tap_max, c->tap_need);
-    g.k_max = std::max(g.k_max, c->desc.n_taps);
+    g.k_max = std::max(g.k_max, k_need(c, c->tap_need));
     ++g.nseg;
     p.segs.push_back(sg);
     p.chans.push_back(c);
@@ -402,6 +418,7 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
     L.nrx = g.nrx;
     L.ntx = g.ntx;
     L.dclass = g.dclass;
+    L.topn = g.topn;
     L.smem = g.smem;
     L.grid = -1;  // occupancy query
     cudaError_t err = tt_launch_conv_fp32(L, e->stream);
@@ -444,6 +461,7 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
     L.dclass = g.dclass;
     L.tap_max = g.tap_max;
     L.k_max = g.k_max;
+    L.topn = g.topn;
     L.smem = g.smem;
     L.grid = g.grid;
     L.cursors = cursors;
@@ -734,6 +752,8 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   if (cfg->max_delay > TT_MAX_DELAY) return fail(TT_ERR_INVALID, "max_delay must be <= %d", TT_MAX_DELAY);
   if (cfg->precision > TT_FP16_TC) return fail(TT_ERR_INVALID, "unknown precision");
   if (cfg->output_format > TT_OUT_CF32) return fail(TT_ERR_INVALID, "unknown output_format");
+  if (cfg->top_n && (cfg->precision != TT_FP32 || e->form == TT_FORM_PLAIN))
+    return fail(TT_ERR_INVALID, "top_n needs the FP32 batched form");
   if (!(cfg->noise_var >= 0.0f) || !std::isfinite(cfg->noise_var)) return fail(TT_ERR_INVALID, "bad noise_var");
   uint64_t sum = 0;
   for (uint32_t j = 0; j < cfg->symbols_per_slot; ++j) {
@@ -793,6 +813,7 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   d.seed = cfg->seed;
   d.noise_std = cfg->noise_var > 0.f ? (float)std::sqrt((double)cfg->noise_var / 2.0) : 0.f;
   d.out_f32 = cfg->output_format == TT_OUT_CF32 ? 1 : 0;
+  d.top_n = (int)cfg->top_n;
   const std::vector<int> cands = spt_candidates(c->sym_len, e->spt_override, cfg->n_rx);
   tt_status sst = set_spt(c, cands.empty() ? 1 : cands[0]);
   if (sst != TT_OK) {
@@ -1141,7 +1162,8 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
     if (!c || !c->has_trace || c->cfg.precision != TT_FP32) continue;
     std::vector<int64_t> key(c->sym_len.begin(), c->sym_len.end());
     key.insert(key.end(), {(int64_t)c->cfg.n_tx, (int64_t)c->cfg.n_rx, (int64_t)c->desc.n_taps,
-                           (int64_t)c->dclass, (int64_t)(c->desc.noise_std > 0.f), (int64_t)c->desc.out_f32});
+                           (int64_t)c->dclass, (int64_t)(c->desc.noise_std > 0.f), (int64_t)c->desc.out_f32,
+                           (int64_t)c->desc.top_n});
     auto it = std::find_if(classes.begin(), classes.end(), [&](const auto &p) { return p.first == key; });
     if (it == classes.end()) classes.push_back({key, {c}});
     else it->second.push_back(c);

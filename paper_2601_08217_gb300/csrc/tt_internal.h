@@ -53,6 +53,7 @@ struct TTUEDesc {
   int32_t nsym;            // symbols per slot
   int32_t n_tx, n_rx, n_taps;
   int32_t d_max;           // largest delay of the loaded trace
+  int32_t top_n;           // 0: every tap; else the top_n taps per symbol and link (sparse convolution)
   int32_t ring_q;          // ring depth in slots
   int32_t n_anchors;
   int32_t loop;
@@ -92,6 +93,7 @@ struct TTLaunch {
   int grid;             // CTAs; < 0 on input asks for the occupancy (returned as -blocks per SM)
   size_t smem;          // dynamic shared memory bytes (tt_conv_smem_bytes)
   const unsigned long long *cursors;  // non-null: first slot of each run = cursors[ue] (graph replay)
+  int topn;             // 1: every UE of the launch uses sparse convolution (top_n < its tap count)
 };
 
 // cursors[segs[i].ue] += segs[i].n_slots for every segment (device-resident slot cursors).
@@ -107,6 +109,11 @@ cudaError_t tt_launch_conv_s2(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s4(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s8(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s16(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s1_topn(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s2_topn(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s4_topn(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s8_topn(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s16_topn(const TTLaunch &L, cudaStream_t st);
 
 // Block-Toeplitz tensor-core kernel (tcgen05, BF16 or FP16 operands): one work item per
 // (UE, slot, up to 4096 samples of one symbol); status is set to 1 if a bounded wait on the

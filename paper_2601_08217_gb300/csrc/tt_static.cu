@@ -172,6 +172,7 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
     d.ue_id = c.ue_id;
     d.noise_std = c.noise_var > 0.f ? (float)std::sqrt((double)c.noise_var / 2.0) : 0.f;
     d.out_f32 = c.output_format == TT_OUT_CF32 ? 1 : 0;
+    d.top_n = 0;
     d.spt = spt;
     d.dpad = (d_max + spt - 1) / spt * spt;
     d.groups = (int)N / spt;

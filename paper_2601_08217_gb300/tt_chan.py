@@ -45,7 +45,8 @@ class ChanConfig(C.Structure):
                 ("symbols_per_slot", C.c_uint32), ("symbol_len", C.POINTER(C.c_uint32)),
                 ("n_tx", C.c_uint32), ("n_rx", C.c_uint32), ("max_taps", C.c_uint32),
                 ("max_delay", C.c_uint32), ("ring_slots", C.c_uint32), ("seed", C.c_uint64),
-                ("noise_var", C.c_float), ("precision", C.c_uint32), ("output_format", C.c_uint32)]
+                ("noise_var", C.c_float), ("precision", C.c_uint32), ("output_format", C.c_uint32),
+                ("top_n", C.c_uint32)]
 
 
 class TraceDesc(C.Structure):
@@ -235,11 +236,11 @@ def tt_engine_serve(e: int, duration_s: float, warmup_s: float = 0.0, slot_perio
 def tt_chan_create(e: int, samples_per_slot: int, symbol_len: Sequence[int], n_tx: int = 1, n_rx: int = 1,
                    max_taps: int = 128, max_delay: int = 0, ring_slots: int = 0, seed: int = 0,
                    noise_var: float = 0.0, ue_id: int = 0, precision: int = TT_FP32,
-                   output_format: int = TT_OUT_INT16) -> int:
+                   output_format: int = TT_OUT_INT16, top_n: int = 0) -> int:
     lib = load()
     L = (C.c_uint32 * len(symbol_len))(*[int(v) for v in symbol_len])
     cfg = ChanConfig(C.sizeof(ChanConfig), ue_id, samples_per_slot, len(symbol_len), L, n_tx, n_rx,
-                     max_taps, max_delay, ring_slots, seed, noise_var, precision, output_format)
+                     max_taps, max_delay, ring_slots, seed, noise_var, precision, output_format, top_n)
     h = _VP()
     _check(lib.tt_chan_create(e, C.byref(cfg), C.byref(h)))
     return h.value
@@ -414,7 +415,7 @@ class Chan:
     """One UE link.  ``spec`` is an ``inputs.UESpec`` (or anything with its fields)."""
 
     def __init__(self, engine: Engine, spec, ring_slots: int = 0, load: bool = True, cf32: bool = False,
-                 precision: int = TT_FP32):
+                 precision: int = TT_FP32, top_n: int = 0):
         self.engine = engine
         self.spec = spec
         self.cf32 = cf32
@@ -422,7 +423,8 @@ class Chan:
         self.h = tt_chan_create(engine.h, self.n, spec.symbol_len, spec.n_tx, spec.n_rx,
                                 max(int(len(spec.delays)), 1), int(max(spec.max_delay, max(spec.delays))),
                                 ring_slots, int(spec.seed), float(spec.noise_var), int(spec.ue_id),
-                                precision=precision, output_format=TT_OUT_CF32 if cf32 else TT_OUT_INT16)
+                                precision=precision, output_format=TT_OUT_CF32 if cf32 else TT_OUT_INT16,
+                                top_n=top_n)
         engine.chans.append(self)
         if load:
             self.load_trace(spec.taps, spec.delays, spec.step_samples, spec.loop)

@@ -11,7 +11,7 @@ def hist_slots(spec) -> int:
 
 
 def run_gpu(specs, xs, n_slots, first_slot=0, cf32=False, form="batched", spt=0, persistent=False,
-            stream_mode=False, ring_slots=None, precision=tc.TT_FP32):
+            stream_mode=False, ring_slots=None, precision=tc.TT_FP32, top_n=0):
     """Run every UE's slots [first_slot, first_slot + n_slots) and return [n_rx][n_slots*N](...) per UE.
 
     xs[i] is UE i's int16 input [n_tx][n_slots*N][2].  Bulk mode pushes all slots,
@@ -23,7 +23,8 @@ def run_gpu(specs, xs, n_slots, first_slot=0, cf32=False, form="batched", spt=0,
         chans = []
         for sp in specs:
             q = ring_slots if ring_slots else (hist_slots(sp) + 3 if stream_mode else n_slots + hist_slots(sp) + 1)
-            chans.append(tc.Chan(eng, sp, ring_slots=q, cf32=cf32, precision=precision))
+            chans.append(tc.Chan(eng, sp, ring_slots=q, cf32=cf32, precision=precision,
+                                 top_n=top_n[len(chans)] if isinstance(top_n, (list, tuple)) else top_n))
         outs = [[] for _ in specs]
         if stream_mode:
             for s in range(n_slots):
