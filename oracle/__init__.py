@@ -11,6 +11,8 @@ Functions and the passages they follow:
   (Sec. IV: discrete complex taps on a fixed delay grid per time step), plus
   optional AWGN and int16 packing.  The interpolation, anchor placement,
   noise and rounding readings are stated in ``tt_oracle.c``'s header.
+* :func:`run_cell` -- Sec. III-A: uplink aggregation at the gNB, the sum of the
+  members' convolved streams plus the cell's own AWGN, then packing.
 * :func:`philox4x32_10` -- the counter-based generator of Salmon et al. (SC'11).
 * :func:`noise` -- one complex AWGN sample from Philox words via Box-Muller.
 * :func:`anchor` -- the trace value at one OFDM-symbol anchor.
@@ -19,4 +21,4 @@ Functions and the passages they follow:
 Pins: ``tests/test_oracle_*.py`` (run with ``-m "not gpu"``).
 """
 from .oracle import (OracleUE, anchor, build, lib_path, max_threads, noise, philox4x32_10,  # noqa: F401
-                     run_ue)
+                     run_cell, run_ue)

@@ -58,6 +58,9 @@ def _load():
                                       C.c_void_p]
             lib.tto_anchor.argtypes = [C.POINTER(_UE), C.c_uint64, C.c_void_p]
             lib.tto_max_threads.restype = C.c_int
+            lib.tto_cell.argtypes = [C.c_uint32, C.c_void_p, C.c_uint32, C.c_uint64, C.c_uint64, C.c_uint64,
+                                     C.c_uint32, C.c_double, C.c_void_p, C.c_void_p]
+            lib.tto_cell.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -113,6 +116,31 @@ def run_ue(ue: OracleUE, x: np.ndarray, s_first: int = 0, nthreads: int = 0,
         raise ValueError("oracle rejected its arguments")
     yc = None if y is None else (y[..., 0] + 1j * y[..., 1])
     return yc, q
+
+
+def run_cell(members, xs, seed: int, cell_id: int, noise_var: float = 0.0, s_first: int = 0):
+    """Uplink aggregation at a cell: the members' outputs (each an OracleUE with its own noise off,
+    all with the cell's samples per slot and Rx antenna count) summed in member order, plus the
+    cell's AWGN keyed by (seed, cell_id), then packed.  xs[u] is member u's int16 input.
+    Returns (y complex128 [n_rx][n_slots*N], q int16 [n_rx][n_slots*N][2])."""
+    lib = _load()
+    ys = []
+    for ue, x in zip(members, xs):
+        if ue.s.noise_var != 0.0:
+            raise ValueError("cell members carry no noise of their own")
+        yc, _ = run_ue(ue, x, s_first=s_first, want_q=False)
+        ys.append(np.ascontiguousarray(np.stack([yc.real, yc.imag], axis=-1)))
+    n_rx, total = ys[0].shape[0], ys[0].shape[1]
+    if any(v.shape != ys[0].shape for v in ys):
+        raise ValueError("members differ in Rx antennas or length")
+    ptrs = (C.c_void_p * len(ys))(*[v.ctypes.data for v in ys])
+    y = np.empty((n_rx, total, 2), dtype=np.float64)
+    q = np.empty((n_rx, total, 2), dtype=np.int16)
+    rc = lib.tto_cell(len(ys), C.cast(ptrs, C.c_void_p), n_rx, total, s_first * members[0].s.n, seed, cell_id,
+                      float(noise_var), y.ctypes.data, q.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle rejected its arguments")
+    return y[..., 0] + 1j * y[..., 1], q
 
 
 def philox4x32_10(ctr: Sequence[int], key: Sequence[int]) -> np.ndarray:

@@ -250,6 +250,47 @@ int tto_run(const tto_ue *u, uint64_t s_first, uint32_t n_slots, const int16_t *
   return 0;
 }
 
+/*
+ * Uplink aggregation at a cell (Sec. III-A, vanilla rfsim: the gNB convolves each UE's uplink
+ * stream with that UE's channel and aggregates the results): for every Rx antenna r and sample i,
+ *   y[r][i] = sum over members u (in the given order) of y_u[r][i]  +  w_cell[r][m_first + i]
+ * with w_cell the AWGN of the cell's own key (seed, cell_id) at absolute sample m_first + i, then
+ * the same round-half-even, saturating packing as tto_run.  The members' y_u come from tto_run with
+ * their own noise off.  y (double [n_rx][total][2]) and q (int16 [n_rx][total][2]) may be NULL.
+ */
+int tto_cell(uint32_t n_members, const double *const *y_members, uint32_t n_rx, uint64_t total,
+             uint64_t m_first, uint64_t seed, uint32_t cell_id, double noise_var, double *y, int16_t *q) {
+  if (!y_members) return -1;
+  for (uint32_t u = 0; u < n_members; ++u)
+    if (!y_members[u]) return -1;
+  for (uint32_t r = 0; r < n_rx; ++r) {
+    for (uint64_t i = 0; i < total; ++i) {
+      const size_t o = ((size_t)r * total + i) * 2;
+      double acc_re = 0.0, acc_im = 0.0;
+      for (uint32_t u = 0; u < n_members; ++u) {
+        acc_re += y_members[u][o];
+        acc_im += y_members[u][o + 1];
+      }
+      if (noise_var > 0.0) {
+        double nz[2];
+        tto_noise(seed, cell_id, r, m_first + i, noise_var, nz);
+        acc_re += nz[0];
+        acc_im += nz[1];
+      }
+      if (y) { y[o] = acc_re; y[o + 1] = acc_im; }
+      if (q) {
+        double v[2] = {nearbyint(acc_re), nearbyint(acc_im)};
+        for (int c = 0; c < 2; ++c) {
+          if (v[c] > 32767.0) v[c] = 32767.0;
+          if (v[c] < -32768.0) v[c] = -32768.0;
+          q[o + c] = (int16_t)v[c];
+        }
+      }
+    }
+  }
+  return 0;
+}
+
 int tto_max_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -400,3 +400,56 @@ def test_top_n_ties_keep_the_lower_tap_and_follow_each_anchor():
         assert abs(y2[0, m] - (100 * h if m >= 1 else 0)) < 1e-4
     for m in range(4, 8):                                 # symbol 1 keeps tap 3 (delay 3)
         assert abs(y2[0, m] - 100 * a1[3]) < 1e-4
+
+
+# --------------------------------------------------------------------------
+# 10. uplink aggregation at a cell (Sec. III-A: the gNB convolves and aggregates)
+# --------------------------------------------------------------------------
+def _cell_members(rng, n_members, L, n_rx, d, n_slots):
+    n = sum(L)
+    ues, xs = [], []
+    for u in range(n_members):
+        taps = _rand_taps(rng, len(L) * n_slots + 1, n_rx, 1, len(d))
+        ues.append(oracle.OracleUE(L, 1, n_rx, d, taps, ue_id=u))
+        xs.append(rng.integers(-2000, 2000, size=(1, n_slots * n, 2)).astype(np.int16))
+    return ues, xs
+
+
+def test_cell_of_one_member_is_that_member_with_the_cell_noise():
+    """One member: the cell output is the member's own run with AWGN under the cell's key
+    (same FP64 operations in the same order, so bit-identical)."""
+    rng = np.random.default_rng(61)
+    L, d = [6, 5, 5], [0, 2, 7]
+    ues, xs = _cell_members(rng, 1, L, 2, d, 3)
+    nv = 300.0
+    yc, qc = oracle.run_cell(ues, xs, seed=0x1234, cell_id=9, noise_var=nv, s_first=2)
+    u = ues[0]
+    with_noise = oracle.OracleUE(L, 1, 2, d, u.taps, seed=0x1234, ue_id=9, noise_var=nv)
+    y1, q1 = oracle.run_ue(with_noise, xs[0], s_first=2)
+    assert np.array_equal(yc, y1) and np.array_equal(qc, q1)
+
+
+def test_cell_sums_members_superposition():
+    """Members with the same channel and inputs x1, x2 add up to one member fed x1 + x2 (the
+    convolution is linear, so the aggregate is a sum, not an average or a selection); a member
+    with zero input contributes nothing."""
+    rng = np.random.default_rng(62)
+    L, d = [8, 7, 7], [0, 1, 5, 12]
+    n = sum(L)
+    taps = _rand_taps(rng, 3 * 3 + 1, 1, 1, len(d))
+    a = oracle.OracleUE(L, 1, 1, d, taps, ue_id=0)
+    b = oracle.OracleUE(L, 1, 1, d, taps, ue_id=1)
+    x1 = rng.integers(-9000, 9000, size=(1, 3 * n, 2)).astype(np.int16)
+    x2 = rng.integers(-9000, 9000, size=(1, 3 * n, 2)).astype(np.int16)
+    yc, _ = oracle.run_cell([a, b], [x1, x2], seed=1, cell_id=0)
+    ysum, _ = oracle.run_ue(a, (x1.astype(np.int32) + x2).astype(np.int16))
+    assert nrmse(yc, ysum) < 1e-13
+    y0, _ = oracle.run_cell([a, b], [x1, np.zeros_like(x2)], seed=1, cell_id=0)
+    ya, _ = oracle.run_ue(a, x1)
+    assert np.array_equal(y0, ya)
+    # three members, one of them silent, in any order give the same aggregate up to rounding
+    ues, xs = _cell_members(rng, 3, L, 1, d, 3)
+    xs[1] = np.zeros_like(xs[1])
+    y012, _ = oracle.run_cell(ues, xs, seed=1, cell_id=0)
+    y20, _ = oracle.run_cell([ues[2], ues[0]], [xs[2], xs[0]], seed=1, cell_id=0)
+    assert nrmse(y012, y20) < 1e-14
