@@ -496,6 +496,55 @@ def run_sparse(args, device, top_n=8, n_slots=200, warmup=3):
     return out
 
 
+def run_cell(args, device, n_slots=200, warmup=3, steps=5):
+    """Uplink aggregation (Sec. III-A): the 16 headline UEs (40 MHz, 24 taps, noise off, complex64
+    outputs) summed into one cell with AWGN at 20 dB, int16 out, beside the same 16 UEs without
+    the cell; the difference is the aggregation's cost, its traffic 16 x 8 B read + 4 B written
+    per cell sample."""
+    import torch
+    from paper_2601_08217_gb300 import inputs
+    from paper_2601_08217_gb300 import tt_chan as tc
+    specs, iq = make_workload(0)
+    for sp in specs:
+        sp.noise_var = 0.0
+    n = specs[0].n
+    res = {}
+    for name, with_cell in (("members_only", False), ("with_cell", True)):
+        eng = tc.Engine(device=device, persistent=True, graphs=True)
+        cell = tc.Cell(eng, cell_id=0, samples_per_slot=n, ring_slots=n_slots + 1, seed=0x77170002,
+                       noise_var=inputs.noise_var_for_snr(20.0)) if with_cell else None
+        chans = [tc.Chan(eng, sp, ring_slots=n_slots + 2, cf32=True) for sp in specs]
+        if cell:
+            for ch in chans:
+                cell.attach(ch)
+        for ch, x in zip(chans, iq):
+            ch.push(0, cycled_slots(x, n, n_slots + 1))
+        eng.run()
+        if not cell:
+            for ch in chans:
+                tc.tt_chan_release_slots(ch.h, 0, n_slots + 1)
+        eng.sync()
+        stream = torch.cuda.ExternalStream(eng.stream)
+        tc.tt_engine_replay(eng.h, warmup, n_slots)
+        eng.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tc.tt_engine_replay(eng.h, steps, n_slots)
+        b.record(stream)
+        eng.sync()
+        res[name] = a.elapsed_time(b) / steps
+        eng.close()
+    agg_ms = max(res["with_cell"] - res["members_only"], 1e-6)
+    traffic = n_slots * n * (len(specs) * 8 + 4)
+    pk = peaks()
+    return {"workload": f"{len(specs)} UEs x {n_slots} slots, 40 MHz, 24 taps, summed into one cell (AWGN 20 dB at the cell)",
+            "ms_per_step": res["with_cell"], "members_only_ms": res["members_only"],
+            "ue_slots_per_s": len(specs) * n_slots / (res["with_cell"] / 1e3),
+            "aggregation_ms": agg_ms, "aggregation_bytes": traffic,
+            "aggregation_gbs": traffic / (agg_ms / 1e3) / 1e9,
+            "aggregation_frac_of_hbm": traffic / (agg_ms / 1e3) / 1e9 / pk.get("hbm_gbs", 6800.0)}
+
+
 def cpu_baseline(budget_s: float = 12.0):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload.
 
@@ -540,6 +589,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
+    ap.add_argument("--no-cell", action="store_true")
     ap.add_argument("--only-precision", default="", help="profiling: run only these precision forms "
                     "(comma list of bf16_tc,fp16_tc,fp32) with --prec-ues UEs and print their record")
     ap.add_argument("--prec-ues", type=int, default=64)
@@ -616,6 +666,9 @@ def main():
     sparse = None
     if rank == 0 and world == 1 and not args.no_sparse:
         sparse = run_sparse(args, local)
+    cell = None
+    if rank == 0 and world == 1 and not args.no_cell:
+        cell = run_cell(args, local)
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(args, local)
@@ -648,6 +701,7 @@ def main():
         "serving": serving,
         "precision": precision,
         "sparse": sparse,
+        "cell": cell,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))

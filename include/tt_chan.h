@@ -291,6 +291,42 @@ tt_status tt_engine_push_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *c
 tt_status tt_engine_pull_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *chans, const uint64_t *first,
                                const uint32_t *n, void *const *iq_out, int64_t timeout_us);
 
+/* ---- Uplink aggregation at a cell (Sec. III-A: the gNB convolves each UE's
+ * uplink stream with that UE's channel and aggregates the results) ----
+ * A cell owns an output ring of n_rx antennas.  Channels attached to it keep
+ * running their own kernels; after them, every slot that all members have
+ * launched is aggregated: the members' outputs summed in attach order (FP32),
+ * plus the cell's AWGN (key (seed, cell_id), sigma^2 = noise_var), rounded and
+ * saturated into the cell ring like a channel's output.  A member must have
+ * the cell's samples_per_slot (even) and n_rx, TT_OUT_CF32 output, noise_var
+ * 0, and no pushed slot yet; all members start at the same slot.  A member's
+ * output slots are consumed by the aggregation (pulling or releasing them
+ * gives TT_ERR_STATE).  If the cell ring is full the aggregation waits, the
+ * members' rings fill, and pushes report TT_ERR_AGAIN until the cell is
+ * pulled.  A member cannot be destroyed before its cell (TT_ERR_STATE).
+ * No counterpart in the paper beyond the aggregation step itself. */
+typedef struct tt_cell tt_cell;
+typedef struct {
+  uint32_t struct_size;       /* sizeof(tt_cell_config) */
+  uint32_t cell_id;           /* keys the cell's AWGN stream */
+  uint32_t samples_per_slot;  /* N of every member, even */
+  uint32_t n_rx;              /* 1 .. 4, the Rx antennas of the cell and of every member */
+  uint32_t ring_slots;        /* output ring depth, >= 1 (0 = 4) */
+  uint32_t output_format;     /* TT_OUT_INT16 or TT_OUT_CF32 */
+  uint64_t seed;              /* AWGN key */
+  float noise_var;            /* sigma^2 per complex sample at the cell; 0 disables AWGN */
+  uint32_t reserved;
+} tt_cell_config;
+
+tt_status tt_cell_create(tt_engine *e, const tt_cell_config *cfg, tt_cell **out);
+tt_status tt_cell_attach(tt_cell *cell, tt_chan *c);
+/* Pull cell slots [first, first+n) (the oldest not yet pulled) into a host
+ * buffer [n][n_rx][N][2] (int16, or complex64 with TT_OUT_CF32), waiting as
+ * tt_chan_pull_slots does; TT_ERR_AGAIN if they are not aggregated yet. */
+tt_status tt_cell_pull_slots(tt_cell *cell, uint64_t first, uint32_t n, void *out, int64_t timeout_us);
+/* Free the cell (after its queued work) and detach its members. */
+tt_status tt_cell_destroy(tt_cell *cell);
+
 /* Checkpoint / resume.  The state is the next slot index, the last
  * max_delay input samples per Tx antenna and the AWGN key; outputs that have
  * not been pulled are not part of it.  get_state with buf == NULL sets *len

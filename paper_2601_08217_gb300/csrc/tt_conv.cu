@@ -130,3 +130,37 @@ cudaError_t tt_launch_plain(const TTUEDesc *ue_dev, uint64_t slot, int n, cudaSt
   tt_plain_kernel<<<(n + tpb - 1) / tpb, tpb, 0, st>>>(ue_dev, slot);
   return cudaGetLastError();
 }
+
+// ---- uplink aggregation at a cell: one thread per (slot, Rx antenna, pair of samples) ----
+__global__ void __launch_bounds__(256) tt_cell_reduce_kernel(TTCellArgs A, uint64_t first_slot) {
+  const int pairs = A.n >> 1;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= A.n_rx * pairs) return;
+  const uint64_t s = first_slot + blockIdx.y;
+  const int r = idx / pairs, m = 2 * (idx - r * pairs);
+  float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+  for (int u = 0; u < A.n_members; ++u) {  // member order: the FP32 sums are reproducible
+    const TTCellMember mb = A.members[u];
+    const float4 v = *reinterpret_cast<const float4 *>(
+        mb.ring_out + ((size_t)(s % (uint64_t)mb.ring_q) * A.n_rx + r) * A.n + m);
+    y0.x += v.x;
+    y0.y += v.y;
+    y1.x += v.z;
+    y1.y += v.w;
+  }
+  if (A.noise_std > 0.f) tt_awgn_add_pair(A.seed, A.cell_id, (uint32_t)r, s * (uint64_t)A.n + (uint64_t)m, A.noise_std, y0, y1);
+  const size_t o = ((size_t)(s % (uint64_t)A.ring_q) * A.n_rx + r) * A.n + m;
+  if (A.out_f32) {
+    *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(A.ring_out) + o) = make_float4(y0.x, y0.y, y1.x, y1.y);
+  } else {
+    *reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(A.ring_out) + o) =
+        make_uint2(tt_pack_iq(y0.x, y0.y), tt_pack_iq(y1.x, y1.y));
+  }
+}
+
+cudaError_t tt_launch_cell_reduce(const TTCellArgs &A, uint64_t first_slot, uint32_t n_slots, cudaStream_t st) {
+  if (n_slots == 0) return cudaSuccess;
+  const int tpb = 256, work = A.n_rx * (A.n >> 1);
+  tt_cell_reduce_kernel<<<dim3((work + tpb - 1) / tpb, n_slots), tpb, 0, st>>>(A, first_slot);
+  return cudaGetLastError();
+}

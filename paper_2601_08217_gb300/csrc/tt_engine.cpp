@@ -57,6 +57,8 @@ int64_t now_us() {
 
 struct tt_chan;
 
+struct tt_cell;
+
 struct tt_engine {
   int device = 0;
   uint64_t budget = 0;
@@ -102,6 +104,7 @@ struct tt_engine {
   size_t tcseg_cap = 0;
   int *d_status = nullptr;                  // set by a kernel whose bounded wait expired
   std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
+  std::vector<tt_cell *> cells;             // uplink aggregation cells
 };
 
 struct tt_chan {
@@ -124,7 +127,24 @@ struct tt_chan {
   TTUEDesc desc{};
   bool started = false;
   uint64_t pushed_end = 0, launched_end = 0, completed_end = 0, pulled_end = 0;
+  uint64_t start_slot = 0;           // first slot ever pushed
   uint64_t dev_cursor = UINT64_MAX;  // what the engine's device cursor holds for this UE (after queued work)
+  std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
+  tt_cell *cell = nullptr;      // uplink aggregation cell consuming this channel's outputs
+};
+
+struct tt_cell {
+  tt_engine *e = nullptr;
+  tt_cell_config cfg{};
+  int n = 0, Q = 0;
+  size_t slot_out_elems = 0;    // int16 values per slot
+  int16_t *d_out = nullptr;
+  uint64_t ring_bytes = 0;
+  std::vector<tt_chan *> members;
+  TTCellMember *d_members = nullptr;
+  size_t members_cap = 0;
+  bool started = false;
+  uint64_t launched_end = 0, completed_end = 0, pulled_end = 0;
   std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
 };
 
@@ -268,6 +288,7 @@ tt_status check_room(tt_chan *c, uint64_t first, uint32_t n) {
 void mark_pushed(tt_chan *c, uint64_t first, uint32_t n) {
   if (!c->started) {
     c->started = true;
+    c->start_slot = first;
     c->pushed_end = c->launched_end = c->completed_end = c->pulled_end = first;
   }
   c->pushed_end = first + n;
@@ -695,6 +716,13 @@ tt_status tt_engine_destroy(tt_engine *e) {
       c->e = nullptr;
       delete c;
     }
+  for (tt_cell *cl : e->cells) {
+    cudaFree(cl->d_out);
+    cudaFree(cl->d_members);
+    cl->e = nullptr;
+    delete cl;
+  }
+  e->cells.clear();
   for (auto &p : e->events) cudaEventDestroy(p.second);
   for (auto ev : e->pool) cudaEventDestroy(ev);
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
@@ -834,6 +862,7 @@ tt_status tt_chan_destroy(tt_chan *c) {
   if (!valid_chan(c)) return fail(TT_ERR_INVALID, "null channel");
   tt_engine *e = c->e;
   std::lock_guard<std::mutex> lk(e->mu);
+  if (c->cell) return fail(TT_ERR_STATE, "channel is a member of a cell: destroy the cell first");
   cudaSetDevice(e->device);
   cudaStreamSynchronize(e->stream);
   cudaFree(c->d_in);
@@ -1087,6 +1116,166 @@ tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n) {
   return TT_OK;
 }
 
+// Launch the aggregation of every cell whose members have all launched slots the cell has not
+// aggregated yet, as far as the cell ring has room (engine lock held).  Members must start at the
+// same slot.
+static tt_status launch_cells(tt_engine *e, std::vector<std::pair<tt_cell *, uint64_t>> &ends) {
+  for (tt_cell *cl : e->cells) {
+    if (cl->members.empty()) continue;
+    bool all_started = true;
+    uint64_t end = UINT64_MAX;
+    for (tt_chan *m : cl->members) {
+      if (!m->started) { all_started = false; break; }
+      end = std::min(end, m->launched_end);
+    }
+    if (!all_started) continue;
+    if (!cl->started) {
+      const uint64_t s0 = cl->members[0]->start_slot;
+      for (tt_chan *m : cl->members)
+        if (m->start_slot != s0) return fail(TT_ERR_STATE, "cell %u: members start at different slots", cl->cfg.cell_id);
+      cl->started = true;
+      cl->launched_end = cl->completed_end = cl->pulled_end = s0;
+    }
+    end = std::min<uint64_t>(end, cl->pulled_end + (uint64_t)cl->Q);
+    if (end <= cl->launched_end) continue;
+    if (cl->members.size() > cl->members_cap) return fail(TT_ERR_STATE, "cell %u: member table stale", cl->cfg.cell_id);
+    TTCellArgs A{};
+    A.ring_out = cl->d_out;
+    A.members = cl->d_members;
+    A.n_members = (int)cl->members.size();
+    A.n = cl->n;
+    A.n_rx = (int)cl->cfg.n_rx;
+    A.ring_q = cl->Q;
+    A.out_f32 = cl->cfg.output_format == TT_OUT_CF32 ? 1 : 0;
+    A.cell_id = cl->cfg.cell_id;
+    A.seed = cl->cfg.seed;
+    A.noise_std = cl->cfg.noise_var > 0.f ? (float)std::sqrt((double)cl->cfg.noise_var / 2.0) : 0.f;
+    for (uint64_t s0 = cl->launched_end; s0 < end; s0 += 65535) {
+      const uint32_t ns = (uint32_t)std::min<uint64_t>(end - s0, 65535);
+      cudaError_t err = tt_launch_cell_reduce(A, s0, ns, e->stream);
+      if (err != cudaSuccess) return fail(TT_ERR_CUDA, "cell launch: %s", cudaGetErrorString(err));
+      ++e->launches;
+    }
+    ends.push_back({cl, end});
+  }
+  return TT_OK;
+}
+
+tt_status tt_cell_create(tt_engine *e, const tt_cell_config *cfg, tt_cell **out) {
+  if (!e || !cfg || !out || cfg->struct_size < sizeof(tt_cell_config)) return fail(TT_ERR_INVALID, "tt_cell_create: bad config");
+  if (cfg->samples_per_slot == 0 || cfg->samples_per_slot > (1u << 24) || (cfg->samples_per_slot & 1))
+    return fail(TT_ERR_INVALID, "cell samples_per_slot must be even, 2 .. 2^24");
+  if (cfg->n_rx < 1 || cfg->n_rx > TT_MAX_ANT) return fail(TT_ERR_INVALID, "cell n_rx must be 1..%d", TT_MAX_ANT);
+  if (cfg->output_format > TT_OUT_CF32) return fail(TT_ERR_INVALID, "unknown output_format");
+  if (!(cfg->noise_var >= 0.0f) || !std::isfinite(cfg->noise_var)) return fail(TT_ERR_INVALID, "bad noise_var");
+  const int Q = cfg->ring_slots ? (int)cfg->ring_slots : 4;
+  if (Q < 1 || Q > (1 << 20)) return fail(TT_ERR_INVALID, "cell ring_slots out of range");
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  const size_t out_e = (size_t)cfg->n_rx * cfg->samples_per_slot * (cfg->output_format == TT_OUT_CF32 ? 4 : 2);
+  const uint64_t bytes = (uint64_t)Q * out_e * sizeof(int16_t);
+  if (e->budget && e->in_use + bytes > e->budget)
+    return fail(TT_ERR_NO_MEMORY, "admission refused: %llu B needed", (unsigned long long)bytes);
+  tt_cell *cl = new tt_cell();
+  cl->e = e;
+  cl->cfg = *cfg;
+  cl->n = (int)cfg->samples_per_slot;
+  cl->Q = Q;
+  cl->slot_out_elems = out_e;
+  cudaError_t err = cudaMalloc(&cl->d_out, (size_t)Q * out_e * sizeof(int16_t));
+  if (err == cudaSuccess) err = cudaMemsetAsync(cl->d_out, 0, (size_t)Q * out_e * sizeof(int16_t), e->stream);
+  if (err != cudaSuccess) {
+    cudaFree(cl->d_out);
+    delete cl;
+    return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "cell ring: %s", cudaGetErrorString(err));
+  }
+  cl->ring_bytes = bytes;
+  e->in_use += bytes;
+  e->cells.push_back(cl);
+  *out = cl;
+  return TT_OK;
+}
+
+tt_status tt_cell_attach(tt_cell *cl, tt_chan *c) {
+  if (!cl || !cl->e || !c || c->e != cl->e) return fail(TT_ERR_INVALID, "tt_cell_attach: bad cell or channel");
+  tt_engine *e = cl->e;
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  if (c->cell) return fail(TT_ERR_STATE, "channel already attached to a cell");
+  if (c->started || cl->started) return fail(TT_ERR_STATE, "attach before the first push");
+  if (c->n != cl->n || c->cfg.n_rx != cl->cfg.n_rx)
+    return fail(TT_ERR_INVALID, "member must have the cell's samples_per_slot and n_rx");
+  if (c->cfg.output_format != TT_OUT_CF32 || c->cfg.noise_var != 0.f)
+    return fail(TT_ERR_INVALID, "member must have TT_OUT_CF32 output and noise_var 0");
+  if (cl->members.size() + 1 > cl->members_cap) {
+    const size_t cap = std::max<size_t>(8, 2 * cl->members_cap);
+    TTCellMember *d = nullptr;
+    TT_CK(cudaStreamSynchronize(e->stream));  // the old table may still be read
+    TT_CK(cudaMalloc(&d, sizeof(TTCellMember) * cap));
+    cudaFree(cl->d_members);
+    cl->d_members = d;
+    cl->members_cap = cap;
+  }
+  cl->members.push_back(c);
+  c->cell = cl;
+  std::vector<TTCellMember> h(cl->members.size());
+  for (size_t i = 0; i < h.size(); ++i) {
+    h[i].ring_out = reinterpret_cast<const float2 *>(cl->members[i]->d_out);
+    h[i].ring_q = cl->members[i]->Q;
+  }
+  TT_CK(cudaMemcpy(cl->d_members, h.data(), sizeof(TTCellMember) * h.size(), cudaMemcpyHostToDevice));
+  return TT_OK;
+}
+
+tt_status tt_cell_pull_slots(tt_cell *cl, uint64_t first, uint32_t n, void *out, int64_t timeout_us) {
+  if (!cl || !cl->e || (!out && n)) return fail(TT_ERR_INVALID, "tt_cell_pull_slots: bad argument");
+  if (n == 0) return TT_OK;
+  tt_engine *e = cl->e;
+  std::unique_lock<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  if (!cl->started || first != cl->pulled_end)
+    return fail(TT_ERR_STATE, "cell pull must start at the oldest unpulled slot %llu", (unsigned long long)cl->pulled_end);
+  if (first + n > cl->launched_end) return fail(TT_ERR_AGAIN, "cell slot not aggregated yet");
+  uint64_t need = 0;
+  for (auto &p : cl->inflight)
+    if (p.first >= first + n) { need = p.second; break; }
+  if (need && need > e->completed_seq) {
+    tt_status s = wait_seq(e, need, timeout_us, lk);
+    if (s != TT_OK) return s;
+  }
+  while (!cl->inflight.empty() && cl->inflight.front().second <= e->completed_seq) cl->inflight.pop_front();
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  cudaError_t err = ring_copy(cl->d_out, cl->slot_out_elems, cl->Q, first, n, nullptr, out, cudaMemcpyDeviceToHost,
+                              e->copy, false);
+  if (err == cudaSuccess) err = cudaEventRecord(ev, e->copy);
+  if (err == cudaSuccess) {
+    lk.unlock();
+    err = cudaEventSynchronize(ev);
+    lk.lock();
+  }
+  e->pool.push_back(ev);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "cell pull copy: %s", cudaGetErrorString(err));
+  cl->pulled_end = first + n;
+  return TT_OK;
+}
+
+tt_status tt_cell_destroy(tt_cell *cl) {
+  if (!cl || !cl->e) return fail(TT_ERR_INVALID, "null cell");
+  tt_engine *e = cl->e;
+  std::lock_guard<std::mutex> lk(e->mu);
+  cudaSetDevice(e->device);
+  cudaStreamSynchronize(e->stream);
+  for (tt_chan *m : cl->members) m->cell = nullptr;
+  cudaFree(cl->d_out);
+  cudaFree(cl->d_members);
+  e->in_use -= cl->ring_bytes;
+  e->cells.erase(std::remove(e->cells.begin(), e->cells.end(), cl), e->cells.end());
+  cl->e = nullptr;
+  delete cl;
+  return TT_OK;
+}
+
 tt_status tt_engine_run(tt_engine *e) {
   if (!e) return fail(TT_ERR_INVALID, "null engine");
   std::lock_guard<std::mutex> lk(e->mu);
@@ -1097,7 +1286,7 @@ tt_status tt_engine_run(tt_engine *e) {
       if (c->cfg.precision != TT_FP32 && e->form != TT_FORM_PLAIN) tc_ready.push_back(c);
       else ready.push_back(c);
     }
-  if (ready.empty() && tc_ready.empty()) return TT_OK;
+  if (ready.empty() && tc_ready.empty() && e->cells.empty()) return TT_OK;
 
   if (e->form == TT_FORM_PLAIN) {
     for (tt_chan *c : ready) {
@@ -1137,15 +1326,30 @@ tt_status tt_engine_run(tt_engine *e) {
     if (st != TT_OK) return st;
     ready.insert(ready.end(), tc_ready.begin(), tc_ready.end());
   }
+  std::vector<uint64_t> prev_end(ready.size());
+  for (size_t i = 0; i < ready.size(); ++i) {
+    prev_end[i] = ready[i]->launched_end;
+    ready[i]->launched_end = ready[i]->pushed_end;
+  }
+  // uplink aggregation of every slot all members of a cell have launched (after their kernels)
+  std::vector<std::pair<tt_cell *, uint64_t>> cell_ends;
+  tt_status cst = launch_cells(e, cell_ends);
+  if (cst != TT_OK) return cst;
+  if (ready.empty() && cell_ends.empty()) return TT_OK;
   cudaEvent_t ev = get_event(e);
   if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
   TT_CK(cudaEventRecord(ev, e->stream));
   const uint64_t seq = ++e->launch_seq;
   e->events.emplace_back(seq, ev);
-  for (tt_chan *c : ready) {
-    e->slots_processed += c->pushed_end - c->launched_end;
-    c->inflight.emplace_back(c->pushed_end, seq);
-    c->launched_end = c->pushed_end;
+  for (size_t i = 0; i < ready.size(); ++i) {
+    e->slots_processed += ready[i]->launched_end - prev_end[i];
+    ready[i]->inflight.emplace_back(ready[i]->launched_end, seq);
+  }
+  for (auto &ce : cell_ends) {
+    tt_cell *cl = ce.first;
+    cl->inflight.emplace_back(ce.second, seq);
+    cl->launched_end = ce.second;
+    for (tt_chan *m : cl->members) m->pulled_end = std::max(m->pulled_end, ce.second);  // consumed
   }
   return TT_OK;
 }
@@ -1264,6 +1468,10 @@ tt_status tt_engine_replay(tt_engine *e, uint32_t n_steps, uint32_t slots_per_st
         if (!c || !c->has_trace || !c->started) continue;
         // release what the previous steps produced, then reuse the ring in place
         c->pulled_end = std::max(c->pulled_end, std::min(c->launched_end, c->pushed_end));
+      }
+      for (tt_cell *cl : e->cells) cl->pulled_end = std::max(cl->pulled_end, cl->launched_end);
+      for (tt_chan *c : e->table) {
+        if (!c || !c->has_trace || !c->started) continue;
         tt_status st = check_room(c, c->pushed_end, slots_per_step);
         if (st != TT_OK) return st;
         mark_pushed(c, c->pushed_end, slots_per_step);
@@ -1297,6 +1505,7 @@ static tt_status pull_common(tt_chan *c, uint64_t first, uint32_t n, void *out, 
   tt_engine *e = c->e;
   std::unique_lock<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
+  if (c->cell) return fail(TT_ERR_STATE, "the channel's outputs go to its cell");
   if (!c->started || first != c->pulled_end)
     return fail(TT_ERR_STATE, "pull must start at the oldest unpulled slot %llu", (unsigned long long)c->pulled_end);
   if (first + n > c->launched_end) return fail(TT_ERR_AGAIN, "slot not launched yet");
@@ -1334,6 +1543,7 @@ tt_status tt_engine_pull_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *c
   for (uint32_t i = 0; i < n_chans; ++i) {
     tt_chan *c = chans[i];
     if (!valid_chan(c) || c->e != e || (n[i] && !iq_out[i])) return fail(TT_ERR_INVALID, "pull entry %u: bad channel or buffer", i);
+    if (c->cell) return fail(TT_ERR_STATE, "pull entry %u: the channel's outputs go to its cell", i);
     for (uint32_t j = 0; j < i; ++j)
       if (chans[j] == c) return fail(TT_ERR_INVALID, "pull entry %u: channel repeated", i);
     if (!n[i]) continue;
@@ -1390,6 +1600,7 @@ tt_status tt_chan_pull_slots_dev(tt_chan *c, uint64_t first, uint32_t n, void *d
   tt_engine *e = c->e;
   std::lock_guard<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
+  if (c->cell) return fail(TT_ERR_STATE, "the channel's outputs go to its cell");
   if (!c->started || first != c->pulled_end)
     return fail(TT_ERR_STATE, "pull must start at the oldest unpulled slot %llu", (unsigned long long)c->pulled_end);
   if (first + n > c->launched_end) return fail(TT_ERR_AGAIN, "slot not launched yet");
@@ -1417,6 +1628,7 @@ tt_status tt_chan_slot_output(tt_chan *c, uint64_t slot, const void **d_ptr) {
 tt_status tt_chan_release_slots(tt_chan *c, uint64_t first, uint32_t n) {
   if (!valid_chan(c)) return fail(TT_ERR_INVALID, "null channel");
   std::lock_guard<std::mutex> lk(c->e->mu);
+  if (c->cell) return fail(TT_ERR_STATE, "the channel's outputs go to its cell");
   if (!c->started || first != c->pulled_end || first + n > c->launched_end)
     return fail(TT_ERR_STATE, "release must cover launched slots from %llu", (unsigned long long)c->pulled_end);
   c->pulled_end = first + n;

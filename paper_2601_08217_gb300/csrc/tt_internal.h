@@ -104,6 +104,23 @@ size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max)
 // First symbol and number of symbols touched by each work item of a slot (packed jf | nst << 16).
 int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, int max_out);
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st);
+// Uplink aggregation at a cell: output slot s = sum over members (in order) of their complex64
+// output slot s, plus the cell's AWGN, then rounded and saturated (or stored as complex64).
+struct TTCellMember {
+  const float2 *ring_out;  // member's complex64 output ring [Q][n_rx][N]
+  int ring_q;
+  int pad;
+};
+struct TTCellArgs {
+  void *ring_out;          // cell output ring [Q][n_rx][N] of packed int16 IQ (or complex64)
+  const TTCellMember *members;
+  int n_members, n, n_rx, ring_q, out_f32;
+  uint32_t cell_id;
+  uint64_t seed;
+  float noise_std;         // sqrt(noise_var / 2), 0 = no AWGN
+};
+cudaError_t tt_launch_cell_reduce(const TTCellArgs &A, uint64_t first_slot, uint32_t n_slots, cudaStream_t st);
+
 cudaError_t tt_launch_conv_s1(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s2(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s4(const TTLaunch &L, cudaStream_t st);

@@ -49,6 +49,12 @@ class ChanConfig(C.Structure):
                 ("top_n", C.c_uint32)]
 
 
+class CellConfig(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("cell_id", C.c_uint32), ("samples_per_slot", C.c_uint32),
+                ("n_rx", C.c_uint32), ("ring_slots", C.c_uint32), ("output_format", C.c_uint32),
+                ("seed", C.c_uint64), ("noise_var", C.c_float), ("reserved", C.c_uint32)]
+
+
 class TraceDesc(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("taps", C.POINTER(C.c_float)),
                 ("delays", C.POINTER(C.c_int32)), ("n_anchors", C.c_uint32), ("n_taps", C.c_uint32),
@@ -109,6 +115,10 @@ _SIGS = {
     "tt_chan_pull_slots": [_VP, C.c_uint64, C.c_uint32, _VP, C.c_int64],
     "tt_chan_pull_slots_dev": [_VP, C.c_uint64, C.c_uint32, _VP, _VP],
     "tt_engine_push_slots": [_VP, C.c_uint32, _VP, _VP, _VP, _VP],
+    "tt_cell_create": [_VP, _VP, _VP],
+    "tt_cell_attach": [_VP, _VP],
+    "tt_cell_pull_slots": [_VP, C.c_uint64, C.c_uint32, _VP, C.c_int64],
+    "tt_cell_destroy": [_VP],
     "tt_engine_pull_slots": [_VP, C.c_uint32, _VP, _VP, _VP, _VP, C.c_int64],
     "tt_chan_slot_output": [_VP, C.c_uint64, C.POINTER(_VP)],
     "tt_chan_release_slots": [_VP, C.c_uint64, C.c_uint32],
@@ -367,6 +377,27 @@ def tt_conv_static(chans, stream=None):
     _check(load().tt_conv_static(arr, len(chans), _stream_ptr(stream)))
 
 
+def tt_cell_create(e: int, cell_id: int, samples_per_slot: int, n_rx: int = 1, ring_slots: int = 0,
+                   seed: int = 0, noise_var: float = 0.0, output_format: int = TT_OUT_INT16) -> int:
+    cfg = CellConfig(C.sizeof(CellConfig), cell_id, samples_per_slot, n_rx, ring_slots, output_format, seed,
+                     noise_var, 0)
+    h = _VP()
+    _check(load().tt_cell_create(e, C.byref(cfg), C.byref(h)))
+    return h.value
+
+
+def tt_cell_attach(cell: int, c: int):
+    _check(load().tt_cell_attach(cell, c))
+
+
+def tt_cell_pull_slots(cell: int, first: int, n: int, out, timeout_us: int = -1):
+    _check(load().tt_cell_pull_slots(cell, first, n, _ptr(out), timeout_us))
+
+
+def tt_cell_destroy(cell: int):
+    _check(load().tt_cell_destroy(cell))
+
+
 def tt_last_error() -> str:
     return (load().tt_last_error() or b"").decode(errors="replace")
 
@@ -464,3 +495,31 @@ def antenna_major(y: np.ndarray) -> np.ndarray:
     """[n_slots][ant][N](...) -> [ant][n_slots*N](...)."""
     s, a, n = y.shape[:3]
     return np.ascontiguousarray(np.moveaxis(y, 1, 0).reshape((a, s * n) + y.shape[3:]))
+
+
+class Cell:
+    """Uplink aggregation cell: the sum of its members' outputs plus the cell's own AWGN."""
+
+    def __init__(self, engine: Engine, cell_id: int, samples_per_slot: int, n_rx: int = 1, ring_slots: int = 0,
+                 seed: int = 0, noise_var: float = 0.0, cf32: bool = False):
+        self.engine = engine
+        self.n, self.n_rx, self.cf32 = int(samples_per_slot), int(n_rx), cf32
+        self.h = tt_cell_create(engine.h, cell_id, samples_per_slot, n_rx, ring_slots, seed, noise_var,
+                                TT_OUT_CF32 if cf32 else TT_OUT_INT16)
+
+    def attach(self, chan: "Chan"):
+        tt_cell_attach(self.h, chan.h)
+
+    def pull(self, first: int, n_slots: int, timeout_us: int = -1) -> np.ndarray:
+        """int16 [n_slots][n_rx][N][2], or complex64 [n_slots][n_rx][N] for a TT_OUT_CF32 cell."""
+        if self.cf32:
+            out = np.empty((n_slots, self.n_rx, self.n), dtype=np.complex64)
+        else:
+            out = np.empty((n_slots, self.n_rx, self.n, 2), dtype=np.int16)
+        tt_cell_pull_slots(self.h, first, n_slots, out, timeout_us)
+        return out
+
+    def destroy(self):
+        if self.h:
+            tt_cell_destroy(self.h)
+            self.h = 0
