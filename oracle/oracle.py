@@ -170,3 +170,24 @@ def anchor(ue: OracleUE, a: int) -> np.ndarray:
 
 def max_threads() -> int:
     return int(_load().tto_max_threads())
+
+
+def resample_cir(gains: np.ndarray, delays: np.ndarray, n_taps: int) -> np.ndarray:
+    """Continuous CIR -> taps on the integer delay grid 0 .. n_taps-1 for each time step
+    (Sec. IV, 'Tiny-Twin compatible channel traces': a resampling onto a fixed delay grid; the
+    paper does not name the method).  The reading is the band-limited discrete-time equivalent of
+    a multipath channel (Tse and Viswanath, Fundamentals of Wireless Communication, Sec. 2.2.3):
+        h[t][r][x][k] = sum_p a[t][r][x][p] * sinc(k - tau[t][p]),   sinc(v) = sin(pi v) / (pi v),
+    with tau in samples (delay x sampling rate).  FP64; sinc is exactly 1 at v = 0 and exactly 0 at
+    the other integers.
+
+    gains: complex [T][n_rx][n_tx][P]; delays: [T][P] samples.  Returns complex128 [T][n_rx][n_tx][n_taps].
+    """
+    g = np.asarray(gains, dtype=np.complex128)
+    tau = np.asarray(delays, dtype=np.float64)
+    k = np.arange(n_taps, dtype=np.float64)
+    v = k[None, None, :] - tau[:, :, None]                     # [T][P][K]
+    whole = v == np.round(v)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = np.where(whole, (v == 0).astype(np.float64), np.sin(np.pi * v) / (np.pi * v))
+    return np.einsum("trxp,tpk->trxk", g, s)

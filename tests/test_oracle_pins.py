@@ -453,3 +453,32 @@ def test_cell_sums_members_superposition():
     y012, _ = oracle.run_cell(ues, xs, seed=1, cell_id=0)
     y20, _ = oracle.run_cell([ues[2], ues[0]], [xs[2], xs[0]], seed=1, cell_id=0)
     assert nrmse(y012, y20) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# 11. continuous CIR -> fixed delay grid (Sec. IV)
+# --------------------------------------------------------------------------
+def test_cir_resampling_closed_forms():
+    """On-grid paths give exact impulses; a half-sample delay gives sinc(k - 1/2) =
+    2 (-1)^(k+1) / (pi (2k - 1)); paths add linearly; a band-limited signal sampled on the grid
+    is reproduced by summing its sinc-shifted copies (the interpolation identity)."""
+    T, P, K = 3, 4, 12
+    rng = np.random.default_rng(71)
+    a = (rng.standard_normal((T, 2, 1, P)) + 1j * rng.standard_normal((T, 2, 1, P)))
+    tau = np.tile(np.array([0.0, 3.0, 7.0, 11.0]), (T, 1))
+    h = oracle.resample_cir(a, tau, K)
+    ref = np.zeros((T, 2, 1, K), dtype=np.complex128)
+    for p, d in enumerate([0, 3, 7, 11]):
+        ref[..., d] += a[..., p]
+    assert np.array_equal(h, ref)
+    half = oracle.resample_cir(np.ones((1, 1, 1, 1)), np.array([[0.5]]), K)[0, 0, 0]
+    k = np.arange(K)
+    assert np.allclose(half, 2 * (-1.0) ** (k + 1) / (np.pi * (2 * k - 1)), rtol=0, atol=1e-15)
+    tau2 = rng.uniform(0, K - 1, size=(T, P))
+    h2 = oracle.resample_cir(a, tau2, K)
+    parts = sum(oracle.resample_cir(a[..., p:p + 1], tau2[:, p:p + 1], K) for p in range(P))
+    assert np.allclose(h2, parts, rtol=0, atol=1e-13)
+    # interpolation identity: sum_p sinc(k - p) f(p) = f(k) for samples on the grid
+    f = rng.standard_normal(K)
+    ident = oracle.resample_cir(f.reshape(1, 1, 1, K), np.arange(K, dtype=float).reshape(1, K), K)
+    assert np.allclose(ident[0, 0, 0], f, rtol=0, atol=1e-15)
