@@ -233,6 +233,30 @@ tt_status tt_chan_destroy(tt_chan *c);
  * Not allowed while the channel has launched work in flight (TT_ERR_STATE). */
 tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *trace);
 
+/* A continuous CIR: per time step, n_paths paths with complex gains per
+ * (r, t) link and delays in samples (delay x sampling rate, any real >= 0). */
+typedef struct {
+  uint32_t struct_size;       /* sizeof(tt_cir_desc) */
+  uint32_t n_steps, n_paths;  /* time steps (the trace's anchors) and paths per step */
+  uint32_t n_taps;            /* delay grid 0 .. n_taps-1 (<= max_taps, n_taps-1 <= max_delay) */
+  const float *gains;         /* complex64 [n_steps][n_rx][n_tx][n_paths] */
+  const double *delays;       /* [n_steps][n_paths], samples */
+  double step_samples;        /* as tt_trace_desc: 0 = one step per OFDM symbol */
+  int32_t loop;               /* as tt_trace_desc */
+  uint32_t reserved;
+} tt_cir_desc;
+
+/* Trace ingestion (Sec. IV: a continuous CIR is resampled onto a fixed delay
+ * grid for each time step, the method unnamed).  The device computes, in FP64,
+ *   H[t][r][x][k] = sum_p gains[t][r][x][p] * sinc(k - delays[t][p]),
+ *   sinc(v) = sin(pi v) / (pi v),  k = 0 .. n_taps-1,
+ * the band-limited discrete-time equivalent of the multipath channel, rounds
+ * it to complex64 and installs it as the channel's trace with delays 0 ..
+ * n_taps-1, exactly as tt_chan_load_trace would; paths outside the grid
+ * leave sinc tails inside it.  Errors as tt_chan_load_trace; TT_ERR_TRACE for
+ * a non-finite gain or a negative or non-finite delay. */
+tt_status tt_chan_load_cir(tt_chan *c, const tt_cir_desc *cir);
+
 /* Queue input slots [first, first+n).  The first push fixes the channel's
  * starting slot; after that slots must continue in order (TT_ERR_STATE).
  * TT_ERR_AGAIN if the ring has no room (pull or release outputs first).

@@ -5,7 +5,7 @@
 #include "tt_internal.h"
 #include "tt_philox.cuh"
 
-size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max) {
+size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max, int topn) {
   const int dmax = tt_dclass_max(dclass);
   const int np = tt_geo_np(spt, dmax);
   const int wmax = tt_geo_wmax(spt, dmax);
@@ -13,7 +13,7 @@ size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max)
   const size_t raw = (size_t)((n_tx * wmax + 3) & ~3) * sizeof(uint32_t);
   const size_t taps = 2 * (size_t)tap_max * sizeof(float4);
   const size_t dly = 2 * (size_t)((k_max + 3) & ~3) * sizeof(int);
-  return planes + raw + taps + dly;
+  return planes + raw + taps + dly + (topn ? tt_topn_scratch_bytes(tap_max) : 0);
 }
 
 // For each work item (TT_TPB groups of spt samples) of a slot: first symbol it
@@ -162,5 +162,37 @@ cudaError_t tt_launch_cell_reduce(const TTCellArgs &A, uint64_t first_slot, uint
   if (n_slots == 0) return cudaSuccess;
   const int tpb = 256, work = A.n_rx * (A.n >> 1);
   tt_cell_reduce_kernel<<<dim3((work + tpb - 1) / tpb, n_slots), tpb, 0, st>>>(A, first_slot);
+  return cudaGetLastError();
+}
+
+// ---- continuous CIR resampled onto the fixed delay grid: one thread per (step, link, tap) ----
+// Band-limited discrete-time equivalent of the multipath channel: the tap at delay k is the sum of
+// the paths' gains weighted by sinc(k - tau_p), tau_p the path delay in samples; FP64 throughout.
+__global__ void tt_cir_resample_kernel(const float2 *__restrict__ gains, const double *__restrict__ tau, int n_steps,
+                                       int n_links, int n_paths, int n_taps, float2 *__restrict__ taps) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)n_steps * n_links * n_taps;
+  if (idx >= total) return;
+  const int k = (int)(idx % n_taps);
+  const long long tl = idx / n_taps;  // step * n_links + link
+  const int t = (int)(tl / n_links);
+  double re = 0.0, im = 0.0;
+  for (int p = 0; p < n_paths; ++p) {
+    const double v = (double)k - tau[(size_t)t * n_paths + p];
+    const double s = v == 0.0 ? 1.0 : sinpi(v) / (3.141592653589793 * v);
+    const float2 a = gains[(size_t)tl * n_paths + p];
+    re += (double)a.x * s;
+    im += (double)a.y * s;
+  }
+  taps[idx] = make_float2((float)re, (float)im);
+}
+
+cudaError_t tt_launch_cir_resample(const float2 *gains, const double *tau, int n_steps, int n_links, int n_paths,
+                                   int n_taps, float2 *taps, cudaStream_t st) {
+  const long long total = (long long)n_steps * n_links * n_taps;
+  if (total == 0) return cudaSuccess;
+  const int tpb = 256;
+  tt_cir_resample_kernel<<<(unsigned)((total + tpb - 1) / tpb), tpb, 0, st>>>(gains, tau, n_steps, n_links, n_paths,
+                                                                                n_taps, taps);
   return cudaGetLastError();
 }

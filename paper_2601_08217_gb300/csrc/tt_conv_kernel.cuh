@@ -182,19 +182,19 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
 // of largest |H[a]|^2 at the symbol's anchor (ties: lower tap index) and compact them, in tap
 // order, to the front of the tap table: entry ((jl * NRX + r) * n_tx + t) * top_n + i holds
 // (H, dH) of the i-th kept tap and its plane offset.  The powers are binary32,
-// p = fma(re, re, im * im), the precision the oracle takes the same decision in.  The raw window
-// has been converted to planes, so its storage holds the powers, keep flags and compacted lists.
+// p = fma(re, re, im * im), the precision the oracle takes the same decision in.  The launch's
+// scratch area (tt_topn_scratch_bytes(tap_max)) holds the powers, keep flags and compacted lists.
 template <int S, int NRX, int NP>
-__device__ __forceinline__ void tt_select_top_n(const TTUEDesc *__restrict__ U, const TTItem &it, uint32_t *raw,
+__device__ __forceinline__ void tt_select_top_n(const TTUEDesc *__restrict__ U, const TTItem &it, uint32_t *scratch,
                                                 float4 *taps, int *dly, int tid) {
   const int n_tx = U->n_tx, K = U->n_taps, nsel = U->top_n;
   const int ntap_e = it.nst * NRX * n_tx * K;
   const int nseg = it.nst * NRX * n_tx;
-  float *pw = reinterpret_cast<float *>(raw);
-  int *keep = reinterpret_cast<int *>(raw) + ((ntap_e + 3) & ~3);
+  float *pw = reinterpret_cast<float *>(scratch);
+  int *keep = reinterpret_cast<int *>(scratch) + ((ntap_e + 3) & ~3);
   float4 *ctap = reinterpret_cast<float4 *>(keep + ((ntap_e + 3) & ~3));
   int *coff = reinterpret_cast<int *>(ctap + nseg * nsel);
-  __syncthreads();  // every thread is done with the raw window and the (H, dH) conversion
+  __syncthreads();  // every thread is done with the (H, dH) conversion
   for (int e = tid; e < ntap_e; e += TT_TPB) {
     const float4 h = taps[e];
     pw[e] = __fmaf_rn(h.x, h.x, __fmul_rn(h.y, h.y));
@@ -228,7 +228,7 @@ __device__ __forceinline__ void tt_select_top_n(const TTUEDesc *__restrict__ U, 
 template <int S, int NRX, int NP, bool TOPN>
 __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, const TTItem &it,
                                                 const uint32_t *raw, int wmax, float2 *planes, float4 *taps,
-                                                int *dly, int tid) {
+                                                int *dly, uint32_t *scratch, int tid) {
   const int n_tx = U->n_tx, K = U->n_taps, dpad = U->dpad;
   const int wlen = (it.gend - it.g0) * S + dpad;
   for (int t = 0; t < n_tx; ++t) {
@@ -276,7 +276,7 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
     }
   }
   if constexpr (TOPN) {  // every UE of a TOPN launch keeps fewer taps than it has
-    tt_select_top_n<S, NRX, NP>(U, it, const_cast<uint32_t *>(raw), taps, dly, tid);
+    tt_select_top_n<S, NRX, NP>(U, it, scratch, taps, dly, tid);
   } else {
     for (int k = tid; k < K; k += TT_TPB) {
       const int d = dly[k];
@@ -428,6 +428,7 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
   float4 *taps1 = taps0 + tap_max;
   int *dly0 = reinterpret_cast<int *>(taps1 + tap_max);
   int *dly1 = dly0 + kpad;
+  uint32_t *scratch = reinterpret_cast<uint32_t *>(dly1 + kpad);  // TOPN launches only (16-byte aligned)
 
   uint32_t next_static = blockIdx.x;
   auto claim = [&]() -> uint32_t {
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     tt_issue_item<S, NRX>(U, it, raw, WMAX, taps0, dly0, s_sym[0], tid);
     tt_cp_async_wait_all();
     __syncthreads();
-    tt_convert_item<S, NRX, NP, TOPN>(U, it, raw, WMAX, planes, taps0, dly0, tid);
+    tt_convert_item<S, NRX, NP, TOPN>(U, it, raw, WMAX, planes, taps0, dly0, scratch, tid);
     if (tid == 0) tt_locate(ues, segs, n_segs, s_claim, total_items, cursors, s_it[1]);
     __syncthreads();
   }
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     tt_cp_async_wait_all();
     __syncthreads();
     if (!nxt.valid) return;
-    tt_convert_item<S, NRX, NP, TOPN>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
+    tt_convert_item<S, NRX, NP, TOPN>(Un, nxt, raw, WMAX, planes, tn, dn, scratch, tid);
     if (tid == 0) tt_locate(ues, segs, n_segs, nn, total_items, cursors, s_it[cb]);
     __syncthreads();
     cb ^= 1;

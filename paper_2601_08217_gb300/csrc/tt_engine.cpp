@@ -337,19 +337,14 @@ bool sparse(const tt_chan *c) { return c->desc.top_n > 0 && c->desc.top_n < c->d
 // the compacted lists of every touched symbol and link (at most tap_need entries).
 int k_need(const tt_chan *c, int tap_need) { return sparse(c) ? std::max(c->desc.n_taps, tap_need) : c->desc.n_taps; }
 
-// Shared-memory need of a traced channel at spt samples per thread (0 if it does not fit).  With
-// sparse convolution the kernel selects taps in its raw staging area (powers, keep flags,
-// compacted taps and offsets), which must hold them.
+// Shared-memory need of a traced channel at spt samples per thread (0 if it does not fit); sparse
+// convolution adds the selection's scratch.
 size_t smem_need(const tt_chan *c, int spt, int *tap_need) {
   int touched = 1;
   chunk_table(c->sym_len, spt, &touched);
   *tap_need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * (uint32_t)c->desc.n_taps);
-  if (sparse(c)) {
-    const size_t raw = (size_t)(((int)c->cfg.n_tx * tt_geo_wmax(spt, tt_dclass_max(c->dclass)) + 3) & ~3) * 4;
-    const size_t scratch = (size_t)((*tap_need + 3) & ~3) * 4 * 2 + (size_t)*tap_need * (16 + 4);
-    if (scratch > raw) return 0;
-  }
-  const size_t b = tt_conv_smem_bytes(spt, c->dclass, (int)c->cfg.n_tx, *tap_need, k_need(c, *tap_need));
+  const size_t b = tt_conv_smem_bytes(spt, c->dclass, (int)c->cfg.n_tx, *tap_need, k_need(c, *tap_need),
+                                      sparse(c) ? 1 : 0);
   return b <= 200 * 1024 ? b : 0;
 }
 
@@ -433,7 +428,7 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
   }
   if ((int)p.groups.size() > e->counter_cap) return fail(TT_ERR_INVALID, "too many kernel variants in one run");
   for (PlanGroup &g : p.groups) {
-    g.smem = tt_conv_smem_bytes(g.spt, g.dclass, g.ntx, g.tap_max, g.k_max);
+    g.smem = tt_conv_smem_bytes(g.spt, g.dclass, g.ntx, g.tap_max, g.k_max, g.topn);
     TTLaunch L{};
     L.spt = g.spt;
     L.nrx = g.nrx;
@@ -878,6 +873,100 @@ tt_status tt_chan_destroy(tt_chan *c) {
   return TT_OK;
 }
 
+// Check a trace's delays and geometry against the channel and pick the tiled-kernel geometry
+// (engine lock not needed: reads the channel's configuration only).
+struct TraceGeo {
+  int d_max = 0, dclass = 0, spt = 0, tap_need = 0;
+  size_t smem = 0;
+};
+static tt_status trace_geometry(const tt_chan *c, const int32_t *delays, uint32_t n_taps, TraceGeo &g) {
+  g.d_max = 0;
+  for (uint32_t k = 0; k < n_taps; ++k) {
+    const int32_t d = delays[k];
+    if (d < 0 || (uint32_t)d > c->cfg.max_delay) return fail(TT_ERR_TRACE, "delay %d outside 0..%u", d, c->cfg.max_delay);
+    if (k && d < delays[k - 1]) return fail(TT_ERR_TRACE, "delays must be non-decreasing");
+    g.d_max = std::max(g.d_max, (int)d);
+  }
+  g.dclass = pick_dclass(g.d_max);
+  const bool tc = c->cfg.precision != TT_FP32;
+  if (tc && g.d_max > tt_tc_max_delay())
+    return fail(TT_ERR_TRACE, "tensor-core channels take delays up to %d (got %d)", tt_tc_max_delay(), g.d_max);
+  if (tc)
+    for (uint32_t v : c->sym_len)
+      if (v % 8) return fail(TT_ERR_INVALID, "tensor-core channels need symbol lengths divisible by 8");
+  // largest samples-per-thread whose shared-memory footprint fits (the tensor-core form keeps the
+  // smallest valid tiled geometry, unused)
+  const bool topn = c->cfg.top_n > 0 && c->cfg.top_n < n_taps;
+  g.spt = 0;
+  for (int s : spt_candidates(c->sym_len, c->e->spt_override, c->cfg.n_rx)) {
+    if (tc) {
+      g.spt = 1;
+      break;
+    }
+    int touched = 1;
+    chunk_table(c->sym_len, s, &touched);
+    const int need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * n_taps);
+    const size_t b = tt_conv_smem_bytes(s, g.dclass, c->cfg.n_tx, need, topn ? std::max((int)n_taps, need) : (int)n_taps,
+                                        topn ? 1 : 0);
+    if (b <= 200 * 1024) {
+      g.spt = s;
+      g.tap_need = need;
+      g.smem = b;
+      break;
+    }
+  }
+  if (g.spt == 0)
+    return fail(TT_ERR_INVALID, "channel too large for the tiled kernel: %u x %u antennas, %u taps, delay %d",
+                c->cfg.n_rx, c->cfg.n_tx, n_taps, g.d_max);
+  return TT_OK;
+}
+
+// Replace the channel's trace by device buffers already filled (ownership passes to the channel).
+// Engine lock held; no launched work of the channel may be in flight.
+static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64_t bytes, uint32_t n_anchors,
+                        uint32_t n_taps, double step_samples, int loop, const TraceGeo &g) {
+  tt_engine *e = c->e;
+  cudaFree(c->d_taps);
+  cudaFree(c->d_delays);
+  e->in_use = e->in_use - c->trace_bytes + bytes;
+  c->trace_bytes = bytes;
+  c->d_taps = taps;
+  c->d_delays = delays;
+  c->has_trace = true;
+  c->dclass = g.dclass;
+  c->smem = g.smem;
+  c->tap_need = g.tap_need;
+  drop_graph(e);
+  TTUEDesc &d = c->desc;
+  d.taps = taps;
+  d.delays = delays;
+  d.step_samples = step_samples;
+  d.n_taps = (int)n_taps;
+  d.d_max = g.d_max;
+  d.n_anchors = (int)n_anchors;
+  d.loop = loop ? 1 : 0;
+  tt_status sst = set_spt(c, g.spt);
+  if (sst != TT_OK) return sst;
+  if (c->cfg.precision != TT_FP32) {  // the tensor-core kernel's work items: one per symbol
+    std::vector<int32_t> L32(c->sym_len.begin(), c->sym_len.end());
+    d.items_per_slot = tt_tc_items_per_slot(L32.data(), (int)L32.size());
+  }
+  return upload_desc(c);
+}
+
+// Engine lock held: fail unless the channel has no launched work in flight.
+static tt_status idle_or_fail(tt_chan *c) {
+  tt_engine *e = c->e;
+  update_chan(c);
+  if (c->launched_end != c->completed_end) {
+    cudaError_t q = update_completed(e);
+    if (q != cudaSuccess) return fail(TT_ERR_CUDA, "%s", cudaGetErrorString(q));
+    update_chan(c);
+    if (c->launched_end != c->completed_end) return fail(TT_ERR_STATE, "work in flight; sync first");
+  }
+  return TT_OK;
+}
+
 tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   if (!valid_chan(c) || !tr || tr->struct_size < sizeof(tt_trace_desc))
     return fail(TT_ERR_INVALID, "tt_chan_load_trace: bad argument");
@@ -888,57 +977,18 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
                                                 c->cfg.max_taps);
   if (!(tr->step_samples >= 0.0) || !std::isfinite(tr->step_samples))
     return fail(TT_ERR_TRACE, "bad step_samples");
-  int d_max = 0;
-  for (uint32_t k = 0; k < tr->n_taps; ++k) {
-    const int32_t d = tr->delays[k];
-    if (d < 0 || (uint32_t)d > c->cfg.max_delay) return fail(TT_ERR_TRACE, "delay %d outside 0..%u", d,
-                                                            c->cfg.max_delay);
-    if (k && d < tr->delays[k - 1]) return fail(TT_ERR_TRACE, "delays must be non-decreasing");
-    d_max = std::max(d_max, (int)d);
-  }
+  TraceGeo g;
+  tt_status gs = trace_geometry(c, tr->delays, tr->n_taps, g);
+  if (gs != TT_OK) return gs;
   const size_t per = (size_t)c->cfg.n_rx * c->cfg.n_tx * tr->n_taps;
   const size_t nval = per * tr->n_anchors * 2;
   for (size_t i = 0; i < nval; ++i)
     if (!std::isfinite(tr->taps[i])) return fail(TT_ERR_TRACE, "non-finite tap value at %zu", i);
-  const int dclass = pick_dclass(d_max);
-  const bool tc = c->cfg.precision != TT_FP32;
-  if (tc && d_max > tt_tc_max_delay())
-    return fail(TT_ERR_TRACE, "tensor-core channels take delays up to %d (got %d)", tt_tc_max_delay(), d_max);
-  if (tc)
-    for (uint32_t v : c->sym_len)
-      if (v % 8) return fail(TT_ERR_INVALID, "tensor-core channels need symbol lengths divisible by 8");
-  // largest samples-per-thread whose shared-memory footprint fits
-  int spt = 0, tap_need = 0;
-  size_t smem = 0;
-  for (int s : spt_candidates(c->sym_len, c->e->spt_override, c->cfg.n_rx)) {
-    if (tc) {  // the tiled geometry is unused; keep the smallest valid one
-      spt = 1;
-      break;
-    }
-    int touched = 1;
-    chunk_table(c->sym_len, s, &touched);
-    const int need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * tr->n_taps);
-    const size_t b = tt_conv_smem_bytes(s, dclass, c->cfg.n_tx, need, tr->n_taps);
-    if (b <= 200 * 1024) {
-      spt = s;
-      tap_need = need;
-      smem = b;
-      break;
-    }
-  }
-  if (spt == 0)
-    return fail(TT_ERR_INVALID, "channel too large for the tiled kernel: %u x %u antennas, %u taps, delay %d",
-                c->cfg.n_rx, c->cfg.n_tx, tr->n_taps, d_max);
 
   std::lock_guard<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
-  update_chan(c);
-  if (c->launched_end != c->completed_end) {
-    cudaError_t q = update_completed(e);
-    if (q != cudaSuccess) return fail(TT_ERR_CUDA, "%s", cudaGetErrorString(q));
-    update_chan(c);
-    if (c->launched_end != c->completed_end) return fail(TT_ERR_STATE, "work in flight; sync first");
-  }
+  tt_status st = idle_or_fail(c);
+  if (st != TT_OK) return st;
   const uint64_t bytes = nval * sizeof(float) + tr->n_taps * sizeof(int32_t);
   if (e->budget && e->in_use - c->trace_bytes + bytes > e->budget)
     return fail(TT_ERR_NO_MEMORY, "admission refused: trace of %llu B does not fit the budget",
@@ -956,32 +1006,63 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
     return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "trace upload: %s",
                 cudaGetErrorString(err));
   }
-  cudaFree(c->d_taps);
-  cudaFree(c->d_delays);
-  e->in_use = e->in_use - c->trace_bytes + bytes;
-  c->trace_bytes = bytes;
-  c->d_taps = taps;
-  c->d_delays = delays;
-  c->has_trace = true;
-  c->dclass = dclass;
-  c->smem = smem;
-  c->tap_need = tap_need;
-  drop_graph(e);
-  TTUEDesc &d = c->desc;
-  d.taps = taps;
-  d.delays = delays;
-  d.step_samples = tr->step_samples;
-  d.n_taps = (int)tr->n_taps;
-  d.d_max = d_max;
-  d.n_anchors = (int)tr->n_anchors;
-  d.loop = tr->loop ? 1 : 0;
-  tt_status sst = set_spt(c, spt);
-  if (sst != TT_OK) return sst;
-  if (tc) {  // the tensor-core kernel's work items: up to 4096 samples of one symbol
-    std::vector<int32_t> L32(c->sym_len.begin(), c->sym_len.end());
-    d.items_per_slot = tt_tc_items_per_slot(L32.data(), (int)L32.size());
+  return install_trace(c, taps, delays, bytes, tr->n_anchors, tr->n_taps, tr->step_samples, tr->loop, g);
+}
+
+tt_status tt_chan_load_cir(tt_chan *c, const tt_cir_desc *cir) {
+  if (!valid_chan(c) || !cir || cir->struct_size < sizeof(tt_cir_desc))
+    return fail(TT_ERR_INVALID, "tt_chan_load_cir: bad argument");
+  tt_engine *e = c->e;
+  if (!cir->gains || !cir->delays || cir->n_steps == 0 || cir->n_paths == 0 || cir->n_taps == 0)
+    return fail(TT_ERR_TRACE, "empty CIR");
+  if (cir->n_taps > c->cfg.max_taps) return fail(TT_ERR_TRACE, "grid of %u taps, max_taps is %u", cir->n_taps,
+                                                 c->cfg.max_taps);
+  if (!(cir->step_samples >= 0.0) || !std::isfinite(cir->step_samples)) return fail(TT_ERR_TRACE, "bad step_samples");
+  const int n_links = (int)(c->cfg.n_rx * c->cfg.n_tx);
+  const size_t ng = (size_t)cir->n_steps * n_links * cir->n_paths * 2, nd = (size_t)cir->n_steps * cir->n_paths;
+  for (size_t i = 0; i < ng; ++i)
+    if (!std::isfinite(cir->gains[i])) return fail(TT_ERR_TRACE, "non-finite path gain at %zu", i);
+  for (size_t i = 0; i < nd; ++i)
+    if (!std::isfinite(cir->delays[i]) || cir->delays[i] < 0.0) return fail(TT_ERR_TRACE, "bad path delay at %zu", i);
+  std::vector<int32_t> grid(cir->n_taps);
+  for (uint32_t k = 0; k < cir->n_taps; ++k) grid[k] = (int32_t)k;
+  TraceGeo g;
+  tt_status gs = trace_geometry(c, grid.data(), cir->n_taps, g);
+  if (gs != TT_OK) return gs;
+
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  tt_status st = idle_or_fail(c);
+  if (st != TT_OK) return st;
+  const size_t nval = (size_t)cir->n_steps * n_links * cir->n_taps;
+  const uint64_t bytes = nval * sizeof(float2) + cir->n_taps * sizeof(int32_t);
+  if (e->budget && e->in_use - c->trace_bytes + bytes > e->budget)
+    return fail(TT_ERR_NO_MEMORY, "admission refused: trace of %llu B does not fit the budget",
+                (unsigned long long)bytes);
+  TT_CK(cudaStreamSynchronize(e->stream));
+  float2 *taps = nullptr, *d_gains = nullptr;
+  int32_t *delays = nullptr;
+  double *d_tau = nullptr;
+  cudaError_t err = cudaMalloc(&taps, nval * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&delays, cir->n_taps * sizeof(int32_t));
+  if (err == cudaSuccess) err = cudaMalloc(&d_gains, ng * sizeof(float));
+  if (err == cudaSuccess) err = cudaMalloc(&d_tau, nd * sizeof(double));
+  if (err == cudaSuccess) err = cudaMemcpy(delays, grid.data(), cir->n_taps * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(d_gains, cir->gains, ng * sizeof(float), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(d_tau, cir->delays, nd * sizeof(double), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess)
+    err = tt_launch_cir_resample(d_gains, d_tau, (int)cir->n_steps, n_links, (int)cir->n_paths, (int)cir->n_taps,
+                                 taps, e->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
+  cudaFree(d_gains);
+  cudaFree(d_tau);
+  if (err != cudaSuccess) {
+    cudaFree(taps);
+    cudaFree(delays);
+    return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "CIR resampling: %s",
+                cudaGetErrorString(err));
   }
-  return upload_desc(c);
+  return install_trace(c, taps, delays, bytes, cir->n_steps, cir->n_taps, cir->step_samples, cir->loop, g);
 }
 
 tt_status tt_chan_push_slot(tt_chan *c, uint64_t slot, const int16_t *iq_in) {

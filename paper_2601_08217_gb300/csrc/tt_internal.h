@@ -100,7 +100,12 @@ struct TTLaunch {
 cudaError_t tt_launch_advance(const TTSeg *segs, int n_segs, unsigned long long *cursors, cudaStream_t st);
 
 // Dynamic shared memory of the tiled kernel for a launch.
-size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max);
+size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max, int topn);
+// Scratch of the sparse (top-n) selection for up to tap_max tap entries: powers and keep flags
+// (4 B each, padded to 4 entries) and the compacted (H, dH) and offsets (16 B + 4 B each).
+__host__ __device__ constexpr size_t tt_topn_scratch_bytes(int tap_max) {
+  return (size_t)((tap_max + 3) & ~3) * 8 + (size_t)tap_max * 20;
+}
 // First symbol and number of symbols touched by each work item of a slot (packed jf | nst << 16).
 int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, int max_out);
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st);
@@ -120,6 +125,10 @@ struct TTCellArgs {
   float noise_std;         // sqrt(noise_var / 2), 0 = no AWGN
 };
 cudaError_t tt_launch_cell_reduce(const TTCellArgs &A, uint64_t first_slot, uint32_t n_slots, cudaStream_t st);
+// Continuous CIR -> taps on the delay grid 0 .. n_taps-1: taps[t][link][k] = sum_p gains[t][link][p] *
+// sinc(k - tau[t][p]), FP64 sums rounded to complex64.
+cudaError_t tt_launch_cir_resample(const float2 *gains, const double *tau, int n_steps, int n_links, int n_paths,
+                                   int n_taps, float2 *taps, cudaStream_t st);
 
 cudaError_t tt_launch_conv_s1(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s2(const TTLaunch &L, cudaStream_t st);

@@ -55,6 +55,12 @@ class CellConfig(C.Structure):
                 ("seed", C.c_uint64), ("noise_var", C.c_float), ("reserved", C.c_uint32)]
 
 
+class CirDesc(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("n_steps", C.c_uint32), ("n_paths", C.c_uint32),
+                ("n_taps", C.c_uint32), ("gains", C.POINTER(C.c_float)), ("delays", C.POINTER(C.c_double)),
+                ("step_samples", C.c_double), ("loop", C.c_int32), ("reserved", C.c_uint32)]
+
+
 class TraceDesc(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("taps", C.POINTER(C.c_float)),
                 ("delays", C.POINTER(C.c_int32)), ("n_anchors", C.c_uint32), ("n_taps", C.c_uint32),
@@ -116,6 +122,7 @@ _SIGS = {
     "tt_chan_pull_slots_dev": [_VP, C.c_uint64, C.c_uint32, _VP, _VP],
     "tt_engine_push_slots": [_VP, C.c_uint32, _VP, _VP, _VP, _VP],
     "tt_cell_create": [_VP, _VP, _VP],
+    "tt_chan_load_cir": [_VP, _VP],
     "tt_cell_attach": [_VP, _VP],
     "tt_cell_pull_slots": [_VP, C.c_uint64, C.c_uint32, _VP, C.c_int64],
     "tt_cell_destroy": [_VP],
@@ -272,6 +279,20 @@ def tt_chan_load_trace(c: int, taps: np.ndarray, delays, step_samples: float = 0
     desc = TraceDesc(C.sizeof(TraceDesc), t.ctypes.data_as(C.POINTER(C.c_float)),
                      d.ctypes.data_as(C.POINTER(C.c_int32)), n_anchors, k, float(step_samples), int(bool(loop)))
     _check(load().tt_chan_load_trace(c, C.byref(desc)))
+
+
+def tt_chan_load_cir(c: int, gains: np.ndarray, delays: np.ndarray, n_taps: int, step_samples: float = 0.0,
+                     loop: bool = False):
+    """gains: complex64 [T][n_rx][n_tx][P]; delays: [T][P] in samples.  The device resamples the CIR
+    onto the delay grid 0 .. n_taps-1 and installs it as the channel's trace."""
+    g = np.ascontiguousarray(np.asarray(gains, dtype=np.complex64))
+    d = np.ascontiguousarray(np.asarray(delays, dtype=np.float64))
+    if g.ndim != 4 or d.shape != (g.shape[0], g.shape[3]):
+        raise ValueError("gains must be [T][n_rx][n_tx][P] and delays [T][P]")
+    desc = CirDesc(C.sizeof(CirDesc), g.shape[0], g.shape[3], int(n_taps),
+                   g.ctypes.data_as(C.POINTER(C.c_float)), d.ctypes.data_as(C.POINTER(C.c_double)),
+                   float(step_samples), 1 if loop else 0, 0)
+    _check(load().tt_chan_load_cir(c, C.byref(desc)))
 
 
 def tt_chan_push_slot(c: int, slot: int, iq_in):
