@@ -15,6 +15,8 @@ Functions and the passages they follow:
   members' convolved streams plus the cell's own AWGN, then packing.
 * :func:`resample_cir` -- Sec. IV: a continuous CIR resampled onto the fixed delay
   grid (band-limited discrete-time equivalent, sum of sincs).
+* :func:`sos_taps` -- Sec. IV (3GPP traces with Jakes-based Doppler): sum-of-
+  sinusoids tap processes at given times, FP64.
 * :func:`philox4x32_10` -- the counter-based generator of Salmon et al. (SC'11).
 * :func:`noise` -- one complex AWGN sample from Philox words via Box-Muller.
 * :func:`anchor` -- the trace value at one OFDM-symbol anchor.
@@ -23,4 +25,4 @@ Functions and the passages they follow:
 Pins: ``tests/test_oracle_*.py`` (run with ``-m "not gpu"``).
 """
 from .oracle import (OracleUE, anchor, build, lib_path, max_threads, noise, philox4x32_10,  # noqa: F401
-                     resample_cir, run_cell, run_ue)
+                     resample_cir, run_cell, run_ue, sos_taps)

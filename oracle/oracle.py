@@ -191,3 +191,22 @@ def resample_cir(gains: np.ndarray, delays: np.ndarray, n_taps: int) -> np.ndarr
     with np.errstate(divide="ignore", invalid="ignore"):
         s = np.where(whole, (v == 0).astype(np.float64), np.sin(np.pi * v) / (np.pi * v))
     return np.einsum("trxp,tpk->trxk", g, s)
+
+
+def sos_taps(amplitude: np.ndarray, freq: np.ndarray, phase: np.ndarray, times_s: np.ndarray) -> np.ndarray:
+    """Sum-of-sinusoids tap processes (the Jakes-based Doppler model of Sec. IV's 3GPP traces):
+        H[t][r][x][k] = amplitude[r][x][k] * M^(-1/2) * sum_n [cos(freq[..][n][0] t + phase[..][n][0])
+                                                          + j cos(freq[..][n][1] t + phase[..][n][1])]
+    at the given times (seconds); freq in rad/s.  FP64.  With freq = w (cos a_n, sin a_n) and
+    a_n = (2 pi n - pi + theta) / (4 M) this is the model of Zheng and Xiao (IEEE Commun. Lett. 2002).
+
+    amplitude [n_rx][n_tx][K]; freq, phase [n_rx][n_tx][K][M][2].  Returns complex128 [T][n_rx][n_tx][K].
+    """
+    t = np.asarray(times_s, dtype=np.float64)
+    f = np.asarray(freq, dtype=np.float64)
+    p = np.asarray(phase, dtype=np.float64)
+    m = f.shape[3]
+    arg_i = t[:, None, None, None, None] * f[None, ..., 0] + p[None, ..., 0]
+    arg_q = t[:, None, None, None, None] * f[None, ..., 1] + p[None, ..., 1]
+    s = np.cos(arg_i).sum(axis=-1) + 1j * np.cos(arg_q).sum(axis=-1)
+    return np.asarray(amplitude, dtype=np.float64)[None] * s / np.sqrt(m)

@@ -123,6 +123,23 @@ def jakes_sos(rng: np.random.Generator, t: np.ndarray, f_d: float, n_proc: int, 
     return out
 
 
+def sos_params(rng: np.random.Generator, f_d: float, pdp: np.ndarray, n_rx: int, n_tx: int, m: int = 16):
+    """Random parameters of independent Zheng-Xiao sum-of-sinusoids Rayleigh processes, one per
+    (r, t, k) link tap, for synthesis on the device: amplitude sqrt(pdp[k] / n_tx), angular
+    frequencies w (cos a_n, sin a_n) with a_n = (2 pi n - pi + theta) / (4 m), phases ~ U[-pi, pi).
+    Returns (amplitude float32 [n_rx][n_tx][K], freq float64 [n_rx][n_tx][K][m][2],
+    phase float64 [n_rx][n_tx][K][m][2])."""
+    k = len(pdp)
+    w = 2.0 * np.pi * f_d
+    n = np.arange(1, m + 1, dtype=np.float64)
+    theta = rng.uniform(-np.pi, np.pi, size=(n_rx, n_tx, k, 1))
+    a = (2.0 * np.pi * n - np.pi + theta) / (4.0 * m)
+    freq = np.stack([w * np.cos(a), w * np.sin(a)], axis=-1)
+    phase = rng.uniform(-np.pi, np.pi, size=(n_rx, n_tx, k, m, 2))
+    amp = np.broadcast_to(np.sqrt(np.asarray(pdp, dtype=np.float64) / n_tx), (n_rx, n_tx, k))
+    return amp.astype(np.float32), freq, phase
+
+
 def gen_trace(rng: np.random.Generator, times_s: np.ndarray, f_d: float, pdp: np.ndarray,
               n_rx: int, n_tx: int) -> np.ndarray:
     """Time-varying taps H[a][r][t][k] (complex64) at the given anchor times.

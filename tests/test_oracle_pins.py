@@ -482,3 +482,28 @@ def test_cir_resampling_closed_forms():
     f = rng.standard_normal(K)
     ident = oracle.resample_cir(f.reshape(1, 1, 1, K), np.arange(K, dtype=float).reshape(1, K), K)
     assert np.allclose(ident[0, 0, 0], f, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# 12. sum-of-sinusoids tap processes (Sec. IV, Jakes-based Doppler)
+# --------------------------------------------------------------------------
+def test_sos_taps_have_unit_power_and_the_jakes_autocorrelation():
+    """With the Zheng-Xiao parameters each process has E|h|^2 = amplitude^2 and the normalised
+    autocorrelation of the classic Jakes spectrum, J0(2 pi f_D tau) (Bessel function of the first
+    kind, order 0); a wrong frequency set, scale or 2 pi factor breaks one of them."""
+    from scipy.special import j0
+    from paper_2601_08217_gb300 import inputs
+    rng = np.random.default_rng(91)
+    f_d, m = 100.0, 16
+    amp, freq, phase = inputs.sos_params(rng, f_d, np.full(400, 2.0), 4, 2, m)   # 3200 processes, power 1 each
+    taus = np.array([0.0, 0.5e-3, 1e-3, 2e-3, 3.8e-3, 6e-3])
+    t0 = rng.uniform(0.0, 10.0, size=8)
+    acc = np.zeros(len(taus), dtype=np.complex128)
+    pw = 0.0
+    for t in t0:
+        h = oracle.sos_taps(amp, freq, phase, t + taus)                          # [len(taus)][4][2][400]
+        acc += (h * np.conj(h[0])[None]).reshape(len(taus), -1).mean(axis=1)
+        pw += np.mean(np.abs(h[0]) ** 2)
+    acc /= len(t0)
+    assert abs(pw / len(t0) - 1.0) < 0.03
+    assert np.allclose(acc.real, j0(2 * np.pi * f_d * taus), atol=0.04)
