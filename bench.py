@@ -545,6 +545,50 @@ def run_cell(args, device, n_slots=200, warmup=3, steps=5):
             "aggregation_frac_of_hbm": traffic / (agg_ms / 1e3) / 1e9 / pk.get("hbm_gbs", 6800.0)}
 
 
+def run_synth(args, device, n_slots=200, warmup=3, steps=5):
+    """Tap processes synthesised on the device (sum of 16 sinusoids per tap, Zheng-Xiao
+    parameters, 100 Hz) for the 16 headline UEs, beside the same UEs replaying stored traces:
+    the time per step of each and the HBM each channel's taps take."""
+    import torch
+    from paper_2601_08217_gb300 import inputs
+    from paper_2601_08217_gb300 import tt_chan as tc
+    specs, iq = make_workload(0)
+    n = specs[0].n
+    res = {}
+    for mode in ("trace", "synthesised"):
+        eng = tc.Engine(device=device, persistent=True, graphs=True)
+        chans = []
+        for u, sp in enumerate(specs):
+            ch = tc.Chan(eng, sp, ring_slots=n_slots + 2, load=(mode == "trace"))
+            if mode == "synthesised":
+                rng = np.random.default_rng([0x77170009, u])
+                amp, freq, phase = inputs.sos_params(rng, 100.0, inputs.pdp_span_decay(sp.delays, 20.0), 1, 1)
+                tc.tt_chan_load_jakes(ch.h, sp.delays, amp, freq, phase, 61.44e6)
+            chans.append(ch)
+        for ch, x in zip(chans, iq):
+            ch.push(0, cycled_slots(x, n, n_slots + 1))
+        eng.run()
+        for ch in chans:
+            tc.tt_chan_release_slots(ch.h, 0, n_slots + 1)
+        eng.sync()
+        st0 = eng.stats()
+        stream = torch.cuda.ExternalStream(eng.stream)
+        tc.tt_engine_replay(eng.h, warmup, n_slots)
+        eng.sync()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tc.tt_engine_replay(eng.h, steps, n_slots)
+        b.record(stream)
+        eng.sync()
+        res[mode] = {"ms_per_step": a.elapsed_time(b) / steps,
+                     "hbm_mb_per_ue": (eng.stats()["hbm_in_use"] / len(specs)) / 1e6}
+        eng.close()
+    res["workload"] = (f"16 UEs x {n_slots} slots, 40 MHz, 24 taps; stored trace of "
+                       f"{specs[0].taps.shape[0]} anchors vs 16-sinusoid synthesis per tap")
+    res["synthesis_overhead"] = res["synthesised"]["ms_per_step"] / res["trace"]["ms_per_step"] - 1.0
+    return res
+
+
 def cpu_baseline(budget_s: float = 12.0):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload.
 
@@ -590,6 +634,7 @@ def main():
     ap.add_argument("--no-precision", action="store_true")
     ap.add_argument("--no-sparse", action="store_true")
     ap.add_argument("--no-cell", action="store_true")
+    ap.add_argument("--no-synth", action="store_true")
     ap.add_argument("--only-precision", default="", help="profiling: run only these precision forms "
                     "(comma list of bf16_tc,fp16_tc,fp32) with --prec-ues UEs and print their record")
     ap.add_argument("--prec-ues", type=int, default=64)
@@ -669,6 +714,9 @@ def main():
     cell = None
     if rank == 0 and world == 1 and not args.no_cell:
         cell = run_cell(args, local)
+    synth = None
+    if rank == 0 and world == 1 and not args.no_synth:
+        synth = run_synth(args, local)
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(args, local)
@@ -702,6 +750,7 @@ def main():
         "precision": precision,
         "sparse": sparse,
         "cell": cell,
+        "synthesis": synth,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))

@@ -257,6 +257,31 @@ typedef struct {
  * a non-finite gain or a negative or non-finite delay. */
 tt_status tt_chan_load_cir(tt_chan *c, const tt_cir_desc *cir);
 
+/* Sum-of-sinusoids tap processes synthesised on the device (Sec. IV: 3GPP
+ * traces whose time variation comes from a Jakes-based Doppler model).  Tap
+ * (r, x, k) at anchor a, which sits at t = b_a / sample_rate_hz seconds (b_a =
+ * its first absolute sample), is
+ *   amplitude[r][x][k] * M^(-1/2) * sum_n [cos(freq[..][n][0] t + phase[..][n][0])
+ *                                     + j cos(freq[..][n][1] t + phase[..][n][1])]
+ * (freq in rad/s; the Zheng-Xiao model is freq = w (cos a_n, sin a_n)).  The
+ * phase is reduced modulo 2 pi in FP64, so long replays keep their accuracy;
+ * the cosines and the sum are FP32.  The engine keeps a ring of anchors sized
+ * for the channel's slot ring and fills each run's anchors before its
+ * kernels, so no trace is stored: the channel replays indefinitely. */
+typedef struct {
+  uint32_t struct_size;       /* sizeof(tt_jakes_desc) */
+  uint32_t n_taps;            /* K */
+  uint32_t n_sinusoids;       /* M, 1 .. 64 */
+  uint32_t reserved;
+  const int32_t *delays;      /* [K], non-decreasing, <= max_delay */
+  const float *amplitude;     /* [n_rx][n_tx][K] */
+  const double *freq;         /* [n_rx][n_tx][K][M][2], rad/s */
+  const double *phase;        /* [n_rx][n_tx][K][M][2], rad */
+  double sample_rate_hz;      /* f_s > 0 */
+} tt_jakes_desc;
+
+tt_status tt_chan_load_jakes(tt_chan *c, const tt_jakes_desc *jakes);
+
 /* Queue input slots [first, first+n).  The first push fixes the channel's
  * starting slot; after that slots must continue in order (TT_ERR_STATE).
  * TT_ERR_AGAIN if the ring has no room (pull or release outputs first).

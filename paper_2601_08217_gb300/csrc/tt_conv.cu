@@ -196,3 +196,55 @@ cudaError_t tt_launch_cir_resample(const float2 *gains, const double *tau, int n
                                                                                 n_taps, taps);
   return cudaGetLastError();
 }
+
+// ---- sum-of-sinusoids anchors: one thread per (job, slot, link tap) ----
+// The phase f t + p at the slot's start is reduced modulo 2 pi in FP64 once per sinusoid; the
+// symbols inside the slot add f (b_j - b_0) / f_s (under 2 pi f_D x one slot) in FP32.
+__global__ void __launch_bounds__(128) tt_sos_kernel(const TTSosJob *__restrict__ jobs, int n_jobs,
+                                                     unsigned long long n_threads) {
+  const unsigned long long idx = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_threads) return;
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].thread_begin <= idx) lo = mid; else hi = mid - 1;
+  }
+  const TTSosJob J = jobs[lo];
+  const unsigned long long rel = idx - J.thread_begin;
+  const int e = (int)(rel % (unsigned long long)J.per);
+  const int sl = (int)(rel / (unsigned long long)J.per);   // 0 .. n_slots (n_slots: the tail anchor)
+  const TTUEDesc *U = J.ue;
+  const int nsym = U->nsym, n_sym_here = sl < J.n_slots ? nsym : 1;
+  const uint64_t s = J.slot_first + (uint64_t)sl;
+  const double t0 = (double)(s * (uint64_t)U->n) * J.inv_fs;
+  const double two_pi = 6.283185307179586, inv_two_pi = 0.15915494309189535;
+  float si[TT_MAX_SYM], sq[TT_MAX_SYM];
+#pragma unroll
+  for (int j = 0; j < TT_MAX_SYM; ++j) si[j] = sq[j] = 0.f;
+  const double *f = J.freq + (size_t)e * J.m * 2, *p = J.phase + (size_t)e * J.m * 2;
+  for (int n = 0; n < J.m; ++n) {
+    const double ai = fma(f[2 * n], t0, p[2 * n]), aq = fma(f[2 * n + 1], t0, p[2 * n + 1]);
+    const float bi = (float)fma(-rint(ai * inv_two_pi), two_pi, ai), bq = (float)fma(-rint(aq * inv_two_pi), two_pi, aq);
+    const float fi = (float)(f[2 * n] * J.inv_fs), fq = (float)(f[2 * n + 1] * J.inv_fs);   // rad per sample
+#pragma unroll
+    for (int j = 0; j < TT_MAX_SYM; ++j) {
+      if (j < n_sym_here) {
+        const float off = (float)U->sym_start[j];
+        si[j] += cosf(fmaf(fi, off, bi));
+        sq[j] += cosf(fmaf(fq, off, bq));
+      }
+    }
+  }
+  const float g = J.amp[e] * rsqrtf((float)J.m);
+  const uint64_t a0 = s * (uint64_t)nsym;
+#pragma unroll
+  for (int j = 0; j < TT_MAX_SYM; ++j)
+    if (j < n_sym_here) J.ring[(size_t)((a0 + (uint64_t)j) % (uint64_t)J.ring_len) * J.per + e] = make_float2(g * si[j], g * sq[j]);
+}
+
+cudaError_t tt_launch_sos(const TTSosJob *jobs, int n_jobs, unsigned long long n_threads, cudaStream_t st) {
+  if (n_threads == 0 || n_jobs == 0) return cudaSuccess;
+  const int tpb = 128;
+  tt_sos_kernel<<<(unsigned)((n_threads + tpb - 1) / tpb), tpb, 0, st>>>(jobs, n_jobs, n_threads);
+  return cudaGetLastError();
+}

@@ -105,6 +105,9 @@ struct tt_engine {
   int *d_status = nullptr;                  // set by a kernel whose bounded wait expired
   std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
   std::vector<tt_cell *> cells;             // uplink aggregation cells
+  std::vector<TTSosJob> sos_jobs;           // synthesis work list of the current run (host copy)
+  TTSosJob *d_sos = nullptr;                // and its device copy
+  size_t sos_cap = 0;
 };
 
 struct tt_chan {
@@ -131,6 +134,12 @@ struct tt_chan {
   uint64_t dev_cursor = UINT64_MAX;  // what the engine's device cursor holds for this UE (after queued work)
   std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
   tt_cell *cell = nullptr;      // uplink aggregation cell consuming this channel's outputs
+  // sum-of-sinusoids synthesis: the trace is a ring of anchors refilled before each run
+  bool synth = false;
+  float *d_amp = nullptr;
+  double *d_freq = nullptr, *d_phase = nullptr;
+  int synth_m = 0;
+  double synth_fs = 0.0;
 };
 
 struct tt_cell {
@@ -708,6 +717,9 @@ tt_status tt_engine_destroy(tt_engine *e) {
       cudaFree(c->d_taps);
       cudaFree(c->d_delays);
       cudaFree(c->d_chunks);
+      cudaFree(c->d_amp);
+      cudaFree(c->d_freq);
+      cudaFree(c->d_phase);
       c->e = nullptr;
       delete c;
     }
@@ -727,6 +739,7 @@ tt_status tt_engine_destroy(tt_engine *e) {
   cudaFree(e->d_counters);
   cudaFree(e->d_cursors);
   cudaFree(e->d_tcsegs);
+  cudaFree(e->d_sos);
   cudaFree(e->d_status);
   if (e->stream) cudaStreamDestroy(e->stream);
   if (e->copy) cudaStreamDestroy(e->copy);
@@ -865,6 +878,9 @@ tt_status tt_chan_destroy(tt_chan *c) {
   cudaFree(c->d_taps);
   cudaFree(c->d_delays);
   cudaFree(c->d_chunks);
+  cudaFree(c->d_amp);
+  cudaFree(c->d_freq);
+  cudaFree(c->d_phase);
   e->in_use -= c->ring_bytes + c->trace_bytes;
   e->table[c->index] = nullptr;
   drop_graph(e);
@@ -928,6 +944,12 @@ static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64
   tt_engine *e = c->e;
   cudaFree(c->d_taps);
   cudaFree(c->d_delays);
+  cudaFree(c->d_amp);
+  cudaFree(c->d_freq);
+  cudaFree(c->d_phase);
+  c->d_amp = nullptr;
+  c->d_freq = c->d_phase = nullptr;
+  c->synth = false;
   e->in_use = e->in_use - c->trace_bytes + bytes;
   c->trace_bytes = bytes;
   c->d_taps = taps;
@@ -1007,6 +1029,66 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
                 cudaGetErrorString(err));
   }
   return install_trace(c, taps, delays, bytes, tr->n_anchors, tr->n_taps, tr->step_samples, tr->loop, g);
+}
+
+tt_status tt_chan_load_jakes(tt_chan *c, const tt_jakes_desc *j) {
+  if (!valid_chan(c) || !j || j->struct_size < sizeof(tt_jakes_desc))
+    return fail(TT_ERR_INVALID, "tt_chan_load_jakes: bad argument");
+  tt_engine *e = c->e;
+  if (!j->delays || !j->amplitude || !j->freq || !j->phase || j->n_taps == 0) return fail(TT_ERR_TRACE, "empty model");
+  if (j->n_sinusoids < 1 || j->n_sinusoids > 64) return fail(TT_ERR_TRACE, "n_sinusoids must be 1..64");
+  if (j->n_taps > c->cfg.max_taps) return fail(TT_ERR_TRACE, "%u taps, max_taps is %u", j->n_taps, c->cfg.max_taps);
+  if (!(j->sample_rate_hz > 0.0) || !std::isfinite(j->sample_rate_hz)) return fail(TT_ERR_TRACE, "bad sample_rate_hz");
+  const size_t per = (size_t)c->cfg.n_rx * c->cfg.n_tx * j->n_taps, nfp = per * j->n_sinusoids * 2;
+  for (size_t i = 0; i < per; ++i)
+    if (!std::isfinite(j->amplitude[i])) return fail(TT_ERR_TRACE, "non-finite amplitude at %zu", i);
+  for (size_t i = 0; i < nfp; ++i)
+    if (!std::isfinite(j->freq[i]) || !std::isfinite(j->phase[i])) return fail(TT_ERR_TRACE, "non-finite sinusoid at %zu", i);
+  TraceGeo g;
+  tt_status gs = trace_geometry(c, j->delays, j->n_taps, g);
+  if (gs != TT_OK) return gs;
+
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  tt_status st = idle_or_fail(c);
+  if (st != TT_OK) return st;
+  // anchor ring: every slot the channel's rings can hold, plus the anchor after the last one
+  const uint32_t ring_len = (uint32_t)((c->Q + 1) * (int)c->sym_len.size() + 1);
+  const uint64_t bytes = (uint64_t)ring_len * per * sizeof(float2) + j->n_taps * sizeof(int32_t) +
+                         per * sizeof(float) + nfp * 2 * sizeof(double);
+  if (e->budget && e->in_use - c->trace_bytes + bytes > e->budget)
+    return fail(TT_ERR_NO_MEMORY, "admission refused: model of %llu B does not fit the budget", (unsigned long long)bytes);
+  TT_CK(cudaStreamSynchronize(e->stream));
+  float2 *taps = nullptr;
+  int32_t *delays = nullptr;
+  float *amp = nullptr;
+  double *freq = nullptr, *phase = nullptr;
+  cudaError_t err = cudaMalloc(&taps, (size_t)ring_len * per * sizeof(float2));
+  if (err == cudaSuccess) err = cudaMalloc(&delays, j->n_taps * sizeof(int32_t));
+  if (err == cudaSuccess) err = cudaMalloc(&amp, per * sizeof(float));
+  if (err == cudaSuccess) err = cudaMalloc(&freq, nfp * sizeof(double));
+  if (err == cudaSuccess) err = cudaMalloc(&phase, nfp * sizeof(double));
+  if (err == cudaSuccess) err = cudaMemcpy(delays, j->delays, j->n_taps * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(amp, j->amplitude, per * sizeof(float), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(freq, j->freq, nfp * sizeof(double), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(phase, j->phase, nfp * sizeof(double), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) {
+    cudaFree(taps);
+    cudaFree(delays);
+    cudaFree(amp);
+    cudaFree(freq);
+    cudaFree(phase);
+    return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "model upload: %s", cudaGetErrorString(err));
+  }
+  st = install_trace(c, taps, delays, bytes, ring_len, j->n_taps, 0.0, 1, g);
+  if (st != TT_OK) return st;
+  c->synth = true;
+  c->d_amp = amp;
+  c->d_freq = freq;
+  c->d_phase = phase;
+  c->synth_m = (int)j->n_sinusoids;
+  c->synth_fs = j->sample_rate_hz;
+  return TT_OK;
 }
 
 tt_status tt_chan_load_cir(tt_chan *c, const tt_cir_desc *cir) {
@@ -1200,6 +1282,49 @@ tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n) {
 // Launch the aggregation of every cell whose members have all launched slots the cell has not
 // aggregated yet, as far as the cell ring has room (engine lock held).  Members must start at the
 // same slot.
+// Fill the anchor rings of synthesised channels for the slots this run launches (every symbol of
+// slots [launched_end, pushed_end) and the first anchor of slot pushed_end), all channels in one
+// launch (engine lock held).  Anchors rewritten here get the same value as before, and the stream
+// orders the rewrite after every kernel that read them.
+static tt_status launch_synth(tt_engine *e, const std::vector<tt_chan *> &chans) {
+  std::vector<TTSosJob> &jobs = e->sos_jobs;
+  jobs.clear();
+  unsigned long long threads = 0;
+  for (tt_chan *c : chans) {
+    if (!c->synth || c->pushed_end <= c->launched_end) continue;
+    TTSosJob J{};
+    J.ue = e->d_ues + c->index;
+    J.ring = c->d_taps;
+    J.amp = c->d_amp;
+    J.freq = c->d_freq;
+    J.phase = c->d_phase;
+    J.inv_fs = 1.0 / c->synth_fs;
+    J.slot_first = c->launched_end;
+    J.thread_begin = threads;
+    J.per = (int)(c->cfg.n_rx * c->cfg.n_tx * (uint32_t)c->desc.n_taps);
+    J.m = c->synth_m;
+    J.ring_len = c->desc.n_anchors;
+    J.n_slots = (int)(c->pushed_end - c->launched_end);
+    J.tail = 1;
+    threads += (unsigned long long)(J.n_slots + 1) * (unsigned long long)J.per;
+    jobs.push_back(J);
+  }
+  if (jobs.empty()) return TT_OK;
+  if (jobs.size() > e->sos_cap) {
+    TT_CK(cudaStreamSynchronize(e->stream));  // the old list may still be read
+    cudaFree(e->d_sos);
+    e->d_sos = nullptr;
+    e->sos_cap = 0;
+    TT_CK(cudaMalloc(&e->d_sos, sizeof(TTSosJob) * jobs.size() * 2));
+    e->sos_cap = jobs.size() * 2;
+  }
+  TT_CK(cudaMemcpyAsync(e->d_sos, jobs.data(), sizeof(TTSosJob) * jobs.size(), cudaMemcpyHostToDevice, e->stream));
+  cudaError_t err = tt_launch_sos(e->d_sos, (int)jobs.size(), threads, e->stream);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "synthesis launch: %s", cudaGetErrorString(err));
+  ++e->launches;
+  return TT_OK;
+}
+
 static tt_status launch_cells(tt_engine *e, std::vector<std::pair<tt_cell *, uint64_t>> &ends) {
   for (tt_cell *cl : e->cells) {
     if (cl->members.empty()) continue;
@@ -1368,6 +1493,12 @@ tt_status tt_engine_run(tt_engine *e) {
       else ready.push_back(c);
     }
   if (ready.empty() && tc_ready.empty() && e->cells.empty()) return TT_OK;
+  {
+    std::vector<tt_chan *> all(ready);
+    all.insert(all.end(), tc_ready.begin(), tc_ready.end());
+    tt_status sst = launch_synth(e, all);
+    if (sst != TT_OK) return sst;
+  }
 
   if (e->form == TT_FORM_PLAIN) {
     for (tt_chan *c : ready) {

@@ -127,6 +127,20 @@ struct TTCellArgs {
 cudaError_t tt_launch_cell_reduce(const TTCellArgs &A, uint64_t first_slot, uint32_t n_slots, cudaStream_t st);
 // Continuous CIR -> taps on the delay grid 0 .. n_taps-1: taps[t][link][k] = sum_p gains[t][link][p] *
 // sinc(k - tau[t][p]), FP64 sums rounded to complex64.
+// Sum-of-sinusoids anchors of one channel for slots [slot_first, slot_first + n_slots) (every
+// symbol) plus, if tail, the first anchor of slot slot_first + n_slots, into its anchor ring.
+struct TTSosJob {
+  const TTUEDesc *ue;         // the channel's descriptor (device): N, symbols, symbol starts
+  float2 *ring;               // [ring_len][per] anchors, anchor a at a % ring_len
+  const float *amp;           // [per]
+  const double *freq, *phase; // [per][m][2]
+  double inv_fs;              // 1 / sample rate
+  unsigned long long slot_first;
+  unsigned long long thread_begin;  // first thread of this job in the launch
+  int per, m, ring_len, n_slots, tail;
+};
+// One launch for every job: thread thread_begin + (slot - slot_first) * per + e of job j.
+cudaError_t tt_launch_sos(const TTSosJob *jobs, int n_jobs, unsigned long long n_threads, cudaStream_t st);
 cudaError_t tt_launch_cir_resample(const float2 *gains, const double *tau, int n_steps, int n_links, int n_paths,
                                    int n_taps, float2 *taps, cudaStream_t st);
 

@@ -61,6 +61,12 @@ class CirDesc(C.Structure):
                 ("step_samples", C.c_double), ("loop", C.c_int32), ("reserved", C.c_uint32)]
 
 
+class JakesDesc(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("n_taps", C.c_uint32), ("n_sinusoids", C.c_uint32),
+                ("reserved", C.c_uint32), ("delays", C.POINTER(C.c_int32)), ("amplitude", C.POINTER(C.c_float)),
+                ("freq", C.POINTER(C.c_double)), ("phase", C.POINTER(C.c_double)), ("sample_rate_hz", C.c_double)]
+
+
 class TraceDesc(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("taps", C.POINTER(C.c_float)),
                 ("delays", C.POINTER(C.c_int32)), ("n_anchors", C.c_uint32), ("n_taps", C.c_uint32),
@@ -123,6 +129,7 @@ _SIGS = {
     "tt_engine_push_slots": [_VP, C.c_uint32, _VP, _VP, _VP, _VP],
     "tt_cell_create": [_VP, _VP, _VP],
     "tt_chan_load_cir": [_VP, _VP],
+    "tt_chan_load_jakes": [_VP, _VP],
     "tt_cell_attach": [_VP, _VP],
     "tt_cell_pull_slots": [_VP, C.c_uint64, C.c_uint32, _VP, C.c_int64],
     "tt_cell_destroy": [_VP],
@@ -293,6 +300,22 @@ def tt_chan_load_cir(c: int, gains: np.ndarray, delays: np.ndarray, n_taps: int,
                    g.ctypes.data_as(C.POINTER(C.c_float)), d.ctypes.data_as(C.POINTER(C.c_double)),
                    float(step_samples), 1 if loop else 0, 0)
     _check(load().tt_chan_load_cir(c, C.byref(desc)))
+
+
+def tt_chan_load_jakes(c: int, delays, amplitude: np.ndarray, freq: np.ndarray, phase: np.ndarray,
+                       sample_rate_hz: float):
+    """Sum-of-sinusoids tap processes synthesised on the device: amplitude [n_rx][n_tx][K],
+    freq and phase [n_rx][n_tx][K][M][2] (rad/s, rad)."""
+    d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+    a = np.ascontiguousarray(np.asarray(amplitude, dtype=np.float32))
+    f = np.ascontiguousarray(np.asarray(freq, dtype=np.float64))
+    p = np.ascontiguousarray(np.asarray(phase, dtype=np.float64))
+    if f.shape != p.shape or f.ndim != 5 or f.shape[:3] != a.shape or f.shape[4] != 2 or a.shape[2] != d.size:
+        raise ValueError("amplitude [n_rx][n_tx][K], freq/phase [n_rx][n_tx][K][M][2], delays [K]")
+    desc = JakesDesc(C.sizeof(JakesDesc), d.size, f.shape[3], 0, d.ctypes.data_as(C.POINTER(C.c_int32)),
+                     a.ctypes.data_as(C.POINTER(C.c_float)), f.ctypes.data_as(C.POINTER(C.c_double)),
+                     p.ctypes.data_as(C.POINTER(C.c_double)), float(sample_rate_hz))
+    _check(load().tt_chan_load_jakes(c, C.byref(desc)))
 
 
 def tt_chan_push_slot(c: int, slot: int, iq_in):
