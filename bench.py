@@ -39,7 +39,7 @@ METRIC = "UE-slots/s and GMAC/s at 1 GB300 vs plain form; p99 slot latency vs 0.
 # DRAM traffic per full launch from the ncu capture summarised in
 # profiles/tt_conv_fp32_kernel_40mhz_16ue.md, valid only for the kernel source it was taken on.
 TRAFFIC_BYTES = 3.54e9
-TRAFFIC_KERNEL_SHA = "58c6e6514ac8be33"
+TRAFFIC_KERNEL_SHA = "95fc6a3fabb6639a"
 WORKLOAD = ("16 UEs SISO, 40 MHz (30720 samples/slot), 1000 slots each, 24 taps (delays <= 256), "
             "100 Hz Jakes, AWGN 20 dB, int16 IQ, FP32 accumulation")
 
