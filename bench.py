@@ -589,18 +589,24 @@ def run_synth(args, device, n_slots=200, warmup=3, steps=5):
     return res
 
 
-def cpu_baseline(budget_s: float = 12.0):
+def cpu_workload():
+    """The CPU baseline's sample: slots 0-7 of every UE of the workload, with the oracle's UEs."""
+    import oracle
+    from paper_2601_08217_gb300 import inputs
+    specs = inputs.workload_plain_16ue(n_slots=8, n_ues=N_UES)
+    xs = [inputs.make_iq(2, sp, 8) for sp in specs]
+    return specs, [oracle.OracleUE.from_spec(sp) for sp in specs], xs
+
+
+def cpu_baseline(budget_s: float = 12.0, work=None):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload.
 
     The sample is the first 8 slots of every UE of the workload, repeated in
     passes until about budget_s seconds of CPU work have been timed.
     """
     import oracle
-    from paper_2601_08217_gb300 import inputs
-    specs = inputs.workload_plain_16ue(n_slots=8, n_ues=N_UES)
+    specs, ues, xs = work if work is not None else cpu_workload()
     per_ue = 8
-    xs = [inputs.make_iq(2, sp, per_ue) for sp in specs]
-    ues = [oracle.OracleUE.from_spec(sp) for sp in specs]
     t = time.perf_counter()
     passes = 0
     while True:
@@ -652,10 +658,12 @@ def main():
         if rank != 0:
             return
         runs = []
+        work = cpu_workload()
+        budget = min(4.0, 90.0 / max(args.steps, 1))  # the whole run stays within a couple of minutes
         for _ in range(max(args.warmup, 0)):
-            cpu_baseline(budget_s=1.0)
+            cpu_baseline(budget_s=min(1.0, budget), work=work)
         for _ in range(max(args.steps, 1)):
-            runs.append(cpu_baseline(budget_s=4.0))
+            runs.append(cpu_baseline(budget_s=budget, work=work))
         v = statistics.median(r["value"] for r in runs)
         ms = statistics.median(r["seconds"] for r in runs) * 1e3
         cb = dict(runs[0])
