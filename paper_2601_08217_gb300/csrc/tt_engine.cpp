@@ -1493,6 +1493,17 @@ tt_status tt_engine_run(tt_engine *e) {
       else ready.push_back(c);
     }
   if (ready.empty() && tc_ready.empty() && e->cells.empty()) return TT_OK;
+  // the batch's completion event is taken before anything launches, so whatever launches below
+  // is always registered
+  cudaEvent_t ev = get_event(e);
+  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  struct EventGuard {
+    tt_engine *e;
+    cudaEvent_t ev;
+    ~EventGuard() {
+      if (ev) e->pool.push_back(ev);
+    }
+  } guard{e, ev};
   {
     std::vector<tt_chan *> all(ready);
     all.insert(all.end(), tc_ready.begin(), tc_ready.end());
@@ -1543,14 +1554,13 @@ tt_status tt_engine_run(tt_engine *e) {
     prev_end[i] = ready[i]->launched_end;
     ready[i]->launched_end = ready[i]->pushed_end;
   }
-  // uplink aggregation of every slot all members of a cell have launched (after their kernels)
+  // uplink aggregation of every slot all members of a cell have launched (after their kernels);
+  // a failure here still registers the channels' launched slots before it is reported
   std::vector<std::pair<tt_cell *, uint64_t>> cell_ends;
-  tt_status cst = launch_cells(e, cell_ends);
-  if (cst != TT_OK) return cst;
-  if (ready.empty() && cell_ends.empty()) return TT_OK;
-  cudaEvent_t ev = get_event(e);
-  if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
+  const tt_status cst = launch_cells(e, cell_ends);
+  if (ready.empty() && cell_ends.empty()) return cst;
   TT_CK(cudaEventRecord(ev, e->stream));
+  guard.ev = nullptr;  // owned by the batch list from here on
   const uint64_t seq = ++e->launch_seq;
   e->events.emplace_back(seq, ev);
   for (size_t i = 0; i < ready.size(); ++i) {
@@ -1563,7 +1573,7 @@ tt_status tt_engine_run(tt_engine *e) {
     cl->launched_end = ce.second;
     for (tt_chan *m : cl->members) m->pulled_end = std::max(m->pulled_end, ce.second);  // consumed
   }
-  return TT_OK;
+  return cst;
 }
 
 tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned) {
