@@ -5,7 +5,7 @@
 #include "tt_internal.h"
 #include "tt_philox.cuh"
 
-size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max, int topn) {
+size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max) {
   const int dmax = tt_dclass_max(dclass);
   const int np = tt_geo_np(spt, dmax);
   const int wmax = tt_geo_wmax(spt, dmax);
@@ -13,7 +13,7 @@ size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max,
   const size_t raw = (size_t)((n_tx * wmax + 3) & ~3) * sizeof(uint32_t);
   const size_t taps = 2 * (size_t)tap_max * sizeof(float4);
   const size_t dly = 2 * (size_t)((k_max + 3) & ~3) * sizeof(int);
-  return planes + raw + taps + dly + (topn ? tt_topn_scratch_bytes(tap_max) : 0);
+  return planes + raw + taps + dly;
 }
 
 // For each work item (TT_TPB groups of spt samples) of a slot: first symbol it
@@ -246,5 +246,80 @@ cudaError_t tt_launch_sos(const TTSosJob *jobs, int n_jobs, unsigned long long n
   if (n_threads == 0 || n_jobs == 0) return cudaSuccess;
   const int tpb = 128;
   tt_sos_kernel<<<(unsigned)((n_threads + tpb - 1) / tpb), tpb, 0, st>>>(jobs, n_jobs, n_threads);
+  return cudaGetLastError();
+}
+
+// ---- sparse convolution: per (anchor, link) tap selection, one warp each ----
+__global__ void __launch_bounds__(256) tt_topn_select_kernel(const TTTopnJob *__restrict__ jobs, int n_jobs,
+                                                             unsigned long long n_warps) {
+  const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= n_warps) return;  // whole warps leave together
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].warp_begin <= gw) lo = mid; else hi = mid - 1;
+  }
+  const TTTopnJob J = jobs[lo];
+  const unsigned long long rel = gw - J.warp_begin;
+  const int l = (int)(rel % (unsigned long long)J.links);
+  const uint64_t a = J.a_first + rel / (unsigned long long)J.links;
+  const TTUEDesc *U = J.ue;
+  const int K = U->n_taps, nsel = U->top_n, per = J.links * K;
+  constexpr int R = TT_MAX_TAPS / 32;  // taps per lane
+  float4 hv[R];
+  float pw[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int k = lane + 32 * i;
+    pw[i] = -1.f;  // below every power: absent taps never beat a present one
+    if (k < K) {
+      const float2 h0 = tt::tt_anchor(U, a, l * K + k, per), h1 = tt::tt_anchor(U, a + 1, l * K + k, per);
+      hv[i] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
+      pw[i] = __fmaf_rn(h0.x, h0.x, __fmul_rn(h0.y, h0.y));
+    }
+  }
+  // rank of each of this lane's taps: the taps that beat it (higher power, or equal and lower index)
+  int beat[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) beat[i] = 0;
+#pragma unroll
+  for (int ji = 0; ji < R; ++ji) {
+    if (32 * ji >= K) break;
+    for (int jl = 0; jl < 32; ++jl) {
+      const int j = 32 * ji + jl;
+      const float pj = __shfl_sync(0xFFFFFFFFu, pw[ji], jl);
+      if (j < K) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const int k = lane + 32 * i;
+          beat[i] += (pj > pw[i]) || (pj == pw[i] && j < k);
+        }
+      }
+    }
+  }
+  // compaction in tap order: position = kept taps of lower index
+  const size_t base = (size_t)(a % (uint64_t)U->sparse_len) * (size_t)(J.links * nsel) + (size_t)l * nsel;
+  float4 *ring = const_cast<float4 *>(U->sparse);
+  int32_t *dring = const_cast<int32_t *>(U->sparse_dly);
+  int before = 0;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int k = lane + 32 * i;
+    const bool keep = k < K && beat[i] < nsel;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, keep);
+    if (keep) {
+      const int pos = before + __popc(m & ((1u << lane) - 1u));
+      ring[base + pos] = hv[i];
+      dring[base + pos] = U->delays[k];
+    }
+    before += __popc(m);
+  }
+}
+
+cudaError_t tt_launch_topn_select(const TTTopnJob *jobs, int n_jobs, unsigned long long n_warps, cudaStream_t st) {
+  if (n_warps == 0 || n_jobs == 0) return cudaSuccess;
+  const unsigned long long threads = n_warps * 32;
+  tt_topn_select_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(jobs, n_jobs, n_warps);
   return cudaGetLastError();
 }

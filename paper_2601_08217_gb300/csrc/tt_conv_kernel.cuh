@@ -128,7 +128,7 @@ __device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, cons
 
 // All threads: start the asynchronous copies of one item's raw window, trace
 // entries, delays and symbol table into shared memory.
-template <int S, int NRX>
+template <int S, int NRX, bool TOPN>
 __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, const TTItem &it, uint32_t *raw,
                                               int wmax, float4 *taps, int *dly, int *sym, int tid) {
   const int n = U->n, n_tx = U->n_tx, Q = U->ring_q, K = U->n_taps, dpad = U->dpad;
@@ -154,6 +154,22 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
   }
   const int per = NRX * n_tx * K;
   const int ntap_e = it.nst * per;
+  if constexpr (TOPN) {
+    // sparse convolution: the kept taps of each touched symbol and link, selected ahead of the run
+    const int ns = NRX * n_tx * U->top_n;
+    const uint64_t L = (uint64_t)U->sparse_len;
+    for (int e = tid; e < it.nst * ns; e += TT_TPB) {
+      const int jl = e / ns;
+      const int rem = e - jl * ns;
+      const uint64_t a = it.slot * (uint64_t)U->nsym + (uint64_t)(it.jf + jl);
+      const size_t src = (size_t)(a % L) * ns + rem;
+      tt_cp_async16(&taps[e], U->sparse + src);
+      tt_cp_async4(dly + e, U->sparse_dly + src);
+    }
+    if (tid <= U->nsym) tt_cp_async4(sym + tid, U->sym_start + tid);
+    tt_cp_async_commit();
+    return;
+  }
   if (U->step_samples == 0.0) {
     const uint64_t T = (uint64_t)U->n_anchors;
     for (int e = tid; e < ntap_e; e += TT_TPB) {
@@ -178,57 +194,10 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
 
 // All threads, after the copies landed: raw window -> phase planes, taps -> (H0, dH),
 // delays -> plane offsets.
-// Sparse convolution (Sec. III-C): for every touched symbol jl and link (r, t), keep the top_n taps
-// of largest |H[a]|^2 at the symbol's anchor (ties: lower tap index) and compact them, in tap
-// order, to the front of the tap table: entry ((jl * NRX + r) * n_tx + t) * top_n + i holds
-// (H, dH) of the i-th kept tap and its plane offset.  The powers are binary32,
-// p = fma(re, re, im * im), the precision the oracle takes the same decision in.  The launch's
-// scratch area (tt_topn_scratch_bytes(tap_max)) holds the powers, keep flags and compacted lists.
-template <int S, int NRX, int NP>
-__device__ __forceinline__ void tt_select_top_n(const TTUEDesc *__restrict__ U, const TTItem &it, uint32_t *scratch,
-                                                float4 *taps, int *dly, int tid) {
-  const int n_tx = U->n_tx, K = U->n_taps, nsel = U->top_n;
-  const int ntap_e = it.nst * NRX * n_tx * K;
-  const int nseg = it.nst * NRX * n_tx;
-  float *pw = reinterpret_cast<float *>(scratch);
-  int *keep = reinterpret_cast<int *>(scratch) + ((ntap_e + 3) & ~3);
-  float4 *ctap = reinterpret_cast<float4 *>(keep + ((ntap_e + 3) & ~3));
-  int *coff = reinterpret_cast<int *>(ctap + nseg * nsel);
-  __syncthreads();  // every thread is done with the (H, dH) conversion
-  for (int e = tid; e < ntap_e; e += TT_TPB) {
-    const float4 h = taps[e];
-    pw[e] = __fmaf_rn(h.x, h.x, __fmul_rn(h.y, h.y));
-  }
-  __syncthreads();
-  for (int e = tid; e < ntap_e; e += TT_TPB) {
-    const int seg = e / K, k = e - seg * K;
-    const float *ps = pw + seg * K;
-    const float pk = ps[k];
-    int beat = 0;
-    for (int j = 0; j < K; ++j) beat += (ps[j] > pk) || (ps[j] == pk && j < k);
-    keep[e] = beat < nsel;
-  }
-  __syncthreads();
-  for (int e = tid; e < ntap_e; e += TT_TPB) {
-    if (!keep[e]) continue;
-    const int seg = e / K, k = e - seg * K;
-    int pos = 0;
-    for (int j = 0; j < k; ++j) pos += keep[seg * K + j];
-    ctap[seg * nsel + pos] = taps[e];
-    const int d = dly[k];  // the trace's delay, not yet an offset
-    coff[seg * nsel + pos] = (S - d % S) * NP - d / S;
-  }
-  __syncthreads();
-  for (int e = tid; e < nseg * nsel; e += TT_TPB) {
-    taps[e] = ctap[e];
-    dly[e] = coff[e];
-  }
-}
-
 template <int S, int NRX, int NP, bool TOPN>
 __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, const TTItem &it,
                                                 const uint32_t *raw, int wmax, float2 *planes, float4 *taps,
-                                                int *dly, uint32_t *scratch, int tid) {
+                                                int *dly, int tid) {
   const int n_tx = U->n_tx, K = U->n_taps, dpad = U->dpad;
   const int wlen = (it.gend - it.g0) * S + dpad;
   for (int t = 0; t < n_tx; ++t) {
@@ -255,6 +224,13 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
       }
     }
   }
+  if constexpr (TOPN) {  // (H, dH) came from the selection; delays become plane offsets
+    for (int e = tid; e < it.nst * NRX * n_tx * U->top_n; e += TT_TPB) {
+      const int d = dly[e];
+      dly[e] = (S - d % S) * NP - d / S;
+    }
+    return;
+  }
   const int per = NRX * n_tx * K;
   const int ntap_e = it.nst * per;
   if (U->step_samples == 0.0) {
@@ -275,13 +251,9 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
       taps[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
     }
   }
-  if constexpr (TOPN) {  // every UE of a TOPN launch keeps fewer taps than it has
-    tt_select_top_n<S, NRX, NP>(U, it, scratch, taps, dly, tid);
-  } else {
-    for (int k = tid; k < K; k += TT_TPB) {
-      const int d = dly[k];
-      dly[k] = (S - d % S) * NP - d / S;
-    }
+  for (int k = tid; k < K; k += TT_TPB) {
+    const int d = dly[k];
+    dly[k] = (S - d % S) * NP - d / S;
   }
 }
 
@@ -428,7 +400,6 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
   float4 *taps1 = taps0 + tap_max;
   int *dly0 = reinterpret_cast<int *>(taps1 + tap_max);
   int *dly1 = dly0 + kpad;
-  uint32_t *scratch = reinterpret_cast<uint32_t *>(dly1 + kpad);  // TOPN launches only (16-byte aligned)
 
   uint32_t next_static = blockIdx.x;
   auto claim = [&]() -> uint32_t {
@@ -448,10 +419,10 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
   {
     const TTItem it = s_it[0];
     const TTUEDesc *U = ues + it.ue;
-    tt_issue_item<S, NRX>(U, it, raw, WMAX, taps0, dly0, s_sym[0], tid);
+    tt_issue_item<S, NRX, TOPN>(U, it, raw, WMAX, taps0, dly0, s_sym[0], tid);
     tt_cp_async_wait_all();
     __syncthreads();
-    tt_convert_item<S, NRX, NP, TOPN>(U, it, raw, WMAX, planes, taps0, dly0, scratch, tid);
+    tt_convert_item<S, NRX, NP, TOPN>(U, it, raw, WMAX, planes, taps0, dly0, tid);
     if (tid == 0) tt_locate(ues, segs, n_segs, s_claim, total_items, cursors, s_it[1]);
     __syncthreads();
   }
@@ -463,14 +434,14 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     float4 *tc = cb ? taps1 : taps0, *tn = cb ? taps0 : taps1;
     int *dc = cb ? dly1 : dly0, *dn = cb ? dly0 : dly1;
     const TTUEDesc *Un = ues + nxt.ue;
-    if (nxt.valid) tt_issue_item<S, NRX>(Un, nxt, raw, WMAX, tn, dn, s_sym[cb ^ 1], tid);
+    if (nxt.valid) tt_issue_item<S, NRX, TOPN>(Un, nxt, raw, WMAX, tn, dn, s_sym[cb ^ 1], tid);
     tt_compute_item<S, NRX, NP, TOPN>(ues + cur.ue, cur, planes, tc, dc, s_sym[cb], tid);
     uint32_t nn = 0;
     if (tid == 0 && nxt.valid) nn = claim();
     tt_cp_async_wait_all();
     __syncthreads();
     if (!nxt.valid) return;
-    tt_convert_item<S, NRX, NP, TOPN>(Un, nxt, raw, WMAX, planes, tn, dn, scratch, tid);
+    tt_convert_item<S, NRX, NP, TOPN>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
     if (tid == 0) tt_locate(ues, segs, n_segs, nn, total_items, cursors, s_it[cb]);
     __syncthreads();
     cb ^= 1;

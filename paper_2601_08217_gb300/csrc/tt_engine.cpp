@@ -108,6 +108,9 @@ struct tt_engine {
   std::vector<TTSosJob> sos_jobs;           // synthesis work list of the current run (host copy)
   TTSosJob *d_sos = nullptr;                // and its device copy
   size_t sos_cap = 0;
+  std::vector<TTTopnJob> topn_jobs;         // tap-selection work list of the current run
+  TTTopnJob *d_topn = nullptr;
+  size_t topn_cap = 0;
 };
 
 struct tt_chan {
@@ -131,6 +134,9 @@ struct tt_chan {
   bool started = false;
   uint64_t pushed_end = 0, launched_end = 0, completed_end = 0, pulled_end = 0;
   uint64_t start_slot = 0;           // first slot ever pushed
+  float4 *d_sparse = nullptr;        // sparse convolution: kept taps per anchor and link (ring)
+  int32_t *d_sparse_dly = nullptr;
+  uint64_t sparse_bytes = 0;
   uint64_t dev_cursor = UINT64_MAX;  // what the engine's device cursor holds for this UE (after queued work)
   std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
   tt_cell *cell = nullptr;      // uplink aggregation cell consuming this channel's outputs
@@ -352,8 +358,7 @@ size_t smem_need(const tt_chan *c, int spt, int *tap_need) {
   int touched = 1;
   chunk_table(c->sym_len, spt, &touched);
   *tap_need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * (uint32_t)c->desc.n_taps);
-  const size_t b = tt_conv_smem_bytes(spt, c->dclass, (int)c->cfg.n_tx, *tap_need, k_need(c, *tap_need),
-                                      sparse(c) ? 1 : 0);
+  const size_t b = tt_conv_smem_bytes(spt, c->dclass, (int)c->cfg.n_tx, *tap_need, k_need(c, *tap_need));
   return b <= 200 * 1024 ? b : 0;
 }
 
@@ -437,7 +442,7 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
   }
   if ((int)p.groups.size() > e->counter_cap) return fail(TT_ERR_INVALID, "too many kernel variants in one run");
   for (PlanGroup &g : p.groups) {
-    g.smem = tt_conv_smem_bytes(g.spt, g.dclass, g.ntx, g.tap_max, g.k_max, g.topn);
+    g.smem = tt_conv_smem_bytes(g.spt, g.dclass, g.ntx, g.tap_max, g.k_max);
     TTLaunch L{};
     L.spt = g.spt;
     L.nrx = g.nrx;
@@ -720,6 +725,8 @@ tt_status tt_engine_destroy(tt_engine *e) {
       cudaFree(c->d_amp);
       cudaFree(c->d_freq);
       cudaFree(c->d_phase);
+      cudaFree(c->d_sparse);
+      cudaFree(c->d_sparse_dly);
       c->e = nullptr;
       delete c;
     }
@@ -740,6 +747,7 @@ tt_status tt_engine_destroy(tt_engine *e) {
   cudaFree(e->d_cursors);
   cudaFree(e->d_tcsegs);
   cudaFree(e->d_sos);
+  cudaFree(e->d_topn);
   cudaFree(e->d_status);
   if (e->stream) cudaStreamDestroy(e->stream);
   if (e->copy) cudaStreamDestroy(e->copy);
@@ -881,7 +889,9 @@ tt_status tt_chan_destroy(tt_chan *c) {
   cudaFree(c->d_amp);
   cudaFree(c->d_freq);
   cudaFree(c->d_phase);
-  e->in_use -= c->ring_bytes + c->trace_bytes;
+  cudaFree(c->d_sparse);
+  cudaFree(c->d_sparse_dly);
+  e->in_use -= c->ring_bytes + c->trace_bytes + c->sparse_bytes;
   e->table[c->index] = nullptr;
   drop_graph(e);
   c->e = nullptr;
@@ -922,8 +932,7 @@ static tt_status trace_geometry(const tt_chan *c, const int32_t *delays, uint32_
     int touched = 1;
     chunk_table(c->sym_len, s, &touched);
     const int need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * n_taps);
-    const size_t b = tt_conv_smem_bytes(s, g.dclass, c->cfg.n_tx, need, topn ? std::max((int)n_taps, need) : (int)n_taps,
-                                        topn ? 1 : 0);
+    const size_t b = tt_conv_smem_bytes(s, g.dclass, c->cfg.n_tx, need, topn ? std::max((int)n_taps, need) : (int)n_taps);
     if (b <= 200 * 1024) {
       g.spt = s;
       g.tap_need = need;
@@ -967,6 +976,33 @@ static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64
   d.d_max = g.d_max;
   d.n_anchors = (int)n_anchors;
   d.loop = loop ? 1 : 0;
+  // sparse convolution: a ring of the kept taps per anchor and link, sized like the slot ring
+  cudaFree(c->d_sparse);
+  cudaFree(c->d_sparse_dly);
+  c->d_sparse = nullptr;
+  c->d_sparse_dly = nullptr;
+  e->in_use -= c->sparse_bytes;
+  c->sparse_bytes = 0;
+  d.sparse = nullptr;
+  d.sparse_dly = nullptr;
+  d.sparse_len = 0;
+  if (c->cfg.top_n > 0 && c->cfg.top_n < n_taps) {
+    const int len = (c->Q + 1) * (int)c->sym_len.size() + 1;
+    const size_t ent = (size_t)len * c->cfg.n_rx * c->cfg.n_tx * c->cfg.top_n;
+    cudaError_t err = cudaMalloc(&c->d_sparse, ent * sizeof(float4));
+    if (err == cudaSuccess) err = cudaMalloc(&c->d_sparse_dly, ent * sizeof(int32_t));
+    if (err != cudaSuccess) {
+      cudaFree(c->d_sparse);
+      c->d_sparse = nullptr;
+      c->has_trace = false;
+      return fail(TT_ERR_NO_MEMORY, "sparse tap ring: %s", cudaGetErrorString(err));
+    }
+    c->sparse_bytes = ent * (sizeof(float4) + sizeof(int32_t));
+    e->in_use += c->sparse_bytes;
+    d.sparse = c->d_sparse;
+    d.sparse_dly = c->d_sparse_dly;
+    d.sparse_len = len;
+  }
   tt_status sst = set_spt(c, g.spt);
   if (sst != TT_OK) return sst;
   if (c->cfg.precision != TT_FP32) {  // the tensor-core kernel's work items: one per symbol
@@ -1325,6 +1361,40 @@ static tt_status launch_synth(tt_engine *e, const std::vector<tt_chan *> &chans)
   return TT_OK;
 }
 
+// Sparse convolution: select the kept taps of every anchor this run's slots use (one launch for all
+// channels), after any synthesis of the anchors themselves (engine lock held).
+static tt_status launch_topn(tt_engine *e, const std::vector<tt_chan *> &chans) {
+  std::vector<TTTopnJob> &jobs = e->topn_jobs;
+  jobs.clear();
+  unsigned long long warps = 0;
+  for (tt_chan *c : chans) {
+    if (!sparse(c) || !c->d_sparse || c->pushed_end <= c->launched_end) continue;
+    const uint64_t nsym = c->sym_len.size();
+    TTTopnJob J{};
+    J.ue = e->d_ues + c->index;
+    J.a_first = c->launched_end * nsym;
+    J.n_anchors = (int)((c->pushed_end - c->launched_end) * nsym);
+    J.links = (int)(c->cfg.n_rx * c->cfg.n_tx);
+    J.warp_begin = warps;
+    warps += (unsigned long long)J.n_anchors * (unsigned long long)J.links;
+    jobs.push_back(J);
+  }
+  if (jobs.empty()) return TT_OK;
+  if (jobs.size() > e->topn_cap) {
+    TT_CK(cudaStreamSynchronize(e->stream));  // the old list may still be read
+    cudaFree(e->d_topn);
+    e->d_topn = nullptr;
+    e->topn_cap = 0;
+    TT_CK(cudaMalloc(&e->d_topn, sizeof(TTTopnJob) * jobs.size() * 2));
+    e->topn_cap = jobs.size() * 2;
+  }
+  TT_CK(cudaMemcpyAsync(e->d_topn, jobs.data(), sizeof(TTTopnJob) * jobs.size(), cudaMemcpyHostToDevice, e->stream));
+  cudaError_t err = tt_launch_topn_select(e->d_topn, (int)jobs.size(), warps, e->stream);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tap selection launch: %s", cudaGetErrorString(err));
+  ++e->launches;
+  return TT_OK;
+}
+
 static tt_status launch_cells(tt_engine *e, std::vector<std::pair<tt_cell *, uint64_t>> &ends) {
   for (tt_cell *cl : e->cells) {
     if (cl->members.empty()) continue;
@@ -1508,6 +1578,7 @@ tt_status tt_engine_run(tt_engine *e) {
     std::vector<tt_chan *> all(ready);
     all.insert(all.end(), tc_ready.begin(), tc_ready.end());
     tt_status sst = launch_synth(e, all);
+    if (sst == TT_OK) sst = launch_topn(e, ready);
     if (sst != TT_OK) return sst;
   }
 

@@ -47,6 +47,8 @@ struct TTUEDesc {
   const float2 *taps;      // [T][n_rx][n_tx][K]
   const int32_t *delays;   // [K]
   const int32_t *chunk_info;  // per work item of a slot: first symbol | (symbols touched << 16)
+  const float4 *sparse;    // sparse convolution: [sparse_len][n_rx * n_tx][top_n] (H, dH) of the kept taps
+  const int32_t *sparse_dly;  // and their delays; anchor a at a % sparse_len
   double step_samples;     // 0: one trace entry per symbol
   uint64_t seed;
   int32_t n;               // samples per slot
@@ -54,6 +56,7 @@ struct TTUEDesc {
   int32_t n_tx, n_rx, n_taps;
   int32_t d_max;           // largest delay of the loaded trace
   int32_t top_n;           // 0: every tap; else the top_n taps per symbol and link (sparse convolution)
+  int32_t sparse_len;      // anchors in the sparse ring
   int32_t ring_q;          // ring depth in slots
   int32_t n_anchors;
   int32_t loop;
@@ -100,12 +103,8 @@ struct TTLaunch {
 cudaError_t tt_launch_advance(const TTSeg *segs, int n_segs, unsigned long long *cursors, cudaStream_t st);
 
 // Dynamic shared memory of the tiled kernel for a launch.
-size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max, int topn);
-// Scratch of the sparse (top-n) selection for up to tap_max tap entries: powers and keep flags
-// (4 B each, padded to 4 entries) and the compacted (H, dH) and offsets (16 B + 4 B each).
-__host__ __device__ constexpr size_t tt_topn_scratch_bytes(int tap_max) {
-  return (size_t)((tap_max + 3) & ~3) * 8 + (size_t)tap_max * 20;
-}
+size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max);
+
 // First symbol and number of symbols touched by each work item of a slot (packed jf | nst << 16).
 int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, int max_out);
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st);
@@ -141,6 +140,16 @@ struct TTSosJob {
 };
 // One launch for every job: thread thread_begin + (slot - slot_first) * per + e of job j.
 cudaError_t tt_launch_sos(const TTSosJob *jobs, int n_jobs, unsigned long long n_threads, cudaStream_t st);
+// Sparse convolution: for anchors [a_first, a_first + n_anchors) of one channel, the top_n taps of
+// each link by binary32 power at the anchor (ties: lower index), compacted in tap order into the
+// channel's sparse ring with (H, H[a+1] - H) and their delays; one warp per (anchor, link).
+struct TTTopnJob {
+  const TTUEDesc *ue;
+  unsigned long long a_first;
+  unsigned long long warp_begin;
+  int n_anchors, links;
+};
+cudaError_t tt_launch_topn_select(const TTTopnJob *jobs, int n_jobs, unsigned long long n_warps, cudaStream_t st);
 cudaError_t tt_launch_cir_resample(const float2 *gains, const double *tau, int n_steps, int n_links, int n_paths,
                                    int n_taps, float2 *taps, cudaStream_t st);
 

@@ -140,7 +140,7 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
       int touched = 1;
       for (int q = 0; q < it; ++q) touched = std::max(touched, (int)(chunks[q] >> 16));
       const int need = touched * (int)(c.n_rx * c.n_tx * c.n_taps);
-      if (tt_conv_smem_bytes(s, dclass, (int)c.n_tx, need, (int)c.n_taps, 0) <= 200 * 1024) {
+      if (tt_conv_smem_bytes(s, dclass, (int)c.n_tx, need, (int)c.n_taps) <= 200 * 1024) {
         spt = s;
         tap_need = need;
         items = it;
@@ -246,7 +246,7 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
     L.dclass = gr.dclass;
     L.tap_max = gr.tap_max;
     L.k_max = gr.k_max;
-    L.smem = tt_conv_smem_bytes(gr.spt, gr.dclass, gr.ntx, gr.tap_max, gr.k_max, 0);
+    L.smem = tt_conv_smem_bytes(gr.spt, gr.dclass, gr.ntx, gr.tap_max, gr.k_max);
     L.grid = -1;
     ce = tt_launch_conv_fp32(L, st);
     if (ce != cudaSuccess) return err(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(ce));
