@@ -739,6 +739,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "ues_per_gpu": N_UES, "slots": N_SLOTS,
+                   "parallelism": f"{world} GPU(s), UEs sharded across them, no data-path collective",
                    "samples_per_slot": SLOT_SAMPLES, "taps": N_TAPS, "max_delay": D_MAX,
                    "form": "batched, persistent CTAs" + (" (device work counter)" if args.persistent else " (strided)"),
                    "iq": f"{DISTINCT_IQ_SLOTS} distinct synthetic slots per UE cycled",

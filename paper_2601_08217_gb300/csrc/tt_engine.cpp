@@ -352,8 +352,8 @@ bool sparse(const tt_chan *c) { return c->desc.top_n > 0 && c->desc.top_n < c->d
 // the compacted lists of every touched symbol and link (at most tap_need entries).
 int k_need(const tt_chan *c, int tap_need) { return sparse(c) ? std::max(c->desc.n_taps, tap_need) : c->desc.n_taps; }
 
-// Shared-memory need of a traced channel at spt samples per thread (0 if it does not fit); sparse
-// convolution adds the selection's scratch.
+// Shared-memory need of a traced channel at spt samples per thread (0 if it does not fit); with
+// sparse convolution the delay-offset array holds the compacted lists of every touched symbol.
 size_t smem_need(const tt_chan *c, int spt, int *tap_need) {
   int touched = 1;
   chunk_table(c->sym_len, spt, &touched);
