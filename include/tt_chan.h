@@ -197,7 +197,8 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
  * meanwhile join the next batch.  Latency = completion seen by the host
  * (event polled) minus arrival, for requests that arrived after the warm-up.
  * release_outputs = 1 frees each output ring position as soon as it is
- * complete; 0 keeps the outputs for tt_chan_pull_* (rings then fill up). */
+ * complete, the rings of uplink aggregation cells included; 0 keeps the
+ * outputs for tt_chan_pull_* / tt_cell_pull_slots (rings then fill up). */
 typedef struct {
   uint32_t struct_size;           /* sizeof(tt_serve_config) */
   uint32_t max_slots_per_ue;      /* 0 = no limit; else each UE stops after this many requests */

@@ -2173,6 +2173,14 @@ tt_status tt_engine_serve(tt_engine *e, const tt_serve_config *cfg, tt_serve_rep
         inflight.pop_front();
         did = true;
       }
+      if (cfg->release_outputs)  // cells aggregated by completed batches free their ring slots too
+        for (tt_cell *cl : e->cells) {
+          while (!cl->inflight.empty() && cl->inflight.front().second <= e->completed_seq) {
+            cl->completed_end = cl->inflight.front().first;
+            cl->inflight.pop_front();
+          }
+          cl->pulled_end = std::max(cl->pulled_end, cl->completed_end);
+        }
     }
     if (now >= t_end && inflight.empty() && unlaunched == 0) break;
     if (!did) std::this_thread::yield();

@@ -151,3 +151,21 @@ def test_cell_refusals():
         cell.destroy()
     finally:
         eng.close()
+
+
+def test_cell_members_served_by_the_request_loop():
+    """The serving loop admits cell members like any channel and drains the cell ring: the
+    aggregation keeps consuming the members' outputs, so requests keep completing (independent
+    arrivals let members drift apart, so some are refused when one runs a ring ahead)."""
+    specs = _members(4, 3)
+    eng = tc.Engine(persistent=True)
+    try:
+        cell = tc.Cell(eng, cell_id=5, samples_per_slot=specs[0].n, ring_slots=4)
+        for sp in specs:
+            ch = tc.Chan(eng, sp, cf32=True, ring_slots=8)
+            cell.attach(ch)
+        rep = tc.tt_engine_serve(eng.h, duration_s=0.2, warmup_s=0.02, slot_period_us=500.0, jitter_us=50.0,
+                                 deadline_us=500.0, seed=3, release_outputs=True)
+        assert rep["completed"] > 0.5 * rep["requests"]
+    finally:
+        eng.close()
