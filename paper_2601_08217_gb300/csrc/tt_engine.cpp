@@ -1198,6 +1198,9 @@ static cudaError_t wait_ring_readers(tt_chan *c, uint64_t first, uint32_t n, cud
   if (q != cudaSuccess) return q;
   update_chan(c);
   const uint64_t last_reader_slot = first + n - (uint64_t)c->Q - 1 + (uint64_t)c->hist;
+  // Completed batches have left the in-flight list: if the reader is among them, nothing to wait
+  // for (the first batch still in flight is a later one, which reads other positions).
+  if (last_reader_slot < c->completed_end) return cudaSuccess;
   for (const auto &p : c->inflight)
     if (p.first > last_reader_slot) {
       cudaEvent_t ev = event_of(e, p.second);

@@ -457,6 +457,7 @@ class Engine:
         f = {"batched": TT_FORM_BATCHED, "plain": TT_FORM_PLAIN}[form]
         self.h = tt_engine_create(device, f, hbm_budget_bytes, max_ues, samples_per_thread, persistent, graphs)
         self.chans = []
+        self.cells = []
 
     def run(self):
         tt_engine_run(self.h)
@@ -475,7 +476,12 @@ class Engine:
         return tt_engine_autotune(self.h, reps)
 
     def close(self):
+        """Destroy the engine.  The C side frees every channel and cell with it, so their handles are
+        cleared here first; a later ``destroy()`` on them is then a no-op rather than a dangling call."""
         if self.h:
+            for obj in self.chans + self.cells:
+                obj.h = None
+            self.chans, self.cells = [], []
             tt_engine_destroy(self.h)
             self.h = None
 
@@ -527,6 +533,8 @@ class Chan:
         if self.h:
             tt_chan_destroy(self.h)
             self.h = None
+            if self in self.engine.chans:
+                self.engine.chans.remove(self)
 
 
 def slots_major(x: np.ndarray, n: int) -> np.ndarray:
@@ -550,6 +558,7 @@ class Cell:
         self.n, self.n_rx, self.cf32 = int(samples_per_slot), int(n_rx), cf32
         self.h = tt_cell_create(engine.h, cell_id, samples_per_slot, n_rx, ring_slots, seed, noise_var,
                                 TT_OUT_CF32 if cf32 else TT_OUT_INT16)
+        engine.cells.append(self)
 
     def attach(self, chan: "Chan"):
         tt_cell_attach(self.h, chan.h)
@@ -566,4 +575,6 @@ class Cell:
     def destroy(self):
         if self.h:
             tt_cell_destroy(self.h)
-            self.h = 0
+            self.h = None
+            if self in self.engine.cells:
+                self.engine.cells.remove(self)

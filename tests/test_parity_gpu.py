@@ -283,7 +283,16 @@ def test_errors_and_admission():
     ch.pull(10, 1)
     st = eng.stats()
     assert st["n_chans"] == 1 and st["hbm_in_use"] > 0 and st["slots_processed"] == 8
-    eng.close()
+    cell = tc.Cell(eng, 0, spec.n, n_rx=spec.n_rx, ring_slots=8)
+    eng.close()                               # frees the channel and the cell with the engine
+    ch.destroy()                              # handles were cleared: no call on freed memory
+    cell.destroy()
+    with pytest.raises(tc.TTError) as ei:
+        ch.push(11, x[:1])
+    assert ei.value.status == tc.TT_ERR_INVALID
+    with pytest.raises(tc.TTError) as ei:
+        cell.pull(0, 1, timeout_us=0)
+    assert ei.value.status == tc.TT_ERR_INVALID
 
 
 def test_device_buffers_and_zero_copy_paths():
