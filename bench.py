@@ -39,7 +39,7 @@ METRIC = "UE-slots/s and GMAC/s at 1 GB300 vs plain form; p99 slot latency vs 0.
 # DRAM traffic per full launch from the ncu capture summarised in
 # profiles/tt_conv_fp32_kernel_40mhz_16ue.md, valid only for the kernel source it was taken on.
 TRAFFIC_BYTES = 3.54e9
-TRAFFIC_KERNEL_SHA = "95fc6a3fabb6639a"
+TRAFFIC_KERNEL_SHA = "874f93de3af1b253"
 WORKLOAD = ("16 UEs SISO, 40 MHz (30720 samples/slot), 1000 slots each, 24 taps (delays <= 256), "
             "100 Hz Jakes, AWGN 20 dB, int16 IQ, FP32 accumulation")
 
@@ -218,48 +218,51 @@ def run_ours(args, rank, world, device):
         slot_bytes = n * 2 * 2
         hs = [ch.h for ch in chans]
 
-        def e2e_step():
-            # a producer thread pushes chunk after chunk (all UEs in one call) and launches it; this
-            # thread pulls each launched chunk, so host-to-device and device-to-host copies overlap
-            # each other and the kernels
+        def e2e_run(n_steps):
+            # one continuous stream of n_steps x N_SLOTS slots, as a streaming user drives it: a
+            # producer thread pushes chunk after chunk (all UEs in one call, host buffers) and
+            # launches it; this thread pulls each launched chunk back to host buffers, so the
+            # host-to-device and device-to-host copies overlap each other and the kernels, also
+            # across step boundaries.  Every step's input copies and output reads are in the run.
             s0 = next_slot[0]
+            total = n_steps * N_SLOTS
             launched = queue.Queue()
+            room = threading.Semaphore(4)   # chunks pushed ahead of the pulls (500 of 1001 ring slots)
             err = []
 
             def producer():
                 try:
-                    prev = None
-                    for c0 in range(0, N_SLOTS, chunk):
+                    for c0 in range(0, total, chunk):
+                        room.acquire()
+                        off = (c0 % N_SLOTS) * slot_bytes
                         tc.tt_engine_push_slots(eng.h, hs, [s0 + c0] * len(hs), [chunk] * len(hs),
-                                                [hi.data_ptr() + c0 * slot_bytes for hi in h_in])
+                                                [hi.data_ptr() + off for hi in h_in])
                         eng.run()
-                        if prev is not None:   # hand over a chunk once the next one is pushed:
-                            launched.put(prev)  # its kernels have finished by then
-                        prev = c0
-                    launched.put(prev)
+                        launched.put(c0)
                 except Exception as ex:  # surfaced below
                     err.append(ex)
                     launched.put(None)
 
-            th = threading.Thread(target=producer)
+            th = threading.Thread(target=producer, daemon=True)   # never outlives a failed pull
             th.start()
-            for _ in range(0, N_SLOTS, chunk):
+            for _ in range(0, total, chunk):
                 c0 = launched.get()
                 if c0 is None:
                     break
+                off = (c0 % N_SLOTS) * slot_bytes
                 tc.tt_engine_pull_slots(eng.h, hs, [s0 + c0] * len(hs), [chunk] * len(hs),
-                                        [ho.data_ptr() + c0 * slot_bytes for ho in h_out], -1)
+                                        [ho.data_ptr() + off for ho in h_out], -1)
+                room.release()
             th.join()
             if err:
                 raise err[0]
-            next_slot[0] = s0 + N_SLOTS
+            next_slot[0] = s0 + total
 
-        e2e_step()
+        e2e_run(1)
         if world > 1:
             torch.distributed.barrier()
         ts = time.perf_counter()
-        for _ in range(e2e_steps):
-            e2e_step()
+        e2e_run(e2e_steps)
         te = shard.max_over_ranks(time.perf_counter() - ts, device="cuda")
         bytes_in = sum(h.numel() * 2 for h in h_in)
         bytes_out = sum(h.numel() * 2 for h in h_out)
@@ -598,7 +601,7 @@ def cpu_workload():
     return specs, [oracle.OracleUE.from_spec(sp) for sp in specs], xs
 
 
-def cpu_baseline(budget_s: float = 12.0, work=None):
+def cpu_baseline(budget_s: float = 12.0, work=None, single_core: bool = True):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload.
 
     The sample is the first 8 slots of every UE of the workload, repeated in
@@ -617,10 +620,28 @@ def cpu_baseline(budget_s: float = 12.0, work=None):
         if dt >= budget_s or passes >= 1000:
             break
     n_us = passes * N_UES * per_ue
-    return {"value": n_us / dt, "unit": "UE-slots/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"slots 0-{per_ue - 1} of all {N_UES} UEs, {passes} pass(es): {n_us} UE-slots, "
-                      f"{n_us * specs[0].n * N_TAPS / 1e9:.2f} G complex MAC in FP64, {dt:.1f} s",
-            "seconds": dt}
+    cores = oracle.max_threads()
+    v = n_us / dt
+    cmac = specs[0].n * N_TAPS  # complex MACs per UE-slot
+    out = {"value": v, "unit": "UE-slots/s", "cores": cores, "kind": "oracle",
+           "sample": f"slots 0-{per_ue - 1} of all {N_UES} UEs, {passes} pass(es): {n_us} UE-slots, "
+                     f"{n_us * cmac / 1e9:.2f} G complex MAC in FP64, {dt:.1f} s",
+           "seconds": dt, "gmac_per_s": v * cmac / 1e9,
+           "realtime_ues": v / 2000.0}   # a 0.5 ms-slot UE needs 2000 UE-slots/s
+    if single_core:
+        # one core: a few UEs of the same sample (the thread count is put back afterwards)
+        t1 = time.perf_counter()
+        n1 = 0
+        while True:
+            for ue, x in zip(ues[:4], xs[:4]):
+                oracle.run_ue(ue, x, want_y=False, nthreads=1)
+                n1 += per_ue
+            d1 = time.perf_counter() - t1
+            if d1 >= min(2.0, budget_s / 4):
+                break
+        oracle.run_ue(ues[0], xs[0][:, :specs[0].n], want_y=False, nthreads=cores)
+        out["single_core"] = {"value": n1 / d1, "unit": "UE-slots/s", "gmac_per_s": n1 / d1 * cmac / 1e9}
+    return out
 
 
 def main():
@@ -661,9 +682,9 @@ def main():
         work = cpu_workload()
         budget = min(4.0, 90.0 / max(args.steps, 1))  # the whole run stays within a couple of minutes
         for _ in range(max(args.warmup, 0)):
-            cpu_baseline(budget_s=min(1.0, budget), work=work)
+            cpu_baseline(budget_s=min(1.0, budget), work=work, single_core=False)
         for _ in range(max(args.steps, 1)):
-            runs.append(cpu_baseline(budget_s=budget, work=work))
+            runs.append(cpu_baseline(budget_s=budget, work=work, single_core=False))
         v = statistics.median(r["value"] for r in runs)
         ms = statistics.median(r["seconds"] for r in runs) * 1e3
         cb = dict(runs[0])
