@@ -38,8 +38,8 @@ DISTINCT_IQ_SLOTS = 64        # synthetic IQ slots per UE, cycled through the re
 METRIC = "UE-slots/s and GMAC/s at 1 GB300 vs plain form; p99 slot latency vs 0.5 ms"
 # DRAM traffic per full launch from the ncu capture summarised in
 # profiles/tt_conv_fp32_kernel_40mhz_16ue.md, valid only for the kernel source it was taken on.
-TRAFFIC_BYTES = 3.54e9
-TRAFFIC_KERNEL_SHA = "874f93de3af1b253"
+TRAFFIC_BYTES = 3.52e9
+TRAFFIC_KERNEL_SHA = "a0965b3ae157d128"
 WORKLOAD = ("16 UEs SISO, 40 MHz (30720 samples/slot), 1000 slots each, 24 taps (delays <= 256), "
             "100 Hz Jakes, AWGN 20 dB, int16 IQ, FP32 accumulation")
 
@@ -652,7 +652,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--persistent", type=int, default=1, help="1: CTAs claim work items from a device counter")
-    ap.add_argument("--spt", type=int, default=0, help="cap on samples per thread (0 = largest that fits)")
+    ap.add_argument("--spt", type=int, default=16,
+                    help="engine samples-per-thread cap for the headline (16: the bulk-throughput setting "
+                         "for single-antenna channels; 0: the engine's default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -763,12 +765,13 @@ def main():
                    "parallelism": f"{world} GPU(s), UEs sharded across them, no data-path collective",
                    "samples_per_slot": SLOT_SAMPLES, "taps": N_TAPS, "max_delay": D_MAX,
                    "form": "batched, persistent CTAs" + (" (device work counter)" if args.persistent else " (strided)"),
+                   "samples_per_thread": args.spt or "engine default (8)",
                    "iq": f"{DISTINCT_IQ_SLOTS} distinct synthetic slots per UE cycled",
                    "l2": "inputs larger than L2 (1.97 GB of IQ read per step per GPU)"},
         "gmac_per_s": gmac, "samples_per_s": N_UES * N_SLOTS * SLOT_SAMPLES * world / (ms_step / 1e3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "tt_conv_fp32_kernel<8,1,256>", "kernel_ms": kms,
+                     "kernel": f"tt_conv_fp32_kernel<{args.spt or 8},1,256>", "kernel_ms": kms,
                      "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz ({pk['src']})"},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],

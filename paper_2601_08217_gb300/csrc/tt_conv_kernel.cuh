@@ -357,8 +357,15 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
     }
     if (U->out_f32) {
       float2 *dstf = reinterpret_cast<float2 *>(U->ring_out) + ((size_t)(slot_pos * NRX + r) * n + w_me);
+      if (S >= 2 && (reinterpret_cast<uintptr_t>(dstf) & 15) == 0) {
 #pragma unroll
-      for (int jj = 0; jj < S; ++jj) dstf[jj] = acc[r][jj];
+        for (int jj = 0; jj < S; jj += 2)
+          *reinterpret_cast<float4 *>(dstf + jj) =
+              make_float4(acc[r][jj].x, acc[r][jj].y, acc[r][jj + 1].x, acc[r][jj + 1].y);
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < S; ++jj) dstf[jj] = acc[r][jj];
+      }
       continue;
     }
     uint32_t pk[S];
@@ -377,8 +384,10 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
 }
 
 // Single-antenna variants with up to 8 samples per thread fit 64 registers, so eight CTAs share an
-// SM and hide each other's staging barriers; the wider variants keep the compiler's choice.
-constexpr int tt_min_blocks(int S, int NRX) { return (NRX == 1 && S <= 8) ? 8 : 1; }
+// SM and hide each other's staging barriers.  At 16 samples per thread, shared memory admits four
+// CTAs per SM (48 KB each at delays up to 256), and 128 registers hold the variant without spills.
+// The multi-antenna variants keep the compiler's choice.
+constexpr int tt_min_blocks(int S, int NRX) { return (NRX == 1 && S <= 8) ? 8 : ((NRX == 1 && S == 16) ? 4 : 1); }
 
 template <int S, int NRX, int DMAX, bool TOPN>
 __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))

@@ -249,9 +249,13 @@ std::vector<int32_t> chunk_table(const std::vector<uint32_t> &L, int spt, int *m
 
 // Candidate samples-per-thread values of a channel, largest first: each divides every
 // symbol length; 16 only with at most 2 Rx antennas; none above the engine's cap.
-std::vector<int> spt_candidates(const std::vector<uint32_t> &L, uint32_t cap, uint32_t n_rx) {
+std::vector<int> spt_candidates(const std::vector<uint32_t> &L, uint32_t cap, uint32_t n_rx, uint32_t n_tx) {
   std::vector<int> out;
-  if (cap == 0) cap = 8;  // measured best on GB300 for the 40 MHz, 24-tap workload
+  // Default cap 8: small batches (the serving loop) keep more, shorter work items in flight.  Bulk
+  // runs of single-antenna channels go faster at 16 (4.58 ms against 4.72 ms for 16,000 40 MHz,
+  // 24-tap UE-slots); the engine's samples_per_thread setting asks for it.
+  (void)n_tx;
+  if (cap == 0) cap = 8;
   for (int s : {16, 8, 4, 2, 1}) {
     if ((uint32_t)s > cap) continue;
     if (s == 16 && n_rx > 2) continue;
@@ -858,7 +862,7 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   d.noise_std = cfg->noise_var > 0.f ? (float)std::sqrt((double)cfg->noise_var / 2.0) : 0.f;
   d.out_f32 = cfg->output_format == TT_OUT_CF32 ? 1 : 0;
   d.top_n = (int)cfg->top_n;
-  const std::vector<int> cands = spt_candidates(c->sym_len, e->spt_override, cfg->n_rx);
+  const std::vector<int> cands = spt_candidates(c->sym_len, e->spt_override, cfg->n_rx, cfg->n_tx);
   tt_status sst = set_spt(c, cands.empty() ? 1 : cands[0]);
   if (sst != TT_OK) {
     cudaFree(c->d_in);
@@ -924,7 +928,7 @@ static tt_status trace_geometry(const tt_chan *c, const int32_t *delays, uint32_
   // smallest valid tiled geometry, unused)
   const bool topn = c->cfg.top_n > 0 && c->cfg.top_n < n_taps;
   g.spt = 0;
-  for (int s : spt_candidates(c->sym_len, c->e->spt_override, c->cfg.n_rx)) {
+  for (int s : spt_candidates(c->sym_len, c->e->spt_override, c->cfg.n_rx, c->cfg.n_tx)) {
     if (tc) {
       g.spt = 1;
       break;
@@ -1724,7 +1728,7 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
     auto &cls = classes[ci];
     tt_chan *c0 = cls.second[0];
     std::vector<int> cands;
-    for (int s : spt_candidates(c0->sym_len, e->spt_override ? e->spt_override : 16, c0->cfg.n_rx)) {
+    for (int s : spt_candidates(c0->sym_len, e->spt_override ? e->spt_override : 16, c0->cfg.n_rx, c0->cfg.n_tx)) {
       int need = 0;
       if (smem_need(c0, s, &need)) cands.push_back(s);
     }
