@@ -601,6 +601,19 @@ def cpu_workload():
     return specs, [oracle.OracleUE.from_spec(sp) for sp in specs], xs
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it (best effort)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return f"{line.split(':', 1)[1].strip()}, {os.cpu_count()} logical CPUs"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return f"{platform.machine()}, {os.cpu_count()} logical CPUs"
+
+
 def cpu_baseline(budget_s: float = 12.0, work=None, single_core: bool = True):
     """The FP64 oracle as it stands on this host's cores, on a bounded sample of the workload.
 
@@ -623,7 +636,7 @@ def cpu_baseline(budget_s: float = 12.0, work=None, single_core: bool = True):
     cores = oracle.max_threads()
     v = n_us / dt
     cmac = specs[0].n * N_TAPS  # complex MACs per UE-slot
-    out = {"value": v, "unit": "UE-slots/s", "cores": cores, "kind": "oracle",
+    out = {"value": v, "unit": "UE-slots/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
            "sample": f"slots 0-{per_ue - 1} of all {N_UES} UEs, {passes} pass(es): {n_us} UE-slots, "
                      f"{n_us * cmac / 1e9:.2f} G complex MAC in FP64, {dt:.1f} s",
            "seconds": dt, "gmac_per_s": v * cmac / 1e9,
@@ -772,7 +785,11 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "kernel": f"tt_conv_fp32_kernel<{args.spt or 8},1,256>", "kernel_ms": kms,
-                     "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz ({pk['src']})"},
+                     "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz ({pk['src']})",
+                     # the complex MACs alone (8 of the 12 flop per tap-sample), and the DRAM side
+                     "mac_only_frac": achieved * 8 / FLOP_PER_TAP_SAMPLE / peak_tflops,
+                     "dram_gbs": (traffic / (kms / 1e3) / 1e9) if traffic else None,
+                     "dram_frac_of_hbm": (traffic / (kms / 1e3) / 1e9 / pk["hbm_gbs"]) if traffic else None},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "e2e": r["e2e"],
