@@ -91,10 +91,11 @@ typedef struct {
   uint64_t hbm_budget_bytes; /* admission limit for all channels; 0 = no limit */
   uint32_t form;             /* TT_FORM_* */
   uint32_t max_ues;          /* capacity of the device UE table; 0 = 1024 */
-  uint32_t samples_per_thread; /* cap on the tiled kernel's samples per thread: 0 = 8 (more, shorter work
-                                  items: the latency setting); 16 runs bulk single-antenna work faster; else 1, 2, 4, 8, 16
-                                  (16 only for channels with at most 2 Rx antennas).
-                                  Each channel uses the largest allowed value dividing all its symbol lengths. */
+  uint32_t samples_per_thread; /* cap on the tiled kernel's samples per thread: 0 = 8 (more, shorter
+                                  work items: the latency setting); else 1, 2, 4, 8 or 16 (16 only for
+                                  channels with at most 2 Rx antennas; it runs bulk single-antenna
+                                  work faster).  Each channel uses the largest allowed value dividing
+                                  all its symbol lengths. */
   uint32_t threads_per_block;  /* reserved: 0 (the tiled kernel runs 128 threads per CTA) */
   uint32_t persistent;       /* 1: persistent CTAs claim work items from a device counter; 0: by stride */
   uint32_t graphs;           /* 1: tt_engine_run captures its launches in a CUDA graph and replays it
