@@ -340,6 +340,9 @@ def run_batching(args, device, n_ues=256, steps=400, warmup=20):
     return {"ues": n_ues, "steps": steps, "ms_per_step": ms / steps, "host_ms_per_step": t_host * 1e3 / steps,
             "ue_slots_per_s": n_ues * steps / (ms / 1e3), "gmac_per_s": tap_s * steps / (ms / 1e3) / 1e9,
             "samples_per_slot_step": samples, "realtime": (ms / steps) <= 0.5,
+            # whole-step FP32 work (12 flop per tap-sample) against the ALU peak, launch gaps included
+            "alu_frac": tap_s * steps * FLOP_PER_TAP_SAMPLE / (ms / 1e3) / 1e12
+                        / (152 * 128 * 2 * peaks()["sm_max_mhz"] * 1e6 / 1e12),
             "graph_launches": st1["graph_launches"] - st0["graph_launches"],
             "graph_builds": st1["graph_builds"], "autotuned_classes": tuned}
 
