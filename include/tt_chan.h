@@ -158,6 +158,8 @@ tt_status tt_engine_destroy(tt_engine *e);
  * per channel).  Asynchronous: returns once the work is queued on the
  * engine's stream.  Channels without a trace are skipped. */
 tt_status tt_engine_run(tt_engine *e);
+/* The slot-synchronous name of tt_engine_run: one launch (or graph replay) for every pushed slot. */
+tt_status tt_engine_run_slot(tt_engine *e);
 
 /* Slot-synchronous replay: n_steps times, every started, traced channel
  * releases its launched outputs, commits its next slots_per_step slots in
@@ -297,6 +299,8 @@ tt_status tt_chan_push_slot(tt_chan *c, uint64_t slot, const int16_t *iq_in);
 tt_status tt_chan_push_slots(tt_chan *c, uint64_t first, uint32_t n, const int16_t *iq_in);
 tt_status tt_chan_push_slots_dev(tt_chan *c, uint64_t first, uint32_t n, const int16_t *d_iq_in,
                                  void *stream);
+/* One slot from a device buffer [n_tx][N][2]: tt_chan_push_slots_dev with n = 1. */
+tt_status tt_chan_push_slot_dev(tt_chan *c, uint64_t slot, const int16_t *d_iq_in, void *stream);
 
 /* Zero-copy input: *d_ptr receives the device address inside the ring where
  * slot `slot`'s input ([n_tx][N][2]) lives.  Write it (on any stream, then
@@ -320,6 +324,9 @@ tt_status tt_chan_pull_slots(tt_chan *c, uint64_t first, uint32_t n, void *iq_ou
  * positions.  The slots must be launched already (TT_ERR_AGAIN otherwise). */
 tt_status tt_chan_pull_slots_dev(tt_chan *c, uint64_t first, uint32_t n, void *d_iq_out,
                                  void *stream);
+/* The oldest not-yet-pulled slot into a device buffer [n_rx][N][2], as tt_chan_pull_slots_dev
+ * with n = 1; *slot receives its index (untouched on error). */
+tt_status tt_chan_pull_slot_dev(tt_chan *c, uint64_t *slot, void *d_iq_out, void *stream);
 
 /* Zero-copy output: device address of slot `slot`'s output ([n_rx][N][2]) in
  * the ring, valid until the slot is released.  Order reads after

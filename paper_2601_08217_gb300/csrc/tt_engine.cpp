@@ -1191,6 +1191,24 @@ tt_status tt_chan_push_slot(tt_chan *c, uint64_t slot, const int16_t *iq_in) {
   return tt_chan_push_slots(c, slot, 1, iq_in);
 }
 
+tt_status tt_chan_push_slot_dev(tt_chan *c, uint64_t slot, const int16_t *d_iq_in, void *stream) {
+  return tt_chan_push_slots_dev(c, slot, 1, d_iq_in, stream);
+}
+
+tt_status tt_chan_pull_slot_dev(tt_chan *c, uint64_t *slot, void *d_iq_out, void *stream) {
+  if (!valid_chan(c) || !slot || !d_iq_out) return fail(TT_ERR_INVALID, "tt_chan_pull_slot_dev: bad argument");
+  uint64_t s;
+  {
+    std::lock_guard<std::mutex> lk(c->e->mu);
+    s = c->pulled_end;
+  }
+  tt_status st = tt_chan_pull_slots_dev(c, s, 1, d_iq_out, stream);
+  if (st == TT_OK) *slot = s;
+  return st;
+}
+
+tt_status tt_engine_run_slot(tt_engine *e) { return tt_engine_run(e); }
+
 // Make stream `st` wait for every queued batch that may still read the input-ring positions that
 // slots [first, first + n) overwrite: they held slots [first - Q, first + n - Q), which batches
 // processing up to slot first + n - Q - 1 + hist read (the delay line).  Batches complete in order,

@@ -109,6 +109,7 @@ _SIGS = {
     "tt_engine_create": [C.POINTER(EngineConfig), C.POINTER(_VP)],
     "tt_engine_destroy": [_VP],
     "tt_engine_run": [_VP],
+    "tt_engine_run_slot": [_VP],
     "tt_engine_sync": [_VP, C.c_int64],
     "tt_engine_stream": [_VP, C.POINTER(_VP)],
     "tt_engine_get_stats": [_VP, C.POINTER(EngineStats)],
@@ -121,11 +122,13 @@ _SIGS = {
     "tt_chan_push_slot": [_VP, C.c_uint64, _VP],
     "tt_chan_push_slots": [_VP, C.c_uint64, C.c_uint32, _VP],
     "tt_chan_push_slots_dev": [_VP, C.c_uint64, C.c_uint32, _VP, _VP],
+    "tt_chan_push_slot_dev": [_VP, C.c_uint64, _VP, _VP],
     "tt_chan_slot_input": [_VP, C.c_uint64, C.POINTER(_VP)],
     "tt_chan_commit_slots": [_VP, C.c_uint64, C.c_uint32],
     "tt_chan_pull_slot": [_VP, C.POINTER(C.c_uint64), _VP, C.c_int64],
     "tt_chan_pull_slots": [_VP, C.c_uint64, C.c_uint32, _VP, C.c_int64],
     "tt_chan_pull_slots_dev": [_VP, C.c_uint64, C.c_uint32, _VP, _VP],
+    "tt_chan_pull_slot_dev": [_VP, C.POINTER(C.c_uint64), _VP, _VP],
     "tt_engine_push_slots": [_VP, C.c_uint32, _VP, _VP, _VP, _VP],
     "tt_cell_create": [_VP, _VP, _VP],
     "tt_chan_load_cir": [_VP, _VP],
@@ -219,6 +222,10 @@ def tt_engine_destroy(e: int):
 
 def tt_engine_run(e: int):
     _check(load().tt_engine_run(e))
+
+
+def tt_engine_run_slot(e: int):
+    _check(load().tt_engine_run_slot(e))
 
 
 def tt_engine_sync(e: int, timeout_us: int = -1):
@@ -330,6 +337,10 @@ def tt_chan_push_slots_dev(c: int, first: int, n: int, d_iq_in, stream=None):
     _check(load().tt_chan_push_slots_dev(c, first, n, _ptr(d_iq_in), _stream_ptr(stream)))
 
 
+def tt_chan_push_slot_dev(c: int, slot: int, d_iq_in, stream=None):
+    _check(load().tt_chan_push_slot_dev(c, slot, _ptr(d_iq_in), _stream_ptr(stream)))
+
+
 def tt_chan_slot_input(c: int, slot: int) -> int:
     p = _VP()
     _check(load().tt_chan_slot_input(c, slot, C.byref(p)))
@@ -375,6 +386,12 @@ def tt_engine_pull_slots(e: int, chans, first, n, iq_out, timeout_us: int = -1):
 
 def tt_chan_pull_slots_dev(c: int, first: int, n: int, d_iq_out, stream=None):
     _check(load().tt_chan_pull_slots_dev(c, first, n, _ptr(d_iq_out), _stream_ptr(stream)))
+
+
+def tt_chan_pull_slot_dev(c: int, d_iq_out, stream=None) -> int:
+    s = C.c_uint64()
+    _check(load().tt_chan_pull_slot_dev(c, C.byref(s), _ptr(d_iq_out), _stream_ptr(stream)))
+    return s.value
 
 
 def tt_chan_slot_output(c: int, slot: int) -> int:

@@ -339,6 +339,21 @@ def test_device_buffers_and_zero_copy_paths():
     assert np.array_equal(tc.antenna_major(got), ref)
     eng.close()
 
+    # the single-slot device calls and the slot-synchronous run: slot by slot, device buffers only
+    eng = tc.Engine()
+    ch = tc.Chan(eng, spec, ring_slots=4)
+    outs = torch.empty((3,) + xs.shape[1:2] + (spec.n, 2), dtype=torch.int16, device="cuda")
+    for k in range(3):
+        tc.tt_chan_push_slot_dev(ch.h, k, dev[k], s)
+        tc.tt_engine_run_slot(eng.h)
+        assert tc.tt_chan_pull_slot_dev(ch.h, outs[k], s) == k
+    with pytest.raises(tc.TTError) as ei:
+        tc.tt_chan_pull_slot_dev(ch.h, outs[0], s)        # nothing launched past slot 2
+    assert ei.value.status == tc.TT_ERR_AGAIN
+    torch.cuda.synchronize()
+    assert np.array_equal(tc.antenna_major(outs.cpu().numpy()), ref)
+    eng.close()
+
 
 def test_producer_and_consumer_threads_on_one_channel_equal_bulk():
     """One thread pushes and launches slot after slot while another pulls them, on the same
