@@ -88,3 +88,49 @@ def test_autotuner_keeps_results_bit_identical():
         other = run_gpu(specs[:3], xs[:3], 3, spt=s)
         for a, b in zip(base[:3], other):
             assert np.array_equal(a, b)
+
+
+def _run_per_slot(specs, xs, n_slots, per_run, cf32, ring_extra):
+    """One engine as the batching benchmark builds it (CUDA graphs, persistent CTAs, autotuned),
+    per_run slots of every UE per run, every UE's output pulled after each run."""
+    eng = tc.Engine(graphs=True, persistent=True)
+    chans = [tc.Chan(eng, sp, ring_slots=hist_slots(sp) + ring_extra, cf32=cf32) for sp in specs]
+    assert eng.autotune(reps=2) >= 0
+    outs = [[] for _ in specs]
+    for s in range(0, n_slots, per_run):
+        for ch, x in zip(chans, xs):
+            ch.push(s, tc.slots_major(x, ch.n)[s:s + per_run])
+        eng.run()
+        for i, ch in enumerate(chans):
+            outs[i].append(ch.pull(s, per_run))
+    st = eng.stats()
+    eng.close()
+    return [tc.antenna_major(np.concatenate(o, 0)) for o in outs], st
+
+
+def test_full_size_256_mixed_ues_against_oracle():
+    """All 256 UEs of the batching workload (5/20/40/100 MHz 1:2:4:1, 4-48 taps, delays <= 512, AWGN
+    20 dB) for 3 slots, one slot of every UE per run as the benchmark runs them (the graph replays from
+    the second run on).  Every UE against the oracle: complex64 NRMSE and int16 within one LSB."""
+    from tests.test_parity_gpu import assert_int16_close
+    specs = inputs.workload_batching(n_ues=256, n_slots_trace=4)
+    xs = [inputs.make_iq(3, sp, 3) for sp in specs]
+    refs = [oracle.run_ue(oracle.OracleUE.from_spec(sp), x) for sp, x in zip(specs, xs)]
+    ys, st = _run_per_slot(specs, xs, 3, 1, True, 4)
+    assert st["graph_launches"] >= 2
+    for y, (y_ref, _) in zip(ys, refs):
+        assert nrmse(y, y_ref) <= 1e-5
+    qs, _ = _run_per_slot(specs, xs, 3, 1, False, 4)
+    for q, (y_ref, q_ref) in zip(qs, refs):
+        assert_int16_close(q, y_ref, q_ref)
+
+
+def test_eight_mixed_ues_over_200_slots_against_oracle():
+    """8 UEs of the batching workload over 200 slots (looping 20-slot traces replayed ten times),
+    20 slots per run: the trace cursors, delay lines and graph replays stay exact over a long run."""
+    specs = inputs.workload_batching(n_ues=8, n_slots_trace=20)
+    xs = [inputs.make_iq(3, sp, 200) for sp in specs]
+    ys, _ = _run_per_slot(specs, xs, 200, 20, True, 21)
+    for sp, x, y in zip(specs, xs, ys):
+        y_ref, _ = oracle.run_ue(oracle.OracleUE.from_spec(sp), x)
+        assert nrmse(y, y_ref) <= 1e-5

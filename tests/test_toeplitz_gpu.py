@@ -100,3 +100,28 @@ def test_tensor_core_and_fp32_channels_in_one_engine():
     alone_fp = run_gpu(specs[2:], xs[2:], 2, cf32=True)
     for a, b in zip(mixed, alone_tc + alone_fp):
         assert np.array_equal(a, b)
+
+
+_FULL = {}
+
+
+def _full_size_refs():
+    """The whole precision workload (64 UEs, 4x4, 96 taps, 100 MHz), one slot, AWGN off; oracle once."""
+    if not _FULL:
+        specs = inputs.workload_precision(n_ues=64, n_slots_trace=2)
+        for sp in specs:
+            sp.noise_var = 0.0
+        xs = [inputs.make_iq(4, sp, 1) for sp in specs]
+        _FULL["specs"], _FULL["xs"] = specs, xs
+        _FULL["refs"] = [oracle.run_ue(oracle.OracleUE.from_spec(sp), x)[0] for sp, x in zip(specs, xs)]
+    return _FULL["specs"], _FULL["xs"], _FULL["refs"]
+
+
+@pytest.mark.parametrize("prec,bound_db", [(tc.TT_BF16_TC, -40.0), (tc.TT_FP16_TC, -55.0)])
+def test_full_size_64_ues_evm_against_oracle(prec, bound_db):
+    """Every UE of the precision workload, one slot in one launch: the EVM bound holds for each."""
+    specs, xs, refs = _full_size_refs()
+    ys = run_gpu(specs, xs, 1, cf32=True, precision=prec)
+    worst = max(evm_db(y, y_ref) for y, y_ref in zip(ys, refs))
+    print(f"precision {prec}: worst EVM over 64 UEs {worst:.1f} dB")
+    assert worst < bound_db
