@@ -444,3 +444,60 @@ def test_many_channel_push_and_pull_equal_per_channel_calls():
             assert np.array_equal(tc.antenna_major(outs[i]), bulk[i])
     finally:
         eng.close()
+
+
+def test_saturation_is_bit_exact():
+    """Full-scale int16 input through integer taps with gain above one: most outputs clamp to
+    -32768 or 32767.  Every product and sum is exact in FP32, so the packed output is bit-exact."""
+    rng = np.random.default_rng(31)
+    L = inputs.nr_symbol_lengths(256)
+    n = sum(L)
+    d = np.array([0, 1, 5], dtype=np.int32)
+    h = np.array([3 + 2j, -2 + 1j, 1 - 3j]).reshape(1, 1, 1, 3)
+    spec = Spec(L, 1, 1, d, np.repeat(h, 14 * 2 + 1, axis=0))
+    x = rng.integers(-32768, 32768, size=(1, 2 * n, 2)).astype(np.int16)
+    _, q_ref = _oracle(spec, x)
+    assert np.mean((q_ref == 32767) | (q_ref == -32768)) > 0.5
+    for kw in VARIANTS:
+        q = run_gpu([spec], [x], 2, cf32=False, **kw)[0]
+        assert np.array_equal(q, q_ref), kw
+
+
+def test_single_tap_and_noise_only_cases():
+    """K = 1 at d = 0 (y = h(m) x(m), the paper's per-symbol scaling case), and zero input with AWGN
+    on (the output is the noise alone) for a 2x2 channel."""
+    rng = np.random.default_rng(32)
+    L = inputs.nr_symbol_lengths(1024)
+    n = sum(L)
+    spec = Spec(L, 1, 1, [0], _taps(rng, 14 * 2 + 1, 1, 1, 1))
+    x = rng.integers(-3000, 3000, size=(1, 2 * n, 2)).astype(np.int16)
+    y_ref, q_ref = _oracle(spec, x)
+    assert nrmse(run_gpu([spec], [x], 2, cf32=True)[0], y_ref) <= NRMSE_MAX
+    assert_int16_close(run_gpu([spec], [x], 2)[0], y_ref, q_ref)
+    noisy = Spec(L, 2, 2, [0, 4, 9], _taps(rng, 14 * 2 + 1, 2, 2, 3), noise_var=2.0 ** 21 / 100, ue_id=9)
+    z = np.zeros((2, 2 * n, 2), dtype=np.int16)
+    y_ref, q_ref = _oracle(noisy, z)
+    assert np.std(y_ref) > 50
+    assert nrmse(run_gpu([noisy], [z], 2, cf32=True)[0], y_ref) <= NRMSE_MAX
+    assert_int16_close(run_gpu([noisy], [z], 2)[0], y_ref, q_ref)
+
+
+def test_maximum_delay_and_maximum_slot_size():
+    """The largest delay class (d = 1024) at 5 MHz, where the delay line spans a quarter slot, and the
+    largest slot (2^24 samples in 32 symbols of 2^19) with a short channel."""
+    rng = np.random.default_rng(33)
+    L = inputs.nr_symbol_lengths(256)
+    spec = Spec(L, 1, 1, [0, 511, 1000, 1024], _taps(rng, 14 * 3 + 1, 1, 1, 4), noise_var=100.0)
+    x = rng.integers(-3000, 3000, size=(1, 3 * spec.n, 2)).astype(np.int16)
+    y_ref, q_ref = _oracle(spec, x)
+    for kw in (dict(form="batched", persistent=True), dict(form="plain")):
+        assert nrmse(run_gpu([spec], [x], 3, cf32=True, **kw)[0], y_ref) <= NRMSE_MAX
+        assert_int16_close(run_gpu([spec], [x], 3, **kw)[0], y_ref, q_ref)
+    big = Spec([1 << 19] * 32, 1, 1, [0, 7], _taps(rng, 32 * 2 + 1, 1, 1, 2))
+    assert big.n == 1 << 24
+    xb = rng.integers(-3000, 3000, size=(1, 2 * big.n, 2)).astype(np.int16)
+    y_ref, q_ref = _oracle(big, xb)
+    yb = run_gpu([big], [xb], 2, cf32=True, persistent=True)[0]
+    assert nrmse(yb, y_ref) <= NRMSE_MAX
+    del yb
+    assert_int16_close(run_gpu([big], [xb], 2, persistent=True)[0], y_ref, q_ref)
