@@ -125,3 +125,22 @@ def test_full_size_64_ues_evm_against_oracle(prec, bound_db):
     worst = max(evm_db(y, y_ref) for y, y_ref in zip(ys, refs))
     print(f"precision {prec}: worst EVM over 64 UEs {worst:.1f} dB")
     assert worst < bound_db
+
+
+@pytest.mark.parametrize("prec", [tc.TT_BF16_TC, tc.TT_FP16_TC])
+def test_fused_awgn_equals_the_fp32_path(prec):
+    """Exact operands, static taps and AWGN on (4x4, 96 taps, 100 MHz: three groups per symbol): the
+    tensor-core sums are exact and its epilogue adds the same Philox noise to them, so the output
+    equals the FP32 path's bit for bit, and the oracle's within the FP32 tolerance."""
+    rng = np.random.default_rng(77)
+    L = inputs.nr_symbol_lengths(4096)
+    K = 96
+    h = (rng.integers(-8, 9, size=(1, 4, 4, K)) + 1j * rng.integers(-8, 9, size=(1, 4, 4, K))) / 8
+    spec = Spec(L, 4, 4, np.arange(K), np.repeat(h, 3, axis=0), noise_var=inputs.noise_var_for_snr(20.0),
+                ue_id=5)
+    x = rng.integers(-127, 128, size=(4, 2 * spec.n, 2)).astype(np.int16)
+    y_fp = run_gpu([spec], [x], 2, cf32=True)[0]
+    y_tc = run_gpu([spec], [x], 2, cf32=True, precision=prec)[0]
+    assert np.array_equal(y_tc, y_fp)
+    y_ref, _ = oracle.run_ue(oracle.OracleUE.from_spec(spec), x)
+    assert np.std(y_ref) > 50 and nrmse(y_tc, y_ref) <= 1e-5
