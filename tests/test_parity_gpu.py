@@ -469,11 +469,19 @@ def test_single_tap_and_noise_only_cases():
     rng = np.random.default_rng(32)
     L = inputs.nr_symbol_lengths(1024)
     n = sum(L)
-    spec = Spec(L, 1, 1, [0], _taps(rng, 14 * 2 + 1, 1, 1, 1))
+    a = np.arange(14 * 2 + 1)
+    g = 10.0 ** (-6.0 * (1 - np.cos(2 * np.pi * a / 9.0)) / 20.0)     # periodic SNR-degradation gain
+    spec = Spec(L, 1, 1, [0], (g * np.exp(0.3j * a)).reshape(-1, 1, 1, 1))
     x = rng.integers(-3000, 3000, size=(1, 2 * n, 2)).astype(np.int16)
     y_ref, q_ref = _oracle(spec, x)
-    assert nrmse(run_gpu([spec], [x], 2, cf32=True)[0], y_ref) <= NRMSE_MAX
+    y = run_gpu([spec], [x], 2, cf32=True)[0]
+    assert nrmse(y, y_ref) <= NRMSE_MAX
     assert_int16_close(run_gpu([spec], [x], 2)[0], y_ref, q_ref)
+    # the output power follows the trace's gain: |y|^2 / |x|^2 = |h(m)|^2, between 1 and -12 dB
+    xc = x[0, :, 0].astype(np.float64) + 1j * x[0, :, 1]
+    nz = np.abs(xc) > 0
+    gain_db = 10 * np.log10(np.abs(y[0][nz]) ** 2 / np.abs(xc[nz]) ** 2)
+    assert gain_db.max() < 1e-3 and gain_db.min() > -12.0 - 1e-3 and gain_db.min() < -10.0
     noisy = Spec(L, 2, 2, [0, 4, 9], _taps(rng, 14 * 2 + 1, 2, 2, 3), noise_var=2.0 ** 21 / 100, ue_id=9)
     z = np.zeros((2, 2 * n, 2), dtype=np.int16)
     y_ref, q_ref = _oracle(noisy, z)
