@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(kTPB, 2)
   __shared__ __align__(8) unsigned long long s_empty[kSteps];  // MMA completion -> builders: step's slots free
   __shared__ __align__(8) unsigned long long s_acc;            // MMA completion of a group -> epilogue
   __shared__ __align__(8) unsigned long long s_tfree;          // epilogue done with the accumulators -> MMA warp
+  __shared__ __align__(8) unsigned long long s_drain;          // the MMA thread's last commit -> tensor memory free
   __shared__ uint32_t s_tmem;
   __shared__ TCItem s_it;
   __shared__ int s_abort;
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(kTPB, 2)
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_acc)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&s_tfree)), "n"(kBuildWarps));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_drain)));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     s_abort = 0;
@@ -482,7 +484,16 @@ __global__ void __launch_bounds__(kTPB, 2)
       }
     }
   }
-  // every MMA was waited for by the epilogue of its group (or a wait expired: nothing more to wait for)
+  // Before tensor memory is freed, the MMA thread commits once more: that commit arrives when every MMA
+  // it issued has completed.  Normally the epilogues have waited for all of them already; after an
+  // expired wait some may still run, so this wait is bounded but does not stop at the abort flag.
+  if (warp == kBuildWarps && lane == 0) {
+    umma_commit(smem_u32(&s_drain));
+    long long spins = 0;
+    while (!mbar_try_wait(smem_u32(&s_drain), 0) && ++spins < kSpinLimit) {
+    }
+    if (spins >= kSpinLimit) atomicExch(status, 1);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
