@@ -29,7 +29,7 @@ TOPN_CASES = [("siso_odd_lengths", 2), ("delay_beyond_slot", 1), ("mimo22_noise"
               ("mimo_4tx_3rx_tracetime", 5), ("nr5mhz_loop_noise", 6), ("nr20mhz_mimo_1ms_trace", 4)]
 
 
-@pytest.mark.parametrize("spt", [0, 1, 2])
+@pytest.mark.parametrize("spt", [0, 1, 2, 16])
 @pytest.mark.parametrize("case,top_n", TOPN_CASES)
 def test_top_n_matches_oracle(case, top_n, spt):
     spec, x, ns = _case(case)
@@ -92,3 +92,17 @@ def test_top_n_is_refused_outside_the_fp32_batched_form():
             assert ex.value.status == tc.TT_ERR_INVALID
         finally:
             eng.close()
+
+
+@pytest.mark.parametrize("spt", [8, 16])
+def test_top_n_on_the_40mhz_siso_workload(spt):
+    """Top 8 of 24 taps on two UEs of the 40 MHz benchmark workload, at 8 and 16 samples per thread
+    (the single-antenna variants with bounded registers), against the oracle's top-n mode."""
+    specs = inputs.workload_plain_16ue(3, n_ues=2)
+    for sp in specs:
+        x = inputs.make_iq(2, sp, 3)
+        y_ref, q_ref = _oracle_topn(sp, x, 8)
+        y = run_gpu([sp], [x], 3, cf32=True, spt=spt, persistent=True, top_n=8)[0]
+        assert nrmse(y, y_ref) <= NRMSE_MAX
+        q = run_gpu([sp], [x], 3, spt=spt, persistent=True, top_n=8)[0]
+        assert_int16_close(q, y_ref, q_ref)
