@@ -1900,7 +1900,11 @@ tt_status tt_engine_pull_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *c
 
 tt_status tt_chan_pull_slot(tt_chan *c, uint64_t *slot, void *iq_out, int64_t timeout_us) {
   if (!valid_chan(c) || !slot || !iq_out) return fail(TT_ERR_INVALID, "tt_chan_pull_slot: bad argument");
-  const uint64_t s = c->pulled_end;
+  uint64_t s;
+  {
+    std::lock_guard<std::mutex> lk(c->e->mu);
+    s = c->pulled_end;
+  }
   tt_status st = pull_common(c, s, 1, iq_out, timeout_us);
   if (st == TT_OK) *slot = s;
   return st;
