@@ -555,19 +555,24 @@ def run_cell(args, device, n_slots=200, warmup=3, steps=5):
 
 def run_synth(args, device, n_slots=200, warmup=3, steps=5):
     """Tap processes synthesised on the device (sum of 16 sinusoids per tap, Zheng-Xiao
-    parameters, 100 Hz) for the 16 headline UEs, beside the same UEs replaying stored traces:
-    the time per step of each and the HBM each channel's taps take."""
+    parameters, 100 Hz) for the 16 headline UEs, beside the same UEs replaying stored traces, one
+    entry per OFDM symbol or one per 1 ms (anchors interpolated in FP64 trace time): the time per
+    step of each and the HBM each channel's taps take."""
     import torch
     from paper_2601_08217_gb300 import inputs
     from paper_2601_08217_gb300 import tt_chan as tc
     specs, iq = make_workload(0)
     n = specs[0].n
     res = {}
-    for mode in ("trace", "synthesised"):
+    for mode in ("trace", "trace_1ms", "synthesised"):
         eng = tc.Engine(device=device, persistent=True, graphs=True)
         chans = []
         for u, sp in enumerate(specs):
             ch = tc.Chan(eng, sp, ring_slots=n_slots + 2, load=(mode == "trace"))
+            if mode == "trace_1ms":   # the same UE's delays, its taps every 61440 samples (1 ms)
+                sp1 = inputs.make_ue(2, sp.ue_id, 2048, N_TAPS, D_MAX, 100.0, n_slots, snr_db=20.0, loop=True,
+                                     delays=sp.delays, step_samples=61440.0)
+                ch.load_trace(sp1.taps, sp1.delays, sp1.step_samples, True)
             if mode == "synthesised":
                 rng = np.random.default_rng([0x77170009, u])
                 amp, freq, phase = inputs.sos_params(rng, 100.0, inputs.pdp_span_decay(sp.delays, 20.0), 1, 1)
@@ -594,6 +599,7 @@ def run_synth(args, device, n_slots=200, warmup=3, steps=5):
     res["workload"] = (f"16 UEs x {n_slots} slots, 40 MHz, 24 taps; stored trace of "
                        f"{specs[0].taps.shape[0]} anchors vs 16-sinusoid synthesis per tap")
     res["synthesis_overhead"] = res["synthesised"]["ms_per_step"] / res["trace"]["ms_per_step"] - 1.0
+    res["trace_1ms_overhead"] = res["trace_1ms"]["ms_per_step"] / res["trace"]["ms_per_step"] - 1.0
     return res
 
 

@@ -249,6 +249,54 @@ cudaError_t tt_launch_sos(const TTSosJob *jobs, int n_jobs, unsigned long long n
   return cudaGetLastError();
 }
 
+// ---- timed traces: per-symbol anchors in FP64 trace time, one warp per (job, anchor) ----
+// Lane 0 places the anchor in trace time (FP64: p = b / step, i0 = floor(p), f = p - i0, the same
+// steps as the convolution kernels' tt_anchor) and broadcasts it; the lanes interpolate the link
+// taps, H = h[i0] + f (h[i0 + 1] - h[i0]) in FP64, coalesced along the taps.
+__global__ void __launch_bounds__(128) tt_retime_kernel(const TTRetimeJob *__restrict__ jobs, int n_jobs,
+                                                        unsigned long long n_warps) {
+  const unsigned long long gw = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= n_warps) return;  // whole warps leave together
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].thread_begin <= gw) lo = mid; else hi = mid - 1;
+  }
+  const TTRetimeJob J = jobs[lo];
+  const TTUEDesc *U = J.ue;
+  const uint64_t nsym = (uint64_t)U->nsym;
+  const uint64_t a = J.slot_first * nsym + (gw - J.thread_begin);   // the job's anchors, the tail last
+  unsigned long long i0 = 0;
+  double f = 0.0;
+  if (lane == 0) {
+    const uint64_t b = (a / nsym) * (uint64_t)U->n + (uint64_t)U->sym_start[a % nsym];
+    const double p = (double)b / J.step;
+    const double fl = floor(p);
+    f = p - fl;
+    i0 = (unsigned long long)fl;
+  }
+  i0 = __shfl_sync(0xFFFFFFFFu, i0, 0);
+  f = __shfl_sync(0xFFFFFFFFu, f, 0);
+  const uint64_t T = J.T;
+  const uint64_t k0 = J.loop ? (i0 % T) : (i0 < T ? i0 : T - 1);
+  const uint64_t k1 = J.loop ? ((i0 + 1) % T) : (i0 + 1 < T ? i0 + 1 : T - 1);
+  const float2 *h0p = J.src + k0 * (uint64_t)J.per, *h1p = J.src + k1 * (uint64_t)J.per;
+  float2 *dst = J.ring + (size_t)(a % (uint64_t)J.ring_len) * J.per;
+  for (int e = lane; e < J.per; e += 32) {
+    const float2 h0 = __ldg(h0p + e), h1 = __ldg(h1p + e);
+    dst[e] = make_float2((float)((double)h0.x + f * ((double)h1.x - (double)h0.x)),
+                         (float)((double)h0.y + f * ((double)h1.y - (double)h0.y)));
+  }
+}
+
+cudaError_t tt_launch_retime(const TTRetimeJob *jobs, int n_jobs, unsigned long long n_warps, cudaStream_t st) {
+  if (n_warps == 0 || n_jobs == 0) return cudaSuccess;
+  const int tpb = 128;
+  tt_retime_kernel<<<(unsigned)((n_warps * 32 + tpb - 1) / tpb), tpb, 0, st>>>(jobs, n_jobs, n_warps);
+  return cudaGetLastError();
+}
+
 // ---- sparse convolution: per (anchor, link) tap selection, one warp each ----
 __global__ void __launch_bounds__(256) tt_topn_select_kernel(const TTTopnJob *__restrict__ jobs, int n_jobs,
                                                              unsigned long long n_warps) {

@@ -108,6 +108,9 @@ struct tt_engine {
   std::vector<TTSosJob> sos_jobs;           // synthesis work list of the current run (host copy)
   TTSosJob *d_sos = nullptr;                // and its device copy
   size_t sos_cap = 0;
+  std::vector<TTRetimeJob> retime_jobs;     // timed-trace anchor work list of the current run
+  TTRetimeJob *d_retime = nullptr;
+  size_t retime_cap = 0;
   std::vector<TTTopnJob> topn_jobs;         // tap-selection work list of the current run
   TTTopnJob *d_topn = nullptr;
   size_t topn_cap = 0;
@@ -146,6 +149,13 @@ struct tt_chan {
   double *d_freq = nullptr, *d_phase = nullptr;
   int synth_m = 0;
   double synth_fs = 0.0;
+  // timed trace (entries every src_step samples): d_taps is a ring of anchors refilled before each
+  // run by FP64 trace-time interpolation from the stored trace d_src
+  bool retime = false;
+  float2 *d_src = nullptr;
+  uint64_t src_T = 0;
+  double src_step = 0.0;
+  int src_loop = 0;
 };
 
 struct tt_cell {
@@ -729,6 +739,7 @@ tt_status tt_engine_destroy(tt_engine *e) {
       cudaFree(c->d_amp);
       cudaFree(c->d_freq);
       cudaFree(c->d_phase);
+      cudaFree(c->d_src);
       cudaFree(c->d_sparse);
       cudaFree(c->d_sparse_dly);
       c->e = nullptr;
@@ -751,6 +762,7 @@ tt_status tt_engine_destroy(tt_engine *e) {
   cudaFree(e->d_cursors);
   cudaFree(e->d_tcsegs);
   cudaFree(e->d_sos);
+  cudaFree(e->d_retime);
   cudaFree(e->d_topn);
   cudaFree(e->d_status);
   if (e->stream) cudaStreamDestroy(e->stream);
@@ -893,6 +905,7 @@ tt_status tt_chan_destroy(tt_chan *c) {
   cudaFree(c->d_amp);
   cudaFree(c->d_freq);
   cudaFree(c->d_phase);
+  cudaFree(c->d_src);
   cudaFree(c->d_sparse);
   cudaFree(c->d_sparse_dly);
   e->in_use -= c->ring_bytes + c->trace_bytes + c->sparse_bytes;
@@ -955,6 +968,43 @@ static tt_status trace_geometry(const tt_chan *c, const int32_t *delays, uint32_
 static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64_t bytes, uint32_t n_anchors,
                         uint32_t n_taps, double step_samples, int loop, const TraceGeo &g) {
   tt_engine *e = c->e;
+  // A timed trace stays as it is; the kernels read a ring of per-symbol anchors, sized like the
+  // synthesis ring, that a pre-pass refills from it before each run.
+  float2 *ring = nullptr;
+  uint32_t ring_len = 0;
+  if (step_samples > 0.0) {
+    ring_len = (uint32_t)((c->Q + 1) * (int)c->sym_len.size() + 1);
+    const uint64_t rb = (uint64_t)ring_len * c->cfg.n_rx * c->cfg.n_tx * n_taps * sizeof(float2);
+    cudaError_t err = cudaSuccess;
+    if (e->budget && e->in_use - c->trace_bytes + bytes + rb > e->budget) {
+      err = cudaErrorMemoryAllocation;
+    } else {
+      err = cudaMalloc(&ring, rb);
+      if (err == cudaSuccess) err = cudaMemsetAsync(ring, 0, rb, e->stream);
+    }
+    if (err != cudaSuccess) {
+      cudaFree(ring);
+      cudaFree(taps);
+      cudaFree(delays);
+      return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA,
+                  "admission refused or failed: anchor ring of %llu B for the timed trace", (unsigned long long)rb);
+    }
+    bytes += rb;
+  }
+  cudaFree(c->d_src);
+  c->d_src = nullptr;
+  c->retime = false;
+  if (ring) {
+    c->retime = true;
+    c->d_src = taps;
+    c->src_T = n_anchors;
+    c->src_step = step_samples;
+    c->src_loop = loop ? 1 : 0;
+    taps = ring;
+    n_anchors = ring_len;
+    step_samples = 0.0;
+    loop = 1;
+  }
   cudaFree(c->d_taps);
   cudaFree(c->d_delays);
   cudaFree(c->d_amp);
@@ -1347,6 +1397,44 @@ tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n) {
 // slots [launched_end, pushed_end) and the first anchor of slot pushed_end), all channels in one
 // launch (engine lock held).  Anchors rewritten here get the same value as before, and the stream
 // orders the rewrite after every kernel that read them.
+static tt_status launch_retime(tt_engine *e, const std::vector<tt_chan *> &chans) {
+  std::vector<TTRetimeJob> &jobs = e->retime_jobs;
+  jobs.clear();
+  unsigned long long threads = 0;
+  for (tt_chan *c : chans) {
+    if (!c->retime || c->pushed_end <= c->launched_end) continue;
+    TTRetimeJob J{};
+    J.ue = e->d_ues + c->index;
+    J.ring = c->d_taps;
+    J.src = c->d_src;
+    J.step = c->src_step;
+    J.T = c->src_T;
+    J.loop = c->src_loop;
+    J.slot_first = c->launched_end;
+    J.thread_begin = threads;
+    J.per = (int)(c->cfg.n_rx * c->cfg.n_tx * (uint32_t)c->desc.n_taps);
+    J.ring_len = c->desc.n_anchors;
+    J.n_slots = (int)(c->pushed_end - c->launched_end);
+    threads += (unsigned long long)J.n_slots * c->sym_len.size() + 1;   // one warp per anchor
+    jobs.push_back(J);
+  }
+  if (jobs.empty()) return TT_OK;
+  if (jobs.size() > e->retime_cap) {
+    TT_CK(cudaStreamSynchronize(e->stream));  // the old list may still be read
+    cudaFree(e->d_retime);
+    e->d_retime = nullptr;
+    e->retime_cap = 0;
+    TT_CK(cudaMalloc(&e->d_retime, sizeof(TTRetimeJob) * jobs.size() * 2));
+    e->retime_cap = jobs.size() * 2;
+  }
+  TT_CK(cudaMemcpyAsync(e->d_retime, jobs.data(), sizeof(TTRetimeJob) * jobs.size(), cudaMemcpyHostToDevice,
+                        e->stream));
+  cudaError_t err = tt_launch_retime(e->d_retime, (int)jobs.size(), threads, e->stream);
+  if (err != cudaSuccess) return fail(TT_ERR_CUDA, "timed-trace anchor launch: %s", cudaGetErrorString(err));
+  ++e->launches;
+  return TT_OK;
+}
+
 static tt_status launch_synth(tt_engine *e, const std::vector<tt_chan *> &chans) {
   std::vector<TTSosJob> &jobs = e->sos_jobs;
   jobs.clear();
@@ -1602,7 +1690,8 @@ tt_status tt_engine_run(tt_engine *e) {
   {
     std::vector<tt_chan *> all(ready);
     all.insert(all.end(), tc_ready.begin(), tc_ready.end());
-    tt_status sst = launch_synth(e, all);
+    tt_status sst = launch_retime(e, all);
+    if (sst == TT_OK) sst = launch_synth(e, all);
     if (sst == TT_OK) sst = launch_topn(e, ready);
     if (sst != TT_OK) return sst;
   }

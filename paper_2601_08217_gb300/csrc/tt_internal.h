@@ -140,6 +140,21 @@ struct TTSosJob {
 };
 // One launch for every job: thread thread_begin + (slot - slot_first) * per + e of job j.
 cudaError_t tt_launch_sos(const TTSosJob *jobs, int n_jobs, unsigned long long n_threads, cudaStream_t st);
+// Timed traces (entries every `step` samples, e.g. 1 ms): before each run, the anchors of the slots
+// it launches are interpolated in FP64 trace time from the stored trace into the channel's anchor
+// ring, so the convolution kernels read per-symbol anchors.  One warp per (job, anchor): anchors
+// 0 .. n_slots * nsym of the job, anchor k being a = slot_first * nsym + k; thread_begin counts warps.
+struct TTRetimeJob {
+  const TTUEDesc *ue;         // the channel's descriptor (device): N, symbols, symbol starts
+  float2 *ring;               // [ring_len][per] anchors, anchor a at a % ring_len
+  const float2 *src;          // [T][per] the stored trace
+  double step;                // samples per stored entry
+  unsigned long long T;       // stored entries
+  unsigned long long slot_first;
+  unsigned long long thread_begin;
+  int loop, per, ring_len, n_slots;
+};
+cudaError_t tt_launch_retime(const TTRetimeJob *jobs, int n_jobs, unsigned long long n_warps, cudaStream_t st);
 // Sparse convolution: for anchors [a_first, a_first + n_anchors) of one channel, the top_n taps of
 // each link by binary32 power at the anchor (ties: lower index), compacted in tap order into the
 // channel's sparse ring with (H, H[a+1] - H) and their delays; one warp per (anchor, link).
