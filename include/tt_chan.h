@@ -235,6 +235,9 @@ tt_status tt_chan_destroy(tt_chan *c);
 
 /* Copy a trace to the device (replacing any previous one).  Counted against
  * the budget: TT_ERR_NO_MEMORY if it does not fit, TT_ERR_TRACE if malformed.
+ * A trace with step_samples > 0 also takes a ring of (ring_slots + 1) x
+ * symbols_per_slot + 1 per-symbol anchors, which each tt_engine_run refills
+ * (FP64 trace-time interpolation) for the slots it launches; it is counted too.
  * Not allowed while the channel has launched work in flight (TT_ERR_STATE). */
 tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *trace);
 
