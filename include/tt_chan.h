@@ -120,7 +120,9 @@ typedef struct {
   uint32_t top_n;             /* sparse convolution (Sec. III-C): 0 = every tap; n > 0 = for each OFDM
                                  symbol and (r, t) link only the n taps of largest |H[a]|^2 at the
                                  symbol's anchor a (ties: lower tap index), each interpolated toward
-                                 its H[a+1].  The powers are binary32, p = fma(re, re, im * im).
+                                 its H[a+1].  The kernel ranks binary32 powers p = fma(re, re, im * im),
+                                 so where two powers lie within binary32 rounding of each other at the
+                                 n-th place, either tap may be the one kept.
                                  TT_FP32 batched form only (TT_ERR_INVALID otherwise) */
 } tt_chan_config;
 

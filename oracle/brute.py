@@ -53,34 +53,16 @@ def anchor_exact(taps: np.ndarray, a_start: int, a: int, step_samples, loop: boo
     return out
 
 
-def round_f32(v: Fraction) -> Fraction:
-    """v rounded to the nearest binary32 value (ties to even), as an exact Fraction."""
-    if v == 0:
-        return Fraction(0)
-    sign = -1 if v < 0 else 1
-    a = abs(v)
-    e = a.numerator.bit_length() - a.denominator.bit_length()   # 2^(e-1) <= a < 2^(e+1)
-    if Fraction(2) ** e > a:
-        e -= 1                                                   # now 2^e <= a < 2^(e+1)
-    e = max(e, -126)                                             # subnormals share the last exponent
-    scale = Fraction(2) ** (e - 23)                              # spacing of binary32 values at a
-    return sign * round(a / scale) * scale                      # round(): ties to even
-
-
 def keep_top_n(H, top_n: int):
     """Sparse convolution (Sec. III-C): per link, the top_n taps of |H[a]|^2, ties to the lower
-    index.  The powers are taken as the kernel takes them: components rounded to binary32 and
-    p = fma(re, re, im * im) in binary32 (each operation rounded once)."""
+    index, the powers compared exactly (Fractions)."""
     n_rx, n_tx, K = len(H), len(H[0]), len(H[0][0])
     keep = [[[True] * K for _ in range(n_tx)] for _ in range(n_rx)]
     if not top_n or top_n >= K:
         return keep
     for r in range(n_rx):
         for t in range(n_tx):
-            p = []
-            for k in range(K):
-                re, im = round_f32(H[r][t][k][0]), round_f32(H[r][t][k][1])
-                p.append(round_f32(re * re + round_f32(im * im)))
+            p = [H[r][t][k][0] ** 2 + H[r][t][k][1] ** 2 for k in range(K)]
             for k in range(K):
                 beat = sum(1 for j in range(K) if p[j] > p[k] or (p[j] == p[k] and j < k))
                 keep[r][t][k] = beat < top_n

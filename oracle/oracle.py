@@ -40,7 +40,7 @@ class _UE(C.Structure):
         ("delays", C.POINTER(C.c_int32)), ("taps", C.POINTER(C.c_float)),
         ("n_anchors", C.c_uint32), ("step_samples", C.c_double), ("loop", C.c_int32),
         ("seed", C.c_uint64), ("ue_id", C.c_uint32), ("noise_var", C.c_double),
-        ("top_n", C.c_uint32),
+        ("top_n", C.c_uint32), ("keep", C.c_void_p),
     ]
 
 
@@ -96,9 +96,11 @@ class OracleUE:
 
 
 def run_ue(ue: OracleUE, x: np.ndarray, s_first: int = 0, nthreads: int = 0,
-           want_y: bool = True, want_q: bool = True):
+           want_y: bool = True, want_q: bool = True, keep: Optional[np.ndarray] = None):
     """Run slots [s_first, s_first + n_slots) of one UE; x is int16 [n_tx][n_slots*N][2].
 
+    keep: None (the UE's top-n rule), or an explicit tap selection bool [n_slots*nsym + 1][n_rx][n_tx][K]
+    that replaces it, anchor s_first*nsym + i at position i.
     Returns (y, q): y complex128 [n_rx][n_slots*N] (or None), q int16 [n_rx][n_slots*N][2] (or None).
     """
     lib = _load()
@@ -109,7 +111,15 @@ def run_ue(ue: OracleUE, x: np.ndarray, s_first: int = 0, nthreads: int = 0,
     n_slots = x.shape[1] // n
     y = np.empty((ue.s.n_rx, x.shape[1], 2), dtype=np.float64) if want_y else None
     q = np.empty((ue.s.n_rx, x.shape[1], 2), dtype=np.int16) if want_q else None
-    rc = lib.tto_run(C.byref(ue.s), s_first, n_slots, x.ctypes.data,
+    km = None
+    if keep is not None:
+        km = np.ascontiguousarray(keep, dtype=np.uint8)
+        want = (n_slots * ue.s.nsym + 1, ue.s.n_rx, ue.s.n_tx, ue.s.n_taps)
+        if km.shape != want:
+            raise ValueError(f"keep must be {want}")
+    s = _UE.from_buffer_copy(ue.s)
+    s.keep = None if km is None else km.ctypes.data
+    rc = lib.tto_run(C.byref(s), s_first, n_slots, x.ctypes.data,
                      None if y is None else y.ctypes.data, None if q is None else q.ctypes.data,
                      int(nthreads))
     if rc != 0:

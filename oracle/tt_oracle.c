@@ -106,6 +106,9 @@ typedef struct {
   uint32_t ue_id;
   double noise_var;         /* sigma^2 per complex sample, 0 = off */
   uint32_t top_n;           /* 0 = every tap; else the top-n taps of each anchor (Sec. III-C) */
+  const unsigned char *keep; /* NULL, or an explicit tap selection that replaces the top-n rule:
+                                [n_slots*nsym + 1][n_rx][n_tx][n_taps], nonzero = tap used, indexed
+                                by the anchor's position in the run (anchor s_first*nsym + i at i) */
 } tto_ue;
 
 static uint64_t trace_index(const tto_ue *u, uint64_t i) {
@@ -136,16 +139,11 @@ void tto_anchor(const tto_ue *u, uint64_t a, double *out) {
     out[e] = (double)h0[e] + f * ((double)h1[e] - (double)h0[e]);
 }
 
-/* Sparse convolution (Sec. III-C): keep[(r*n_tx+t)*n_taps+k] = 1 for the top_n taps of |H[a]|^2
- * per link (ties: lower k).  The selection is a decision taken from floating-point values, so it
- * is taken in the precision of the GPU kernel that also takes it: the anchor rounded to FP32 and
- * p = fma(re, re, im * im) in FP32.  The selection of anchor a holds for the whole symbol
+/* Sparse convolution (Sec. III-C, "top-n dominant taps per time step"):
+ * keep[(r*n_tx+t)*n_taps+k] = 1 for the top_n taps of |H[a]|^2 per link, the powers taken in FP64
+ * from the FP64 anchor, ties to the lower k.  The selection of anchor a holds for the whole symbol
  * [b_a, b_{a+1}); each kept tap is interpolated toward its own H[a+1]. */
-static float tap_power_f32(const double *h) {
-  const float re = (float)h[0], im = (float)h[1];
-  const float im2 = im * im;
-  return fmaf(re, re, im2);
-}
+static double tap_power(const double *h) { return h[0] * h[0] + h[1] * h[1]; }
 
 static void top_n_mask(const tto_ue *u, const double *H, unsigned char *keep) {
   for (uint32_t r = 0; r < u->n_rx; ++r)
@@ -154,10 +152,10 @@ static void top_n_mask(const tto_ue *u, const double *H, unsigned char *keep) {
       for (uint32_t k = 0; k < u->n_taps; ++k) {
         if (u->top_n == 0 || u->top_n >= u->n_taps) { keep[base + k] = 1; continue; }
         /* rank = number of taps that beat tap k */
-        const float pk = tap_power_f32(H + 2 * (base + k));
+        const double pk = tap_power(H + 2 * (base + k));
         uint32_t rank = 0;
         for (uint32_t j = 0; j < u->n_taps; ++j) {
-          const float pj = tap_power_f32(H + 2 * (base + j));
+          const double pj = tap_power(H + 2 * (base + j));
           if (pj > pk || (pj == pk && j < k)) ++rank;
         }
         keep[base + k] = rank < u->top_n;
@@ -189,7 +187,8 @@ int tto_run(const tto_ue *u, uint64_t s_first, uint32_t n_slots, const int16_t *
   if (!A || !keep || !start) { free(A); free(keep); free(start); return -1; }
   for (size_t i = 0; i < n_anch; ++i) {
     tto_anchor(u, s_first * u->nsym + i, A + 2 * per * i);
-    top_n_mask(u, A + 2 * per * i, keep + per * i);
+    if (u->keep) memcpy(keep + per * i, u->keep + per * i, per);
+    else top_n_mask(u, A + 2 * per * i, keep + per * i);
   }
   start[0] = 0;
   for (uint32_t j = 1; j < u->nsym; ++j) start[j] = start[j - 1] + u->sym_len[j - 1];

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from oracle import brute
-from tests.helpers import impulse_x, iq_to_complex, nrmse
+from tests.helpers import impulse_x, iq_to_complex, nrmse, topn_selections
 
 
 def _rand_taps(rng, T, n_rx, n_tx, K, scale=1.0):
@@ -359,8 +359,8 @@ TOPN_CASES = [
 @pytest.mark.parametrize("case", range(len(TOPN_CASES)))
 def test_top_n_equals_exact_brute_force(case):
     """The per-symbol, per-link selection (Sec. III-C) and the convolution with only the kept taps
-    agree with the exact rational brute force, whose selection rounds each power to binary32 as
-    the kernel does; the selection changes from symbol to symbol here (taps drawn per anchor)."""
+    agree with the exact rational brute force, which compares the powers exactly; the selection
+    changes from symbol to symbol here (taps drawn per anchor)."""
     L, n_tx, n_rx, d, n_slots, step, top_n = TOPN_CASES[case]
     rng = np.random.default_rng(300 + case)
     n = sum(L)
@@ -375,6 +375,69 @@ def test_top_n_equals_exact_brute_force(case):
     assert np.array_equal(q, qe)
     full, _ = oracle.run_ue(oracle.OracleUE(L, n_tx, n_rx, d, taps, step_samples=step), x)
     assert nrmse(y, full) > 1e-3                          # the sparse result really differs
+
+
+def test_top_n_is_decided_on_fp64_powers():
+    """Tap 1 = 1 + 2^-12 i has power 1 + 2^-24, above tap 0's power 1 by less than binary32 can
+    resolve at 1.  The oracle ranks in FP64 and keeps tap 1, as the exact brute force does."""
+    L = [4, 4]
+    d = np.array([0, 2, 3], dtype=np.int32)
+    prof = np.array([1.0, 1.0 + 2.0 ** -12 * 1j, 0.5], dtype=np.complex64)
+    taps = np.tile(prof.reshape(1, 1, 1, 3), (3, 1, 1, 1))
+    rng = np.random.default_rng(12)
+    x = rng.integers(-2000, 2000, size=(1, 8, 2)).astype(np.int16)
+    y, q = oracle.run_ue(oracle.OracleUE(L, 1, 1, d, taps, top_n=1), x)
+    xc = iq_to_complex(x[0])
+    ref = np.zeros_like(xc)
+    ref[2:] = complex(prof[1]) * xc[:-2]
+    assert np.allclose(y[0], ref, rtol=0, atol=1e-9)
+    ye, qe = brute.run_exact(L, d, taps, x, top_n=1)
+    assert nrmse(y, brute.to_complex(ye)) < 1e-13 and np.array_equal(q, qe)
+
+
+def test_explicit_selection_replaces_the_top_n_rule():
+    """An explicit tap mask: all taps kept gives the dense result; the FP64 selection of
+    tests.helpers.topn_selections gives the top-n result; one kept tap of a static profile gives
+    that tap's delayed copy of the input."""
+    rng = np.random.default_rng(13)
+    L = [5, 4, 4]
+    n = sum(L)
+    d = np.array([0, 1, 4, 6], dtype=np.int32)
+    taps = _rand_taps(rng, 2 * 3 + 1, 2, 1, 4)
+    x = rng.integers(-900, 900, size=(1, 2 * n, 2)).astype(np.int16)
+    ue = oracle.OracleUE(L, 1, 2, d, taps, top_n=2)
+    dense, _ = oracle.run_ue(oracle.OracleUE(L, 1, 2, d, taps), x)
+    y_all, _ = oracle.run_ue(ue, x, keep=np.ones((7, 2, 1, 4), dtype=bool))
+    assert np.array_equal(y_all, dense)
+    base = np.stack([topn_selections(oracle.anchor(ue, a), 2)[0] for a in range(7)])
+    assert base.sum(axis=-1).max() == 2 and base.sum(axis=-1).min() == 2
+    y_sel, _ = oracle.run_ue(ue, x, keep=base)
+    y_rule, _ = oracle.run_ue(ue, x)
+    assert np.array_equal(y_sel, y_rule)
+    st = np.tile(np.array([0.5, 2 - 1j, 0.25j, 1.0], dtype=np.complex64).reshape(1, 1, 1, 4), (7, 2, 1, 1))
+    one = np.zeros((7, 2, 1, 4), dtype=bool)
+    one[..., 2] = True                                    # keep only tap 2 (delay 4)
+    y1, _ = oracle.run_ue(oracle.OracleUE(L, 1, 2, d, st, top_n=1), x, keep=one)
+    xc = iq_to_complex(x[0])
+    ref = np.zeros_like(xc)
+    ref[4:] = 0.25j * xc[:-4]
+    assert np.allclose(y1, np.stack([ref, ref]), rtol=0, atol=1e-9)
+
+
+def test_topn_selections_lists_only_near_ties():
+    """The valid-selection enumerator of the top-n GPU check: a clear ranking has one selection;
+    powers within binary32 rounding of the n-th place allow each of the near-tied taps."""
+    H = np.array([[[3.0, 1.0, 2.0, 0.5]]], dtype=np.complex128)
+    base, alts = topn_selections(H, 2)
+    assert base[0, 0].tolist() == [True, False, True, False] and not alts
+    H = np.array([[[3.0, 1.0, 1.0 + 2.0 ** -30, 0.5, 1.0]]], dtype=np.complex128)
+    base, alts = topn_selections(H, 2)
+    assert base[0, 0].tolist() == [True, False, True, False, False]
+    sels = [m.tolist() for m in alts[(0, 0)]]
+    assert sels[0] == base[0, 0].tolist() and len(sels) == 3
+    assert [True, True, False, False, False] in sels and [True, False, False, False, True] in sels
+    base, alts = topn_selections(H, 0)
+    assert base.all() and not alts
 
 
 def test_top_n_ties_keep_the_lower_tap_and_follow_each_anchor():
