@@ -33,7 +33,14 @@ sys.path.insert(0, ROOT)
 
 N_UES, N_SLOTS, N_FFT, N_TAPS, D_MAX = 16, 1000, 2048, 24, 256
 SLOT_SAMPLES = 30720
-FLOP_PER_TAP_SAMPLE = 12      # complex MAC (8) + tap interpolation h = H + tau*dH (2 FMA = 4)
+# Algorithmic FP32 work per tap-sample (one link, one tap, one output sample): a complex MAC
+# (4 FFMA, 8 flop) and the tap's interpolation h = H + tau*dH (2 FP32-pipe operations, counted as
+# 2 flop: one add per component).  The roofline fraction is the FP32-pipe instruction rate this
+# implies against SMs x 128 lanes x SM clock; the flop and MAC-only fractions are reported beside it.
+INSTR_PER_TAP_SAMPLE = 6
+FLOP_PER_TAP_SAMPLE = 10
+MAC_FLOP_PER_TAP_SAMPLE = 8
+FP32_LANES_PER_SM = 128
 DISTINCT_IQ_SLOTS = 64        # synthetic IQ slots per UE, cycled through the replay
 METRIC = "UE-slots/s and GMAC/s at 1 GB300 vs plain form; p99 slot latency vs 0.5 ms"
 # DRAM traffic per full launch from the ncu capture summarised in
@@ -49,9 +56,32 @@ def peaks():
     out = {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
     if os.path.exists(p):
         d = json.load(open(p))
-        out.update({k: d[k] for k in ("sm_max_mhz", "hbm_gbs", "bf16_tflops") if k in d})
+        out.update({k: d[k] for k in ("sm_max_mhz", "hbm_gbs", "bf16_tflops", "bf16_tflops_sustained") if k in d})
         out["src"] = "measured"
     return out
+
+
+def sm_count(device) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def alu_roofline(tap_samples_per_launch: float, kernel_ms: float, n_sm: int, clock_mhz: float, clock_src: str):
+    """The FP32-pipe roofline of a tiled-kernel launch, every figure derivable from the fields."""
+    t = kernel_ms / 1e3
+    peak_instr = n_sm * FP32_LANES_PER_SM * clock_mhz * 1e6       # FP32-pipe lane-operations per second
+    achieved = tap_samples_per_launch * INSTR_PER_TAP_SAMPLE / t
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_instr / 1e12,
+            "unit": "T FP32-pipe instructions/s", "frac": achieved / peak_instr,
+            "frac_definition": f"{INSTR_PER_TAP_SAMPLE} algorithmic FP32-pipe instructions per tap-sample "
+                               f"(4 FFMA complex MAC + 2 for the interpolation) x tap-samples per launch / "
+                               f"kernel time, over SMs x {FP32_LANES_PER_SM} lanes x SM clock",
+            "tap_samples_per_launch": tap_samples_per_launch, "kernel_ms": kernel_ms, "sm_count": n_sm,
+            "sm_clock_mhz": clock_mhz, "clock_src": clock_src,
+            "flop_frac": tap_samples_per_launch * FLOP_PER_TAP_SAMPLE / t / (2 * peak_instr),
+            "mac_only_frac": tap_samples_per_launch * MAC_FLOP_PER_TAP_SAMPLE / t / (2 * peak_instr),
+            "flop_definition": f"{FLOP_PER_TAP_SAMPLE} flop per tap-sample (8 complex MAC + 2 interpolation) "
+                               f"and 8 (MAC only), over SMs x {FP32_LANES_PER_SM} x 2 flop x SM clock"}
 
 
 class ClockSampler:
@@ -116,14 +146,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def make_workload(rank: int):
+def make_workload(rank: int, n_slots: int = None, n_ues: int = N_UES, iq_slots: int = DISTINCT_IQ_SLOTS):
+    """Rank `rank`'s UEs: the 16-UE workload with AWGN keyed by the global UE ids of its shard."""
     from paper_2601_08217_gb300 import inputs, shard
-    specs = inputs.workload_plain_16ue(n_slots=N_SLOTS, n_ues=N_UES)
-    for s, uid in zip(specs, shard.shard_ue_ids(N_UES, rank)):
+    specs = inputs.workload_plain_16ue(n_slots=N_SLOTS if n_slots is None else n_slots, n_ues=n_ues)
+    for s, uid in zip(specs, shard.shard_ue_ids(n_ues, rank)):
         s.loop = True            # repeated steps keep replaying the trace
         s.ue_id = uid
-    iq = [inputs.make_iq(2, s, DISTINCT_IQ_SLOTS) for s in specs]
+    iq = [inputs.make_iq(2, s, iq_slots) for s in specs]
     return specs, iq
+
+
+def whole_job_rate(ms_total: float, steps: int, world: int, ue_slots_per_rank_step: int, device=None):
+    """(ms per step of the slowest rank, UE-slots/s of all ranks together): every rank processes
+    ue_slots_per_rank_step UE-slots per step, and the job takes as long as its slowest rank."""
+    from paper_2601_08217_gb300 import shard
+    ms_step = shard.max_over_ranks(ms_total / steps, device=device)
+    return ms_step, ue_slots_per_rank_step * world / (ms_step / 1e3)
 
 
 def cycled_slots(x, n, count, first=0):
@@ -342,9 +381,9 @@ def run_batching(args, device, n_ues=256, steps=400, warmup=20):
     return {"ues": n_ues, "steps": steps, "ms_per_step": ms / steps, "host_ms_per_step": t_host * 1e3 / steps,
             "ue_slots_per_s": n_ues * steps / (ms / 1e3), "gmac_per_s": tap_s * steps / (ms / 1e3) / 1e9,
             "samples_per_slot_step": samples, "realtime": (ms / steps) <= 0.5,
-            # whole-step FP32 work (12 flop per tap-sample) against the ALU peak, launch gaps included
-            "alu_frac": tap_s * steps * FLOP_PER_TAP_SAMPLE / (ms / 1e3) / 1e12
-                        / (152 * 128 * 2 * peaks()["sm_max_mhz"] * 1e6 / 1e12),
+            # whole-step FP32 work against the ALU peak, launch gaps included
+            "roofline": alu_roofline(tap_s, ms / steps, sm_count(device), peaks()["sm_max_mhz"],
+                                     "sm_max_mhz of " + peaks()["src"] + " peaks"),
             "graph_launches": st1["graph_launches"] - st0["graph_launches"],
             "graph_builds": st1["graph_builds"], "autotuned_classes": tuned}
 
@@ -446,7 +485,14 @@ def run_precision(args, device, n_ues=64, n_slots=20, warmup=3, forms=("bf16_tc"
                "useful_tflops": useful_flop / (ms / 1e3) / 1e12, "evm_db_vs_oracle": evm}
         if prec != tc.TT_FP32:
             rec["executed_tflops"] = exec_flop / (ms / 1e3) / 1e12
-            rec["tensor_frac_of_measured_bf16_peak"] = rec["executed_tflops"] / pk.get("bf16_tflops", 1918.0)
+            pkt = pk.get("bf16_tflops", 1900.0)   # FP16 and BF16 share the dense tensor rate
+            rec["roofline"] = {"bound": "tensor", "achieved": rec["executed_tflops"], "peak": pkt,
+                               "unit": "TFLOP/s", "frac": rec["executed_tflops"] / pkt,
+                               "frac_definition": "MMA flop issued per slot (128x128x16 per K-chunk MMA, "
+                                                  "chunks no delay reaches skipped) / time, over the dense "
+                                                  "BF16 GEMM peak (" + pk["src"] + ")",
+                               "useful_frac": rec["useful_tflops"] / pkt,
+                               "executed_flop_per_slot": exec_flop, "useful_flop_per_slot": useful_flop}
         out[name] = rec
         eng.close()
     return out
@@ -743,10 +789,7 @@ def main():
     __graft_entry__.build()
 
     r = run_ours(args, rank, world, local)
-    from paper_2601_08217_gb300 import shard
-    ms_step = shard.max_over_ranks(r["ms_total"] / args.steps, device="cuda")
-    ue_slots = N_UES * N_SLOTS * world
-    value = ue_slots / (ms_step / 1e3)
+    ms_step, value = whole_job_rate(r["ms_total"], args.steps, world, N_UES * N_SLOTS, device="cuda")
     ts = tap_samples(r["specs"]) * N_SLOTS
     gmac = ts * world / (ms_step / 1e3) / 1e9
     pk = peaks()
@@ -755,8 +798,13 @@ def main():
     ksha = hashlib.sha256(open(ksrc, "rb").read()).hexdigest()[:16]
     traffic = TRAFFIC_BYTES if (ksha == TRAFFIC_KERNEL_SHA and N_SLOTS == 1000) else None
     kms = statistics.mean(r["kern_ms"])
-    peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-    achieved = ts * FLOP_PER_TAP_SAMPLE / (kms / 1e3) / 1e12
+    clk_max = r["clocks"].get("sm_max_mhz")
+    roof = alu_roofline(ts, kms, sm_count(local), clk_max or pk["sm_max_mhz"],
+                        "clocks.max.sm sampled by nvidia-smi" if clk_max else "sm_max_mhz of " + pk["src"] + " peaks")
+    roof.update({"traffic": traffic, "kernel": f"tt_conv_fp32_kernel<{args.spt or 8},1,256>",
+                 "dram_gbs": (traffic / (kms / 1e3) / 1e9) if traffic else None,
+                 "dram_frac_of_hbm": (traffic / (kms / 1e3) / 1e9 / pk["hbm_gbs"]) if traffic else None,
+                 "hbm_peak_gbs": pk["hbm_gbs"]})
     batching = None
     if rank == 0 and world == 1 and not args.no_batching:
         batching = run_batching(args, local)
@@ -793,14 +841,7 @@ def main():
                    "iq": f"{DISTINCT_IQ_SLOTS} distinct synthetic slots per UE cycled",
                    "l2": "inputs larger than L2 (1.97 GB of IQ read per step per GPU)"},
         "gmac_per_s": gmac, "samples_per_s": N_UES * N_SLOTS * SLOT_SAMPLES * world / (ms_step / 1e3),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": f"tt_conv_fp32_kernel<{args.spt or 8},1,256>", "kernel_ms": kms,
-                     "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz ({pk['src']})",
-                     # the complex MACs alone (8 of the 12 flop per tap-sample), and the DRAM side
-                     "mac_only_frac": achieved * 8 / FLOP_PER_TAP_SAMPLE / peak_tflops,
-                     "dram_gbs": (traffic / (kms / 1e3) / 1e9) if traffic else None,
-                     "dram_frac_of_hbm": (traffic / (kms / 1e3) / 1e9 / pk["hbm_gbs"]) if traffic else None},
+        "roofline": roof,
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "e2e": r["e2e"],

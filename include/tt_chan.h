@@ -414,7 +414,10 @@ tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len);
  *
  * Limits, rejected with TT_ERR_INVALID: at most 64 channels per call,
  * samples_per_slot <= 65536, at most 128 taps, delays <= 1024, and a
- * channel must fit the kernel's shared memory.
+ * channel must fit the kernel's shared memory.  Alignment, also rejected with
+ * TT_ERR_INVALID: d_ring_in 16-byte aligned, d_taps 8-byte, d_ring_out 4-byte
+ * (TT_OUT_INT16) or 8-byte (TT_OUT_CF32).  Every argument is checked on the
+ * host before the call touches the device.
  *
  * Layout and semantics follow the engine's rings: slot s of a channel sits at
  * ring position s % ring_slots, input [ring_slots][n_tx][N][2] int16, output
@@ -436,7 +439,8 @@ typedef struct {
   uint32_t symbols_per_slot;
   const uint32_t *symbol_len; /* host, [symbols_per_slot], summing to N */
   uint32_t n_tx, n_rx;        /* 1 .. 4 */
-  uint32_t ring_slots;        /* ring depth Q of both rings: >= ceil(max delay / N) + 1 and >= n_slots */
+  uint32_t ring_slots;        /* ring depth Q of both rings: >= n_slots + ceil(max delay / N), so that the
+                                 delay line of the call's first slot is not overwritten by its own slots */
   const int16_t *d_ring_in;   /* device, caller-owned input ring */
   void *d_ring_out;           /* device, caller-owned output ring */
   const float *d_taps;        /* device, caller-owned complex64 [n_anchors][n_rx][n_tx][n_taps] */

@@ -70,27 +70,6 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
   if (n_chans > (uint32_t)kMaxChans)
     return err(TT_ERR_INVALID, "tt_conv_static: %u channels, at most %d per call", n_chans, kMaxChans);
 
-  int dev = 0;
-  cudaError_t ce = cudaGetDevice(&dev);
-  if (ce != cudaSuccess) return err(TT_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(ce));
-  if (dev < 0 || dev >= kMaxDevices) return err(TT_ERR_INVALID, "device %d out of range", dev);
-  unsigned char *scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch[dev]) {
-      void *p = nullptr;
-      ce = cudaGetSymbolAddress(&p, tt_static_scratch);
-      if (ce != cudaSuccess || !p) return err(TT_ERR_CUDA, "scratch lookup: %s", cudaGetErrorString(ce));
-      g_scratch[dev] = static_cast<unsigned char *>(p);
-    }
-    scratch = g_scratch[dev];
-  }
-  TTUEDesc *d_desc = reinterpret_cast<TTUEDesc *>(scratch + kOffDesc);
-  TTSeg *d_seg = reinterpret_cast<TTSeg *>(scratch + kOffSeg);
-  int32_t *d_chunk = reinterpret_cast<int32_t *>(scratch + kOffChunk);
-  int32_t *d_delay = reinterpret_cast<int32_t *>(scratch + kOffDelay);
-  uint32_t *d_count = reinterpret_cast<uint32_t *>(scratch + kOffCount);
-
   // ---- validate and describe every channel (host only) ----
   std::vector<TTUEDesc> desc(n_chans);
   std::vector<int32_t> chunk_host((size_t)kMaxItems * n_chans, 0), delay_host((size_t)kMaxTaps * n_chans, 0);
@@ -110,6 +89,14 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
       return err(TT_ERR_INVALID, "chan %u: need 1..%d taps, host delays, device taps, >= 1 anchor", i, kMaxTaps);
     if (!c.d_ring_in || !c.d_ring_out) return err(TT_ERR_INVALID, "chan %u: null ring", i);
     if (c.output_format > TT_OUT_CF32) return err(TT_ERR_INVALID, "chan %u: unknown output_format", i);
+    // the kernel stages the input ring with 16-byte copies, reads taps as 8-byte complex64 and stores
+    // 4-byte packed IQ or 8-byte complex64 outputs
+    const uintptr_t out_align = c.output_format == TT_OUT_CF32 ? 8 : 4;
+    if ((reinterpret_cast<uintptr_t>(c.d_ring_in) & 15) || (reinterpret_cast<uintptr_t>(c.d_taps) & 7) ||
+        (reinterpret_cast<uintptr_t>(c.d_ring_out) & (out_align - 1)))
+      return err(TT_ERR_INVALID,
+                 "chan %u: d_ring_in must be 16-byte aligned, d_taps 8-byte, d_ring_out %u-byte", i,
+                 (unsigned)out_align);
     if (!(c.step_samples >= 0.0) || !std::isfinite(c.step_samples) || !(c.noise_var >= 0.f) ||
         !std::isfinite(c.noise_var))
       return err(TT_ERR_INVALID, "chan %u: bad step_samples or noise_var", i);
@@ -124,9 +111,12 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
         return err(TT_ERR_INVALID, "chan %u: delays must be non-decreasing in 0..%d", i, TT_MAX_DELAY);
       d_max = std::max(d_max, (int)d);
     }
-    const int hist = (d_max + (int)N - 1) / (int)N;
-    if (c.ring_slots < (uint32_t)hist + 1 || c.n_slots > c.ring_slots)
-      return err(TT_ERR_INVALID, "chan %u: ring_slots must be >= %d and >= n_slots", i, hist + 1);
+    // slot s reads its delay line from the positions of slots s - hist .. s - 1; those of slots before
+    // first_slot must not be positions that this call's own slots occupy
+    const uint64_t hist = ((uint64_t)d_max + N - 1) / N;
+    if ((uint64_t)c.ring_slots < (uint64_t)c.n_slots + hist || c.ring_slots == 0)
+      return err(TT_ERR_INVALID, "chan %u: ring_slots %u < n_slots %u + %llu history slot(s) of the delay line", i,
+                 c.ring_slots, c.n_slots, (unsigned long long)hist);
     const int dclass = d_max <= TT_DCLASS0 ? 0 : d_max <= TT_DCLASS1 ? 1 : d_max <= TT_DCLASS2 ? 2 : 3;
     // largest samples-per-thread (<= 8) dividing every symbol length and fitting shared memory
     int spt = 0, tap_need = 0, items = 0;
@@ -156,8 +146,6 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
     d.ring_in = c.d_ring_in;
     d.ring_out = c.d_ring_out;
     d.taps = reinterpret_cast<const float2 *>(c.d_taps);
-    d.delays = d_delay + (size_t)i * kMaxTaps;
-    d.chunk_info = d_chunk + (size_t)i * kMaxItems;
     d.step_samples = c.step_samples;
     d.seed = c.seed;
     d.n = (int)N;
@@ -188,6 +176,31 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
     d.grp_start[d.nsym] = g;
     meta[i] = {spt, dclass, tap_need, (int)c.n_tx, (int)c.n_rx, (int)c.n_taps, c.n_slots, c.first_slot};
   }
+
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce != cudaSuccess) return err(TT_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(ce));
+  if (dev < 0 || dev >= kMaxDevices) return err(TT_ERR_INVALID, "device %d out of range", dev);
+  unsigned char *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch[dev]) {
+      void *p = nullptr;
+      ce = cudaGetSymbolAddress(&p, tt_static_scratch);
+      if (ce != cudaSuccess || !p) return err(TT_ERR_CUDA, "scratch lookup: %s", cudaGetErrorString(ce));
+      g_scratch[dev] = static_cast<unsigned char *>(p);
+    }
+    scratch = g_scratch[dev];
+  }
+  for (uint32_t i = 0; i < n_chans; ++i) {  // descriptor pointers into the scratch array
+    desc[i].delays = reinterpret_cast<int32_t *>(scratch + kOffDelay) + (size_t)i * kMaxTaps;
+    desc[i].chunk_info = reinterpret_cast<int32_t *>(scratch + kOffChunk) + (size_t)i * kMaxItems;
+  }
+  TTUEDesc *d_desc = reinterpret_cast<TTUEDesc *>(scratch + kOffDesc);
+  TTSeg *d_seg = reinterpret_cast<TTSeg *>(scratch + kOffSeg);
+  int32_t *d_chunk = reinterpret_cast<int32_t *>(scratch + kOffChunk);
+  int32_t *d_delay = reinterpret_cast<int32_t *>(scratch + kOffDelay);
+  uint32_t *d_count = reinterpret_cast<uint32_t *>(scratch + kOffCount);
 
   // ---- work list: one run of slots per channel, grouped by kernel variant ----
   std::vector<uint32_t> order(n_chans);
