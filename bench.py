@@ -446,12 +446,12 @@ def run_precision(args, device, n_ues=64, n_slots=20, warmup=3, forms=("bf16_tc"
     y_ref, _ = oracle.run_ue(oracle.OracleUE.from_spec(specs[0]), x0)
     out = {}
     n = specs[0].n
-    # tensor-core MMAs issued per slot: per symbol, groups of <= 4096 samples in tiles of 1024
-    # samples (128 block rows of 8), each tile 2 x 4 x kc K-chunks of a 128x128x16 MMA, where the
+    # tensor-core MMAs issued per slot: per symbol, groups of <= 1536 samples (192 block rows of 8),
+    # each group one 128 x N x 16 MMA per K-chunk with N = its block rows rounded up to 16; the
     # 144-wide window per (Tx, part) skips the 16-wide chunks no delay reaches: kc = 9 - (128 - d_max) // 16
-    tiles = sum(-(-min(4096, L - g) // 1024) for L in specs[0].symbol_len for g in range(0, L, 4096))
+    ncols = sum(-(-(-(-min(1536, L - g) // 8)) // 16) * 16 for L in specs[0].symbol_len for g in range(0, L, 1536))
     kc = 9 - (128 - int(np.max(specs[0].delays))) // 16
-    exec_flop = n_ues * tiles * (4 * 2 * kc) * 128 * 128 * 16 * 2
+    exec_flop = n_ues * ncols * (4 * 2 * kc) * 128 * 16 * 2
     useful_flop = n_ues * n * 16 * 96 * 8                        # complex MACs per slot
     for name, prec in (("bf16_tc", tc.TT_BF16_TC), ("fp16_tc", tc.TT_FP16_TC), ("fp32", tc.TT_FP32)):
         if name not in forms:
@@ -488,9 +488,9 @@ def run_precision(args, device, n_ues=64, n_slots=20, warmup=3, forms=("bf16_tc"
             pkt = pk.get("bf16_tflops", 1900.0)   # FP16 and BF16 share the dense tensor rate
             rec["roofline"] = {"bound": "tensor", "achieved": rec["executed_tflops"], "peak": pkt,
                                "unit": "TFLOP/s", "frac": rec["executed_tflops"] / pkt,
-                               "frac_definition": "MMA flop issued per slot (128x128x16 per K-chunk MMA, "
-                                                  "chunks no delay reaches skipped) / time, over the dense "
-                                                  "BF16 GEMM peak (" + pk["src"] + ")",
+                               "frac_definition": "MMA flop issued per slot (one 128 x N x 16 MMA per K-chunk "
+                                                  "and group, chunks no delay reaches skipped) / time, over "
+                                                  "the dense BF16 GEMM peak (" + pk["src"] + ")",
                                "useful_frac": rec["useful_tflops"] / pkt,
                                "executed_flop_per_slot": exec_flop, "useful_flop_per_slot": useful_flop}
         out[name] = rec

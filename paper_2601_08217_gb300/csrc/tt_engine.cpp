@@ -12,6 +12,7 @@
 #include <cstddef>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <chrono>
 #include <deque>
@@ -103,6 +104,7 @@ struct tt_engine {
   TTSeg *d_tcsegs = nullptr;                // work list of the tensor-core channels
   size_t tcseg_cap = 0;
   int *d_status = nullptr;                  // set by a kernel whose bounded wait expired
+  int tc_no_mma = 0;                        // tests only (TT_TEST_TC_NO_MMA=1 at creation): no MMA is issued
   std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
   std::vector<tt_cell *> cells;             // uplink aggregation cells
   std::vector<TTSosJob> sos_jobs;           // synthesis work list of the current run (host copy)
@@ -659,10 +661,10 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
     L.total_items = items;
     L.counter = nullptr;
     L.grid = -1;
-    cudaError_t err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->stream);
+    cudaError_t err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->tc_no_mma, e->stream);
     if (err != cudaSuccess) return fail(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(err));
     L.grid = (int)std::min<uint64_t>((uint64_t)(-L.grid) * e->num_sms, items);
-    err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->stream);
+    err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->tc_no_mma, e->stream);
     if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tensor-core launch: %s", cudaGetErrorString(err));
     ++e->launches;
   }
@@ -701,6 +703,10 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   e->max_ues = cfg->max_ues ? cfg->max_ues : 1024;
   e->spt_override = cfg->samples_per_thread;
   e->persistent = cfg->persistent;
+  {  // failure-detection tests: the tensor-core kernel issues no MMA, so its bounded waits run out
+    const char *v = std::getenv("TT_TEST_TC_NO_MMA");
+    e->tc_no_mma = (v && v[0] == '1') ? 1 : 0;
+  }
   e->graphs = cfg->struct_size >= offsetof(tt_engine_config, graphs) + sizeof(uint32_t) && cfg->graphs != 0;
   cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
   e->table.assign(e->max_ues, nullptr);

@@ -180,12 +180,13 @@ cudaError_t tt_launch_conv_s8_topn(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s16_topn(const TTLaunch &L, cudaStream_t st);
 
 // Block-Toeplitz tensor-core kernel (tcgen05, BF16 or FP16 operands): one work item per
-// (UE, slot, up to 4096 samples of one symbol); status is set to 1 if a bounded wait on the
-// tensor core expires.
+// (UE, slot, symbol), in groups of up to 1536 samples; status is set to 1 if a bounded wait on the
+// tensor core expires.  no_mma (tests only): the MMA warp issues no MMA, so the other roles' bounded
+// waits run out with nothing in flight on the tensor core.
 size_t tt_tc_smem_bytes();
 int tt_tc_max_delay();
 int tt_tc_items_per_slot(const int32_t *sym_len, int nsym);  // work items per slot of a channel
-cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, cudaStream_t st);
+cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, int no_mma, cudaStream_t st);
 
 // Record a message for tt_last_error() (thread-local) and return the status.
 int32_t tt_set_error(int32_t status, const char *msg);

@@ -10,21 +10,26 @@
 // convolutions whose sum over delays is a matrix product.
 //
 // Block form (blocks of 8 output samples, delays d < 128):
-//     D[c][(i, n)] = sum_{t, p, j} X_{t,p}[c][j] * W[(i, n)][(t, p, j)]
+//     D[(i, n)][c] = sum_{t, p, j} W[(i, n)][(t, p, j)] * X_{t,p}[c][j]
 //     X_{t,p}[c][j] = x_{t,p}[8 c + j - 128],     W[(i, n)][(t, p, j)] = tap of delay i + 128 - j
-//     c = block row (M), i = sample in the block, n = (r, output part, A or B), p = re/im part of x
-// so output sample 8 c + i of (r, part) is D[c][(i, n)].  X is a Hankel-like
+//     c = block row, i = sample in the block, n = (r, output part, A or B), p = re/im part of x
+// so output sample 8 c + i of (r, part) is D[(i, n)][c].  X is a Hankel-like
 // view of one contiguous run of 16-bit samples: element (c, j) sits at byte
 // 16 c + 2 j.  That is a K-major shared-memory matrix descriptor whose 8-row
-// core matrices are 128 bytes apart along M and only 16 bytes apart along K,
-// so the Toeplitz-expanded operand is never stored: the tensor core reads the
-// staged window itself.  The tap operand W (128 x 1152 for 4 Tx) is too big to
-// keep, so it streams in 4 KB K-chunks built in shared memory while the tensor
-// core consumes the previous chunk; each chunk feeds up to four 128x128x16 MMAs
-// (1024 samples each) whose accumulators fill the 512 tensor-memory columns.
+// core matrices are 128 bytes apart along N and only 16 bytes apart along K,
+// so the Toeplitz-expanded signal is never stored: the tensor core reads the
+// staged window itself (the B operand, N = up to 192 block rows, 1536 samples).
 //
-// Every wait on the MMA-completion barrier is bounded; on expiry the kernel
-// sets the status word to 1, frees its tensor memory and exits.
+// The tap operand W (128 rows x 1152 for 4 Tx) is the A operand and lives in
+// tensor memory: builder warps expand each 16-wide K-chunk from compact
+// component tables straight into a ring of tensor-memory columns
+// (tcgen05.st), so the only shared-memory traffic of an MMA is its signal
+// view and the builders' table reads.  Accumulators take 192 of the CTA's
+// 256 tensor-memory columns, the chunk ring the other 64; two CTAs share an
+// SM.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel sets the status
+// word to 1, frees its tensor memory and exits.
 #include <cstdint>
 
 #include <cuda_bf16.h>
@@ -40,41 +45,42 @@ constexpr int kBuildWarps = 8;                  // stage, build tap chunks, epil
 constexpr int kTPB = (kBuildWarps + 1) * 32;    // + one warp that issues the MMAs
 constexpr int kBuilders = kBuildWarps * 32;
 constexpr int kB = 8;                 // output samples per block row (16-byte rows of the signal view)
-constexpr int kRows = 128;            // block rows per MMA tile (M): 1024 samples
-constexpr int kTilesMax = 2;          // tiles accumulating at once: 2 x 128 TMEM columns
-constexpr int kGroup = kRows * kB * kTilesMax;  // samples per group (2048)
+constexpr int kM = 128;               // D rows: (i, r, part, A|B)
+constexpr int kNMax = 192;            // D columns per group: block rows (1536 samples)
+constexpr int kGroup = kNMax * kB;    // samples per group
 constexpr int kMaxDelayTC = 127;
 constexpr int kW = 144;               // window per (t, p): j in [0, 135) used, padded to 9 K-chunks of 16
 constexpr int kKC = kW / 16;          // K-chunks per (t, p)
-constexpr int kN = 128;               // D columns: (i, r, part, A|B)
 constexpr int kSig = kGroup + kW;     // staged samples per (t, p)
-constexpr uint32_t kTmemCols = kTilesMax * kN;  // two CTAs per SM share the 512 columns
+constexpr uint32_t kTmemCols = 256;   // two CTAs per SM share the 512 columns
+constexpr uint32_t kAccCols = kNMax;  // accumulator columns [0, 192)
+constexpr uint32_t kChunkCols = 8;    // one K-chunk of A: 128 lanes x 16 16-bit values
 constexpr long long kSpinLimit = 1ll << 24;
 
-constexpr int kQW = 88;               // words per component table: q = j - i + 8 in [1, 151] needs 76, plus shift <= 3
+constexpr int kQW = 88;               // words per component table: q = j - i + 8 in [1, 151] needs 76, plus shift <= 8
 constexpr int kComps = 4;             // hr, hi of H and of dH; -hi is hi with the sign bits flipped
 constexpr int kPer = 4;               // tap chunks per pipeline step
 constexpr int kSteps = 2;             // steps in the ring: builders run up to one step ahead of the MMAs
 constexpr int kStages = kPer * kSteps;
-constexpr int kChunkBytes = kN * 16 * 2;
+static_assert(kAccCols + kStages * kChunkCols <= kTmemCols, "accumulators and chunk ring fit the allocation");
 
 // shared memory layout (bytes).  The dense delay table is only read while the component tables
 // are built, before any signal is staged for the item, so it shares the signal's space.
 constexpr int kOffSig = 0;                               // [4 tx][2 parts][kSig] 16-bit operands
 constexpr int kOffTap = 0;                               // [16 links][128 delays] float4 (H, dH), by tap_pos(d)
-constexpr int kOffW = kOffSig + 4 * 2 * kSig * 2;        // kStages x 4 KB tap chunks: [16 n-groups][2 k-groups][8][8]
-constexpr int kOffComp = kOffW + kStages * kChunkBytes;  // [4 tx][2 parities][kComps][4 rx][kQW words]
+constexpr int kSigBytes = 4 * 2 * kSig * 2;
+constexpr int kTapBytes = 16 * 128 * 16;
+constexpr int kOffComp = kSigBytes > kTapBytes ? kSigBytes : kTapBytes;  // [4 tx][2 parities][kComps][4 rx][kQW words]
 constexpr int kSmemUsed = kOffComp + 16 * kComps * 2 * kQW * 4;
-static_assert(16 * 128 * 16 <= 4 * 2 * kSig * 2, "delay table must fit in the signal area");
 
-// Component tables, one per (t, parity, c, r), kQW words each.  A builder warp handles one sample i
-// of the block and all 16 rows (r, output part, A|B) for both K-groups (4 words apart); for either
-// input part it reads, at one (t, parity), the four tables c of every r.  Table (t, par, c, r) starts
-// at word ((t * 2 + par) * 4 + c) * 4 + r) * kQW, whose bank is 24 r (mod 32) because kQW = 88 is
-// 24 mod 32; shifting its data by c words puts the warp's 32 words of every 32-bit load on 32
-// distinct banks.
+// Component tables, one per (t, parity, c, r), kQW words each.  Table (t, par, c, r) starts at
+// word ((t * 2 + par) * 4 + c) * 4 + r) * kQW, whose bank is 24 r (mod 32) because kQW = 88 is
+// 24 mod 32, and its data is shifted by c + 5 par words.  A builder warp's 32 rows are two samples
+// i (of opposite parity, whose word offsets differ by one), four Rx antennas and four components:
+// their words land on banks 24 r + c + 4 par + const, all 32 distinct.
 __host__ __device__ constexpr int comp_slot(int t, int par, int c, int r) { return ((t * 2 + par) * kComps + c) * 4 + r; }
-static_assert(kQW % 32 == 24 && 76 + (kComps - 1) <= kQW, "component table stride and shift");
+__host__ __device__ constexpr int comp_shift(int c, int par) { return c + 5 * par; }
+static_assert(kQW % 32 == 24 && 76 + comp_shift(kComps - 1, 1) <= kQW, "component table stride and shift");
 // Two CTAs per SM (each with half the tensor-memory columns): one stages, builds tables or drains
 // its accumulators while the other keeps the tensor core busy.  A third never fits.
 constexpr int kSmemBytes = kSmemUsed;
@@ -100,12 +106,13 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (tensor memory) (+)= A (tensor memory, M = 128 lanes x K = 16) * B (shared-memory descriptor)^T
+__device__ __forceinline__ void umma_f16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t mbar) {
@@ -139,6 +146,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// 4 consecutive columns of this thread's lane (32-bit each); complete at tmem_wait_st().
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(taddr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// Transpose of a 4 x 4 block held by lanes 4g .. 4g + 3 (lane 4g + j holds row j in v): afterwards
+// lane 4g + j holds column j, v[s] = row s's element j.  Two butterfly exchanges.
+__device__ __forceinline__ void transpose4(float v[4], int j) {
+  const bool b1 = (j & 2) != 0, b0 = (j & 1) != 0;
+  float x0 = b1 ? v[0] : v[2], x1 = b1 ? v[1] : v[3];
+  float y0 = __shfl_xor_sync(0xFFFFFFFFu, x0, 2), y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, 2);
+  float a0 = b1 ? y0 : v[0], a1 = b1 ? y1 : v[1], a2 = b1 ? v[2] : y0, a3 = b1 ? v[3] : y1;
+  x0 = b0 ? a0 : a1;
+  x1 = b0 ? a2 : a3;
+  y0 = __shfl_xor_sync(0xFFFFFFFFu, x0, 1);
+  y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, 1);
+  v[0] = b0 ? y0 : a0;
+  v[1] = b0 ? a1 : y0;
+  v[2] = b0 ? y1 : a2;
+  v[3] = b0 ? a3 : y1;
+}
 
 template <bool FP16>
 __device__ __forceinline__ uint16_t to_op(float v) {
@@ -174,7 +206,8 @@ __device__ __forceinline__ void warp_wait(uint32_t mbar, uint32_t phase, int *st
 template <bool FP16>
 __global__ void __launch_bounds__(kTPB, 2)
     tt_toeplitz_tc_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
-                          uint32_t total_items, uint32_t *__restrict__ counter, int *__restrict__ status) {
+                          uint32_t total_items, uint32_t *__restrict__ counter, int *__restrict__ status,
+                          int no_mma) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) unsigned long long s_full[kSteps];   // builders -> MMA warp: step's chunks written
   __shared__ __align__(8) unsigned long long s_empty[kSteps];  // MMA completion -> builders: step's slots free
@@ -187,7 +220,6 @@ __global__ void __launch_bounds__(kTPB, 2)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint16_t *sig = reinterpret_cast<uint16_t *>(sm + kOffSig);
-  uint16_t *wbuf = reinterpret_cast<uint16_t *>(sm + kOffW);
   float4 *tapd = reinterpret_cast<float4 *>(sm + kOffTap);
   uint32_t *comp_w = reinterpret_cast<uint32_t *>(sm + kOffComp);
   volatile int *abort_flag = &s_abort;
@@ -214,22 +246,21 @@ __global__ void __launch_bounds__(kTPB, 2)
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = s_tmem;
 
-  // idesc: D = F32, A/B = F16 (0) or BF16 (1), both K-major, N = 128, M = 128
+  // idesc: D = F32, A/B = F16 (0) or BF16 (1), both K-major, M = 128; N (bits 17..22) per group
   const uint32_t fmt = FP16 ? 0u : 1u;
-  const uint32_t idesc =
-      (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-  const uint32_t sig_base = smem_u32(sig), w_base = smem_u32(wbuf);
+  const uint32_t idesc0 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kM >> 4) << 24);
+  const uint32_t sig_base = smem_u32(sig);
 
-  // this builder thread's fixed segment of every tap chunk: row (i, r, part, A|B), k-group kg.
-  // Lanes 8h .. 8h + 7 of a warp take rows 8 (h >> 1) .. + 7 of its 16 and k-group h & 1, so each
-  // quarter-warp stores one contiguous 128-byte run of the chunk.
-  const int row = warp * 16 + ((lane >> 4) << 3) + (lane & 7), kg = (lane >> 3) & 1;
+  // this builder thread's row of every tap chunk in tensor memory: lane 32 (warp % 4) + lane, row
+  // (i, r, part, A|B) = that lane; warps w and w + 4 write K-halves kg = w / 4 of the same lanes
+  const int quad = warp & 3, kg = warp >> 2;
+  const int row = quad * 32 + lane;
   const int ii = row >> 4, nn = row & 15, rr = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
   const int qoff = kg * 8 - ii + 8, par = qoff & 1;
   // (op, p) -> component: (0,0) hr, (0,1) -hi, (1,0) hi, (1,1) hr
   const int c_p0 = ab * 2 + (op == 0 ? 0 : 1), c_p1 = ab * 2 + (op == 0 ? 1 : 0);
   const uint32_t neg_p1 = op == 0 ? 0x80008000u : 0u;
-  const int w_off = ((row >> 3) * 256 + kg * 128 + (row & 7) * 16) / 2;
+  const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);  // this warp's lanes, column 0
 
   uint32_t gstep = 0;  // pipeline steps since launch (both roles count them alike)
   uint32_t ggroup = 0; // accumulator groups since launch
@@ -274,28 +305,25 @@ __global__ void __launch_bounds__(kTPB, 2)
 
     if (warp == kBuildWarps) {
       // ================= MMA warp: lane 0 issues, the warp waits =================
-      const uint64_t bdesc0 = umma_desc(w_base, /*lbo K*/ 128, /*sbo N*/ 256);
-      const uint64_t adesc0 = umma_desc(sig_base, /*lbo K*/ 16, /*sbo M*/ 128);
       for (int gs = sym0; gs < sym1; gs += kGroup) {
         const int blocks = (min(gs + kGroup, sym1) - gs + kB - 1) / kB;
-        const int n_tiles = (blocks + kRows - 1) / kRows;
+        const int ncols = (blocks + 15) & ~15;  // N: a multiple of 16 for M = 128
+        const uint32_t idesc = idesc0 | ((uint32_t)(ncols >> 3) << 17);
         if (ggroup > 0) warp_wait(smem_u32(&s_tfree), (ggroup - 1) & 1u, status, abort_flag);
+        // signal view: element (block row c, k) at 16 c + 2 k bytes from the window of (t, p) at 16 jc
+        const uint64_t bdesc0 = umma_desc(sig_base, /*lbo K*/ 16, /*sbo N*/ 128);
         int tp = 0, jc = jlo;
         for (int s = 0; s < steps; ++s, ++gstep) {
           const uint32_t ss = gstep % kSteps;
           warp_wait(smem_u32(&s_full[ss]), (gstep / kSteps) & 1u, status, abort_flag);
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-          if (lane == 0) {
+          if (lane == 0 && !no_mma) {
             const int kk0 = s * kPer, kend = min(kk0 + kPer, nk);
-            uint64_t bd = bdesc0 + (uint64_t)((ss * kPer * kChunkBytes) >> 4);
+            uint32_t ta = tmem + kAccCols + ss * (kPer * kChunkCols);
             for (int kk = kk0; kk < kend; ++kk) {
-              // signal view: element (row c, k) at 16 c + 2 k from the tile's first sample, k from 16 jc
-              const uint64_t ad = adesc0 + (uint64_t)(((tp * kSig + jc * 16) * 2) >> 4);
-              const uint32_t acc = kk > 0 ? 1u : 0u;
-              // tiles are 2048 bytes of signal apart
-              if (n_tiles > 1) umma_f16(tmem + kN, ad + 128, bd, idesc, acc);
-              umma_f16(tmem, ad, bd, idesc, acc);
-              bd += kChunkBytes >> 4;
+              const uint64_t bd = bdesc0 + (uint64_t)(((tp * kSig + jc * 16) * 2) >> 4);
+              umma_f16_ta(tmem, ta, bd, idesc, kk > 0 ? 1u : 0u);
+              ta += kChunkCols;
               if (++jc == kKC) { jc = jlo; ++tp; }
             }
             umma_commit(smem_u32(&s_empty[ss]));
@@ -338,7 +366,7 @@ __global__ void __launch_bounds__(kTPB, 2)
       //      (t, par, c, r) slot of kQW words at shift c; two q per 32-bit store ----
       for (int slot = warp; slot < 16 * kComps * 2; slot += kBuildWarps) {
         const int r = slot & 3, c = (slot >> 2) & (kComps - 1), tpar = (slot >> 4) & 1, t = slot >> 5;
-        uint32_t *dst = comp_w + slot * kQW + c;
+        uint32_t *dst = comp_w + slot * kQW + comp_shift(c, tpar);
         const float4 *tl = tapd + (r * 4 + t) * 128;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -361,24 +389,24 @@ __global__ void __launch_bounds__(kTPB, 2)
         }
       }
       builders_sync();
-      // table word bases of this thread's segment for input part p (Tx antenna added per chunk)
+      // table word bases of this thread's row for input part p (Tx antenna added per chunk)
       // (rows of absent Rx antennas read table r = 0 and write zeros)
       const int rq = rr < n_rx ? rr : 0;
       const uint32_t keep = rr < n_rx ? 0xFFFFFFFFu : 0u;
-      const int tb0 = comp_slot(0, par, c_p0, rq) * kQW + c_p0 + (qoff - par) / 2;
-      const int tb1 = comp_slot(0, par, c_p1, rq) * kQW + c_p1 + (qoff - par) / 2;
+      const int tb0 = comp_slot(0, par, c_p0, rq) * kQW + comp_shift(c_p0, par) + (qoff - par) / 2;
+      const int tb1 = comp_slot(0, par, c_p1, rq) * kQW + comp_shift(c_p1, par) + (qoff - par) / 2;
 
-      // ---- the symbol in groups of up to 4096 samples (4 tensor-memory tiles each) ----
+      // ---- the symbol in groups of up to kGroup samples (one accumulator of up to 192 columns) ----
       for (int gs = sym0; gs < sym1; gs += kGroup) {
         const int ge = min(gs + kGroup, sym1);
         const int blocks = (ge - gs + kB - 1) / kB;
-        const int n_tiles = (blocks + kRows - 1) / kRows;
+        const int ncols = (blocks + 15) & ~15;
         // signal: sig[t][p][u] = x_{t,p}[gs - 128 + u], 16-bit operands, zero past the slot end;
         // four samples per load (the window start is 8-aligned and N is a multiple of 8).  The
         // accumulators of the previous group are complete, so nothing reads the old signal.
         {
           const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
-          const int quads = (n_tiles * kRows * kB + kW) / 4;
+          const int quads = (ncols * kB + kW) / 4;
 #pragma unroll 2
           for (int qd = tid; qd < quads; qd += kBuilders) {
             const int u = qd * 4;
@@ -411,67 +439,105 @@ __global__ void __launch_bounds__(kTPB, 2)
             }
           }
         }
-        // tap chunks, kPer per step, into the step's ring slots once the MMAs of the step that
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the signal, for the tensor core
+        // tap chunks, kPer per step, into the step's ring columns once the MMAs of the step that
         // last used them are done; each warp then arrives on the step's full barrier
         int tp = 0, jc = jlo;
         for (int s = 0; s < steps; ++s, ++gstep) {
           const uint32_t ss = gstep % kSteps;
-          if (gstep >= kSteps) warp_wait(smem_u32(&s_empty[ss]), (gstep / kSteps - 1) & 1u, status, abort_flag);
+          if (gstep >= kSteps) {
+            warp_wait(smem_u32(&s_empty[ss]), (gstep / kSteps - 1) & 1u, status, abort_flag);
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+          }
           const int kk0 = s * kPer, kend = min(kk0 + kPer, nk);
-          uint16_t *wdst = wbuf + ss * kPer * (kN * 16) + w_off;
+          const uint32_t tdst = t_row + kAccCols + ss * (kPer * kChunkCols) + kg * 4;
 #pragma unroll
           for (int e = 0; e < kPer; ++e) {
             if (kk0 + e < kend) {
               const int t = tp >> 1, p = tp & 1;
               const uint32_t *src = comp_w + (p ? tb1 : tb0) + t * (2 * kComps * 4 * kQW) + jc * 8;
               const uint32_t ng = p ? neg_p1 : 0u;
-              *reinterpret_cast<uint4 *>(wdst + e * (kN * 16)) =
-                  make_uint4((src[0] ^ ng) & keep, (src[1] ^ ng) & keep, (src[2] ^ ng) & keep, (src[3] ^ ng) & keep);
+              tmem_st4(tdst + e * kChunkCols, (src[0] ^ ng) & keep, (src[1] ^ ng) & keep, (src[2] ^ ng) & keep,
+                       (src[3] ^ ng) & keep);
               if (++jc == kKC) { jc = jlo; ++tp; }
             }
           }
-          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          tmem_wait_st();
+          asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_u32(&s_full[ss]));
         }
-        // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (block rows) and samples
-        //      i in [4 (w / 4), 4 (w / 4) + 4) of each block; AWGN per pair of samples (one Philox block) ----
+        // ---- epilogue: warp w reads its lanes (rows 32 (w % 4) ..: samples i = 2 (w % 4) + lane / 16,
+        //      Rx r = (lane / 4) % 4, (part, A|B) = lane % 4) over every other 16-column chunk, starting
+        //      at chunk w / 4.  A 4 x 4 transpose among lanes 4g .. 4g + 3 gives lane 4g + j the four
+        //      (part, A|B) values of block row c0 + j; lanes l and l ^ 16 hold samples i and i + 1,
+        //      which share a Philox block.  Each lane computes one block per two block rows. ----
         warp_wait(smem_u32(&s_acc), ggroup & 1u, status, abort_flag);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
         {
-          const int quad = warp & 3, ihalf = warp >> 2;
+          const int j4 = lane & 3, hi16 = lane >> 4, r = (lane >> 2) & 3;
+          const int i_me = quad * 2 + hi16;
           const float rl = 1.0f / (float)(sym1 - sym0);
-          for (int mt = 0; mt < n_tiles; ++mt) {
-            const int c = mt * kRows + quad * 32 + lane;
-            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(mt * kN + ihalf * 4 * 16);
+          const bool live_r = r < n_rx;
+          const float nstd = U->noise_std;
+          for (int cc = kg; cc * 16 < ncols; cc += 2) {
+            uint32_t raw[16];
+            tmem_ld16(t_row + (uint32_t)(cc * 16), raw);
+            tmem_wait_ld();
+            float u[4][4];
 #pragma unroll
-            for (int q = 0; q < 4; q += 2) {
-              uint32_t v0[16], v1[16];  // samples i and i + 1 of this lane's block row: 16 columns each
-              tmem_ld16(tbase + (uint32_t)q * 16, v0);
-              tmem_ld16(tbase + (uint32_t)(q + 1) * 16, v1);
-              tmem_wait_ld();
-              const int i = ihalf * 4 + q;
-              const int m = gs + c * kB + i;  // even: pairs (m, m + 1) share a Philox block
-              if (m < ge) {
-                const float tau0 = (float)(m - sym0) * rl, tau1 = (float)(m + 1 - sym0) * rl;
-                const uint64_t mabs = it.slot * (uint64_t)n + (uint64_t)m;
+            for (int qd = 0; qd < 4; ++qd) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                  if (r >= n_rx) break;
-                  float2 y0 = make_float2(fmaf(tau0, __uint_as_float(v0[r * 4 + 1]), __uint_as_float(v0[r * 4 + 0])),
-                                          fmaf(tau0, __uint_as_float(v0[r * 4 + 3]), __uint_as_float(v0[r * 4 + 2])));
-                  float2 y1 = make_float2(fmaf(tau1, __uint_as_float(v1[r * 4 + 1]), __uint_as_float(v1[r * 4 + 0])),
-                                          fmaf(tau1, __uint_as_float(v1[r * 4 + 3]), __uint_as_float(v1[r * 4 + 2])));
-                  if (U->noise_std > 0.f)
-                    tt_awgn_add_pair(U->seed, U->ue_id, (uint32_t)r, mabs, U->noise_std, y0, y1);
-                  const size_t o = (size_t)(slot_pos * n_rx + r) * n + m;
-                  if (U->out_f32) {
-                    *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(U->ring_out) + o) =
-                        make_float4(y0.x, y0.y, y1.x, y1.y);
-                  } else {
-                    *reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(U->ring_out) + o) =
-                        make_uint2(tt_pack_iq(y0.x, y0.y), tt_pack_iq(y1.x, y1.y));
-                  }
+              for (int e = 0; e < 4; ++e) u[qd][e] = __uint_as_float(raw[qd * 4 + e]);
+              transpose4(u[qd], j4);
+            }
+            // block quads (0, 1) and (2, 3): lane l computes the Philox block of its (r, sample pair)
+            // at quad 2h + hi16 and trades half of it with lane l ^ 16
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int c_mine = cc * 16 + (2 * h + hi16) * 4 + j4;      // block row of the block I compute
+              const int m_pair = gs + c_mine * kB + quad * 2;              // even sample of that pair
+              uint4 wv = make_uint4(0u, 0u, 0u, 0u);
+              if (nstd > 0.f && live_r) {
+                const uint64_t pabs = (it.slot * (uint64_t)n + (uint64_t)m_pair) >> 1;
+                wv = tt_philox4x32_10(make_uint4((uint32_t)pabs, (uint32_t)(pabs >> 32), U->ue_id, (uint32_t)r),
+                                      (uint32_t)U->seed, (uint32_t)(U->seed >> 32));
+              }
+              // hi16 = 0 keeps words 0, 1 (its even sample) of its own block, quad 2h; hi16 = 1 keeps
+              // words 2, 3 (its odd sample) of its own block, quad 2h + 1
+              const uint32_t s0 = hi16 ? wv.x : wv.z, s1 = hi16 ? wv.y : wv.w;
+              const uint32_t g0 = __shfl_xor_sync(0xFFFFFFFFu, s0, 16), g1 = __shfl_xor_sync(0xFFFFFFFFu, s1, 16);
+              // my sample at quad 2h (uses the partner's block when hi16 = 1) and at quad 2h + 1
+              float2 y[2];
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int qd = 2 * h + e;
+                const int c = cc * 16 + qd * 4 + j4;
+                const int m = gs + c * kB + i_me;
+                const float tau = (float)(m - sym0) * rl;
+                y[e] = make_float2(fmaf(tau, u[qd][1], u[qd][0]), fmaf(tau, u[qd][3], u[qd][2]));
+                if (nstd > 0.f) {
+                  // words of my sample: quad 2h + hi16 is my own block, the other quad the partner's
+                  const bool own = e == hi16;
+                  const uint32_t w0 = own ? (hi16 ? wv.z : wv.x) : g0, w1 = own ? (hi16 ? wv.w : wv.y) : g1;
+                  tt_box_muller_add(w0, w1, nstd, y[e]);
+                }
+              }
+              // lane l (hi16 = 0) stores the pair (i, i + 1) of quad 2h, lane l ^ 16 that of quad 2h + 1
+              const float2 give = hi16 ? y[0] : y[1];
+              const float2 got = make_float2(__shfl_xor_sync(0xFFFFFFFFu, give.x, 16),
+                                             __shfl_xor_sync(0xFFFFFFFFu, give.y, 16));
+              const float2 ylo = hi16 ? got : y[0], yhi = hi16 ? y[1] : got;  // samples i_even, i_even + 1
+              const int c_st = cc * 16 + (2 * h + hi16) * 4 + j4;
+              const int m_st = gs + c_st * kB + quad * 2;
+              if (live_r && c_st < blocks && m_st < ge) {
+                const size_t o = (size_t)(slot_pos * n_rx + r) * n + m_st;
+                if (U->out_f32) {
+                  *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(U->ring_out) + o) =
+                      make_float4(ylo.x, ylo.y, yhi.x, yhi.y);
+                } else {
+                  *reinterpret_cast<uint2 *>(reinterpret_cast<uint32_t *>(U->ring_out) + o) =
+                      make_uint2(tt_pack_iq(ylo.x, ylo.y), tt_pack_iq(yhi.x, yhi.y));
                 }
               }
             }
@@ -505,10 +571,10 @@ size_t tt_tc_smem_bytes() { return (size_t)kSmemBytes; }
 int tt_tc_max_delay() { return kMaxDelayTC; }
 int tt_tc_items_per_slot(const int32_t *sym_len, int nsym) {
   (void)sym_len;
-  return nsym;  // one work item per symbol; its samples run in groups of up to 4096
+  return nsym;  // one work item per symbol; its samples run in groups of up to 1536
 }
 
-cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, cudaStream_t st) {
+cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, int no_mma, cudaStream_t st) {
   auto kern = fp16 ? tt_toeplitz_tc_kernel<true> : tt_toeplitz_tc_kernel<false>;
   static bool attr[2] = {false, false};
   if (!attr[fp16]) {
@@ -524,6 +590,6 @@ cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, cud
     return cudaSuccess;
   }
   if (L.grid == 0 || L.total_items == 0) return cudaSuccess;
-  kern<<<L.grid, kTPB, kSmemBytes, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter, status);
+  kern<<<L.grid, kTPB, kSmemBytes, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter, status, no_mma);
   return cudaGetLastError();
 }
