@@ -104,7 +104,7 @@ struct tt_engine {
   TTSeg *d_tcsegs = nullptr;                // work list of the tensor-core channels
   size_t tcseg_cap = 0;
   int *d_status = nullptr;                  // set by a kernel whose bounded wait expired
-  int tc_no_mma = 0;                        // tests only (TT_TEST_TC_NO_MMA=1 at creation): no MMA is issued
+  int tc_no_mma = 0;                        // tests only (TT_TEST_TC_NO_MMA=1 at a run): no MMA is issued
   std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
   std::vector<tt_cell *> cells;             // uplink aggregation cells
   std::vector<TTSosJob> sos_jobs;           // synthesis work list of the current run (host copy)
@@ -619,6 +619,10 @@ tt_status launch_cached_graph(tt_engine *e, const std::vector<tt_chan *> &chans,
 
 // Tensor-core channels: one item per (UE, slot, symbol), BF16 and FP16 channels in separate launches.
 tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
+  {  // failure-detection tests: the kernel issues no MMA, so its bounded waits run out
+    const char *v = std::getenv("TT_TEST_TC_NO_MMA");
+    e->tc_no_mma = (v && v[0] == '1') ? 1 : 0;
+  }
   std::vector<TTSeg> segs;
   int n16 = 0;
   for (int pass = 0; pass < 2; ++pass)  // BF16 channels first, then FP16
@@ -703,10 +707,6 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   e->max_ues = cfg->max_ues ? cfg->max_ues : 1024;
   e->spt_override = cfg->samples_per_thread;
   e->persistent = cfg->persistent;
-  {  // failure-detection tests: the tensor-core kernel issues no MMA, so its bounded waits run out
-    const char *v = std::getenv("TT_TEST_TC_NO_MMA");
-    e->tc_no_mma = (v && v[0] == '1') ? 1 : 0;
-  }
   e->graphs = cfg->struct_size >= offsetof(tt_engine_config, graphs) + sizeof(uint32_t) && cfg->graphs != 0;
   cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
   e->table.assign(e->max_ues, nullptr);

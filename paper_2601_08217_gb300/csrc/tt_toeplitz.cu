@@ -55,7 +55,10 @@ constexpr int kSig = kGroup + kW;     // staged samples per (t, p)
 constexpr uint32_t kTmemCols = 256;   // two CTAs per SM share the 512 columns
 constexpr uint32_t kAccCols = kNMax;  // accumulator columns [0, 192)
 constexpr uint32_t kChunkCols = 8;    // one K-chunk of A: 128 lanes x 16 16-bit values
-constexpr long long kSpinLimit = 1ll << 24;
+// Bounded waits: each poll may suspend the thread for up to kSuspendNs until the phase completes
+// (the thread wakes when it does), so 2^20 polls bound a wait at about one second.
+constexpr long long kSpinLimit = 1ll << 20;
+constexpr uint32_t kSuspendNs = 1000;
 
 constexpr int kQW = 88;               // words per component table: q = j - i + 8 in [1, 151] needs 76, plus shift <= 8
 constexpr int kComps = 4;             // hr, hi of H and of dH; -hi is hi with the sign bits flipped
@@ -127,9 +130,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
   uint32_t ok;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(mbar), "r"(phase)
+      : "r"(mbar), "r"(phase), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -146,12 +149,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+// The same wait, tied to the 16 registers of an earlier tmem_ld16 so that no use of them is
+// scheduled before the data has arrived.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t *r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
 
-// 4 consecutive columns of this thread's lane (32-bit each); complete at tmem_wait_st().
+// 4 consecutive columns of this thread's lane (32-bit each); complete at tmem_wait_st().  It touches
+// tensor memory only (no memory clobber), so the shared-memory loads of later chunks may be issued
+// ahead of it; tcgen05.wait::st orders it before the step's barrier arrival.
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(taddr), "r"(a), "r"(b), "r"(c),
-               "r"(d)
-               : "memory");
+               "r"(d));
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
@@ -203,6 +216,8 @@ __device__ __forceinline__ void warp_wait(uint32_t mbar, uint32_t phase, int *st
 
 }  // namespace
 
+// Two CTAs per SM: 18 warps, five on some SM sub-partition, whose 16,384 registers then allow 96 a
+// thread (5 warps x 32 x 96 = 15,360); the launch bounds give the compiler that limit.
 template <bool FP16>
 __global__ void __launch_bounds__(kTPB, 2)
     tt_toeplitz_tc_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
@@ -451,17 +466,28 @@ __global__ void __launch_bounds__(kTPB, 2)
           }
           const int kk0 = s * kPer, kend = min(kk0 + kPer, nk);
           const uint32_t tdst = t_row + kAccCols + ss * (kPer * kChunkCols) + kg * 4;
+          uint32_t wv[kPer][4];
+          // every chunk of the step loads (a chunk past the end re-reads the last one and stores
+          // nothing), so the step's 16 loads are independent and all in flight at once
+          const uint32_t *srcs[kPer];
+          uint32_t ngs[kPer];
 #pragma unroll
           for (int e = 0; e < kPer; ++e) {
-            if (kk0 + e < kend) {
-              const int t = tp >> 1, p = tp & 1;
-              const uint32_t *src = comp_w + (p ? tb1 : tb0) + t * (2 * kComps * 4 * kQW) + jc * 8;
-              const uint32_t ng = p ? neg_p1 : 0u;
-              tmem_st4(tdst + e * kChunkCols, (src[0] ^ ng) & keep, (src[1] ^ ng) & keep, (src[2] ^ ng) & keep,
-                       (src[3] ^ ng) & keep);
-              if (++jc == kKC) { jc = jlo; ++tp; }
-            }
+            const int t = tp >> 1, p = tp & 1;
+            srcs[e] = comp_w + (p ? tb1 : tb0) + t * (2 * kComps * 4 * kQW) + jc * 8;
+            ngs[e] = p ? neg_p1 : 0u;
+            if (kk0 + e + 1 < kend && ++jc == kKC) { jc = jlo; ++tp; }
           }
+          if (kend - kk0 == kPer && ++jc == kKC) { jc = jlo; ++tp; }  // advance past the step's last chunk
+#pragma unroll
+          for (int e = 0; e < kPer; ++e)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) wv[e][q] = srcs[e][q];
+#pragma unroll
+          for (int e = 0; e < kPer; ++e)
+            if (kk0 + e < kend)
+              tmem_st4(tdst + e * kChunkCols, (wv[e][0] ^ ngs[e]) & keep, (wv[e][1] ^ ngs[e]) & keep,
+                       (wv[e][2] ^ ngs[e]) & keep, (wv[e][3] ^ ngs[e]) & keep);
           tmem_wait_st();
           asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
           __syncwarp();
@@ -483,18 +509,18 @@ __global__ void __launch_bounds__(kTPB, 2)
           for (int cc = kg; cc * 16 < ncols; cc += 2) {
             uint32_t raw[16];
             tmem_ld16(t_row + (uint32_t)(cc * 16), raw);
-            tmem_wait_ld();
-            float u[4][4];
-#pragma unroll
-            for (int qd = 0; qd < 4; ++qd) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) u[qd][e] = __uint_as_float(raw[qd * 4 + e]);
-              transpose4(u[qd], j4);
-            }
+            tmem_wait_ld16(raw);
             // block quads (0, 1) and (2, 3): lane l computes the Philox block of its (r, sample pair)
             // at quad 2h + hi16 and trades half of it with lane l ^ 16
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
+              float u[2][4];
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) u[e][q] = __uint_as_float(raw[(2 * h + e) * 4 + q]);
+                transpose4(u[e], j4);
+              }
               const int c_mine = cc * 16 + (2 * h + hi16) * 4 + j4;      // block row of the block I compute
               const int m_pair = gs + c_mine * kB + quad * 2;              // even sample of that pair
               uint4 wv = make_uint4(0u, 0u, 0u, 0u);
@@ -515,7 +541,7 @@ __global__ void __launch_bounds__(kTPB, 2)
                 const int c = cc * 16 + qd * 4 + j4;
                 const int m = gs + c * kB + i_me;
                 const float tau = (float)(m - sym0) * rl;
-                y[e] = make_float2(fmaf(tau, u[qd][1], u[qd][0]), fmaf(tau, u[qd][3], u[qd][2]));
+                y[e] = make_float2(fmaf(tau, u[e][1], u[e][0]), fmaf(tau, u[e][3], u[e][2]));
                 if (nstd > 0.f) {
                   // words of my sample: quad 2h + hi16 is my own block, the other quad the partner's
                   const bool own = e == hi16;
