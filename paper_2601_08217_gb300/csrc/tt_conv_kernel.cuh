@@ -90,7 +90,9 @@ struct TTItem {
   unsigned long long slot;
   unsigned long long idx0;  // trace entry of the item's first anchor (per-symbol traces)
   int ue, g0, gend, jf, nst, valid;
+  int slot_pos;             // ring position of the slot: slot mod ring_q (once per item, not per thread)
 };
+
 
 // Thread 0: item index -> (UE, slot, groups, first symbol, symbols touched).
 // With device cursors (graph replay), a run's first slot is cursors[ue] instead of seg.first_slot.
@@ -123,6 +125,7 @@ __device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, cons
   it.gend = min(g0 + TT_TPB, U->groups);
   it.jf = jf;
   it.nst = ci >> 16;
+  it.slot_pos = (int)(slot % (uint64_t)U->ring_q);
   it.valid = 1;
 }
 
@@ -134,7 +137,7 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
   const int n = U->n, n_tx = U->n_tx, Q = U->ring_q, K = U->n_taps, dpad = U->dpad;
   const int ws = it.g0 * S - dpad;
   const int wlen = (it.gend - it.g0) * S + dpad;
-  const int slot_pos = (int)(it.slot % (uint64_t)Q);
+  const int slot_pos = it.slot_pos;
   const uint32_t *__restrict__ rin = reinterpret_cast<const uint32_t *>(U->ring_in);
   constexpr int V = S >= 4 ? 4 : 1;  // samples per copy: 16-byte copies when windows are 4-aligned
   for (int t = 0; t < n_tx; ++t) {
@@ -194,7 +197,7 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
 
 // All threads, after the copies landed: raw window -> phase planes, taps -> (H0, dH),
 // delays -> plane offsets.
-template <int S, int NRX, int NP, bool TOPN>
+template <int S, int NRX, int NP, bool TOPN, int WMAXC>
 __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, const TTItem &it,
                                                 const uint32_t *raw, int wmax, float2 *planes, float4 *taps,
                                                 int *dly, int tid) {
@@ -204,15 +207,26 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
     const uint32_t *rt = raw + t * wmax;
     float2 *pl = planes + t * (2 * S * NP);
     if constexpr (S >= 4) {
-      for (int e = 4 * tid; e < wlen; e += 4 * TT_TPB) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(rt + e);
-        const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
-        const int beta = e % S, i = e / S;
+      // every 16-byte load of the thread first (at most NV), then the unpacking and plane stores
+      constexpr int NV = (WMAXC + 4 * TT_TPB - 1) / (4 * TT_TPB);
+      uint4 v[NV];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float2 xv = tt_unpack_iq(vv[c]);
-          pl[(beta + c) * NP + i + 1] = xv;
-          pl[(beta + c + S) * NP + i] = xv;
+      for (int q = 0; q < NV; ++q) {
+        const int e = 4 * tid + q * 4 * TT_TPB;
+        if (e < wlen) v[q] = *reinterpret_cast<const uint4 *>(rt + e);
+      }
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int e = 4 * tid + q * 4 * TT_TPB;
+        if (e < wlen) {
+          const uint32_t vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+          const int beta = e % S, i = e / S;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float2 xv = tt_unpack_iq(vv[c]);
+            pl[(beta + c) * NP + i + 1] = xv;
+            pl[(beta + c + S) * NP + i] = xv;
+          }
         }
       }
     } else {
@@ -343,7 +357,7 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
 
   const float nstd = U->noise_std;
   const uint64_t m0 = it.slot * (uint64_t)n + (uint64_t)w_me;
-  const int slot_pos = (int)(it.slot % (uint64_t)U->ring_q);
+  const int slot_pos = it.slot_pos;
 #pragma unroll
   for (int r = 0; r < NRX; ++r) {
     if (nstd > 0.f) {
@@ -431,7 +445,7 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     tt_issue_item<S, NRX, TOPN>(U, it, raw, WMAX, taps0, dly0, s_sym[0], tid);
     tt_cp_async_wait_all();
     __syncthreads();
-    tt_convert_item<S, NRX, NP, TOPN>(U, it, raw, WMAX, planes, taps0, dly0, tid);
+    tt_convert_item<S, NRX, NP, TOPN, WMAX>(U, it, raw, WMAX, planes, taps0, dly0, tid);
     if (tid == 0) tt_locate(ues, segs, n_segs, s_claim, total_items, cursors, s_it[1]);
     __syncthreads();
   }
@@ -445,12 +459,13 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     const TTUEDesc *Un = ues + nxt.ue;
     if (nxt.valid) tt_issue_item<S, NRX, TOPN>(Un, nxt, raw, WMAX, tn, dn, s_sym[cb ^ 1], tid);
     tt_compute_item<S, NRX, NP, TOPN>(ues + cur.ue, cur, planes, tc, dc, s_sym[cb], tid);
+    // claimed after the arithmetic: claiming before it measured 4.5% slower on the 16-UE step
     uint32_t nn = 0;
     if (tid == 0 && nxt.valid) nn = claim();
     tt_cp_async_wait_all();
     __syncthreads();
     if (!nxt.valid) return;
-    tt_convert_item<S, NRX, NP, TOPN>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
+    tt_convert_item<S, NRX, NP, TOPN, WMAX>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
     if (tid == 0) tt_locate(ues, segs, n_segs, nn, total_items, cursors, s_it[cb]);
     __syncthreads();
     cb ^= 1;
