@@ -426,7 +426,11 @@ def run_serving(args, device, n_ues=512, duration=2.0, warmup=0.2, plain_duratio
                      "refused_requests": rep["refused"], "ue_slots_per_s": rep["throughput"],
                      "p50_us": rep["p50_us"], "p99_us": rep["p99_us"], "p999_us": rep["p999_us"],
                      "max_us": rep["max_us"], "deadline_misses": rep["deadline_misses"],
-                     "mean_batch": rep["mean_batch"], "batches": rep["batches"]}
+                     "mean_batch": rep["mean_batch"], "batches": rep["batches"],
+                     "gpu_us_per_batch": rep["gpu_us_per_batch"], "gpu_busy": rep["gpu_busy"],
+                     "stamp_error_us": rep["stamp_error_us"],
+                     "latency": "device completion stamp (%globaltimer, calibrated to the host steady clock) "
+                                "minus the request's host arrival time"}
     out["p99_under_deadline"] = out["batched"]["p99_us"] < 500.0
     return out
 

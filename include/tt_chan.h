@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define TT_CHAN_ABI_VERSION 2
+#define TT_CHAN_ABI_VERSION 3
 
 typedef struct tt_engine tt_engine; /* one per GPU: stream, HBM budget, form, UE table */
 typedef struct tt_chan tt_chan;     /* one per UE link: config, trace, delay line, rings */
@@ -191,17 +191,18 @@ tt_status tt_engine_get_stats(tt_engine *e, tt_engine_stats *out);
  * (may be NULL) receives the number of classes that had a choice to make. */
 tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned);
 
-/* Serving form.  Runs a request loop on the calling thread for warmup_s +
+/* Serving benchmark.  Generates requests on the calling thread for warmup_s +
  * duration_s seconds: every channel with a trace receives slot-push requests
  * at Poisson times (mean inter-arrival slot_period_us, plus uniform
  * +-jitter_us, kept increasing).  A request commits the UE's next slot in
  * place: the IQ the caller left at that ring position (device-resident input).
- * A request that finds the UE's ring full is refused (counted, not queued).
- * Continuous batching: whenever requests are pending and fewer than
- * max_inflight_batches batches run, everything pending is launched as one
- * batch (any UEs, several slots of one UE allowed); requests that arrive
- * meanwhile join the next batch.  Latency = completion seen by the host
- * (event polled) minus arrival, for requests that arrived after the warm-up.
+ * The requests go through the serving path of tt_server_start (started and
+ * stopped by this call): its batching thread launches them, and their latency
+ * is the device-stamped completion of their batch minus their arrival.  A
+ * request that finds the UE's ring full waits in a per-UE queue of 64 and is
+ * committed, with its own arrival time, when completed slots free the ring;
+ * only a request that finds that queue full is refused.  Latencies count the
+ * requests that arrived after the warm-up.
  * release_outputs = 1 frees each output ring position as soon as it is
  * complete, the rings of uplink aggregation cells included; 0 keeps the
  * outputs for tt_chan_pull_* / tt_cell_pull_slots (rings then fill up). */
@@ -214,17 +215,71 @@ typedef struct {
   double deadline_us;             /* latency bound counted as a miss (0 = 500) */
   uint64_t seed;                  /* arrival-process seed */
   uint32_t release_outputs;
-  uint32_t max_inflight_batches;  /* 0 = 2 (one running, one forming) */
+  uint32_t max_inflight_batches;  /* as tt_server_config (0 = 3) */
 } tt_serve_config;
 
 typedef struct {
   uint64_t requests, refused, completed, batches, deadline_misses;
   double mean_batch;              /* requests per batch */
   double throughput;              /* completed requests (UE-slots) per second of the measured window */
-  double p50_us, p99_us, p999_us, max_us, mean_us;
+  double p50_us, p99_us, p999_us, max_us, mean_us;  /* device-stamped completion - arrival */
+  double stamp_error_us, gpu_us_per_batch, gpu_busy; /* as tt_server_report */
 } tt_serve_report;
 
 tt_status tt_engine_serve(tt_engine *e, const tt_serve_config *cfg, tt_serve_report *out);
+
+/* Serving with callers' own pushes (spec: continuous batching of slot pushes from many UEs
+ * as they arrive; Sec. III-C: per-UE isolation).  tt_server_start starts an engine-owned batching
+ * thread.  From then on every slot pushed by any thread, through tt_chan_push_slot(s)(_dev),
+ * tt_engine_push_slots or tt_chan_commit_slots, is a request.  Its arrival time is the push call's
+ * host steady-clock time.  The thread launches whatever is pending as one batch whenever fewer
+ * than max_inflight_batches run, so requests that arrive while others are on the GPU join the
+ * next batch.  tt_engine_run from any other thread returns TT_ERR_STATE meanwhile.
+ *
+ * Back-pressure is a queue, not a refusal: a push that finds its slot ring full waits (the calling
+ * thread blocks) until completed, released outputs free room, for up to queue_timeout_us.  Only
+ * then does it return TT_ERR_AGAIN (counted as refused).
+ *
+ * Each batch's completion is stamped on the device: a one-thread kernel after the batch's kernels
+ * writes %globaltimer into pinned host memory.  tt_server_start calibrates that clock against the
+ * host steady clock (the shortest of 32 launch round trips, uncertainty = half of it).  A request's
+ * latency is its batch's device stamp, on the host clock, minus its arrival.  tt_server_stop waits
+ * for every launched batch, stops the thread and fills the report.  The batching thread polls the
+ * running batch without the engine lock, so pushing threads are not kept waiting by it. */
+typedef struct {
+  uint32_t struct_size;           /* sizeof(tt_server_config) */
+  uint32_t max_inflight_batches;  /* 0 = 3 (one running, one queued behind it, one forming) */
+  uint32_t release_outputs;       /* 1: completed slots' outputs are released without pulls */
+  int32_t queue_timeout_us;       /* wait of a push into a full ring: 0 = 1 s, < 0 = no wait */
+  double deadline_us;             /* latency counted as a deadline miss above this (0 = 500) */
+  double warmup_us;               /* requests arriving earlier after the start are not counted */
+  double coalesce_us;             /* while a batch runs, the next one forms until its oldest request
+                                     has waited this long (0 = 20); with none running it launches at once */
+} tt_server_config;
+
+typedef struct {
+  uint32_t struct_size;           /* sizeof(tt_server_report) */
+  uint64_t requests;              /* slots pushed while serving (warm-up included) */
+  uint64_t completed;             /* requests after the warm-up whose latency was measured */
+  uint64_t queued;                /* pushes that found the ring full and waited for room */
+  uint64_t refused;               /* pushes whose wait ran out (TT_ERR_AGAIN) */
+  uint64_t batches, deadline_misses;
+  double mean_batch;              /* requests per batch */
+  double p50_us, p99_us, p999_us, max_us, mean_us, min_us;
+  double stamp_error_us;          /* uncertainty of the device-clock calibration */
+  double gpu_us_per_batch;        /* device time from a batch's first kernel to its completion stamp */
+  double gpu_busy;                /* those times' sum over the span from the first start to the last end */
+} tt_server_report;
+
+tt_status tt_server_start(tt_engine *e, const tt_server_config *cfg);
+tt_status tt_server_stop(tt_engine *e, tt_server_report *out);
+
+/* Admission with a waiting list: like tt_chan_create, but a channel that does not fit the HBM
+ * budget waits (the calling thread blocks) until channels destroyed on this engine free enough
+ * memory, or for timeout_us (< 0: no limit).  Waiters are admitted in arrival order: a later
+ * request does not overtake an earlier one that still waits.  TT_ERR_NO_MEMORY when the wait runs
+ * out; other errors as tt_chan_create. */
+tt_status tt_chan_create_queued(tt_engine *e, const tt_chan_config *cfg, int64_t timeout_us, tt_chan **out);
 
 /* ---------------------------------------------------------------- channel */
 
@@ -316,7 +371,8 @@ tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n);
 
 /* Pull the oldest not-yet-pulled slot into a host buffer [n_rx][N][2].
  * Waits at most timeout_us for it to complete (0: do not wait, < 0: no limit);
- * TT_ERR_AGAIN if it has not been launched, TT_ERR_TIMEOUT if it is still running. */
+ * TT_ERR_AGAIN if it has not been launched (or nothing was pushed yet), TT_ERR_TIMEOUT if it is still
+ * running. */
 tt_status tt_chan_pull_slot(tt_chan *c, uint64_t *slot, void *iq_out, int64_t timeout_us);
 
 /* Pull slots [first, first+n) (must be the oldest not yet pulled) into a host

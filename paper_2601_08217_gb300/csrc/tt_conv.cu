@@ -125,6 +125,19 @@ __global__ void __launch_bounds__(256) tt_plain_kernel(const TTUEDesc *__restric
   }
 }
 
+// Completion stamp of a batch: the device's global nanosecond timer, written by one thread after
+// every earlier kernel of the stream has finished.
+__global__ void tt_stamp_kernel(unsigned long long *dst) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *dst = t;
+}
+
+cudaError_t tt_launch_stamp(unsigned long long *dst, cudaStream_t st) {
+  tt_stamp_kernel<<<1, 1, 0, st>>>(dst);
+  return cudaGetLastError();
+}
+
 cudaError_t tt_launch_plain(const TTUEDesc *ue_dev, uint64_t slot, int n, cudaStream_t st) {
   const int tpb = 256;
   tt_plain_kernel<<<(n + tpb - 1) / tpb, tpb, 0, st>>>(ue_dev, slot);

@@ -26,9 +26,10 @@
 #include <vector>
 
 #include "tt_chan.h"
+#include "tt_engine_impl.h"
 #include "tt_internal.h"
 
-namespace {
+namespace ttx {
 
 thread_local std::string g_err;
 
@@ -42,138 +43,28 @@ tt_status fail(tt_status s, const char *fmt, ...) {
   return s;
 }
 
-#define TT_CK(call)                                                                   \
-  do {                                                                                \
-    cudaError_t e_ = (call);                                                          \
-    if (e_ != cudaSuccess) return fail(TT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
-
 int64_t now_us() {
   return std::chrono::duration_cast<std::chrono::microseconds>(
              std::chrono::steady_clock::now().time_since_epoch())
       .count();
 }
 
-}  // namespace
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
 
-struct tt_chan;
+}  // namespace ttx
 
-struct tt_cell;
+using ttx::fail;
+using ttx::now_ns;
+using ttx::now_us;
 
-struct tt_engine {
-  int device = 0;
-  uint64_t budget = 0;
-  uint64_t in_use = 0;
-  uint32_t form = TT_FORM_BATCHED;
-  uint32_t max_ues = 1024;
-  uint32_t spt_override = 0;
-  uint32_t persistent = 0;
-  int num_sms = 1;
-  cudaStream_t stream = nullptr;  // all compute and device copies, in order
-  cudaStream_t copy = nullptr;    // host pulls
-  cudaStream_t h2d = nullptr;     // host pushes: wait only for kernels that still read the overwritten ring slots
-  // Kernel variants of one run go on parallel branches (side streams forked from and joined
-  // back to `stream`), so each variant's tail overlaps the others' work.
-  static constexpr int kSide = 3;
-  cudaStream_t side[kSide] = {};
-  cudaEvent_t fork = nullptr, join[kSide] = {};
-  std::mutex mu;
-  std::vector<tt_chan *> table;   // UE table slot -> channel
-  TTUEDesc *d_ues = nullptr;
-  TTSeg *d_segs = nullptr;
-  size_t seg_cap = 0;
-  uint32_t *d_counters = nullptr;  // one work counter per launch class
-  int counter_cap = 64;
-  uint64_t launch_seq = 0;         // batches issued
-  uint64_t completed_seq = 0;      // batches known complete
-  std::deque<std::pair<uint64_t, cudaEvent_t>> events;  // (seq, event) not yet known complete
-  std::vector<cudaEvent_t> pool;
-  uint64_t launches = 0, slots_processed = 0;
-  // CUDA-graph replay of the batched launch (tt_engine_config.graphs)
-  bool graphs = false;
-  unsigned long long *d_cursors = nullptr;  // device-resident next slot of every UE table entry
-  TTSeg *d_gsegs = nullptr;                 // work list owned by the cached graph
-  size_t gseg_cap = 0;
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<uint64_t> gkey;               // shape of the cached graph
-  std::vector<tt_chan *> gchans;            // channels of the cached graph, in table order
-  std::vector<uint64_t> gcounts;            // their slots per run
-  std::vector<tt_chan *> gplan_chans;       // the same channels in the graph's segment order
-  uint64_t graph_builds = 0, graph_launches = 0;
-  uint64_t graph_nodes = 0;                 // tiled-kernel launches inside the cached graph
-  TTSeg *d_tcsegs = nullptr;                // work list of the tensor-core channels
-  size_t tcseg_cap = 0;
-  int *d_status = nullptr;                  // set by a kernel whose bounded wait expired
-  int tc_no_mma = 0;                        // tests only (TT_TEST_TC_NO_MMA=1 at a run): no MMA is issued
-  std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
-  std::vector<tt_cell *> cells;             // uplink aggregation cells
-  std::vector<TTSosJob> sos_jobs;           // synthesis work list of the current run (host copy)
-  TTSosJob *d_sos = nullptr;                // and its device copy
-  size_t sos_cap = 0;
-  std::vector<TTRetimeJob> retime_jobs;     // timed-trace anchor work list of the current run
-  TTRetimeJob *d_retime = nullptr;
-  size_t retime_cap = 0;
-  std::vector<TTTopnJob> topn_jobs;         // tap-selection work list of the current run
-  TTTopnJob *d_topn = nullptr;
-  size_t topn_cap = 0;
-};
-
-struct tt_chan {
-  tt_engine *e = nullptr;
-  uint32_t index = 0;
-  tt_chan_config cfg{};
-  std::vector<uint32_t> sym_len;
-  int n = 0, Q = 0, hist = 0;
-  size_t slot_in_elems = 0, slot_out_elems = 0;  // int16 values per slot
-  int16_t *d_in = nullptr, *d_out = nullptr;
-  uint64_t ring_bytes = 0;
-  float2 *d_taps = nullptr;
-  int32_t *d_delays = nullptr;
-  uint64_t trace_bytes = 0;
-  bool has_trace = false;
-  int spt = 1, dclass = 0, max_sym_touched = 1;
-  int32_t *d_chunks = nullptr;  // per work item of a slot: first symbol | symbols touched << 16
-  int tap_need = 0;             // max symbols touched x n_rx x n_tx x K
-  size_t smem = 0;
-  TTUEDesc desc{};
-  bool started = false;
-  uint64_t pushed_end = 0, launched_end = 0, completed_end = 0, pulled_end = 0;
-  uint64_t start_slot = 0;           // first slot ever pushed
-  float4 *d_sparse = nullptr;        // sparse convolution: kept taps per anchor and link (ring)
-  int32_t *d_sparse_dly = nullptr;
-  uint64_t sparse_bytes = 0;
-  uint64_t dev_cursor = UINT64_MAX;  // what the engine's device cursor holds for this UE (after queued work)
-  std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
-  tt_cell *cell = nullptr;      // uplink aggregation cell consuming this channel's outputs
-  // sum-of-sinusoids synthesis: the trace is a ring of anchors refilled before each run
-  bool synth = false;
-  float *d_amp = nullptr;
-  double *d_freq = nullptr, *d_phase = nullptr;
-  int synth_m = 0;
-  double synth_fs = 0.0;
-  // timed trace (entries every src_step samples): d_taps is a ring of anchors refilled before each
-  // run by FP64 trace-time interpolation from the stored trace d_src
-  bool retime = false;
-  float2 *d_src = nullptr;
-  uint64_t src_T = 0;
-  double src_step = 0.0;
-  int src_loop = 0;
-};
-
-struct tt_cell {
-  tt_engine *e = nullptr;
-  tt_cell_config cfg{};
-  int n = 0, Q = 0;
-  size_t slot_out_elems = 0;    // int16 values per slot
-  int16_t *d_out = nullptr;
-  uint64_t ring_bytes = 0;
-  std::vector<tt_chan *> members;
-  TTCellMember *d_members = nullptr;
-  size_t members_cap = 0;
-  bool started = false;
-  uint64_t launched_end = 0, completed_end = 0, pulled_end = 0;
-  std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
-};
+#define TT_CK(call)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return fail(TT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
 
 namespace {
 
@@ -316,14 +207,21 @@ tt_status check_room(tt_chan *c, uint64_t first, uint32_t n) {
   return TT_OK;
 }
 
-void mark_pushed(tt_chan *c, uint64_t first, uint32_t n) {
+void mark_pushed_at(tt_chan *c, uint64_t first, uint32_t n, int64_t arrival_ns) {
   if (!c->started) {
     c->started = true;
     c->start_slot = first;
     c->pushed_end = c->launched_end = c->completed_end = c->pulled_end = first;
   }
   c->pushed_end = first + n;
+  if (!c->in_pending) {
+    c->in_pending = true;
+    c->e->pending.push_back(c);
+  }
+  if (c->e->server) ttx::server_note_push(c, first, n, arrival_ns);
 }
+
+void mark_pushed(tt_chan *c, uint64_t first, uint32_t n) { mark_pushed_at(c, first, n, now_ns()); }
 
 bool valid_chan(const tt_chan *c) { return c && c->e; }
 
@@ -677,15 +575,26 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
 
 }  // namespace
 
+namespace ttx {
+cudaEvent_t get_event(tt_engine *e) { return ::get_event(e); }
+cudaError_t update_completed(tt_engine *e) { return ::update_completed(e); }
+void update_chan(tt_chan *c) { ::update_chan(c); }
+tt_status check_room(tt_chan *c, uint64_t first, uint32_t n) { return ::check_room(c, first, n); }
+void mark_pushed(tt_chan *c, uint64_t first, uint32_t n) { ::mark_pushed(c, first, n); }
+void mark_pushed_at(tt_chan *c, uint64_t first, uint32_t n, int64_t arrival_ns) {
+  ::mark_pushed_at(c, first, n, arrival_ns);
+}
+}  // namespace ttx
+
 int32_t tt_set_error(int32_t status, const char *msg) {
-  g_err = msg ? msg : "";
+  ttx::g_err = msg ? msg : "";
   return status;
 }
 
 // =========================================================================
 extern "C" {
 
-const char *tt_last_error(void) { return g_err.c_str(); }
+const char *tt_last_error(void) { return ttx::g_err.c_str(); }
 int32_t tt_abi_version(void) { return TT_CHAN_ABI_VERSION; }
 
 tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
@@ -733,6 +642,7 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
 
 tt_status tt_engine_destroy(tt_engine *e) {
   if (!e) return fail(TT_ERR_INVALID, "null engine");
+  if (e->server) tt_server_stop(e, nullptr);  // its thread launches on this engine
   cudaSetDevice(e->device);
   if (e->stream) cudaStreamSynchronize(e->stream);
   for (tt_chan *c : e->table)
@@ -916,9 +826,11 @@ tt_status tt_chan_destroy(tt_chan *c) {
   cudaFree(c->d_sparse_dly);
   e->in_use -= c->ring_bytes + c->trace_bytes + c->sparse_bytes;
   e->table[c->index] = nullptr;
+  e->pending.erase(std::remove(e->pending.begin(), e->pending.end(), c), e->pending.end());
   drop_graph(e);
   c->e = nullptr;
   delete c;
+  ttx::admission_notify(e);  // channels waiting for budget may fit now
   return TT_OK;
 }
 
@@ -1294,6 +1206,7 @@ tt_status tt_chan_push_slots(tt_chan *c, uint64_t first, uint32_t n, const int16
   std::unique_lock<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
   tt_status s = check_room(c, first, n);
+  if (s == TT_ERR_AGAIN && e->server) s = ttx::server_wait_room(e, lk, [&] { return check_room(c, first, n); });
   if (s != TT_OK) return s;
   // On the push stream, after any queued kernel that still reads the ring positions being
   // overwritten (others keep running), then wait, with the engine unlocked, so the caller's
@@ -1313,6 +1226,7 @@ tt_status tt_chan_push_slots(tt_chan *c, uint64_t first, uint32_t n, const int16
   e->pool.push_back(ev);
   if (err != cudaSuccess) return fail(TT_ERR_CUDA, "push copy: %s", cudaGetErrorString(err));
   mark_pushed(c, first, n);
+  if (e->server) e->work_cv.notify_one();
   return TT_OK;
 }
 
@@ -1327,6 +1241,8 @@ tt_status tt_engine_push_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *c
     for (uint32_t j = 0; j < i; ++j)
       if (chans[j] == c) return fail(TT_ERR_INVALID, "push entry %u: channel repeated", i);
     tt_status s = check_room(c, first[i], n[i]);
+    if (s == TT_ERR_AGAIN && e->server)
+      s = ttx::server_wait_room(e, lk, [&] { return check_room(c, first[i], n[i]); });
     if (s != TT_OK) return s;
   }
   cudaEvent_t ev = get_event(e);
@@ -1350,6 +1266,7 @@ tt_status tt_engine_push_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *c
   if (err != cudaSuccess) return fail(TT_ERR_CUDA, "push copy: %s", cudaGetErrorString(err));
   for (uint32_t i = 0; i < n_chans; ++i)
     if (n[i]) mark_pushed(chans[i], first[i], n[i]);
+  if (e->server) e->work_cv.notify_one();
   return TT_OK;
 }
 
@@ -1358,9 +1275,10 @@ tt_status tt_chan_push_slots_dev(tt_chan *c, uint64_t first, uint32_t n, const i
   if (!valid_chan(c) || (!d_iq_in && n)) return fail(TT_ERR_INVALID, "tt_chan_push_slots_dev: bad argument");
   if (n == 0) return TT_OK;
   tt_engine *e = c->e;
-  std::lock_guard<std::mutex> lk(e->mu);
+  std::unique_lock<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
   tt_status s = check_room(c, first, n);
+  if (s == TT_ERR_AGAIN && e->server) s = ttx::server_wait_room(e, lk, [&] { return check_room(c, first, n); });
   if (s != TT_OK) return s;
   cudaEvent_t ev = get_event(e);
   if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
@@ -1372,6 +1290,7 @@ tt_status tt_chan_push_slots_dev(tt_chan *c, uint64_t first, uint32_t n, const i
   e->pool.push_back(ev);
   if (err != cudaSuccess) return fail(TT_ERR_CUDA, "push copy: %s", cudaGetErrorString(err));
   mark_pushed(c, first, n);
+  if (e->server) e->work_cv.notify_one();
   return TT_OK;
 }
 
@@ -1389,10 +1308,13 @@ tt_status tt_chan_slot_input(tt_chan *c, uint64_t slot, int16_t **d_ptr) {
 tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n) {
   if (!valid_chan(c)) return fail(TT_ERR_INVALID, "null channel");
   if (n == 0) return TT_OK;
-  std::lock_guard<std::mutex> lk(c->e->mu);
+  tt_engine *e = c->e;
+  std::unique_lock<std::mutex> lk(e->mu);
   tt_status s = check_room(c, first, n);
+  if (s == TT_ERR_AGAIN && e->server) s = ttx::server_wait_room(e, lk, [&] { return check_room(c, first, n); });
   if (s != TT_OK) return s;
   mark_pushed(c, first, n);
+  if (e->server) e->work_cv.notify_one();
   return TT_OK;
 }
 
@@ -1674,10 +1596,14 @@ tt_status tt_cell_destroy(tt_cell *cl) {
 tt_status tt_engine_run(tt_engine *e) {
   if (!e) return fail(TT_ERR_INVALID, "null engine");
   std::lock_guard<std::mutex> lk(e->mu);
+  if (e->server && !ttx::is_server_thread(e))
+    return fail(TT_ERR_STATE, "a server is running on this engine: it launches the pushed slots itself");
   TT_CK(cudaSetDevice(e->device));
   std::vector<tt_chan *> ready, tc_ready;
-  for (tt_chan *c : e->table)
-    if (c && c->has_trace && c->started && c->pushed_end > c->launched_end) {
+  // the channels with unlaunched slots, in table order (the order the plan and a cached graph use)
+  std::sort(e->pending.begin(), e->pending.end(), [](const tt_chan *a, const tt_chan *b) { return a->index < b->index; });
+  for (tt_chan *c : e->pending)
+    if (c->has_trace && c->started && c->pushed_end > c->launched_end) {
       if (c->cfg.precision != TT_FP32 && e->form != TT_FORM_PLAIN) tc_ready.push_back(c);
       else ready.push_back(c);
     }
@@ -1693,6 +1619,10 @@ tt_status tt_engine_run(tt_engine *e) {
       if (ev) e->pool.push_back(ev);
     }
   } guard{e, ev};
+  if (e->server) {  // the batch's first device-side moment, for the server's GPU-time statistics
+    tt_status sst = ttx::server_stamp_start(e, e->launch_seq + 1);
+    if (sst != TT_OK) return sst;
+  }
   {
     std::vector<tt_chan *> all(ready);
     all.insert(all.end(), tc_ready.begin(), tc_ready.end());
@@ -1745,11 +1675,23 @@ tt_status tt_engine_run(tt_engine *e) {
     prev_end[i] = ready[i]->launched_end;
     ready[i]->launched_end = ready[i]->pushed_end;
   }
+  {  // channels still holding unlaunched slots (no trace yet) stay listed
+    size_t k = 0;
+    for (tt_chan *c : e->pending) {
+      if (c->pushed_end > c->launched_end) e->pending[k++] = c;
+      else c->in_pending = false;
+    }
+    e->pending.resize(k);
+  }
   // uplink aggregation of every slot all members of a cell have launched (after their kernels);
   // a failure here still registers the channels' launched slots before it is reported
   std::vector<std::pair<tt_cell *, uint64_t>> cell_ends;
   const tt_status cst = launch_cells(e, cell_ends);
   if (ready.empty() && cell_ends.empty()) return cst;
+  if (e->server) {
+    tt_status sst = ttx::server_stamp(e, e->launch_seq + 1);
+    if (sst != TT_OK) return sst;
+  }
   TT_CK(cudaEventRecord(ev, e->stream));
   guard.ev = nullptr;  // owned by the batch list from here on
   const uint64_t seq = ++e->launch_seq;
@@ -1757,6 +1699,7 @@ tt_status tt_engine_run(tt_engine *e) {
   for (size_t i = 0; i < ready.size(); ++i) {
     e->slots_processed += ready[i]->launched_end - prev_end[i];
     ready[i]->inflight.emplace_back(ready[i]->launched_end, seq);
+    if (e->server) ttx::server_note_launch(ready[i], prev_end[i], ready[i]->launched_end, seq);
   }
   for (auto &ce : cell_ends) {
     tt_cell *cl = ce.first;
@@ -1919,7 +1862,8 @@ static tt_status pull_common(tt_chan *c, uint64_t first, uint32_t n, void *out, 
   std::unique_lock<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
   if (c->cell) return fail(TT_ERR_STATE, "the channel's outputs go to its cell");
-  if (!c->started || first != c->pulled_end)
+  if (!c->started) return fail(TT_ERR_AGAIN, "nothing pushed to this channel yet");
+  if (first != c->pulled_end)
     return fail(TT_ERR_STATE, "pull must start at the oldest unpulled slot %llu", (unsigned long long)c->pulled_end);
   if (first + n > c->launched_end) return fail(TT_ERR_AGAIN, "slot not launched yet");
   update_chan(c);
@@ -2018,7 +1962,8 @@ tt_status tt_chan_pull_slots_dev(tt_chan *c, uint64_t first, uint32_t n, void *d
   std::lock_guard<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
   if (c->cell) return fail(TT_ERR_STATE, "the channel's outputs go to its cell");
-  if (!c->started || first != c->pulled_end)
+  if (!c->started) return fail(TT_ERR_AGAIN, "nothing pushed to this channel yet");
+  if (first != c->pulled_end)
     return fail(TT_ERR_STATE, "pull must start at the oldest unpulled slot %llu", (unsigned long long)c->pulled_end);
   if (first + n > c->launched_end) return fail(TT_ERR_AGAIN, "slot not launched yet");
   cudaEvent_t ev = get_event(e);
@@ -2176,160 +2121,4 @@ tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len) {
 
 
 // ---------------------------------------------------------------- serving form
-namespace {
-int64_t now_ns() {
-  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
-      .count();
-}
-struct Pending {
-  uint64_t slot;
-  int64_t t_arrival;
-  bool counted;
-};
-}  // namespace
-
-tt_status tt_engine_serve(tt_engine *e, const tt_serve_config *cfg, tt_serve_report *out) {
-  if (!e || !cfg || !out || cfg->struct_size < sizeof(tt_serve_config))
-    return fail(TT_ERR_INVALID, "tt_engine_serve: bad argument");
-  if (!(cfg->duration_s > 0.0) || !(cfg->slot_period_us > 0.0) || cfg->warmup_s < 0.0 || cfg->jitter_us < 0.0)
-    return fail(TT_ERR_INVALID, "tt_engine_serve: bad timing parameters");
-  std::vector<tt_chan *> chans;
-  {
-    std::lock_guard<std::mutex> lk(e->mu);
-    for (tt_chan *c : e->table)
-      if (c && c->has_trace) chans.push_back(c);
-  }
-  if (chans.empty()) return fail(TT_ERR_STATE, "tt_engine_serve: no channel with a trace");
-  const int64_t period = (int64_t)(cfg->slot_period_us * 1e3), jitter = (int64_t)(cfg->jitter_us * 1e3);
-  std::mt19937_64 rng(cfg->seed);
-  std::exponential_distribution<double> expo(1.0 / (double)period);
-  std::uniform_int_distribution<int64_t> jit(-jitter, jitter), phase(0, period);
-  auto gap = [&]() -> int64_t { return std::max<int64_t>(expo(rng) + (double)jit(rng), 1000); };
-
-  const int64_t t0 = now_ns();
-  const int64_t t_warm = t0 + (int64_t)(cfg->warmup_s * 1e9), t_end = t_warm + (int64_t)(cfg->duration_s * 1e9);
-  using Ev = std::pair<int64_t, uint32_t>;
-  std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> heap;
-  for (uint32_t u = 0; u < chans.size(); ++u) heap.push({t0 + phase(rng), u});
-  std::vector<std::deque<Pending>> pend(chans.size());
-  std::vector<uint32_t> pushed(chans.size(), 0);
-  std::unordered_map<tt_chan *, uint32_t> idx;
-  for (uint32_t u = 0; u < chans.size(); ++u) idx[chans[u]] = u;
-  struct Batch { uint64_t seq; std::vector<std::pair<uint32_t, uint64_t>> ends; uint32_t reqs; };
-  std::deque<Batch> inflight;
-  std::vector<double> lat;
-  lat.reserve(1 << 20);
-  uint64_t requests = 0, refused = 0, batches = 0, batched_reqs = 0, misses = 0, completed = 0;
-  uint32_t unlaunched = 0;
-  const uint32_t max_inflight = cfg->max_inflight_batches ? cfg->max_inflight_batches : 2;
-  const double deadline_ns = (cfg->deadline_us > 0 ? cfg->deadline_us : 500.0) * 1e3;
-
-  for (;;) {
-    int64_t now = now_ns();
-    bool did = false;
-    // 1. arrivals due now: commit the UE's next slot in place (its IQ is already in the ring)
-    while (!heap.empty() && heap.top().first <= now && heap.top().first < t_end) {
-      const Ev ev = heap.top();
-      heap.pop();
-      const uint32_t u = ev.second;
-      if (cfg->max_slots_per_ue && pushed[u] >= cfg->max_slots_per_ue) continue;
-      tt_chan *c = chans[u];
-      {
-        std::lock_guard<std::mutex> lk(e->mu);
-        const uint64_t slot = c->started ? c->pushed_end : 0;
-        ++requests;
-        if (check_room(c, slot, 1) == TT_OK) {
-          mark_pushed(c, slot, 1);
-          pend[u].push_back({slot, ev.first, ev.first >= t_warm});
-          ++pushed[u];
-          ++unlaunched;
-        } else {
-          ++refused;  // ring full: the engine is behind this UE
-        }
-      }
-      heap.push({ev.first + gap(), u});
-      did = true;
-    }
-    // 2. continuous batching: launch everything pending while fewer than max_inflight batches run
-    if (unlaunched > 0 && inflight.size() < max_inflight) {
-      Batch b;
-      b.reqs = unlaunched;
-      {
-        std::lock_guard<std::mutex> lk(e->mu);
-        for (uint32_t u = 0; u < chans.size(); ++u)
-          if (chans[u]->started && chans[u]->pushed_end > chans[u]->launched_end)
-            b.ends.push_back({u, chans[u]->pushed_end});
-      }
-      tt_status st = tt_engine_run(e);
-      if (st != TT_OK) return st;
-      {
-        std::lock_guard<std::mutex> lk(e->mu);
-        b.seq = e->launch_seq;
-      }
-      unlaunched = 0;
-      ++batches;
-      batched_reqs += b.reqs;
-      inflight.push_back(std::move(b));
-      did = true;
-    }
-    // 3. completions: stamp every request of every finished batch
-    if (!inflight.empty()) {
-      std::lock_guard<std::mutex> lk(e->mu);
-      cudaError_t q = update_completed(e);
-      if (q != cudaSuccess) return fail(TT_ERR_CUDA, "kernel failed: %s", cudaGetErrorString(q));
-      const int64_t t_done = now_ns();
-      while (!inflight.empty() && inflight.front().seq <= e->completed_seq) {
-        for (auto &pe : inflight.front().ends) {
-          tt_chan *c = chans[pe.first];
-          auto &dq = pend[pe.first];
-          while (!dq.empty() && dq.front().slot < pe.second) {
-            const double l = (double)(t_done - dq.front().t_arrival);
-            if (dq.front().counted) {
-              lat.push_back(l);
-              if (l > deadline_ns) ++misses;
-              ++completed;
-            }
-            dq.pop_front();
-          }
-          update_chan(c);
-          if (cfg->release_outputs) c->pulled_end = std::max(c->pulled_end, std::min(pe.second, c->completed_end));
-        }
-        inflight.pop_front();
-        did = true;
-      }
-      if (cfg->release_outputs)  // cells aggregated by completed batches free their ring slots too
-        for (tt_cell *cl : e->cells) {
-          while (!cl->inflight.empty() && cl->inflight.front().second <= e->completed_seq) {
-            cl->completed_end = cl->inflight.front().first;
-            cl->inflight.pop_front();
-          }
-          cl->pulled_end = std::max(cl->pulled_end, cl->completed_end);
-        }
-    }
-    if (now >= t_end && inflight.empty() && unlaunched == 0) break;
-    if (!did) std::this_thread::yield();
-  }
-  tt_serve_report r{};
-  r.requests = requests;
-  r.refused = refused;
-  r.completed = completed;
-  r.batches = batches;
-  r.mean_batch = batches ? (double)batched_reqs / (double)batches : 0.0;
-  r.deadline_misses = misses;
-  r.throughput = (double)completed / cfg->duration_s;
-  if (!lat.empty()) {
-    std::sort(lat.begin(), lat.end());
-    auto pct = [&](double p) { return lat[std::min(lat.size() - 1, (size_t)(p * (double)(lat.size() - 1) + 0.5))] / 1e3; };
-    r.p50_us = pct(0.50);
-    r.p99_us = pct(0.99);
-    r.p999_us = pct(0.999);
-    r.max_us = lat.back() / 1e3;
-    double s = 0;
-    for (double v : lat) s += v;
-    r.mean_us = s / (double)lat.size() / 1e3;
-  }
-  *out = r;
-  return TT_OK;
-}
-
 }  // extern "C"

@@ -1,0 +1,209 @@
+// Internal state of the channel engine (host side), shared by the engine's translation units:
+// tt_engine.cpp (the C ABI of channels, runs and copies) and tt_server.cpp (serving: the batching
+// thread, request latencies, admission waiting list).  Not part of the public ABI.
+#pragma once
+
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "tt_chan.h"
+#include "tt_internal.h"
+
+struct TTServer;  // defined in tt_server.cpp
+
+struct tt_chan;
+
+struct tt_cell;
+
+struct tt_engine {
+  int device = 0;
+  uint64_t budget = 0;
+  uint64_t in_use = 0;
+  uint32_t form = TT_FORM_BATCHED;
+  uint32_t max_ues = 1024;
+  uint32_t spt_override = 0;
+  uint32_t persistent = 0;
+  int num_sms = 1;
+  cudaStream_t stream = nullptr;  // all compute and device copies, in order
+  cudaStream_t copy = nullptr;    // host pulls
+  cudaStream_t h2d = nullptr;     // host pushes: wait only for kernels that still read the overwritten ring slots
+  // Kernel variants of one run go on parallel branches (side streams forked from and joined
+  // back to `stream`), so each variant's tail overlaps the others' work.
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
+  std::mutex mu;
+  std::vector<tt_chan *> table;   // UE table slot -> channel
+  TTUEDesc *d_ues = nullptr;
+  TTSeg *d_segs = nullptr;
+  size_t seg_cap = 0;
+  uint32_t *d_counters = nullptr;  // one work counter per launch class
+  int counter_cap = 64;
+  uint64_t launch_seq = 0;         // batches issued
+  uint64_t completed_seq = 0;      // batches known complete
+  std::deque<std::pair<uint64_t, cudaEvent_t>> events;  // (seq, event) not yet known complete
+  std::vector<cudaEvent_t> pool;
+  uint64_t launches = 0, slots_processed = 0;
+  // CUDA-graph replay of the batched launch (tt_engine_config.graphs)
+  bool graphs = false;
+  unsigned long long *d_cursors = nullptr;  // device-resident next slot of every UE table entry
+  TTSeg *d_gsegs = nullptr;                 // work list owned by the cached graph
+  size_t gseg_cap = 0;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint64_t> gkey;               // shape of the cached graph
+  std::vector<tt_chan *> gchans;            // channels of the cached graph, in table order
+  std::vector<uint64_t> gcounts;            // their slots per run
+  std::vector<tt_chan *> gplan_chans;       // the same channels in the graph's segment order
+  uint64_t graph_builds = 0, graph_launches = 0;
+  uint64_t graph_nodes = 0;                 // tiled-kernel launches inside the cached graph
+  TTSeg *d_tcsegs = nullptr;                // work list of the tensor-core channels
+  size_t tcseg_cap = 0;
+  int *d_status = nullptr;                  // set by a kernel whose bounded wait expired
+  int tc_no_mma = 0;                        // tests only (TT_TEST_TC_NO_MMA=1 at a run): no MMA is issued
+  std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
+  std::vector<tt_cell *> cells;             // uplink aggregation cells
+  std::vector<TTSosJob> sos_jobs;           // synthesis work list of the current run (host copy)
+  TTSosJob *d_sos = nullptr;                // and its device copy
+  size_t sos_cap = 0;
+  std::vector<TTRetimeJob> retime_jobs;     // timed-trace anchor work list of the current run
+  TTRetimeJob *d_retime = nullptr;
+  size_t retime_cap = 0;
+  std::vector<TTTopnJob> topn_jobs;         // tap-selection work list of the current run
+  TTTopnJob *d_topn = nullptr;
+  size_t topn_cap = 0;
+  // serving (tt_server_start): the batching thread's state, null when no server runs
+  TTServer *server = nullptr;
+  std::condition_variable room_cv;          // a batch completed: ring room may have freed up
+  std::condition_variable work_cv;          // a push arrived: the server may launch
+  // admission waiting list (tt_chan_create_queued): tickets in arrival order
+  std::mutex admit_mu;
+  std::condition_variable admit_cv;
+  std::deque<uint64_t> admit_queue;
+  uint64_t admit_next = 0;
+  // channels with pushed slots not launched yet (each once), so a run looks at those only
+  std::vector<tt_chan *> pending;
+};
+
+struct tt_chan {
+  tt_engine *e = nullptr;
+  uint32_t index = 0;
+  tt_chan_config cfg{};
+  std::vector<uint32_t> sym_len;
+  int n = 0, Q = 0, hist = 0;
+  size_t slot_in_elems = 0, slot_out_elems = 0;  // int16 values per slot
+  int16_t *d_in = nullptr, *d_out = nullptr;
+  uint64_t ring_bytes = 0;
+  float2 *d_taps = nullptr;
+  int32_t *d_delays = nullptr;
+  uint64_t trace_bytes = 0;
+  bool has_trace = false;
+  int spt = 1, dclass = 0, max_sym_touched = 1;
+  int32_t *d_chunks = nullptr;  // per work item of a slot: first symbol | symbols touched << 16
+  int tap_need = 0;             // max symbols touched x n_rx x n_tx x K
+  size_t smem = 0;
+  TTUEDesc desc{};
+  bool started = false;
+  uint64_t pushed_end = 0, launched_end = 0, completed_end = 0, pulled_end = 0;
+  uint64_t start_slot = 0;           // first slot ever pushed
+  float4 *d_sparse = nullptr;        // sparse convolution: kept taps per anchor and link (ring)
+  int32_t *d_sparse_dly = nullptr;
+  uint64_t sparse_bytes = 0;
+  uint64_t dev_cursor = UINT64_MAX;  // what the engine's device cursor holds for this UE (after queued work)
+  std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
+  std::deque<std::pair<uint64_t, int64_t>> arrivals;   // served requests not launched yet: (slot, arrival ns)
+  bool in_pending = false;                             // listed in the engine's pending list
+  tt_cell *cell = nullptr;      // uplink aggregation cell consuming this channel's outputs
+  // sum-of-sinusoids synthesis: the trace is a ring of anchors refilled before each run
+  bool synth = false;
+  float *d_amp = nullptr;
+  double *d_freq = nullptr, *d_phase = nullptr;
+  int synth_m = 0;
+  double synth_fs = 0.0;
+  // timed trace (entries every src_step samples): d_taps is a ring of anchors refilled before each
+  // run by FP64 trace-time interpolation from the stored trace d_src
+  bool retime = false;
+  float2 *d_src = nullptr;
+  uint64_t src_T = 0;
+  double src_step = 0.0;
+  int src_loop = 0;
+};
+
+struct tt_cell {
+  tt_engine *e = nullptr;
+  tt_cell_config cfg{};
+  int n = 0, Q = 0;
+  size_t slot_out_elems = 0;    // int16 values per slot
+  int16_t *d_out = nullptr;
+  uint64_t ring_bytes = 0;
+  std::vector<tt_chan *> members;
+  TTCellMember *d_members = nullptr;
+  size_t members_cap = 0;
+  bool started = false;
+  uint64_t launched_end = 0, completed_end = 0, pulled_end = 0;
+  std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
+};
+
+
+namespace ttx {
+
+// Record a message for tt_last_error() and return the status.
+tt_status fail(tt_status s, const char *fmt, ...);
+int64_t now_us();
+int64_t now_ns();
+cudaEvent_t get_event(tt_engine *e);
+// Poll batch events in order (engine lock held); returns the first hard CUDA error seen.
+cudaError_t update_completed(tt_engine *e);
+void update_chan(tt_chan *c);
+// TT_OK if slots [first, first + n) may be pushed now (engine lock held).
+tt_status check_room(tt_chan *c, uint64_t first, uint32_t n);
+void mark_pushed(tt_chan *c, uint64_t first, uint32_t n);                      // arrival: now
+void mark_pushed_at(tt_chan *c, uint64_t first, uint32_t n, int64_t arrival_ns);
+
+// ---- serving hooks (tt_server.cpp) ----
+// A push of [first, first + n) became visible (engine lock held): its arrival is recorded.
+void server_note_push(tt_chan *c, uint64_t first, uint32_t n, int64_t arrival_ns);
+// Batch `seq` launched channel c's slots [from, to) (engine lock held).
+void server_note_launch(tt_chan *c, uint64_t from, uint64_t to, uint64_t seq);
+// Before a batch's completion event: stamp its completion on the device (engine lock held).
+tt_status server_stamp(tt_engine *e, uint64_t seq);
+// Before a batch's first kernel: stamp when the device starts it (engine lock held).
+tt_status server_stamp_start(tt_engine *e, uint64_t seq);
+// A push found the ring full while a server runs: wait (engine lock held, released while waiting)
+// until room() or the queue timeout; TT_OK or the failure status.
+template <class Room>
+tt_status server_wait_room(tt_engine *e, std::unique_lock<std::mutex> &lk, Room room);
+// A push waited for ring room (refused: the wait ran out); counted in the server's report.
+void server_count_wait(tt_engine *e, bool refused);
+// A channel was destroyed: admission waiters may now fit.
+void admission_notify(tt_engine *e);
+// The thread running the server's batching loop (tt_engine_run from others is refused).
+bool is_server_thread(const tt_engine *e);
+int64_t server_queue_timeout_us(const tt_engine *e);
+
+template <class Room>
+tt_status server_wait_room(tt_engine *e, std::unique_lock<std::mutex> &lk, Room room) {
+  const int64_t deadline = now_us() + server_queue_timeout_us(e);
+  bool counted = false;
+  for (;;) {
+    tt_status st = room();
+    if (st != TT_ERR_AGAIN || !e->server) return st;
+    if (!counted) {
+      server_count_wait(e, false);
+      counted = true;
+    }
+    const int64_t left = deadline - now_us();
+    if (left <= 0) {
+      server_count_wait(e, true);
+      return st;
+    }
+    e->room_cv.wait_for(lk, std::chrono::microseconds(left < 1000 ? left : 1000));
+  }
+}
+
+}  // namespace ttx

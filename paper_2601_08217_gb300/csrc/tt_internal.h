@@ -191,5 +191,8 @@ cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, int
 // Record a message for tt_last_error() (thread-local) and return the status.
 int32_t tt_set_error(int32_t status, const char *msg);
 
+// Write the device's %globaltimer (ns) to dst once every earlier kernel on st has finished.
+cudaError_t tt_launch_stamp(unsigned long long *dst, cudaStream_t st);
+
 // Plain comparison form: one launch per UE per slot.
 cudaError_t tt_launch_plain(const TTUEDesc *ue_dev, uint64_t slot, int n, cudaStream_t st);

@@ -90,7 +90,23 @@ class ServeReport(C.Structure):
     _fields_ = [("requests", C.c_uint64), ("refused", C.c_uint64), ("completed", C.c_uint64),
                 ("batches", C.c_uint64), ("deadline_misses", C.c_uint64), ("mean_batch", C.c_double),
                 ("throughput", C.c_double), ("p50_us", C.c_double), ("p99_us", C.c_double),
-                ("p999_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double)]
+                ("p999_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double),
+                ("stamp_error_us", C.c_double), ("gpu_us_per_batch", C.c_double), ("gpu_busy", C.c_double)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("max_inflight_batches", C.c_uint32), ("release_outputs", C.c_uint32),
+                ("queue_timeout_us", C.c_int32), ("deadline_us", C.c_double), ("warmup_us", C.c_double),
+                ("coalesce_us", C.c_double)]
+
+
+class ServerReport(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("requests", C.c_uint64), ("completed", C.c_uint64),
+                ("queued", C.c_uint64), ("refused", C.c_uint64), ("batches", C.c_uint64),
+                ("deadline_misses", C.c_uint64), ("mean_batch", C.c_double), ("p50_us", C.c_double),
+                ("p99_us", C.c_double), ("p999_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double),
+                ("min_us", C.c_double), ("stamp_error_us", C.c_double), ("gpu_us_per_batch", C.c_double),
+                ("gpu_busy", C.c_double)]
 
 
 class StaticChan(C.Structure):
@@ -117,6 +133,9 @@ _SIGS = {
     "tt_engine_replay": [_VP, C.c_uint32, C.c_uint32],
     "tt_engine_serve": [_VP, C.POINTER(ServeConfig), C.POINTER(ServeReport)],
     "tt_chan_create": [_VP, C.POINTER(ChanConfig), C.POINTER(_VP)],
+    "tt_chan_create_queued": [_VP, C.POINTER(ChanConfig), C.c_int64, C.POINTER(_VP)],
+    "tt_server_start": [_VP, C.POINTER(ServerConfig)],
+    "tt_server_stop": [_VP, C.POINTER(ServerReport)],
     "tt_chan_destroy": [_VP],
     "tt_chan_load_trace": [_VP, C.POINTER(TraceDesc)],
     "tt_chan_push_slot": [_VP, C.c_uint64, _VP],
@@ -264,16 +283,35 @@ def tt_engine_serve(e: int, duration_s: float, warmup_s: float = 0.0, slot_perio
     return {f: getattr(rep, f) for f, _ in ServeReport._fields_}
 
 
+def tt_server_start(e: int, max_inflight_batches: int = 0, release_outputs: bool = False,
+                    queue_timeout_us: int = 0, deadline_us: float = 500.0, warmup_us: float = 0.0,
+                    coalesce_us: float = 0.0):
+    cfg = ServerConfig(C.sizeof(ServerConfig), max_inflight_batches, int(bool(release_outputs)), queue_timeout_us,
+                       deadline_us, warmup_us, coalesce_us)
+    _check(load().tt_server_start(e, C.byref(cfg)))
+
+
+def tt_server_stop(e: int) -> dict:
+    rep = ServerReport()
+    rep.struct_size = C.sizeof(ServerReport)
+    _check(load().tt_server_stop(e, C.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in ServerReport._fields_ if f != "struct_size"}
+
+
 def tt_chan_create(e: int, samples_per_slot: int, symbol_len: Sequence[int], n_tx: int = 1, n_rx: int = 1,
                    max_taps: int = 128, max_delay: int = 0, ring_slots: int = 0, seed: int = 0,
                    noise_var: float = 0.0, ue_id: int = 0, precision: int = TT_FP32,
-                   output_format: int = TT_OUT_INT16, top_n: int = 0) -> int:
+                   output_format: int = TT_OUT_INT16, top_n: int = 0, wait_us: Optional[int] = None) -> int:
+    """wait_us: None = plain admission; else tt_chan_create_queued with that timeout (< 0: no limit)."""
     lib = load()
     L = (C.c_uint32 * len(symbol_len))(*[int(v) for v in symbol_len])
     cfg = ChanConfig(C.sizeof(ChanConfig), ue_id, samples_per_slot, len(symbol_len), L, n_tx, n_rx,
                      max_taps, max_delay, ring_slots, seed, noise_var, precision, output_format, top_n)
     h = _VP()
-    _check(lib.tt_chan_create(e, C.byref(cfg), C.byref(h)))
+    if wait_us is None:
+        _check(lib.tt_chan_create(e, C.byref(cfg), C.byref(h)))
+    else:
+        _check(lib.tt_chan_create_queued(e, C.byref(cfg), int(wait_us), C.byref(h)))
     return h.value
 
 
@@ -513,7 +551,7 @@ class Chan:
     """One UE link.  ``spec`` is an ``inputs.UESpec`` (or anything with its fields)."""
 
     def __init__(self, engine: Engine, spec, ring_slots: int = 0, load: bool = True, cf32: bool = False,
-                 precision: int = TT_FP32, top_n: int = 0):
+                 precision: int = TT_FP32, top_n: int = 0, wait_us: Optional[int] = None):
         self.engine = engine
         self.spec = spec
         self.cf32 = cf32
@@ -522,7 +560,7 @@ class Chan:
                                 max(int(len(spec.delays)), 1), int(max(spec.max_delay, max(spec.delays))),
                                 ring_slots, int(spec.seed), float(spec.noise_var), int(spec.ue_id),
                                 precision=precision, output_format=TT_OUT_CF32 if cf32 else TT_OUT_INT16,
-                                top_n=top_n)
+                                top_n=top_n, wait_us=wait_us)
         engine.chans.append(self)
         if load:
             self.load_trace(spec.taps, spec.delays, spec.step_samples, spec.loop)

@@ -27,7 +27,7 @@ def test_every_declared_function_is_exported(lib):
 
 
 def test_abi_version_and_error_string(lib):
-    assert tc.tt_abi_version() == 2
+    assert tc.tt_abi_version() == 3
     assert isinstance(tc.tt_last_error(), str)
 
 

@@ -1,8 +1,10 @@
 """Serving form: Poisson slot requests from many UEs, continuous batching, latency report.
 
-The results a UE gets while served in the mix equal the results of the same
-UE run alone (bit for bit), and a full ring refuses requests instead of
-corrupting state."""
+tt_engine_serve generates the arrivals and commits them through the engine's request path (the
+batching thread of tt_server_start).  The results a UE gets while served in the mix equal the
+results of the same UE run alone (bit for bit).  Arrivals that find a UE's ring full wait in a
+bounded per-UE queue; only when that queue overflows is a request refused, and state is never
+corrupted."""
 import numpy as np
 import pytest
 
@@ -48,7 +50,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         assert np.array_equal(alone, served[i]), i
 
 
-def test_full_ring_refuses_requests():
+def test_arrivals_beyond_a_full_ring_and_its_queue_are_refused():
+    """Nothing pulls and outputs are kept, so each ring fills: the next 64 arrivals of a UE queue,
+    later ones are refused, and every queued one still waiting at the end counts as refused."""
     specs = inputs.workload_serving(n_ues=4, n_slots_trace=2)
     eng = tc.Engine()
     _prefill(eng, specs, 3, n=2)
