@@ -341,7 +341,7 @@ def run_ours(args, rank, world, device):
 def run_batching(args, device, n_ues=256, steps=400, warmup=20):
     """256 UEs of mixed bandwidth (5/20/40/100 MHz, 1:2:4:1), 4-48 taps, delays <= 512, AWGN 20 dB:
     one slot of every UE per step, one CUDA-graph replay of the persistent kernel per step,
-    samples-per-thread picked by the engine's autotuner."""
+    samples per thread and threads per CTA picked by the engine's autotuner."""
     import torch
     from paper_2601_08217_gb300 import inputs
     from paper_2601_08217_gb300 import tt_chan as tc
@@ -361,8 +361,34 @@ def run_batching(args, device, n_ues=256, steps=400, warmup=20):
         ch.push(9, x[1:2])
     eng.run()
     eng.sync()
-    tuned = eng.autotune(reps=3)
     stream = torch.cuda.ExternalStream(eng.stream)
+
+    def timed_replay():
+        tc.tt_engine_replay(eng.h, warmup, 1)
+        eng.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        tc.tt_engine_replay(eng.h, steps, 1)
+        ev1.record(stream)
+        eng.sync()
+        return ev0.elapsed_time(ev1) / steps
+
+    ms_default = timed_replay()                      # the engine's default geometry, before tuning
+    tuned = eng.autotune(reps=3)
+    # the tuner's choice per class (samples per thread x threads per CTA = the work item's span)
+    choice = {}
+    for sp, ch in zip(specs, chans):
+        g = ch.geometry()
+        bucket = 8
+        while bucket < len(sp.delays):
+            bucket *= 2
+        key = (sp.n, f"{sp.n_tx}x{sp.n_rx}", bucket)
+        c = choice.setdefault(key, {"samples_per_slot": sp.n, "antennas": key[1], "taps_up_to": bucket, "ues": 0,
+                                    "geometry": set()})
+        c["ues"] += 1
+        c["geometry"].add(f"S={g['samples_per_thread']} x {g['threads_per_cta']} threads = "
+                          f"{g['samples_per_item']} samples per item")
+    classes = [dict(v, geometry=sorted(v["geometry"])) for _, v in sorted(choice.items())]
     tc.tt_engine_replay(eng.h, warmup, 1)
     eng.sync()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -385,7 +411,8 @@ def run_batching(args, device, n_ues=256, steps=400, warmup=20):
             "roofline": alu_roofline(tap_s, ms / steps, sm_count(device), peaks()["sm_max_mhz"],
                                      "sm_max_mhz of " + peaks()["src"] + " peaks"),
             "graph_launches": st1["graph_launches"] - st0["graph_launches"],
-            "graph_builds": st1["graph_builds"], "autotuned_classes": tuned}
+            "graph_builds": st1["graph_builds"], "autotuned_classes": tuned, "tuned_geometry": classes,
+            "ms_per_step_before_tuning": ms_default}
 
 
 def run_serving(args, device, n_ues=512, duration=2.0, warmup=0.2, plain_duration=0.3):
@@ -805,7 +832,7 @@ def main():
     clk_max = r["clocks"].get("sm_max_mhz")
     roof = alu_roofline(ts, kms, sm_count(local), clk_max or pk["sm_max_mhz"],
                         "clocks.max.sm sampled by nvidia-smi" if clk_max else "sm_max_mhz of " + pk["src"] + " peaks")
-    roof.update({"traffic": traffic, "kernel": f"tt_conv_fp32_kernel<{args.spt or 8},1,256>",
+    roof.update({"traffic": traffic, "kernel": f"tt_conv_fp32_kernel<{args.spt or 8},1,256,false,128>",
                  "dram_gbs": (traffic / (kms / 1e3) / 1e9) if traffic else None,
                  "dram_frac_of_hbm": (traffic / (kms / 1e3) / 1e9 / pk["hbm_gbs"]) if traffic else None,
                  "hbm_peak_gbs": pk["hbm_gbs"]})

@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define TT_CHAN_ABI_VERSION 3
+#define TT_CHAN_ABI_VERSION 4
 
 typedef struct tt_engine tt_engine; /* one per GPU: stream, HBM budget, form, UE table */
 typedef struct tt_chan tt_chan;     /* one per UE link: config, trace, delay line, rings */
@@ -68,7 +68,8 @@ enum {
   TT_ERR_TRACE = -4,     /* malformed trace: sizes, delays out of range, non-finite taps */
   TT_ERR_AGAIN = -5,     /* nothing ready yet, or the slot ring is full */
   TT_ERR_TIMEOUT = -6,   /* a bounded wait ran out */
-  TT_ERR_STATE = -7      /* out-of-order slot, no trace loaded, wrong form, bad state blob */
+  TT_ERR_STATE = -7,     /* out-of-order slot, no trace loaded, wrong form, bad state blob */
+  TT_ERR_IO = -8         /* the tuning cache file (TT_TUNE_CACHE) could not be written */
 };
 
 /* How tt_engine_run executes pending slots. */
@@ -96,7 +97,10 @@ typedef struct {
                                   channels with at most 2 Rx antennas; it runs bulk single-antenna
                                   work faster).  Each channel uses the largest allowed value dividing
                                   all its symbol lengths. */
-  uint32_t threads_per_block;  /* reserved: 0 (the tiled kernel runs 128 threads per CTA) */
+  uint32_t threads_per_block;  /* tiled kernel's threads per CTA: 0 = 128 unless the tuning cache or
+                                  tt_engine_autotune picks 256 for a channel's class; 128 or 256 =
+                                  every channel uses it (the tuner then searches samples per thread
+                                  only, and cached choices of the other count are ignored) */
   uint32_t persistent;       /* 1: persistent CTAs claim work items from a device counter; 0: by stride */
   uint32_t graphs;           /* 1: tt_engine_run captures its launches in a CUDA graph and replays it
                                 while the set of channels and slots per run stays the same */
@@ -180,16 +184,43 @@ tt_status tt_engine_stream(tt_engine *e, void **stream);
 
 tt_status tt_engine_get_stats(tt_engine *e, tt_engine_stats *out);
 
-/* Autotune the tiled kernel's samples-per-thread for every class of admitted,
- * traced FP32 channels (same symbol lengths, antennas, tap count, delay
- * class).  The objective is the whole batch: one slot of every channel that
- * has a free ring position (written to that free position, so no queued or
- * unpulled slot is touched), launched as tt_engine_run launches it, best of
- * `reps` timings.  Classes are visited largest first; each candidate that
- * fits shared memory replaces the class's current choice only if the batch
- * gets at least 1% faster.  Waits for queued work first.  *classes_tuned
- * (may be NULL) receives the number of classes that had a choice to make. */
+/* Autotune the tiled FP32 kernel's geometry for every class of admitted,
+ * traced FP32 channels (same symbol lengths, antennas, tap-count bucket: the
+ * next power of two, at least 8, delay class, AWGN on/off, output format,
+ * top-n).  Two axes: samples per thread
+ * S in {1, 2, 4, 8, 16} (those dividing every symbol length, 16 with at most
+ * 2 Rx antennas, none above the engine's samples_per_thread setting or 16
+ * when it is 0) and threads per CTA in {128, 256}; a work item (the tile)
+ * spans S x threads samples, 128 to 4096.  The objective is the whole batch:
+ * one slot of every channel that has a free ring position (written to that
+ * free position, so no queued or unpulled slot is touched), launched as
+ * tt_engine_run launches it, best of `reps` timings.  Classes are visited
+ * largest first; each (S, threads) pair that fits shared memory replaces the
+ * class's current choice only if the batch gets at least 1% faster in two
+ * timings in a row.  Waits
+ * for queued work first.  *classes_tuned (may be NULL) receives the number of
+ * classes that had a choice to make.
+ *
+ * Tuning cache: if the environment variable TT_TUNE_CACHE names a file when
+ * the engine is created, the engine reads the choices stored there for its
+ * device model (device name and SM count); a channel of a stored class starts
+ * at the stored geometry when its trace is loaded.  tt_engine_autotune writes
+ * every class's choice back into that file (lines of other device models and
+ * classes are kept; the file is replaced through a temporary file and a
+ * rename).  TT_ERR_IO if it cannot be written; the tuned geometry stays in
+ * effect for the engine.  Unreadable or malformed lines are ignored. */
 tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned);
+
+/* The work decomposition a channel launches with (for reports and tests). */
+typedef struct {
+  uint32_t tensor_core;        /* 1: tensor-core kernel (BF16/FP16 precision), 0: tiled FP32 kernel */
+  uint32_t samples_per_thread; /* tiled kernel: S (0 for the tensor-core kernel) */
+  uint32_t threads_per_cta;    /* tiled kernel: 128 or 256 (0 for the tensor-core kernel) */
+  uint32_t samples_per_item;   /* tiled kernel: the tile, S x threads_per_cta */
+  uint32_t items_per_slot;     /* work items (CTAs' units of work) per slot */
+  uint32_t has_trace;          /* 0: the geometry is provisional until a trace is loaded */
+} tt_chan_geometry;
+tt_status tt_chan_get_geometry(tt_chan *c, tt_chan_geometry *out);
 
 /* Serving benchmark.  Generates requests on the calling thread for warmup_s +
  * duration_s seconds: every channel with a trace receives slot-push requests

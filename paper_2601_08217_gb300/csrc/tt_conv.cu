@@ -5,10 +5,10 @@
 #include "tt_internal.h"
 #include "tt_philox.cuh"
 
-size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max) {
+size_t tt_conv_smem_bytes(int spt, int tpb, int dclass, int n_tx, int tap_max, int k_max) {
   const int dmax = tt_dclass_max(dclass);
-  const int np = tt_geo_np(spt, dmax);
-  const int wmax = tt_geo_wmax(spt, dmax);
+  const int np = tt_geo_np(tpb, spt, dmax);
+  const int wmax = tt_geo_wmax(tpb, spt, dmax);
   const size_t planes = (size_t)n_tx * 2 * spt * np * sizeof(float2);
   const size_t raw = (size_t)((n_tx * wmax + 3) & ~3) * sizeof(uint32_t);
   const size_t taps = 2 * (size_t)tap_max * sizeof(float4);
@@ -16,18 +16,18 @@ size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max)
   return planes + raw + taps + dly;
 }
 
-// For each work item (TT_TPB groups of spt samples) of a slot: first symbol it
+// For each work item (tpb groups of spt samples) of a slot: first symbol it
 // touches and how many symbols it touches, packed as jf | (nst << 16).
-int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, int max_out) {
+int tt_conv_chunk_info(int spt, int tpb, const int32_t *sym_len, int nsym, int32_t *out, int max_out) {
   int n = 0;
   for (int j = 0; j < nsym; ++j) n += sym_len[j];
   const int groups = n / spt;
-  const int items = (groups + TT_TPB - 1) / TT_TPB;
+  const int items = (groups + tpb - 1) / tpb;
   if (items > max_out) return -1;
   for (int c = 0; c < items; ++c) {
-    const int g0 = c * TT_TPB;
+    const int g0 = c * tpb;
     const int w0 = g0 * spt;
-    const int wl = (g0 + TT_TPB < groups ? g0 + TT_TPB : groups) * spt - 1;
+    const int wl = (g0 + tpb < groups ? g0 + tpb : groups) * spt - 1;
     int b = 0, j0 = -1, j1 = -1;
     for (int j = 0; j < nsym; ++j) {
       if (j0 < 0 && w0 < b + sym_len[j]) j0 = j;
@@ -40,22 +40,24 @@ int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, 
 }
 
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st) {
+  const bool w = L.tpb == TT_TPB_WIDE;
+  if (!w && L.tpb != TT_TPB) return cudaErrorInvalidValue;
   if (L.topn) {
     switch (L.spt) {
-      case 1: return tt_launch_conv_s1_topn(L, st);
-      case 2: return tt_launch_conv_s2_topn(L, st);
-      case 4: return tt_launch_conv_s4_topn(L, st);
-      case 8: return tt_launch_conv_s8_topn(L, st);
-      case 16: return tt_launch_conv_s16_topn(L, st);
+      case 1: return w ? tt_launch_conv_s1_w_topn(L, st) : tt_launch_conv_s1_topn(L, st);
+      case 2: return w ? tt_launch_conv_s2_w_topn(L, st) : tt_launch_conv_s2_topn(L, st);
+      case 4: return w ? tt_launch_conv_s4_w_topn(L, st) : tt_launch_conv_s4_topn(L, st);
+      case 8: return w ? tt_launch_conv_s8_w_topn(L, st) : tt_launch_conv_s8_topn(L, st);
+      case 16: return w ? tt_launch_conv_s16_w_topn(L, st) : tt_launch_conv_s16_topn(L, st);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (L.spt) {
-    case 1: return tt_launch_conv_s1(L, st);
-    case 2: return tt_launch_conv_s2(L, st);
-    case 4: return tt_launch_conv_s4(L, st);
-    case 8: return tt_launch_conv_s8(L, st);
-    case 16: return tt_launch_conv_s16(L, st);
+    case 1: return w ? tt_launch_conv_s1_w(L, st) : tt_launch_conv_s1(L, st);
+    case 2: return w ? tt_launch_conv_s2_w(L, st) : tt_launch_conv_s2(L, st);
+    case 4: return w ? tt_launch_conv_s4_w(L, st) : tt_launch_conv_s4(L, st);
+    case 8: return w ? tt_launch_conv_s8_w(L, st) : tt_launch_conv_s8(L, st);
+    case 16: return w ? tt_launch_conv_s16_w(L, st) : tt_launch_conv_s16(L, st);
     default: return cudaErrorInvalidValue;
   }
 }

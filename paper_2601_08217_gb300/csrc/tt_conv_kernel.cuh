@@ -5,9 +5,10 @@
 //
 // Work decomposition.  A slot of one UE is cut into groups of S consecutive
 // samples (S divides every symbol length, so a group never straddles a symbol
-// and shares one set of taps).  A work item is TT_TPB consecutive groups of
-// one (UE, slot): one group per thread, all Rx antennas per thread so every
-// staged input sample is reused n_rx times.
+// and shares one set of taps).  A work item is TPB consecutive groups of
+// one (UE, slot), TPB being the CTA's thread count (128 or 256): one group per
+// thread, all Rx antennas per thread so every staged input sample is reused
+// n_rx times.  The item's span TPB * S samples is the kernel's tile.
 //
 // Persistent, software-pipelined CTAs.  While a CTA computes item i it has
 // already issued cp.async copies of item i+1's raw input window, raw trace
@@ -96,6 +97,7 @@ struct TTItem {
 
 // Thread 0: item index -> (UE, slot, groups, first symbol, symbols touched).
 // With device cursors (graph replay), a run's first slot is cursors[ue] instead of seg.first_slot.
+template <int TPB>
 __device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs,
                                           int n_segs, uint32_t item, uint32_t total_items,
                                           const unsigned long long *__restrict__ cursors, TTItem &it) {
@@ -114,7 +116,7 @@ __device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, cons
   const uint32_t ips = (uint32_t)U->items_per_slot;
   const uint32_t c = rel % ips;
   const int ci = __ldg(U->chunk_info + c);
-  const int g0 = (int)c * TT_TPB;
+  const int g0 = (int)c * TPB;
   const uint64_t slot = (cursors ? cursors[sg.ue] : sg.first_slot) + rel / ips;
   const int jf = ci & 0xFFFF;
   const uint64_t a0 = slot * (uint64_t)U->nsym + (uint64_t)jf;
@@ -122,7 +124,7 @@ __device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, cons
   it.idx0 = U->loop ? a0 % (uint64_t)U->n_anchors : a0;
   it.ue = (int)sg.ue;
   it.g0 = g0;
-  it.gend = min(g0 + TT_TPB, U->groups);
+  it.gend = min(g0 + TPB, U->groups);
   it.jf = jf;
   it.nst = ci >> 16;
   it.slot_pos = (int)(slot % (uint64_t)U->ring_q);
@@ -131,7 +133,7 @@ __device__ __forceinline__ void tt_locate(const TTUEDesc *__restrict__ ues, cons
 
 // All threads: start the asynchronous copies of one item's raw window, trace
 // entries, delays and symbol table into shared memory.
-template <int S, int NRX, bool TOPN>
+template <int S, int NRX, bool TOPN, int TPB>
 __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, const TTItem &it, uint32_t *raw,
                                               int wmax, float4 *taps, int *dly, int *sym, int tid) {
   const int n = U->n, n_tx = U->n_tx, Q = U->ring_q, K = U->n_taps, dpad = U->dpad;
@@ -142,7 +144,7 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
   constexpr int V = S >= 4 ? 4 : 1;  // samples per copy: 16-byte copies when windows are 4-aligned
   for (int t = 0; t < n_tx; ++t) {
     uint32_t *rt = raw + t * wmax;
-    for (int e = V * tid; e < wlen; e += V * TT_TPB) {
+    for (int e = V * tid; e < wlen; e += V * TPB) {
       int w = ws + e;
       int pos = slot_pos;
       if (w < 0) {  // delay line: earlier slots of this UE
@@ -161,7 +163,7 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
     // sparse convolution: the kept taps of each touched symbol and link, selected ahead of the run
     const int ns = NRX * n_tx * U->top_n;
     const uint64_t L = (uint64_t)U->sparse_len;
-    for (int e = tid; e < it.nst * ns; e += TT_TPB) {
+    for (int e = tid; e < it.nst * ns; e += TPB) {
       const int jl = e / ns;
       const int rem = e - jl * ns;
       const uint64_t a = it.slot * (uint64_t)U->nsym + (uint64_t)(it.jf + jl);
@@ -175,7 +177,7 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
   }
   if (U->step_samples == 0.0) {
     const uint64_t T = (uint64_t)U->n_anchors;
-    for (int e = tid; e < ntap_e; e += TT_TPB) {
+    for (int e = tid; e < ntap_e; e += TPB) {
       const int jl = e / per;
       const int rem = e - jl * per;
       uint64_t i0 = it.idx0 + (uint64_t)jl, i1 = i0 + 1;
@@ -190,14 +192,14 @@ __device__ __forceinline__ void tt_issue_item(const TTUEDesc *__restrict__ U, co
       tt_cp_async8(&taps[e].z, U->taps + i1 * (uint64_t)per + (uint64_t)rem);
     }
   }
-  for (int k = tid; k < K; k += TT_TPB) tt_cp_async4(dly + k, U->delays + k);
+  for (int k = tid; k < K; k += TPB) tt_cp_async4(dly + k, U->delays + k);
   if (tid <= U->nsym) tt_cp_async4(sym + tid, U->sym_start + tid);
   tt_cp_async_commit();
 }
 
 // All threads, after the copies landed: raw window -> phase planes, taps -> (H0, dH),
 // delays -> plane offsets.
-template <int S, int NRX, int NP, bool TOPN, int WMAXC>
+template <int S, int NRX, int NP, bool TOPN, int WMAXC, int TPB>
 __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, const TTItem &it,
                                                 const uint32_t *raw, int wmax, float2 *planes, float4 *taps,
                                                 int *dly, int tid) {
@@ -208,16 +210,16 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
     float2 *pl = planes + t * (2 * S * NP);
     if constexpr (S >= 4) {
       // every 16-byte load of the thread first (at most NV), then the unpacking and plane stores
-      constexpr int NV = (WMAXC + 4 * TT_TPB - 1) / (4 * TT_TPB);
+      constexpr int NV = (WMAXC + 4 * TPB - 1) / (4 * TPB);
       uint4 v[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        const int e = 4 * tid + q * 4 * TT_TPB;
+        const int e = 4 * tid + q * 4 * TPB;
         if (e < wlen) v[q] = *reinterpret_cast<const uint4 *>(rt + e);
       }
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        const int e = 4 * tid + q * 4 * TT_TPB;
+        const int e = 4 * tid + q * 4 * TPB;
         if (e < wlen) {
           const uint32_t vv[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
           const int beta = e % S, i = e / S;
@@ -230,7 +232,7 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
         }
       }
     } else {
-      for (int e = tid; e < wlen; e += TT_TPB) {
+      for (int e = tid; e < wlen; e += TPB) {
         const float2 xv = tt_unpack_iq(rt[e]);
         const int beta = e % S, i = e / S;
         pl[beta * NP + i + 1] = xv;
@@ -239,7 +241,7 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
     }
   }
   if constexpr (TOPN) {  // (H, dH) came from the selection; delays become plane offsets
-    for (int e = tid; e < it.nst * NRX * n_tx * U->top_n; e += TT_TPB) {
+    for (int e = tid; e < it.nst * NRX * n_tx * U->top_n; e += TPB) {
       const int d = dly[e];
       dly[e] = (S - d % S) * NP - d / S;
     }
@@ -248,7 +250,7 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
   const int per = NRX * n_tx * K;
   const int ntap_e = it.nst * per;
   if (U->step_samples == 0.0) {
-    for (int e = tid; e < ntap_e; e += TT_TPB) {
+    for (int e = tid; e < ntap_e; e += TPB) {
       float4 h = taps[e];
       h.z -= h.x;
       h.w -= h.y;
@@ -256,7 +258,7 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
     }
   } else {  // trace-time interpolation (FP64) straight from global memory
     const int nsym = U->nsym;
-    for (int e = tid; e < ntap_e; e += TT_TPB) {
+    for (int e = tid; e < ntap_e; e += TPB) {
       const int jl = e / per;
       const int rem = e - jl * per;
       const uint64_t a = it.slot * (uint64_t)nsym + (uint64_t)(it.jf + jl);
@@ -265,7 +267,7 @@ __device__ __forceinline__ void tt_convert_item(const TTUEDesc *__restrict__ U, 
       taps[e] = make_float4(h0.x, h0.y, h1.x - h0.x, h1.y - h0.y);
     }
   }
-  for (int k = tid; k < K; k += TT_TPB) {
+  for (int k = tid; k < K; k += TPB) {
     const int d = dly[k];
     dly[k] = (S - d % S) * NP - d / S;
   }
@@ -397,19 +399,23 @@ __device__ __forceinline__ void tt_compute_item(const TTUEDesc *__restrict__ U, 
   }
 }
 
-// Single-antenna variants with up to 8 samples per thread fit 64 registers, so eight CTAs share an
-// SM and hide each other's staging barriers.  At 16 samples per thread, shared memory admits four
-// CTAs per SM (48 KB each at delays up to 256), and 128 registers hold the variant without spills.
-// The multi-antenna variants keep the compiler's choice.
-constexpr int tt_min_blocks(int S, int NRX) { return (NRX == 1 && S <= 8) ? 8 : ((NRX == 1 && S == 16) ? 4 : 1); }
+// Single-antenna variants with up to 8 samples per thread fit 64 registers, so eight 128-thread CTAs
+// share an SM and hide each other's staging barriers.  At 16 samples per thread, shared memory
+// admits four (48 KB each at delays up to 256), and 128 registers hold the variant without spills.
+// 256-thread CTAs ask for half as many, so the registers per thread stay the same.  The
+// multi-antenna variants keep the compiler's choice.
+constexpr int tt_min_blocks_128(int S, int NRX) { return (NRX == 1 && S <= 8) ? 8 : ((NRX == 1 && S == 16) ? 4 : 1); }
+constexpr int tt_min_blocks(int S, int NRX, int TPB) {
+  return tt_min_blocks_128(S, NRX) * TT_TPB / TPB > 0 ? tt_min_blocks_128(S, NRX) * TT_TPB / TPB : 1;
+}
 
-template <int S, int NRX, int DMAX, bool TOPN>
-__global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
+template <int S, int NRX, int DMAX, bool TOPN, int TPB>
+__global__ void __launch_bounds__(TPB, tt_min_blocks(S, NRX, TPB))
     tt_conv_fp32_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                         uint32_t total_items, uint32_t *__restrict__ counter, int ntx, int tap_max, int k_max,
                         const unsigned long long *__restrict__ cursors) {
-  constexpr int NP = tt_geo_np(S, DMAX);
-  constexpr int WMAX = tt_geo_wmax(S, DMAX);
+  constexpr int NP = tt_geo_np(TPB, S, DMAX);
+  constexpr int WMAX = tt_geo_wmax(TPB, S, DMAX);
   extern __shared__ float4 dyn_smem[];
   __shared__ TTItem s_it[2];
   __shared__ uint32_t s_claim;
@@ -434,7 +440,7 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
 
   // ---- prologue: first item fully staged, second item located ----
   if (tid == 0) {
-    tt_locate(ues, segs, n_segs, claim(), total_items, cursors, s_it[0]);
+    tt_locate<TPB>(ues, segs, n_segs, claim(), total_items, cursors, s_it[0]);
     s_claim = claim();
   }
   __syncthreads();
@@ -442,11 +448,11 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
   {
     const TTItem it = s_it[0];
     const TTUEDesc *U = ues + it.ue;
-    tt_issue_item<S, NRX, TOPN>(U, it, raw, WMAX, taps0, dly0, s_sym[0], tid);
+    tt_issue_item<S, NRX, TOPN, TPB>(U, it, raw, WMAX, taps0, dly0, s_sym[0], tid);
     tt_cp_async_wait_all();
     __syncthreads();
-    tt_convert_item<S, NRX, NP, TOPN, WMAX>(U, it, raw, WMAX, planes, taps0, dly0, tid);
-    if (tid == 0) tt_locate(ues, segs, n_segs, s_claim, total_items, cursors, s_it[1]);
+    tt_convert_item<S, NRX, NP, TOPN, WMAX, TPB>(U, it, raw, WMAX, planes, taps0, dly0, tid);
+    if (tid == 0) tt_locate<TPB>(ues, segs, n_segs, s_claim, total_items, cursors, s_it[1]);
     __syncthreads();
   }
 
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     float4 *tc = cb ? taps1 : taps0, *tn = cb ? taps0 : taps1;
     int *dc = cb ? dly1 : dly0, *dn = cb ? dly0 : dly1;
     const TTUEDesc *Un = ues + nxt.ue;
-    if (nxt.valid) tt_issue_item<S, NRX, TOPN>(Un, nxt, raw, WMAX, tn, dn, s_sym[cb ^ 1], tid);
+    if (nxt.valid) tt_issue_item<S, NRX, TOPN, TPB>(Un, nxt, raw, WMAX, tn, dn, s_sym[cb ^ 1], tid);
     tt_compute_item<S, NRX, NP, TOPN>(ues + cur.ue, cur, planes, tc, dc, s_sym[cb], tid);
     // claimed after the arithmetic: claiming before it measured 4.5% slower on the 16-UE step
     uint32_t nn = 0;
@@ -465,16 +471,16 @@ __global__ void __launch_bounds__(TT_TPB, tt_min_blocks(S, NRX))
     tt_cp_async_wait_all();
     __syncthreads();
     if (!nxt.valid) return;
-    tt_convert_item<S, NRX, NP, TOPN, WMAX>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
-    if (tid == 0) tt_locate(ues, segs, n_segs, nn, total_items, cursors, s_it[cb]);
+    tt_convert_item<S, NRX, NP, TOPN, WMAX, TPB>(Un, nxt, raw, WMAX, planes, tn, dn, tid);
+    if (tid == 0) tt_locate<TPB>(ues, segs, n_segs, nn, total_items, cursors, s_it[cb]);
     __syncthreads();
     cb ^= 1;
   }
 }
 
-template <int S, int NRX, int DMAX, bool TOPN>
+template <int S, int NRX, int DMAX, bool TOPN, int TPB>
 cudaError_t tt_launch_variant(const TTLaunch &L, cudaStream_t st) {
-  auto kern = tt_conv_fp32_kernel<S, NRX, DMAX, TOPN>;
+  auto kern = tt_conv_fp32_kernel<S, NRX, DMAX, TOPN, TPB>;
   static bool attr_done = false;  // benign race: the attribute call is idempotent
   if (!attr_done) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -483,37 +489,38 @@ cudaError_t tt_launch_variant(const TTLaunch &L, cudaStream_t st) {
   }
   if (L.grid < 0) {  // occupancy query: blocks per SM returned through grid
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, TT_TPB, L.smem) != cudaSuccess) blocks = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, TPB, L.smem) != cudaSuccess) blocks = 1;
     const_cast<TTLaunch &>(L).grid = -(blocks > 0 ? blocks : 1);
     return cudaSuccess;
   }
   if (L.grid == 0 || L.total_items == 0) return cudaSuccess;
-  kern<<<L.grid, TT_TPB, L.smem, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter, L.ntx, L.tap_max,
+  kern<<<L.grid, TPB, L.smem, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter, L.ntx, L.tap_max,
                                        L.k_max, L.cursors);
   return cudaGetLastError();
 }
 
-template <int S, int NRX, bool TOPN>
+template <int S, int NRX, bool TOPN, int TPB>
 cudaError_t tt_launch_dclass(const TTLaunch &L, cudaStream_t st) {
   switch (L.dclass) {
-    case 0: return tt_launch_variant<S, NRX, TT_DCLASS0, TOPN>(L, st);
-    case 1: return tt_launch_variant<S, NRX, TT_DCLASS1, TOPN>(L, st);
-    case 2: return tt_launch_variant<S, NRX, TT_DCLASS2, TOPN>(L, st);
-    case 3: return tt_launch_variant<S, NRX, TT_DCLASS3, TOPN>(L, st);
+    case 0: return tt_launch_variant<S, NRX, TT_DCLASS0, TOPN, TPB>(L, st);
+    case 1: return tt_launch_variant<S, NRX, TT_DCLASS1, TOPN, TPB>(L, st);
+    case 2: return tt_launch_variant<S, NRX, TT_DCLASS2, TOPN, TPB>(L, st);
+    case 3: return tt_launch_variant<S, NRX, TT_DCLASS3, TOPN, TPB>(L, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int S, bool TOPN>
+template <int S, bool TOPN, int TPB>
 cudaError_t tt_launch_spt(const TTLaunch &L, cudaStream_t st) {
+  if (L.tpb != TPB) return cudaErrorInvalidValue;
   switch (L.nrx) {
-    case 1: return tt_launch_dclass<S, 1, TOPN>(L, st);
-    case 2: return tt_launch_dclass<S, 2, TOPN>(L, st);
+    case 1: return tt_launch_dclass<S, 1, TOPN, TPB>(L, st);
+    case 2: return tt_launch_dclass<S, 2, TOPN, TPB>(L, st);
     case 3:
-      if constexpr (S <= 8) return tt_launch_dclass<S, 3, TOPN>(L, st);
+      if constexpr (S <= 8) return tt_launch_dclass<S, 3, TOPN, TPB>(L, st);
       return cudaErrorInvalidValue;
     case 4:
-      if constexpr (S <= 8) return tt_launch_dclass<S, 4, TOPN>(L, st);
+      if constexpr (S <= 8) return tt_launch_dclass<S, 4, TOPN, TPB>(L, st);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }

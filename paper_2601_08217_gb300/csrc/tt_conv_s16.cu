@@ -1,4 +1,4 @@
-// Samples-per-thread = 16 variants of the tiled FP32 channel kernel (up to 2 Rx antennas).
+// Samples-per-thread = 16 variants of the tiled FP32 channel kernel, 128 threads per CTA (one TU per S).
 #include "tt_conv_kernel.cuh"
 
-cudaError_t tt_launch_conv_s16(const TTLaunch &L, cudaStream_t st) { return tt::tt_launch_spt<16, false>(L, st); }
+cudaError_t tt_launch_conv_s16(const TTLaunch &L, cudaStream_t st) { return tt::tt_launch_spt<16, false, TT_TPB>(L, st); }

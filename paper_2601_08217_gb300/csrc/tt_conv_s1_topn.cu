@@ -1,5 +1,5 @@
 // Samples-per-thread = 1 variants of the tiled FP32 channel kernel with sparse convolution
-// (top-n taps per symbol and link, Sec. III-C); one TU per S.
+// (top-n taps per symbol and link, Sec. III-C), 128 threads per CTA; one TU per S.
 #include "tt_conv_kernel.cuh"
 
-cudaError_t tt_launch_conv_s1_topn(const TTLaunch &L, cudaStream_t st) { return tt::tt_launch_spt<1, true>(L, st); }
+cudaError_t tt_launch_conv_s1_topn(const TTLaunch &L, cudaStream_t st) { return tt::tt_launch_spt<1, true, TT_TPB>(L, st); }

@@ -138,13 +138,14 @@ int pick_dclass(int d_max) {
   return 3;
 }
 
-// Work-item geometry of a channel for samples-per-thread spt: (chunk table, largest symbols touched).
-std::vector<int32_t> chunk_table(const std::vector<uint32_t> &L, int spt, int *max_touched) {
+// Work-item geometry of a channel for samples-per-thread spt and tpb threads per CTA: (chunk
+// table, largest symbols touched).
+std::vector<int32_t> chunk_table(const std::vector<uint32_t> &L, int spt, int tpb, int *max_touched) {
   int n = 0;
   for (uint32_t v : L) n += (int)v;
-  const int items = (n / spt + TT_TPB - 1) / TT_TPB;
+  const int items = (n / spt + tpb - 1) / tpb;
   std::vector<int32_t> L32(L.begin(), L.end()), chunks(items);
-  tt_conv_chunk_info(spt, L32.data(), (int)L32.size(), chunks.data(), items);
+  tt_conv_chunk_info(spt, tpb, L32.data(), (int)L32.size(), chunks.data(), items);
   *max_touched = 1;
   for (int32_t v : chunks) *max_touched = std::max(*max_touched, (int)(v >> 16));
   return chunks;
@@ -225,10 +226,11 @@ void mark_pushed(tt_chan *c, uint64_t first, uint32_t n) { mark_pushed_at(c, fir
 
 bool valid_chan(const tt_chan *c) { return c && c->e; }
 
-// Switch a channel's tiled-kernel geometry to spt samples per thread (engine lock held).
-tt_status set_spt(tt_chan *c, int spt) {
+// Switch a channel's tiled-kernel geometry to spt samples per thread and tpb threads per CTA
+// (engine lock held).
+tt_status set_geom(tt_chan *c, int spt, int tpb) {
   int touched = 1;
-  std::vector<int32_t> chunks = chunk_table(c->sym_len, spt, &touched);
+  std::vector<int32_t> chunks = chunk_table(c->sym_len, spt, tpb, &touched);
   int32_t *d_chunks = nullptr;
   cudaError_t err = cudaMalloc(&d_chunks, chunks.size() * sizeof(int32_t));
   if (err == cudaSuccess)
@@ -240,10 +242,12 @@ tt_status set_spt(tt_chan *c, int spt) {
   cudaFree(c->d_chunks);
   c->d_chunks = d_chunks;
   c->spt = spt;
+  c->tpb = tpb;
   c->max_sym_touched = touched;
   TTUEDesc &d = c->desc;
   d.chunk_info = d_chunks;
   d.spt = spt;
+  d.tpb = tpb;
   d.groups = c->n / spt;
   d.items_per_slot = (int)chunks.size();
   int b = 0, g = 0;
@@ -266,22 +270,23 @@ bool sparse(const tt_chan *c) { return c->desc.top_n > 0 && c->desc.top_n < c->d
 // the compacted lists of every touched symbol and link (at most tap_need entries).
 int k_need(const tt_chan *c, int tap_need) { return sparse(c) ? std::max(c->desc.n_taps, tap_need) : c->desc.n_taps; }
 
-// Shared-memory need of a traced channel at spt samples per thread (0 if it does not fit); with
-// sparse convolution the delay-offset array holds the compacted lists of every touched symbol.
-size_t smem_need(const tt_chan *c, int spt, int *tap_need) {
+// Shared-memory need of a traced channel at spt samples per thread and tpb threads per CTA (0 if
+// it does not fit); with sparse convolution the delay-offset array holds the compacted lists of
+// every touched symbol.
+size_t smem_need(const tt_chan *c, int spt, int tpb, int *tap_need) {
   int touched = 1;
-  chunk_table(c->sym_len, spt, &touched);
+  chunk_table(c->sym_len, spt, tpb, &touched);
   *tap_need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * (uint32_t)c->desc.n_taps);
-  const size_t b = tt_conv_smem_bytes(spt, c->dclass, (int)c->cfg.n_tx, *tap_need, k_need(c, *tap_need));
+  const size_t b = tt_conv_smem_bytes(spt, tpb, c->dclass, (int)c->cfg.n_tx, *tap_need, k_need(c, *tap_need));
   return b <= 200 * 1024 ? b : 0;
 }
 
-// Switch a traced channel to spt and refresh its launch parameters (engine lock held).
-tt_status apply_spt(tt_chan *c, int spt) {
+// Switch a traced channel to (spt, tpb) and refresh its launch parameters (engine lock held).
+tt_status apply_geom(tt_chan *c, int spt, int tpb) {
   int need = 0;
-  const size_t b = smem_need(c, spt, &need);
-  if (!b) return fail(TT_ERR_INVALID, "samples per thread %d does not fit", spt);
-  tt_status st = set_spt(c, spt);
+  const size_t b = smem_need(c, spt, tpb, &need);
+  if (!b) return fail(TT_ERR_INVALID, "%d samples per thread at %d threads does not fit", spt, tpb);
+  tt_status st = set_geom(c, spt, tpb);
   if (st != TT_OK) return st;
   c->tap_need = need;
   c->smem = b;
@@ -295,7 +300,7 @@ struct PlanGroup {
   int nseg = 0;
   uint32_t items = 0;
   size_t smem = 0;
-  int spt = 1, nrx = 1, ntx = 1, dclass = 0, tap_max = 1, k_max = 1, grid = 1;
+  int spt = 1, tpb = TT_TPB, nrx = 1, ntx = 1, dclass = 0, tap_max = 1, k_max = 1, grid = 1;
   int topn = 0;  // the group's UEs use sparse convolution
 };
 struct Plan {
@@ -313,7 +318,8 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
   auto vkey = [&](size_t i) {
     const tt_chan *c = chans[i];
-    return (((c->spt * 8 + (int)c->cfg.n_rx) * 8 + (int)c->cfg.n_tx) * 8 + c->dclass) * 2 + (sparse(c) ? 1 : 0);
+    return ((((c->spt * 8 + (int)c->cfg.n_rx) * 8 + (int)c->cfg.n_tx) * 8 + c->dclass) * 2 + (sparse(c) ? 1 : 0)) * 2 +
+           (c->tpb == TT_TPB_WIDE ? 1 : 0);
   };
   auto cost = [&](size_t i) {
     const tt_chan *c = chans[i];
@@ -333,6 +339,7 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
       PlanGroup g;
       g.seg0 = p.segs.size();
       g.spt = c->spt;
+      g.tpb = c->tpb;
       g.nrx = (int)c->cfg.n_rx;
       g.ntx = (int)c->cfg.n_tx;
       g.dclass = c->dclass;
@@ -356,9 +363,10 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
   }
   if ((int)p.groups.size() > e->counter_cap) return fail(TT_ERR_INVALID, "too many kernel variants in one run");
   for (PlanGroup &g : p.groups) {
-    g.smem = tt_conv_smem_bytes(g.spt, g.dclass, g.ntx, g.tap_max, g.k_max);
+    g.smem = tt_conv_smem_bytes(g.spt, g.tpb, g.dclass, g.ntx, g.tap_max, g.k_max);
     TTLaunch L{};
     L.spt = g.spt;
+    L.tpb = g.tpb;
     L.nrx = g.nrx;
     L.ntx = g.ntx;
     L.dclass = g.dclass;
@@ -400,6 +408,7 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
     L.total_items = g.items;
     L.counter = e->persistent ? e->d_counters + gi : nullptr;
     L.spt = g.spt;
+    L.tpb = g.tpb;
     L.nrx = g.nrx;
     L.ntx = g.ntx;
     L.dclass = g.dclass;
@@ -577,6 +586,31 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
 
 namespace ttx {
 cudaEvent_t get_event(tt_engine *e) { return ::get_event(e); }
+std::vector<int> spt_candidates(const std::vector<uint32_t> &L, uint32_t cap, uint32_t n_rx, uint32_t n_tx) {
+  return ::spt_candidates(L, cap, n_rx, n_tx);
+}
+size_t smem_need(const tt_chan *c, int spt, int tpb, int *tap_need) { return ::smem_need(c, spt, tpb, tap_need); }
+tt_status apply_geom(tt_chan *c, int spt, int tpb) { return ::apply_geom(c, spt, tpb); }
+tt_status upload_desc(tt_chan *c) { return ::upload_desc(c); }
+void drop_graph(tt_engine *e) { ::drop_graph(e); }
+tt_status time_batch(tt_engine *e, const std::vector<tt_chan *> &chans, const std::vector<uint64_t> &first,
+                     const std::vector<uint64_t> &count, int reps, cudaEvent_t a, cudaEvent_t b, float *best_ms) {
+  Plan plan;
+  tt_status st = build_plan(e, chans, first, count, plan);
+  if (st != TT_OK) return st;
+  if ((st = launch_direct(e, plan)) != TT_OK) return st;  // warm-up
+  *best_ms = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(a, e->stream);
+    if ((st = launch_direct(e, plan)) != TT_OK) return st;
+    cudaEventRecord(b, e->stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) return fail(TT_ERR_CUDA, "autotune: timing failed");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    *best_ms = std::min(*best_ms, ms);
+  }
+  return TT_OK;
+}
 cudaError_t update_completed(tt_engine *e) { return ::update_completed(e); }
 void update_chan(tt_chan *c) { ::update_chan(c); }
 tt_status check_room(tt_chan *c, uint64_t first, uint32_t n) { return ::check_room(c, first, n); }
@@ -604,6 +638,8 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   if (cfg->samples_per_thread && cfg->samples_per_thread != 1 && cfg->samples_per_thread != 2 &&
       cfg->samples_per_thread != 4 && cfg->samples_per_thread != 8 && cfg->samples_per_thread != 16)
     return fail(TT_ERR_INVALID, "samples_per_thread must be 0, 1, 2, 4, 8 or 16");
+  if (cfg->threads_per_block && cfg->threads_per_block != TT_TPB && cfg->threads_per_block != TT_TPB_WIDE)
+    return fail(TT_ERR_INVALID, "threads_per_block must be 0, %d or %d", TT_TPB, TT_TPB_WIDE);
   int ndev = 0;
   cudaError_t q = cudaGetDeviceCount(&ndev);
   if (q != cudaSuccess || ndev == 0) return fail(TT_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(q));
@@ -615,9 +651,11 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   e->form = cfg->form;
   e->max_ues = cfg->max_ues ? cfg->max_ues : 1024;
   e->spt_override = cfg->samples_per_thread;
+  e->tpb_override = cfg->threads_per_block;
   e->persistent = cfg->persistent;
   e->graphs = cfg->struct_size >= offsetof(tt_engine_config, graphs) + sizeof(uint32_t) && cfg->graphs != 0;
   cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
+  ttx::tune_load(e);  // choices stored for this device model (TT_TUNE_CACHE)
   e->table.assign(e->max_ues, nullptr);
   cudaError_t err = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
   if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking);
@@ -791,7 +829,7 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   d.out_f32 = cfg->output_format == TT_OUT_CF32 ? 1 : 0;
   d.top_n = (int)cfg->top_n;
   const std::vector<int> cands = spt_candidates(c->sym_len, e->spt_override, cfg->n_rx, cfg->n_tx);
-  tt_status sst = set_spt(c, cands.empty() ? 1 : cands[0]);
+  tt_status sst = set_geom(c, cands.empty() ? 1 : cands[0], e->tpb_override ? (int)e->tpb_override : TT_TPB);
   if (sst != TT_OK) {
     cudaFree(c->d_in);
     cudaFree(c->d_out);
@@ -835,9 +873,9 @@ tt_status tt_chan_destroy(tt_chan *c) {
 }
 
 // Check a trace's delays and geometry against the channel and pick the tiled-kernel geometry
-// (engine lock not needed: reads the channel's configuration only).
+// (engine lock not needed: reads the channel's configuration and the tuning cache only).
 struct TraceGeo {
-  int d_max = 0, dclass = 0, spt = 0, tap_need = 0;
+  int d_max = 0, dclass = 0, spt = 0, tpb = TT_TPB, tap_need = 0;
   size_t smem = 0;
 };
 static tt_status trace_geometry(const tt_chan *c, const int32_t *delays, uint32_t n_taps, TraceGeo &g) {
@@ -855,29 +893,42 @@ static tt_status trace_geometry(const tt_chan *c, const int32_t *delays, uint32_
   if (tc)
     for (uint32_t v : c->sym_len)
       if (v % 8) return fail(TT_ERR_INVALID, "tensor-core channels need symbol lengths divisible by 8");
-  // largest samples-per-thread whose shared-memory footprint fits (the tensor-core form keeps the
-  // smallest valid tiled geometry, unused)
   const bool topn = c->cfg.top_n > 0 && c->cfg.top_n < n_taps;
+  auto fits = [&](int s, int t) {
+    int touched = 1;
+    chunk_table(c->sym_len, s, t, &touched);
+    const int need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * n_taps);
+    const size_t b = tt_conv_smem_bytes(s, t, g.dclass, c->cfg.n_tx, need, topn ? std::max((int)n_taps, need) : (int)n_taps);
+    if (b > 200 * 1024) return false;
+    g.spt = s;
+    g.tpb = t;
+    g.tap_need = need;
+    g.smem = b;
+    return true;
+  };
+  // largest samples-per-thread whose shared-memory footprint fits at 128 threads, or at the
+  // engine's thread count (the tensor-core form keeps the smallest valid tiled geometry, unused)
+  const int tpb = c->e->tpb_override ? (int)c->e->tpb_override : TT_TPB;
   g.spt = 0;
   for (int s : spt_candidates(c->sym_len, c->e->spt_override, c->cfg.n_rx, c->cfg.n_tx)) {
     if (tc) {
       g.spt = 1;
       break;
     }
-    int touched = 1;
-    chunk_table(c->sym_len, s, &touched);
-    const int need = touched * (int)(c->cfg.n_rx * c->cfg.n_tx * n_taps);
-    const size_t b = tt_conv_smem_bytes(s, g.dclass, c->cfg.n_tx, need, topn ? std::max((int)n_taps, need) : (int)n_taps);
-    if (b <= 200 * 1024) {
-      g.spt = s;
-      g.tap_need = need;
-      g.smem = b;
-      break;
-    }
+    if (fits(s, tpb)) break;
   }
   if (g.spt == 0)
     return fail(TT_ERR_INVALID, "channel too large for the tiled kernel: %u x %u antennas, %u taps, delay %d",
                 c->cfg.n_rx, c->cfg.n_tx, n_taps, g.d_max);
+  // a choice the autotuner made for this class on this device model (TT_TUNE_CACHE) replaces it
+  int cs = 0, ct = 0;
+  if (!tc && ttx::tune_lookup(c->e, ttx::tune_class_key(c, n_taps, g.dclass), &cs, &ct)) {
+    const TraceGeo keep = g;
+    const std::vector<int> ok = spt_candidates(c->sym_len, ttx::tune_spt_cap(c->e), c->cfg.n_rx, c->cfg.n_tx);
+    const bool count_ok = c->e->tpb_override ? ct == (int)c->e->tpb_override : (ct == TT_TPB || ct == TT_TPB_WIDE);
+    if (!count_ok || std::find(ok.begin(), ok.end(), cs) == ok.end() || !fits(cs, ct))
+      g = keep;
+  }
   return TT_OK;
 }
 
@@ -975,7 +1026,7 @@ static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64
     d.sparse_dly = c->d_sparse_dly;
     d.sparse_len = len;
   }
-  tt_status sst = set_spt(c, g.spt);
+  tt_status sst = set_geom(c, g.spt, g.tpb);
   if (sst != TT_OK) return sst;
   if (c->cfg.precision != TT_FP32) {  // the tensor-core kernel's work items: one per symbol
     std::vector<int32_t> L32(c->sym_len.begin(), c->sym_len.end());
@@ -1708,111 +1759,6 @@ tt_status tt_engine_run(tt_engine *e) {
     for (tt_chan *m : cl->members) m->pulled_end = std::max(m->pulled_end, ce.second);  // consumed
   }
   return cst;
-}
-
-tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned) {
-  if (!e) return fail(TT_ERR_INVALID, "null engine");
-  if (reps < 1) reps = 3;
-  std::lock_guard<std::mutex> lk(e->mu);
-  TT_CK(cudaSetDevice(e->device));
-  TT_CK(cudaStreamSynchronize(e->stream));
-  // classes: same numerology, antennas, taps and delay class tune alike
-  std::vector<std::pair<std::vector<int64_t>, std::vector<tt_chan *>>> classes;
-  for (tt_chan *c : e->table) {
-    if (!c || !c->has_trace || c->cfg.precision != TT_FP32) continue;
-    std::vector<int64_t> key(c->sym_len.begin(), c->sym_len.end());
-    key.insert(key.end(), {(int64_t)c->cfg.n_tx, (int64_t)c->cfg.n_rx, (int64_t)c->desc.n_taps,
-                           (int64_t)c->dclass, (int64_t)(c->desc.noise_std > 0.f), (int64_t)c->desc.out_f32,
-                           (int64_t)c->desc.top_n});
-    auto it = std::find_if(classes.begin(), classes.end(), [&](const auto &p) { return p.first == key; });
-    if (it == classes.end()) classes.push_back({key, {c}});
-    else it->second.push_back(c);
-  }
-  // The objective is the whole batch: one slot of every channel that has a free ring position,
-  // launched as the engine launches it.  A class's samples-per-thread is changed only when the
-  // batch gets faster, so the tuner never splits the launch into more kernel variants for a
-  // class-local gain.
-  std::vector<tt_chan *> room;
-  std::vector<uint64_t> first, count;
-  for (auto &cls : classes)
-    for (tt_chan *c : cls.second) {
-      const uint64_t f = c->started ? c->pushed_end : 0, start = c->started ? c->pulled_end : 0;
-      if (f + 1 - start + (uint64_t)c->hist <= (uint64_t)c->Q) {
-        room.push_back(c);
-        first.push_back(f);
-        count.push_back(1);
-      }
-    }
-  if (room.empty()) {
-    if (classes_tuned) *classes_tuned = 0;
-    return TT_OK;
-  }
-  cudaEvent_t a = nullptr, b = nullptr;
-  TT_CK(cudaEventCreate(&a));
-  TT_CK(cudaEventCreate(&b));
-  tt_status result = TT_OK;
-  auto time_batch = [&](float *best_ms) -> tt_status {
-    Plan plan;
-    tt_status st = build_plan(e, room, first, count, plan);
-    if (st != TT_OK) return st;
-    if ((st = launch_direct(e, plan)) != TT_OK) return st;  // warm-up
-    *best_ms = 1e30f;
-    for (int r = 0; r < reps; ++r) {
-      cudaEventRecord(a, e->stream);
-      if ((st = launch_direct(e, plan)) != TT_OK) return st;
-      cudaEventRecord(b, e->stream);
-      if (cudaEventSynchronize(b) != cudaSuccess) return fail(TT_ERR_CUDA, "autotune: timing failed");
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
-      *best_ms = std::min(*best_ms, ms);
-    }
-    return TT_OK;
-  };
-  // largest classes first: their choice moves the batch most
-  std::stable_sort(classes.begin(), classes.end(), [](const auto &x, const auto &y) {
-    auto work = [](const std::vector<tt_chan *> &v) {
-      double w = 0;
-      for (const tt_chan *c : v) w += (double)c->n * c->desc.n_taps * c->cfg.n_tx * c->cfg.n_rx;
-      return w;
-    };
-    return work(x.second) > work(y.second);
-  });
-  float cur_ms = 0.f;
-  uint32_t tuned = 0;
-  result = time_batch(&cur_ms);
-  for (size_t ci = 0; ci < classes.size() && result == TT_OK; ++ci) {
-    auto &cls = classes[ci];
-    tt_chan *c0 = cls.second[0];
-    std::vector<int> cands;
-    for (int s : spt_candidates(c0->sym_len, e->spt_override ? e->spt_override : 16, c0->cfg.n_rx, c0->cfg.n_tx)) {
-      int need = 0;
-      if (smem_need(c0, s, &need)) cands.push_back(s);
-    }
-    if (cands.size() < 2) continue;
-    const int start_spt = c0->spt;
-    int best = start_spt;
-    for (int s : cands) {
-      if (s == start_spt) continue;
-      for (tt_chan *c : cls.second)
-        if ((result = apply_spt(c, s)) != TT_OK || (result = upload_desc(c)) != TT_OK) break;
-      if (result != TT_OK) break;
-      float ms = 0.f;
-      if ((result = time_batch(&ms)) != TT_OK) break;
-      if (ms < 0.99f * cur_ms) {
-        cur_ms = ms;
-        best = s;
-      }
-    }
-    if (result != TT_OK) break;
-    for (tt_chan *c : cls.second)
-      if ((result = apply_spt(c, best)) != TT_OK || (result = upload_desc(c)) != TT_OK) break;
-    ++tuned;
-  }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  drop_graph(e);  // tuned geometry invalidates the cached graph
-  if (result == TT_OK && classes_tuned) *classes_tuned = tuned;
-  return result;
 }
 
 tt_status tt_engine_replay(tt_engine *e, uint32_t n_steps, uint32_t slots_per_step) {

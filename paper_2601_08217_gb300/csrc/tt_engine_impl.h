@@ -1,12 +1,14 @@
 // Internal state of the channel engine (host side), shared by the engine's translation units:
-// tt_engine.cpp (the C ABI of channels, runs and copies) and tt_server.cpp (serving: the batching
-// thread, request latencies, admission waiting list).  Not part of the public ABI.
+// tt_engine.cpp (the C ABI of channels, runs and copies), tt_server.cpp (serving: the batching
+// thread, request latencies, admission waiting list) and tt_tune.cpp (the autotuner and its
+// on-disk cache).  Not part of the public ABI.
 #pragma once
 
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -28,6 +30,7 @@ struct tt_engine {
   uint32_t form = TT_FORM_BATCHED;
   uint32_t max_ues = 1024;
   uint32_t spt_override = 0;
+  uint32_t tpb_override = 0;  // tiled kernel's threads per CTA forced for every channel (0: 128 or tuned)
   uint32_t persistent = 0;
   int num_sms = 1;
   cudaStream_t stream = nullptr;  // all compute and device copies, in order
@@ -88,6 +91,12 @@ struct tt_engine {
   uint64_t admit_next = 0;
   // channels with pushed slots not launched yet (each once), so a run looks at those only
   std::vector<tt_chan *> pending;
+  // tuning cache: class key -> (samples per thread, threads per CTA) for this device model, loaded
+  // from the file TT_TUNE_CACHE names at creation and written back by the autotuner
+  std::mutex tune_mu;
+  std::string dev_name;
+  std::string tune_path;
+  std::map<std::string, std::pair<int, int>> tune;
 };
 
 struct tt_chan {
@@ -103,7 +112,7 @@ struct tt_chan {
   int32_t *d_delays = nullptr;
   uint64_t trace_bytes = 0;
   bool has_trace = false;
-  int spt = 1, dclass = 0, max_sym_touched = 1;
+  int spt = 1, tpb = TT_TPB, dclass = 0, max_sym_touched = 1;
   int32_t *d_chunks = nullptr;  // per work item of a slot: first symbol | symbols touched << 16
   int tap_need = 0;             // max symbols touched x n_rx x n_tx x K
   size_t smem = 0;
@@ -185,6 +194,29 @@ void admission_notify(tt_engine *e);
 // The thread running the server's batching loop (tt_engine_run from others is refused).
 bool is_server_thread(const tt_engine *e);
 int64_t server_queue_timeout_us(const tt_engine *e);
+
+// ---- tiled-kernel geometry and the autotuner (tt_engine.cpp, tt_tune.cpp) ----
+// Samples-per-thread values a channel's symbol lengths allow, largest first, none above cap.
+std::vector<int> spt_candidates(const std::vector<uint32_t> &L, uint32_t cap, uint32_t n_rx, uint32_t n_tx);
+// Shared memory of a traced channel at (spt, tpb); 0 if it does not fit (engine lock held).
+size_t smem_need(const tt_chan *c, int spt, int tpb, int *tap_need);
+// Switch a traced channel to (spt, tpb) (engine lock held); upload_desc publishes it.
+tt_status apply_geom(tt_chan *c, int spt, int tpb);
+tt_status upload_desc(tt_chan *c);
+void drop_graph(tt_engine *e);
+// One batched launch of slots [first[i], first[i] + count[i]) of chans[i], as a run launches it:
+// a warm-up, then the best of reps timings between events a and b (engine lock held).
+tt_status time_batch(tt_engine *e, const std::vector<tt_chan *> &chans, const std::vector<uint64_t> &first,
+                     const std::vector<uint64_t> &count, int reps, cudaEvent_t a, cudaEvent_t b, float *best_ms);
+// Tuning class of an FP32 channel with this trace: symbol lengths, antennas, tap-count bucket (next
+// power of two, at least 8), delay class, AWGN on/off, output format, top-n.
+std::string tune_class_key(const tt_chan *c, uint32_t n_taps, int dclass);
+// Samples-per-thread cap of the autotuner's search (the engine's setting, else 16).
+uint32_t tune_spt_cap(const tt_engine *e);
+// The cached choice for a class on this engine's device model (any thread).
+bool tune_lookup(tt_engine *e, const std::string &key, int *spt, int *tpb);
+// Read TT_TUNE_CACHE (if set) into the engine's cache; a missing file is an empty cache.
+void tune_load(tt_engine *e);
 
 template <class Room>
 tt_status server_wait_room(tt_engine *e, std::unique_lock<std::mutex> &lk, Room room) {

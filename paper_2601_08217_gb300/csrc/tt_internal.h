@@ -10,7 +10,8 @@
 #define TT_MAX_ANT 4
 #define TT_MAX_TAPS 128
 #define TT_MAX_DELAY 1024
-#define TT_TPB 128  // threads per CTA of the tiled kernel
+#define TT_TPB 128       // threads per CTA of the tiled kernel: the default choice
+#define TT_TPB_WIDE 256  // the other choice the autotuner tries (a work item spans twice the samples)
 #define TT_STATIC_MAX_CHANS 64            // channels per tt_conv_static call
 #define TT_STATIC_MAX_ITEMS_PER_SLOT 512  // work items per slot in tt_conv_static (N <= 65536)
 
@@ -21,23 +22,23 @@
 #define TT_DCLASS2 512
 #define TT_DCLASS3 1024
 
-// Window geometry of the tiled kernel (samples per thread S, delay class DMAX):
-// delay padding DP (a multiple of S) and phase-plane pitch NP in float2 words.
+// Window geometry of the tiled kernel (TPB threads per CTA, samples per thread S, delay class
+// DMAX): delay padding DP (a multiple of S) and phase-plane pitch NP in float2 words.
 // NP is padded so that NP = 16/S (mod 16): sixteen consecutive window
 // elements written by a half-warp then land in sixteen distinct 8-byte bank
 // pairs (element e goes to plane e mod S, row e / S).
 __host__ __device__ constexpr int tt_geo_dp(int S, int DMAX) { return (DMAX + S - 1) / S * S; }
-__host__ __device__ constexpr int tt_geo_np_raw(int S, int DMAX) {
-  return (TT_TPB * S + tt_geo_dp(S, DMAX)) / S + 1;
+__host__ __device__ constexpr int tt_geo_np_raw(int TPB, int S, int DMAX) {
+  return (TPB * S + tt_geo_dp(S, DMAX)) / S + 1;
 }
-__host__ __device__ constexpr int tt_geo_np(int S, int DMAX) {
-  return tt_geo_np_raw(S, DMAX) + ((16 / (S < 16 ? S : 16)) % 16 - tt_geo_np_raw(S, DMAX) % 16 + 16) % 16;
+__host__ __device__ constexpr int tt_geo_np(int TPB, int S, int DMAX) {
+  return tt_geo_np_raw(TPB, S, DMAX) + ((16 / (S < 16 ? S : 16)) % 16 - tt_geo_np_raw(TPB, S, DMAX) % 16 + 16) % 16;
 }
 __host__ __device__ constexpr int tt_dclass_max(int dclass) {
   return dclass == 0 ? TT_DCLASS0 : (dclass == 1 ? TT_DCLASS1 : (dclass == 2 ? TT_DCLASS2 : TT_DCLASS3));
 }
 // Longest input window of one work item (samples): the item's span plus the delay line.
-__host__ __device__ constexpr int tt_geo_wmax(int S, int DMAX) { return TT_TPB * S + tt_geo_dp(S, DMAX); }
+__host__ __device__ constexpr int tt_geo_wmax(int TPB, int S, int DMAX) { return TPB * S + tt_geo_dp(S, DMAX); }
 
 // Device-resident description of one admitted UE link.  The engine keeps an
 // array of these on the device; work items index into it.
@@ -66,6 +67,7 @@ struct TTUEDesc {
   int32_t spt;             // samples per thread of the tiled kernel for this UE
   int32_t dpad;            // d_max rounded up to a multiple of spt: delay-line part of the window
   int32_t groups;          // groups of spt samples per slot
+  int32_t tpb;             // threads per CTA of the tiled kernel: groups per work item
   int32_t items_per_slot;  // CTAs (work items) per slot
   int32_t sym_start[TT_MAX_SYM + 1];  // symbol starts, sym_start[nsym] = n
   int32_t grp_start[TT_MAX_SYM + 1];  // first group of each symbol, grp_start[nsym] = groups
@@ -88,6 +90,7 @@ struct TTLaunch {
   uint32_t *counter;    // non-null: CTAs claim items from this device counter (zeroed before launch);
                         // null: CTA b takes items b, b + grid, b + 2 grid, ...
   int spt;              // 1, 2, 4, 8, 16
+  int tpb;              // threads per CTA: TT_TPB or TT_TPB_WIDE (every UE of the launch has this)
   int nrx;              // 1..4 (every UE of the launch has this many Rx antennas)
   int ntx;              // 1..4 (every UE of the launch has this many Tx antennas)
   int dclass;           // delay class, see TT_DCLASS*
@@ -103,10 +106,11 @@ struct TTLaunch {
 cudaError_t tt_launch_advance(const TTSeg *segs, int n_segs, unsigned long long *cursors, cudaStream_t st);
 
 // Dynamic shared memory of the tiled kernel for a launch.
-size_t tt_conv_smem_bytes(int spt, int dclass, int n_tx, int tap_max, int k_max);
+size_t tt_conv_smem_bytes(int spt, int tpb, int dclass, int n_tx, int tap_max, int k_max);
 
-// First symbol and number of symbols touched by each work item of a slot (packed jf | nst << 16).
-int tt_conv_chunk_info(int spt, const int32_t *sym_len, int nsym, int32_t *out, int max_out);
+// First symbol and number of symbols touched by each work item (tpb groups of spt samples) of a
+// slot, packed jf | nst << 16; returns the item count, or -1 if it exceeds max_out.
+int tt_conv_chunk_info(int spt, int tpb, const int32_t *sym_len, int nsym, int32_t *out, int max_out);
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st);
 // Uplink aggregation at a cell: output slot s = sum over members (in order) of their complex64
 // output slot s, plus the cell's AWGN, then rounded and saturated (or stored as complex64).
@@ -178,6 +182,17 @@ cudaError_t tt_launch_conv_s2_topn(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s4_topn(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s8_topn(const TTLaunch &L, cudaStream_t st);
 cudaError_t tt_launch_conv_s16_topn(const TTLaunch &L, cudaStream_t st);
+// the same variants at TT_TPB_WIDE threads per CTA
+cudaError_t tt_launch_conv_s1_w(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s2_w(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s4_w(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s8_w(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s16_w(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s1_w_topn(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s2_w_topn(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s4_w_topn(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s8_w_topn(const TTLaunch &L, cudaStream_t st);
+cudaError_t tt_launch_conv_s16_w_topn(const TTLaunch &L, cudaStream_t st);
 
 // Block-Toeplitz tensor-core kernel (tcgen05, BF16 or FP16 operands): one work item per
 // (UE, slot, symbol), in groups of up to 1536 samples; status is set to 1 if a bounded wait on the

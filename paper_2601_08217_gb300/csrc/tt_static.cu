@@ -125,12 +125,12 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
       bool ok = true;
       for (uint32_t v : L) ok = ok && (v % (uint32_t)s == 0);
       if (!ok) continue;
-      const int it = tt_conv_chunk_info(s, L32.data(), (int)L32.size(), chunks.data(), kMaxItems);
+      const int it = tt_conv_chunk_info(s, TT_TPB, L32.data(), (int)L32.size(), chunks.data(), kMaxItems);
       if (it < 0) continue;
       int touched = 1;
       for (int q = 0; q < it; ++q) touched = std::max(touched, (int)(chunks[q] >> 16));
       const int need = touched * (int)(c.n_rx * c.n_tx * c.n_taps);
-      if (tt_conv_smem_bytes(s, dclass, (int)c.n_tx, need, (int)c.n_taps) <= 200 * 1024) {
+      if (tt_conv_smem_bytes(s, TT_TPB, dclass, (int)c.n_tx, need, (int)c.n_taps) <= 200 * 1024) {
         spt = s;
         tap_need = need;
         items = it;
@@ -162,6 +162,7 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
     d.out_f32 = c.output_format == TT_OUT_CF32 ? 1 : 0;
     d.top_n = 0;
     d.spt = spt;
+    d.tpb = TT_TPB;
     d.dpad = (d_max + spt - 1) / spt * spt;
     d.groups = (int)N / spt;
     d.items_per_slot = items;
@@ -254,12 +255,13 @@ extern "C" tt_status tt_conv_static(const tt_static_chan *chans, uint32_t n_chan
     L.total_items = gr.items;
     L.counter = d_count + gi;
     L.spt = gr.spt;
+    L.tpb = TT_TPB;
     L.nrx = gr.nrx;
     L.ntx = gr.ntx;
     L.dclass = gr.dclass;
     L.tap_max = gr.tap_max;
     L.k_max = gr.k_max;
-    L.smem = tt_conv_smem_bytes(gr.spt, gr.dclass, gr.ntx, gr.tap_max, gr.k_max);
+    L.smem = tt_conv_smem_bytes(gr.spt, TT_TPB, gr.dclass, gr.ntx, gr.tap_max, gr.k_max);
     L.grid = -1;
     ce = tt_launch_conv_fp32(L, st);
     if (ce != cudaSuccess) return err(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(ce));

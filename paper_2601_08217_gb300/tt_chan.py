@@ -19,13 +19,14 @@ LIB_PATH = os.path.join(HERE, "_build", "libttchan.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "tt_chan.h")
 
 TT_OK, TT_ERR_INVALID, TT_ERR_NO_MEMORY, TT_ERR_CUDA = 0, -1, -2, -3
-TT_ERR_TRACE, TT_ERR_AGAIN, TT_ERR_TIMEOUT, TT_ERR_STATE = -4, -5, -6, -7
+TT_ERR_TRACE, TT_ERR_AGAIN, TT_ERR_TIMEOUT, TT_ERR_STATE, TT_ERR_IO = -4, -5, -6, -7, -8
 TT_FORM_BATCHED, TT_FORM_PLAIN = 0, 1
 TT_FP32, TT_BF16_TC, TT_FP16_TC = 0, 1, 2
 TT_OUT_INT16, TT_OUT_CF32 = 0, 1
 
 STATUS_NAMES = {0: "TT_OK", -1: "TT_ERR_INVALID", -2: "TT_ERR_NO_MEMORY", -3: "TT_ERR_CUDA",
-                -4: "TT_ERR_TRACE", -5: "TT_ERR_AGAIN", -6: "TT_ERR_TIMEOUT", -7: "TT_ERR_STATE"}
+                -4: "TT_ERR_TRACE", -5: "TT_ERR_AGAIN", -6: "TT_ERR_TIMEOUT", -7: "TT_ERR_STATE",
+                -8: "TT_ERR_IO"}
 
 
 class TTError(RuntimeError):
@@ -120,6 +121,11 @@ class StaticChan(C.Structure):
                 ("n_slots", C.c_uint32)]
 
 
+class ChanGeometry(C.Structure):
+    _fields_ = [("tensor_core", C.c_uint32), ("samples_per_thread", C.c_uint32), ("threads_per_cta", C.c_uint32),
+                ("samples_per_item", C.c_uint32), ("items_per_slot", C.c_uint32), ("has_trace", C.c_uint32)]
+
+
 _VP = C.c_void_p
 _SIGS = {
     "tt_engine_create": [C.POINTER(EngineConfig), C.POINTER(_VP)],
@@ -130,6 +136,7 @@ _SIGS = {
     "tt_engine_stream": [_VP, C.POINTER(_VP)],
     "tt_engine_get_stats": [_VP, C.POINTER(EngineStats)],
     "tt_engine_autotune": [_VP, C.c_int32, C.POINTER(C.c_uint32)],
+    "tt_chan_get_geometry": [_VP, C.POINTER(ChanGeometry)],
     "tt_engine_replay": [_VP, C.c_uint32, C.c_uint32],
     "tt_engine_serve": [_VP, C.POINTER(ServeConfig), C.POINTER(ServeReport)],
     "tt_chan_create": [_VP, C.POINTER(ChanConfig), C.POINTER(_VP)],
@@ -226,10 +233,10 @@ def _stream_ptr(stream) -> int:
 # ---------------------------------------------------------------- C-named calls
 def tt_engine_create(device: int = 0, form: int = TT_FORM_BATCHED, hbm_budget_bytes: int = 0,
                      max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False,
-                     graphs: bool = False) -> int:
+                     graphs: bool = False, threads_per_block: int = 0) -> int:
     lib = load()
     cfg = EngineConfig(C.sizeof(EngineConfig), device, hbm_budget_bytes, form, max_ues,
-                       samples_per_thread, 0, int(bool(persistent)), int(bool(graphs)))
+                       samples_per_thread, threads_per_block, int(bool(persistent)), int(bool(graphs)))
     h = _VP()
     _check(lib.tt_engine_create(C.byref(cfg), C.byref(h)))
     return h.value
@@ -267,6 +274,12 @@ def tt_engine_autotune(e: int, reps: int = 3) -> int:
     n = C.c_uint32(0)
     _check(load().tt_engine_autotune(e, reps, C.byref(n)))
     return n.value
+
+
+def tt_chan_get_geometry(c: int) -> dict:
+    g = ChanGeometry()
+    _check(load().tt_chan_get_geometry(c, C.byref(g)))
+    return {f: getattr(g, f) for f, _ in ChanGeometry._fields_}
 
 
 def tt_engine_replay(e: int, n_steps: int, slots_per_step: int = 1):
@@ -508,9 +521,11 @@ def tt_abi_version() -> int:
 # ---------------------------------------------------------------- conveniences
 class Engine:
     def __init__(self, device: int = 0, form: str = "batched", hbm_budget_bytes: int = 0,
-                 max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False, graphs: bool = False):
+                 max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False, graphs: bool = False,
+                 threads_per_block: int = 0):
         f = {"batched": TT_FORM_BATCHED, "plain": TT_FORM_PLAIN}[form]
-        self.h = tt_engine_create(device, f, hbm_budget_bytes, max_ues, samples_per_thread, persistent, graphs)
+        self.h = tt_engine_create(device, f, hbm_budget_bytes, max_ues, samples_per_thread, persistent, graphs,
+                                  threads_per_block)
         self.chans = []
         self.cells = []
 
@@ -583,6 +598,9 @@ class Chan:
             out = np.empty((n_slots, self.spec.n_rx, self.n, 2), dtype=np.int16)
         tt_chan_pull_slots(self.h, first, n_slots, out, timeout_us)
         return out
+
+    def geometry(self) -> dict:
+        return tt_chan_get_geometry(self.h)
 
     def destroy(self):
         if self.h:

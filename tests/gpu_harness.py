@@ -11,14 +11,15 @@ def hist_slots(spec) -> int:
 
 
 def run_gpu(specs, xs, n_slots, first_slot=0, cf32=False, form="batched", spt=0, persistent=False,
-            stream_mode=False, ring_slots=None, precision=tc.TT_FP32, top_n=0):
+            stream_mode=False, ring_slots=None, precision=tc.TT_FP32, top_n=0, tpb=0):
     """Run every UE's slots [first_slot, first_slot + n_slots) and return [n_rx][n_slots*N](...) per UE.
 
-    xs[i] is UE i's int16 input [n_tx][n_slots*N][2].  Bulk mode pushes all slots,
+    xs[i] is UE i's int16 input [n_tx][n_slots*N][2]; tpb forces the tiled kernel's threads per
+    CTA (0: the engine's choice).  Bulk mode pushes all slots,
     runs once and pulls all; stream mode pushes, runs and pulls slot by slot
     through a small ring.
     """
-    eng = tc.Engine(form=form, samples_per_thread=spt, persistent=persistent)
+    eng = tc.Engine(form=form, samples_per_thread=spt, persistent=persistent, threads_per_block=tpb)
     try:
         chans = []
         for sp in specs:

@@ -27,13 +27,14 @@ def test_every_declared_function_is_exported(lib):
 
 
 def test_abi_version_and_error_string(lib):
-    assert tc.tt_abi_version() == 3
+    assert tc.tt_abi_version() == 4
     assert isinstance(tc.tt_last_error(), str)
 
 
 def test_null_arguments_are_rejected_without_touching_cuda(lib):
     assert lib.tt_engine_run(None) == tc.TT_ERR_INVALID
     assert lib.tt_chan_destroy(None) == tc.TT_ERR_INVALID
+    assert lib.tt_chan_get_geometry(None, None) == tc.TT_ERR_INVALID
     assert lib.tt_engine_create(None, None) == tc.TT_ERR_INVALID
     assert "bad config" in tc.tt_last_error()
 

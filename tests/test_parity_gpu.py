@@ -81,7 +81,10 @@ def _case(name):
 CASES = ["siso_odd_lengths", "delay_beyond_slot", "mimo22_noise", "mimo_4tx_3rx_tracetime",
          "nr5mhz_loop_noise", "nr20mhz_mimo_1ms_trace"]
 VARIANTS = [dict(form="batched"), dict(form="batched", persistent=True), dict(form="batched", spt=1),
-            dict(form="batched", spt=2), dict(form="batched", spt=16), dict(form="plain")]
+            dict(form="batched", spt=2), dict(form="batched", spt=16), dict(form="plain"),
+            # 256 threads per CTA: work items twice as long
+            dict(form="batched", tpb=256), dict(form="batched", spt=1, tpb=256),
+            dict(form="batched", persistent=True, spt=16, tpb=256)]
 
 
 def _oracle(spec, x, first_slot=0):

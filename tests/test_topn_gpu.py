@@ -74,11 +74,11 @@ def _topn_reference(spec, x, top_n, out, cf32, first_slot=0):
     return y_ref, q_ref, changed
 
 
-def _check_topn(spec, x, ns, top_n, spt=0, persistent=True):
-    y = run_gpu([spec], [x], ns, cf32=True, spt=spt, persistent=persistent, top_n=top_n)[0]
+def _check_topn(spec, x, ns, top_n, spt=0, persistent=True, tpb=0):
+    y = run_gpu([spec], [x], ns, cf32=True, spt=spt, persistent=persistent, top_n=top_n, tpb=tpb)[0]
     y_ref, _, changed_y = _topn_reference(spec, x, top_n, y, cf32=True)
     assert nrmse(y, y_ref) <= NRMSE_MAX
-    q = run_gpu([spec], [x], ns, spt=spt, persistent=persistent, top_n=top_n)[0]
+    q = run_gpu([spec], [x], ns, spt=spt, persistent=persistent, top_n=top_n, tpb=tpb)[0]
     y_ref, q_ref, changed_q = _topn_reference(spec, x, top_n, q, cf32=False)
     assert_int16_close(q, y_ref, q_ref)
     return changed_y, changed_q
@@ -88,14 +88,14 @@ TOPN_CASES = [("siso_odd_lengths", 2), ("delay_beyond_slot", 1), ("mimo22_noise"
               ("mimo_4tx_3rx_tracetime", 5), ("nr5mhz_loop_noise", 6), ("nr20mhz_mimo_1ms_trace", 4)]
 
 
-@pytest.mark.parametrize("spt", [0, 1, 2, 16])
+@pytest.mark.parametrize("spt,tpb", [(0, 0), (1, 0), (2, 0), (16, 0), (0, 256), (16, 256)])
 @pytest.mark.parametrize("case,top_n", TOPN_CASES)
-def test_top_n_matches_oracle(case, top_n, spt):
+def test_top_n_matches_oracle(case, top_n, spt, tpb):
     spec, x, ns = _case(case)
     y_ref, _ = _oracle_topn(spec, x, top_n)
     y_full, _ = _oracle_topn(spec, x, 0)
     assert nrmse(y_ref, y_full) > 1e-3                  # the sparse result differs from all taps
-    _check_topn(spec, x, ns, top_n, spt=spt)
+    _check_topn(spec, x, ns, top_n, spt=spt, tpb=tpb)
 
 
 def test_near_tie_accepts_the_binary32_choice():
