@@ -179,6 +179,30 @@ tt_status tt_engine_replay(tt_engine *e, uint32_t n_steps, uint32_t slots_per_st
  * that one of its bounded waits expired (the affected slots are invalid). */
 tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us);
 
+/* Bounds-checked build.  The library can be built a second time with
+ * TT_CHECKED=1 (libttchan_checked.so beside libttchan.so; the Python binding
+ * loads it when the environment variable TT_CHECKED is 1).  There the tiled
+ * FP32 kernel tests every shared- and global-memory index before the access.
+ * An index out of bounds is not accessed: the kernel counts it in the
+ * engine's check report and keeps the code of the first one, without a trap,
+ * so the GPU and the process stay usable (the affected slots' outputs are
+ * invalid).  Codes: 1 staged input window (shared) written, 2 input ring
+ * read, 3 tap buffer (shared), 4 trace or sparse tap ring read, 5 delay
+ * buffer (shared), 6 symbol table (shared), 7 phase planes (shared) written,
+ * 8 staged input window read, 9 phase planes read, 10 tap or delay buffer
+ * read by the tap loop, 11 output ring written.  tt_engine_get_check waits
+ * for the launched work, reads the report and clears it.  In the normal
+ * build checked_build is 0 and the report stays empty.  The kernels of the
+ * tensor-core form, the static entry and the auxiliary passes are not
+ * instrumented. */
+typedef struct {
+  uint32_t checked_build; /* 1: this library tests indices */
+  uint32_t violations;    /* out-of-bounds indices since the last call (not accessed) */
+  uint32_t first_code;    /* the first one's code (list above), 0 if none */
+  uint32_t pad;
+} tt_check_report;
+tt_status tt_engine_get_check(tt_engine *e, tt_check_report *out);
+
 /* The engine's CUDA stream (a cudaStream_t) for ordering caller work. */
 tt_status tt_engine_stream(tt_engine *e, void **stream);
 

@@ -39,6 +39,14 @@ int tt_conv_chunk_info(int spt, int tpb, const int32_t *sym_len, int nsym, int32
   return items;
 }
 
+int tt_checked_build() {
+#if defined(TT_CHECKED) && TT_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st) {
   const bool w = L.tpb == TT_TPB_WIDE;
   if (!w && L.tpb != TT_TPB) return cudaErrorInvalidValue;

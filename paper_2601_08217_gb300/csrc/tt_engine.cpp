@@ -418,6 +418,8 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
     L.smem = g.smem;
     L.grid = g.grid;
     L.cursors = cursors;
+    L.check.report = e->d_check;
+    L.check.shrink = e->check_shrink;
     cudaStream_t st = oi == 0 || n_side == 0 ? e->stream : e->side[(oi - 1) % n_side];
     cudaError_t err = tt_launch_conv_fp32(L, st);
     if (err != cudaSuccess) return err;
@@ -618,6 +620,7 @@ void mark_pushed(tt_chan *c, uint64_t first, uint32_t n) { ::mark_pushed(c, firs
 void mark_pushed_at(tt_chan *c, uint64_t first, uint32_t n, int64_t arrival_ns) {
   ::mark_pushed_at(c, first, n, arrival_ns);
 }
+bool cells_have_work(const tt_engine *e);
 }  // namespace ttx
 
 int32_t tt_set_error(int32_t status, const char *msg) {
@@ -670,6 +673,8 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   if (err == cudaSuccess) err = cudaMalloc(&e->d_cursors, sizeof(unsigned long long) * e->max_ues);
   if (err == cudaSuccess) err = cudaMalloc(&e->d_status, sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(e->d_status, 0, sizeof(int));
+  if (err == cudaSuccess) err = cudaMalloc(&e->d_check, 2 * sizeof(uint32_t));
+  if (err == cudaSuccess) err = cudaMemset(e->d_check, 0, 2 * sizeof(uint32_t));
   if (err != cudaSuccess) {
     tt_engine_destroy(e);
     return fail(TT_ERR_CUDA, "engine setup: %s", cudaGetErrorString(err));
@@ -719,6 +724,7 @@ tt_status tt_engine_destroy(tt_engine *e) {
   cudaFree(e->d_retime);
   cudaFree(e->d_topn);
   cudaFree(e->d_status);
+  cudaFree(e->d_check);
   if (e->stream) cudaStreamDestroy(e->stream);
   if (e->copy) cudaStreamDestroy(e->copy);
   if (e->h2d) cudaStreamDestroy(e->h2d);
@@ -1487,6 +1493,25 @@ static tt_status launch_topn(tt_engine *e, const std::vector<tt_chan *> &chans) 
   return TT_OK;
 }
 
+// Engine lock held: whether launch_cells would aggregate something now (every member started and
+// the cell has ring room for slots all members have launched).
+static bool cells_have_work(const tt_engine *e) {
+  for (const tt_cell *cl : e->cells) {
+    if (cl->members.empty()) continue;
+    uint64_t end = UINT64_MAX;
+    bool all_started = true;
+    for (const tt_chan *m : cl->members) {
+      if (!m->started) { all_started = false; break; }
+      end = std::min(end, m->launched_end);
+    }
+    if (!all_started) continue;
+    const uint64_t launched = cl->started ? cl->launched_end : cl->members[0]->start_slot;
+    const uint64_t pulled = cl->started ? cl->pulled_end : launched;
+    if (std::min<uint64_t>(end, pulled + (uint64_t)cl->Q) > launched) return true;
+  }
+  return false;
+}
+
 static tt_status launch_cells(tt_engine *e, std::vector<std::pair<tt_cell *, uint64_t>> &ends) {
   for (tt_cell *cl : e->cells) {
     if (cl->members.empty()) continue;
@@ -1650,6 +1675,10 @@ tt_status tt_engine_run(tt_engine *e) {
   if (e->server && !ttx::is_server_thread(e))
     return fail(TT_ERR_STATE, "a server is running on this engine: it launches the pushed slots itself");
   TT_CK(cudaSetDevice(e->device));
+  if (tt_checked_build()) {  // bounds-checked build, tests only: lower the output-store bound
+    const char *v = std::getenv("TT_TEST_CHECK_SHRINK");
+    e->check_shrink = v ? std::atoi(v) : 0;
+  }
   std::vector<tt_chan *> ready, tc_ready;
   // the channels with unlaunched slots, in table order (the order the plan and a cached graph use)
   std::sort(e->pending.begin(), e->pending.end(), [](const tt_chan *a, const tt_chan *b) { return a->index < b->index; });
@@ -1800,6 +1829,24 @@ tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us) {
   }
   for (tt_chan *c : e->table)
     if (c) update_chan(c);
+  return TT_OK;
+}
+
+tt_status tt_engine_get_check(tt_engine *e, tt_check_report *out) {
+  if (!e || !out) return fail(TT_ERR_INVALID, "null engine or output");
+  std::unique_lock<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  tt_status s = wait_seq(e, e->launch_seq, -1, lk);
+  if (s != TT_OK) return s;
+  TT_CK(cudaStreamSynchronize(e->stream));
+  uint32_t w[2] = {0, 0};
+  TT_CK(cudaMemcpy(w, e->d_check, sizeof w, cudaMemcpyDeviceToHost));
+  TT_CK(cudaMemset(e->d_check, 0, sizeof w));
+  tt_check_report r{};
+  r.checked_build = (uint32_t)tt_checked_build();
+  r.violations = w[0];
+  r.first_code = w[1];
+  *out = r;
   return TT_OK;
 }
 
@@ -2068,3 +2115,7 @@ tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len) {
 
 // ---------------------------------------------------------------- serving form
 }  // extern "C"
+
+namespace ttx {
+bool cells_have_work(const tt_engine *e) { return ::cells_have_work(e); }
+}  // namespace ttx

@@ -68,6 +68,8 @@ struct tt_engine {
   TTSeg *d_tcsegs = nullptr;                // work list of the tensor-core channels
   size_t tcseg_cap = 0;
   int *d_status = nullptr;                  // set by a kernel whose bounded wait expired
+  uint32_t *d_check = nullptr;              // bounds-checked build: {violations, first code}
+  int check_shrink = 0;                     // tests only (TT_TEST_CHECK_SHRINK at a run, checked build)
   int tc_no_mma = 0;                        // tests only (TT_TEST_TC_NO_MMA=1 at a run): no MMA is issued
   std::vector<TTSeg> gsegs_host;            // the cached graph's work list (first_slot refreshed per replay)
   std::vector<tt_cell *> cells;             // uplink aggregation cells
@@ -173,6 +175,8 @@ void update_chan(tt_chan *c);
 tt_status check_room(tt_chan *c, uint64_t first, uint32_t n);
 void mark_pushed(tt_chan *c, uint64_t first, uint32_t n);                      // arrival: now
 void mark_pushed_at(tt_chan *c, uint64_t first, uint32_t n, int64_t arrival_ns);
+// Engine lock held: an uplink cell has member slots to aggregate and ring room for them.
+bool cells_have_work(const tt_engine *e);
 
 // ---- serving hooks (tt_server.cpp) ----
 // A push of [first, first + n) became visible (engine lock held): its arrival is recorded.

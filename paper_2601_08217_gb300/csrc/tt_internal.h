@@ -82,6 +82,31 @@ struct TTSeg {
   uint32_t items;       // n_slots * items_per_slot
 };
 
+// Bounds-checked build.  Compiled with -DTT_CHECKED=1 (a separate library), the tiled kernel tests
+// every shared- and global-memory index before the access; an index out of bounds skips the access
+// and is recorded here instead of faulting: report[0] counts violations, report[1] holds the code
+// (TT_CHK_*) of the first.  In the normal build the tests compile away.
+struct TTCheck {
+  uint32_t *report;  // two words on the device, or null (violations are then skipped unrecorded)
+  int32_t shrink;    // tests only: the output-store bound is lowered by this many words
+  int32_t tap_max;   // set by the kernel: entries of each tap buffer
+  int32_t kpad;      // set by the kernel: entries of each delay-offset buffer
+};
+enum {
+  TT_CHK_RAW_WRITE = 1,   // staged raw window (shared), written by the copies
+  TT_CHK_RING_IN = 2,     // input ring (global), read by the copies
+  TT_CHK_TAP_SMEM = 3,    // tap buffer (shared)
+  TT_CHK_TAP_GLOBAL = 4,  // trace or sparse tap ring (global)
+  TT_CHK_DLY_SMEM = 5,    // delay-offset buffer (shared)
+  TT_CHK_SYM = 6,         // symbol-start table (shared)
+  TT_CHK_PLANE_WRITE = 7, // phase planes (shared), written by the conversion
+  TT_CHK_RAW_READ = 8,    // staged raw window (shared), read by the conversion
+  TT_CHK_PLANE_READ = 9,  // phase planes (shared), read by the tap loop
+  TT_CHK_TAP_READ = 10,   // tap and delay-offset buffers (shared), read by the tap loop
+  TT_CHK_RING_OUT = 11    // output ring (global), written by the epilogue
+};
+int tt_checked_build();  // 1 in the TT_CHECKED library, else 0
+
 struct TTLaunch {
   const TTUEDesc *ues;
   const TTSeg *segs;
@@ -100,6 +125,7 @@ struct TTLaunch {
   size_t smem;          // dynamic shared memory bytes (tt_conv_smem_bytes)
   const unsigned long long *cursors;  // non-null: first slot of each run = cursors[ue] (graph replay)
   int topn;             // 1: every UE of the launch uses sparse convolution (top_n < its tap count)
+  TTCheck check;        // bounds-checked build: where violations are recorded
 };
 
 // cursors[segs[i].ue] += segs[i].n_slots for every segment (device-resident slot cursors).

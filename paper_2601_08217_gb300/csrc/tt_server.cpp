@@ -151,16 +151,20 @@ void collect_completed(tt_engine *e) {
     S->batches.pop_front();
     any = true;
   }
-  if (!any) return;
-  if (S->cfg.release_outputs)  // cells aggregated by completed batches free their ring slots too
+  // cells aggregated by completed batches free their ring slots too, also after a batch that only
+  // aggregated (it carries no requests, so it is not in the list above)
+  if (S->cfg.release_outputs)
     for (tt_cell *cl : e->cells) {
       while (!cl->inflight.empty() && cl->inflight.front().second <= e->completed_seq) {
         cl->completed_end = cl->inflight.front().first;
         cl->inflight.pop_front();
       }
-      cl->pulled_end = std::max(cl->pulled_end, cl->completed_end);
+      if (cl->completed_end > cl->pulled_end) {
+        cl->pulled_end = cl->completed_end;
+        any = true;
+      }
     }
-  e->room_cv.notify_all();
+  if (any) e->room_cv.notify_all();
 }
 
 bool has_pending(const tt_engine *e) {
@@ -193,8 +197,12 @@ void server_loop(tt_engine *e) {
       const size_t running = S->batches.size();
       const int64_t oldest = S->first_pending_ns.load(std::memory_order_relaxed);
       // a batch forms until its oldest request has waited the coalescing window: that bounds the
-      // batch rate (each launch holds the engine lock for a few microseconds) and the wait
-      launch = pending && running < max_inflight && oldest != 0 && now_ns() - oldest >= S->coalesce_ns;
+      // batch rate (each launch holds the engine lock for a few microseconds) and the wait.  An
+      // uplink cell whose ring freed up aggregates at once even with no push pending: its members'
+      // rings free only when it consumes their outputs, so waiting for a push could wait forever.
+      const bool cell_work = !pending && !e->cells.empty() && ttx::cells_have_work(e);
+      launch = running < max_inflight &&
+               ((pending && oldest != 0 && now_ns() - oldest >= S->coalesce_ns) || cell_work);
       done = S->stop.load() && !pending && running == 0;
       if (!running && !pending && !done && !launch) {
         // idle: sleep until a push arrives (the pushes notify) or the stop flag

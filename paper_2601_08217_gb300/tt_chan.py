@@ -16,6 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libttchan.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "_build", "libttchan_checked.so")  # loaded when TT_CHECKED=1
 HEADER = os.path.join(os.path.dirname(HERE), "include", "tt_chan.h")
 
 TT_OK, TT_ERR_INVALID, TT_ERR_NO_MEMORY, TT_ERR_CUDA = 0, -1, -2, -3
@@ -121,6 +122,11 @@ class StaticChan(C.Structure):
                 ("n_slots", C.c_uint32)]
 
 
+class CheckReport(C.Structure):
+    _fields_ = [("checked_build", C.c_uint32), ("violations", C.c_uint32), ("first_code", C.c_uint32),
+                ("pad", C.c_uint32)]
+
+
 class ChanGeometry(C.Structure):
     _fields_ = [("tensor_core", C.c_uint32), ("samples_per_thread", C.c_uint32), ("threads_per_cta", C.c_uint32),
                 ("samples_per_item", C.c_uint32), ("items_per_slot", C.c_uint32), ("has_trace", C.c_uint32)]
@@ -137,6 +143,7 @@ _SIGS = {
     "tt_engine_get_stats": [_VP, C.POINTER(EngineStats)],
     "tt_engine_autotune": [_VP, C.c_int32, C.POINTER(C.c_uint32)],
     "tt_chan_get_geometry": [_VP, C.POINTER(ChanGeometry)],
+    "tt_engine_get_check": [_VP, C.POINTER(CheckReport)],
     "tt_engine_replay": [_VP, C.c_uint32, C.c_uint32],
     "tt_engine_serve": [_VP, C.POINTER(ServeConfig), C.POINTER(ServeReport)],
     "tt_chan_create": [_VP, C.POINTER(ChanConfig), C.POINTER(_VP)],
@@ -181,11 +188,12 @@ def header_functions(path: str = HEADER) -> list:
 
 
 def load(path: Optional[str] = None):
-    """Load libttchan.so (raises if it has not been built)."""
+    """Load libttchan.so, or with TT_CHECKED=1 in the environment its bounds-checked build (raises if
+    it has not been built)."""
     global _lib
     if _lib is not None:
         return _lib
-    p = path or LIB_PATH
+    p = path or (LIB_CHECKED_PATH if os.environ.get("TT_CHECKED") == "1" else LIB_PATH)
     if not os.path.exists(p):
         raise RuntimeError(f"libttchan.so is not built ({p}); run __graft_entry__.build()")
     lib = C.CDLL(p)
@@ -274,6 +282,12 @@ def tt_engine_autotune(e: int, reps: int = 3) -> int:
     n = C.c_uint32(0)
     _check(load().tt_engine_autotune(e, reps, C.byref(n)))
     return n.value
+
+
+def tt_engine_get_check(e: int) -> dict:
+    r = CheckReport()
+    _check(load().tt_engine_get_check(e, C.byref(r)))
+    return {f: getattr(r, f) for f, _ in CheckReport._fields_ if f != "pad"}
 
 
 def tt_chan_get_geometry(c: int) -> dict:
@@ -544,6 +558,9 @@ class Engine:
 
     def autotune(self, reps: int = 3) -> int:
         return tt_engine_autotune(self.h, reps)
+
+    def check_report(self) -> dict:
+        return tt_engine_get_check(self.h)
 
     def close(self):
         """Destroy the engine.  The C side frees every channel and cell with it, so their handles are

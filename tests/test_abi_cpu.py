@@ -26,6 +26,15 @@ def test_every_declared_function_is_exported(lib):
         assert hasattr(lib, n), f"{n} declared but not exported"
 
 
+def test_the_bounds_checked_build_exports_the_same_symbols(lib):
+    chk = C.CDLL(tc.LIB_CHECKED_PATH)
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            for n in tc.header_functions(os.path.join(ROOT, "include", h)):
+                assert hasattr(chk, n), f"{n} missing from the checked build"
+    assert chk.tt_engine_get_check(None, None) == tc.TT_ERR_INVALID
+
+
 def test_abi_version_and_error_string(lib):
     assert tc.tt_abi_version() == 4
     assert isinstance(tc.tt_last_error(), str)
