@@ -104,6 +104,16 @@ typedef struct {
   uint32_t persistent;       /* 1: persistent CTAs claim work items from a device counter; 0: by stride */
   uint32_t graphs;           /* 1: tt_engine_run captures its launches in a CUDA graph and replays it
                                 while the set of channels and slots per run stays the same */
+  /* Optional allocator hook (both set, or both NULL for cudaMalloc/cudaFree).  Every device buffer
+   * the engine owns (rings, traces, tables, work lists) comes from dev_alloc(bytes, alloc_ctx), which
+   * returns device memory on cfg->device aligned to 256 bytes, or NULL (then the call fails with
+   * TT_ERR_NO_MEMORY or TT_ERR_CUDA).  The engine calls dev_free(ptr, alloc_ctx) only after its own
+   * streams are idle, so the allocator may hand the memory to other work at once.  The hooks may
+   * be called from any engine call and from the serving thread (tt_server_start).  Fields present
+   * when struct_size covers them. */
+  void *(*dev_alloc)(size_t bytes, void *ctx);
+  void (*dev_free)(void *ptr, void *ctx);
+  void *alloc_ctx;
 } tt_engine_config;
 
 typedef struct {

@@ -85,7 +85,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         kern = [objs[(s_, checked)] for s_ in srcs if s_.endswith(".cu")]
         tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "-rpath", "-Xlinker", cudalib,
-                               "-o", tmp] + kern + host + ["-lpthread"]
+                               "-o", tmp] + kern + host + ["-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -25,6 +25,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tt_chan.h"
 #include "tt_engine_impl.h"
 #include "tt_internal.h"
@@ -54,7 +56,46 @@ int64_t now_ns() {
       .count();
 }
 
+cudaError_t dev_alloc(tt_engine *e, void **p, size_t bytes) {
+  *p = nullptr;
+  if (!e->alloc_fn) return cudaMalloc(p, bytes);
+  if (bytes == 0) return cudaSuccess;
+  *p = e->alloc_fn(bytes, e->alloc_ctx);
+  if (!*p) return cudaErrorMemoryAllocation;
+  if (reinterpret_cast<uintptr_t>(*p) & 255) {  // the kernels' vector accesses rely on this
+    e->free_fn(*p, e->alloc_ctx);
+    *p = nullptr;
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+void dev_free(tt_engine *e, void *p) {
+  if (!p) return;
+  if (!e->alloc_fn) {
+    cudaFree(p);
+    return;
+  }
+  // the hook's memory may be reused as soon as it is returned: nothing of the engine may still use it
+  if (e->quiesced) {
+    e->free_fn(p, e->alloc_ctx);
+    return;
+  }
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  if (e->copy) cudaStreamSynchronize(e->copy);
+  if (e->h2d) cudaStreamSynchronize(e->h2d);
+  for (cudaStream_t s : e->side)
+    if (s) cudaStreamSynchronize(s);
+  e->free_fn(p, e->alloc_ctx);
+}
+
+NvtxScope::NvtxScope(const char *name) { nvtxRangePushA(name); }
+NvtxScope::~NvtxScope() { nvtxRangePop(); }
+
 }  // namespace ttx
+
+using ttx::dfree;
+using ttx::dmalloc;
 
 using ttx::fail;
 using ttx::now_ns;
@@ -232,14 +273,14 @@ tt_status set_geom(tt_chan *c, int spt, int tpb) {
   int touched = 1;
   std::vector<int32_t> chunks = chunk_table(c->sym_len, spt, tpb, &touched);
   int32_t *d_chunks = nullptr;
-  cudaError_t err = cudaMalloc(&d_chunks, chunks.size() * sizeof(int32_t));
+  cudaError_t err = dmalloc(c->e, &d_chunks, chunks.size() * sizeof(int32_t));
   if (err == cudaSuccess)
     err = cudaMemcpy(d_chunks, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
-    cudaFree(d_chunks);
+    dfree(c->e, d_chunks);
     return fail(TT_ERR_CUDA, "chunk table: %s", cudaGetErrorString(err));
   }
-  cudaFree(c->d_chunks);
+  dfree(c->e, c->d_chunks);
   c->d_chunks = d_chunks;
   c->spt = spt;
   c->tpb = tpb;
@@ -435,10 +476,10 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
 // Direct launch: the work list is uploaded from the host and the device cursors are not used.
 tt_status launch_direct(tt_engine *e, const Plan &p) {
   if (p.segs.size() > e->seg_cap) {
-    cudaFree(e->d_segs);
+    dfree(e, e->d_segs);
     e->d_segs = nullptr;
     e->seg_cap = 0;
-    TT_CK(cudaMalloc(&e->d_segs, sizeof(TTSeg) * p.segs.size() * 2));
+    TT_CK(dmalloc(e, &e->d_segs, sizeof(TTSeg) * p.segs.size() * 2));
     e->seg_cap = p.segs.size() * 2;
   }
   TT_CK(cudaMemcpyAsync(e->d_segs, p.segs.data(), sizeof(TTSeg) * p.segs.size(), cudaMemcpyHostToDevice,
@@ -476,10 +517,10 @@ tt_status launch_graph(tt_engine *e, const Plan &p) {
     e->gkey.clear();
     TT_CK(cudaStreamSynchronize(e->stream));  // the old graph may still read d_gsegs
     if (p.segs.size() > e->gseg_cap) {
-      cudaFree(e->d_gsegs);
+      dfree(e, e->d_gsegs);
       e->d_gsegs = nullptr;
       e->gseg_cap = 0;
-      TT_CK(cudaMalloc(&e->d_gsegs, sizeof(TTSeg) * p.segs.size() * 2));
+      TT_CK(dmalloc(e, &e->d_gsegs, sizeof(TTSeg) * p.segs.size() * 2));
       e->gseg_cap = p.segs.size() * 2;
     }
     TT_CK(cudaMemcpy(e->d_gsegs, p.segs.data(), sizeof(TTSeg) * p.segs.size(), cudaMemcpyHostToDevice));
@@ -547,10 +588,10 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
       n16 += fp16;
     }
   if (segs.size() > e->tcseg_cap) {
-    cudaFree(e->d_tcsegs);
+    dfree(e, e->d_tcsegs);
     e->d_tcsegs = nullptr;
     e->tcseg_cap = 0;
-    TT_CK(cudaMalloc(&e->d_tcsegs, sizeof(TTSeg) * segs.size() * 2));
+    TT_CK(dmalloc(e, &e->d_tcsegs, sizeof(TTSeg) * segs.size() * 2));
     e->tcseg_cap = segs.size() * 2;
   }
   const size_t nbf = segs.size() - (size_t)n16;
@@ -657,6 +698,15 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   e->tpb_override = cfg->threads_per_block;
   e->persistent = cfg->persistent;
   e->graphs = cfg->struct_size >= offsetof(tt_engine_config, graphs) + sizeof(uint32_t) && cfg->graphs != 0;
+  if (cfg->struct_size >= offsetof(tt_engine_config, alloc_ctx) + sizeof(void *)) {
+    if ((cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr)) {
+      delete e;
+      return fail(TT_ERR_INVALID, "dev_alloc and dev_free must be set together");
+    }
+    e->alloc_fn = cfg->dev_alloc;
+    e->free_fn = cfg->dev_free;
+    e->alloc_ctx = cfg->alloc_ctx;
+  }
   cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
   ttx::tune_load(e);  // choices stored for this device model (TT_TUNE_CACHE)
   e->table.assign(e->max_ues, nullptr);
@@ -668,12 +718,17 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->join[i], cudaEventDisableTiming);
   }
   if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->fork, cudaEventDisableTiming);
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_ues, sizeof(TTUEDesc) * e->max_ues);
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_counters, sizeof(uint32_t) * e->counter_cap);
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_cursors, sizeof(unsigned long long) * e->max_ues);
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_status, sizeof(int));
+  if (err == cudaSuccess) err = dmalloc(e, &e->d_ues, sizeof(TTUEDesc) * e->max_ues);
+  if (err == cudaSuccess) err = dmalloc(e, &e->d_counters, sizeof(uint32_t) * e->counter_cap);
+  if (err == cudaSuccess) err = dmalloc(e, &e->d_cursors, sizeof(unsigned long long) * e->max_ues);
+  // work lists hold at most one run of slots per channel: sized once, never regrown during runs
+  if (err == cudaSuccess) err = dmalloc(e, &e->d_segs, sizeof(TTSeg) * e->max_ues);
+  if (err == cudaSuccess) err = dmalloc(e, &e->d_gsegs, sizeof(TTSeg) * e->max_ues);
+  if (err == cudaSuccess) err = dmalloc(e, &e->d_tcsegs, sizeof(TTSeg) * e->max_ues);
+  if (err == cudaSuccess) e->seg_cap = e->gseg_cap = e->tcseg_cap = e->max_ues;
+  if (err == cudaSuccess) err = dmalloc(e, &e->d_status, sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(e->d_status, 0, sizeof(int));
-  if (err == cudaSuccess) err = cudaMalloc(&e->d_check, 2 * sizeof(uint32_t));
+  if (err == cudaSuccess) err = dmalloc(e, &e->d_check, 2 * sizeof(uint32_t));
   if (err == cudaSuccess) err = cudaMemset(e->d_check, 0, 2 * sizeof(uint32_t));
   if (err != cudaSuccess) {
     tt_engine_destroy(e);
@@ -688,25 +743,28 @@ tt_status tt_engine_destroy(tt_engine *e) {
   if (e->server) tt_server_stop(e, nullptr);  // its thread launches on this engine
   cudaSetDevice(e->device);
   if (e->stream) cudaStreamSynchronize(e->stream);
+  for (cudaStream_t s : {e->copy, e->h2d, e->side[0], e->side[1], e->side[2]})
+    if (s) cudaStreamSynchronize(s);
+  e->quiesced = true;  // nothing runs any more: the frees below need no further waits
   for (tt_chan *c : e->table)
     if (c) {
-      cudaFree(c->d_in);
-      cudaFree(c->d_out);
-      cudaFree(c->d_taps);
-      cudaFree(c->d_delays);
-      cudaFree(c->d_chunks);
-      cudaFree(c->d_amp);
-      cudaFree(c->d_freq);
-      cudaFree(c->d_phase);
-      cudaFree(c->d_src);
-      cudaFree(c->d_sparse);
-      cudaFree(c->d_sparse_dly);
+      dfree(e, c->d_in);
+      dfree(e, c->d_out);
+      dfree(e, c->d_taps);
+      dfree(e, c->d_delays);
+      dfree(e, c->d_chunks);
+      dfree(e, c->d_amp);
+      dfree(e, c->d_freq);
+      dfree(e, c->d_phase);
+      dfree(e, c->d_src);
+      dfree(e, c->d_sparse);
+      dfree(e, c->d_sparse_dly);
       c->e = nullptr;
       delete c;
     }
   for (tt_cell *cl : e->cells) {
-    cudaFree(cl->d_out);
-    cudaFree(cl->d_members);
+    dfree(e, cl->d_out);
+    dfree(e, cl->d_members);
     cl->e = nullptr;
     delete cl;
   }
@@ -714,17 +772,17 @@ tt_status tt_engine_destroy(tt_engine *e) {
   for (auto &p : e->events) cudaEventDestroy(p.second);
   for (auto ev : e->pool) cudaEventDestroy(ev);
   if (e->gexec) cudaGraphExecDestroy(e->gexec);
-  cudaFree(e->d_ues);
-  cudaFree(e->d_segs);
-  cudaFree(e->d_gsegs);
-  cudaFree(e->d_counters);
-  cudaFree(e->d_cursors);
-  cudaFree(e->d_tcsegs);
-  cudaFree(e->d_sos);
-  cudaFree(e->d_retime);
-  cudaFree(e->d_topn);
-  cudaFree(e->d_status);
-  cudaFree(e->d_check);
+  dfree(e, e->d_ues);
+  dfree(e, e->d_segs);
+  dfree(e, e->d_gsegs);
+  dfree(e, e->d_counters);
+  dfree(e, e->d_cursors);
+  dfree(e, e->d_tcsegs);
+  dfree(e, e->d_sos);
+  dfree(e, e->d_retime);
+  dfree(e, e->d_topn);
+  dfree(e, e->d_status);
+  dfree(e, e->d_check);
   if (e->stream) cudaStreamDestroy(e->stream);
   if (e->copy) cudaStreamDestroy(e->copy);
   if (e->h2d) cudaStreamDestroy(e->h2d);
@@ -808,13 +866,13 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   c->hist = hist;
   c->slot_in_elems = in_e;
   c->slot_out_elems = out_e;
-  cudaError_t err = cudaMalloc(&c->d_in, (size_t)Q * in_e * sizeof(int16_t));
-  if (err == cudaSuccess) err = cudaMalloc(&c->d_out, (size_t)Q * out_e * sizeof(int16_t));
+  cudaError_t err = dmalloc(e, &c->d_in, (size_t)Q * in_e * sizeof(int16_t));
+  if (err == cudaSuccess) err = dmalloc(e, &c->d_out, (size_t)Q * out_e * sizeof(int16_t));
   if (err == cudaSuccess) err = cudaMemsetAsync(c->d_in, 0, (size_t)Q * in_e * sizeof(int16_t), e->stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(c->d_out, 0, (size_t)Q * out_e * sizeof(int16_t), e->stream);
   if (err != cudaSuccess) {
-    cudaFree(c->d_in);
-    cudaFree(c->d_out);
+    dfree(e, c->d_in);
+    dfree(e, c->d_out);
     delete c;
     return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "ring allocation: %s",
                 cudaGetErrorString(err));
@@ -837,8 +895,8 @@ tt_status tt_chan_create(tt_engine *e, const tt_chan_config *cfg, tt_chan **out)
   const std::vector<int> cands = spt_candidates(c->sym_len, e->spt_override, cfg->n_rx, cfg->n_tx);
   tt_status sst = set_geom(c, cands.empty() ? 1 : cands[0], e->tpb_override ? (int)e->tpb_override : TT_TPB);
   if (sst != TT_OK) {
-    cudaFree(c->d_in);
-    cudaFree(c->d_out);
+    dfree(e, c->d_in);
+    dfree(e, c->d_out);
     e->in_use -= bytes;
     delete c;
     return sst;
@@ -857,17 +915,17 @@ tt_status tt_chan_destroy(tt_chan *c) {
   if (c->cell) return fail(TT_ERR_STATE, "channel is a member of a cell: destroy the cell first");
   cudaSetDevice(e->device);
   cudaStreamSynchronize(e->stream);
-  cudaFree(c->d_in);
-  cudaFree(c->d_out);
-  cudaFree(c->d_taps);
-  cudaFree(c->d_delays);
-  cudaFree(c->d_chunks);
-  cudaFree(c->d_amp);
-  cudaFree(c->d_freq);
-  cudaFree(c->d_phase);
-  cudaFree(c->d_src);
-  cudaFree(c->d_sparse);
-  cudaFree(c->d_sparse_dly);
+  dfree(e, c->d_in);
+  dfree(e, c->d_out);
+  dfree(e, c->d_taps);
+  dfree(e, c->d_delays);
+  dfree(e, c->d_chunks);
+  dfree(e, c->d_amp);
+  dfree(e, c->d_freq);
+  dfree(e, c->d_phase);
+  dfree(e, c->d_src);
+  dfree(e, c->d_sparse);
+  dfree(e, c->d_sparse_dly);
   e->in_use -= c->ring_bytes + c->trace_bytes + c->sparse_bytes;
   e->table[c->index] = nullptr;
   e->pending.erase(std::remove(e->pending.begin(), e->pending.end(), c), e->pending.end());
@@ -954,19 +1012,19 @@ static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64
     if (e->budget && e->in_use - c->trace_bytes + bytes + rb > e->budget) {
       err = cudaErrorMemoryAllocation;
     } else {
-      err = cudaMalloc(&ring, rb);
+      err = dmalloc(e, &ring, rb);
       if (err == cudaSuccess) err = cudaMemsetAsync(ring, 0, rb, e->stream);
     }
     if (err != cudaSuccess) {
-      cudaFree(ring);
-      cudaFree(taps);
-      cudaFree(delays);
+      dfree(e, ring);
+      dfree(e, taps);
+      dfree(e, delays);
       return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA,
                   "admission refused or failed: anchor ring of %llu B for the timed trace", (unsigned long long)rb);
     }
     bytes += rb;
   }
-  cudaFree(c->d_src);
+  dfree(e, c->d_src);
   c->d_src = nullptr;
   c->retime = false;
   if (ring) {
@@ -980,11 +1038,11 @@ static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64
     step_samples = 0.0;
     loop = 1;
   }
-  cudaFree(c->d_taps);
-  cudaFree(c->d_delays);
-  cudaFree(c->d_amp);
-  cudaFree(c->d_freq);
-  cudaFree(c->d_phase);
+  dfree(e, c->d_taps);
+  dfree(e, c->d_delays);
+  dfree(e, c->d_amp);
+  dfree(e, c->d_freq);
+  dfree(e, c->d_phase);
   c->d_amp = nullptr;
   c->d_freq = c->d_phase = nullptr;
   c->synth = false;
@@ -1006,8 +1064,8 @@ static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64
   d.n_anchors = (int)n_anchors;
   d.loop = loop ? 1 : 0;
   // sparse convolution: a ring of the kept taps per anchor and link, sized like the slot ring
-  cudaFree(c->d_sparse);
-  cudaFree(c->d_sparse_dly);
+  dfree(e, c->d_sparse);
+  dfree(e, c->d_sparse_dly);
   c->d_sparse = nullptr;
   c->d_sparse_dly = nullptr;
   e->in_use -= c->sparse_bytes;
@@ -1018,10 +1076,10 @@ static tt_status install_trace(tt_chan *c, float2 *taps, int32_t *delays, uint64
   if (c->cfg.top_n > 0 && c->cfg.top_n < n_taps) {
     const int len = (c->Q + 1) * (int)c->sym_len.size() + 1;
     const size_t ent = (size_t)len * c->cfg.n_rx * c->cfg.n_tx * c->cfg.top_n;
-    cudaError_t err = cudaMalloc(&c->d_sparse, ent * sizeof(float4));
-    if (err == cudaSuccess) err = cudaMalloc(&c->d_sparse_dly, ent * sizeof(int32_t));
+    cudaError_t err = dmalloc(e, &c->d_sparse, ent * sizeof(float4));
+    if (err == cudaSuccess) err = dmalloc(e, &c->d_sparse_dly, ent * sizeof(int32_t));
     if (err != cudaSuccess) {
-      cudaFree(c->d_sparse);
+      dfree(e, c->d_sparse);
       c->d_sparse = nullptr;
       c->has_trace = false;
       return fail(TT_ERR_NO_MEMORY, "sparse tap ring: %s", cudaGetErrorString(err));
@@ -1083,13 +1141,13 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   TT_CK(cudaStreamSynchronize(e->stream));
   float2 *taps = nullptr;
   int32_t *delays = nullptr;
-  cudaError_t err = cudaMalloc(&taps, nval * sizeof(float));
-  if (err == cudaSuccess) err = cudaMalloc(&delays, tr->n_taps * sizeof(int32_t));
+  cudaError_t err = dmalloc(c->e, &taps, nval * sizeof(float));
+  if (err == cudaSuccess) err = dmalloc(c->e, &delays, tr->n_taps * sizeof(int32_t));
   if (err == cudaSuccess) err = cudaMemcpy(taps, tr->taps, nval * sizeof(float), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(delays, tr->delays, tr->n_taps * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
-    cudaFree(taps);
-    cudaFree(delays);
+    dfree(c->e, taps);
+    dfree(c->e, delays);
     return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "trace upload: %s",
                 cudaGetErrorString(err));
   }
@@ -1128,21 +1186,21 @@ tt_status tt_chan_load_jakes(tt_chan *c, const tt_jakes_desc *j) {
   int32_t *delays = nullptr;
   float *amp = nullptr;
   double *freq = nullptr, *phase = nullptr;
-  cudaError_t err = cudaMalloc(&taps, (size_t)ring_len * per * sizeof(float2));
-  if (err == cudaSuccess) err = cudaMalloc(&delays, j->n_taps * sizeof(int32_t));
-  if (err == cudaSuccess) err = cudaMalloc(&amp, per * sizeof(float));
-  if (err == cudaSuccess) err = cudaMalloc(&freq, nfp * sizeof(double));
-  if (err == cudaSuccess) err = cudaMalloc(&phase, nfp * sizeof(double));
+  cudaError_t err = dmalloc(c->e, &taps, (size_t)ring_len * per * sizeof(float2));
+  if (err == cudaSuccess) err = dmalloc(c->e, &delays, j->n_taps * sizeof(int32_t));
+  if (err == cudaSuccess) err = dmalloc(c->e, &amp, per * sizeof(float));
+  if (err == cudaSuccess) err = dmalloc(c->e, &freq, nfp * sizeof(double));
+  if (err == cudaSuccess) err = dmalloc(c->e, &phase, nfp * sizeof(double));
   if (err == cudaSuccess) err = cudaMemcpy(delays, j->delays, j->n_taps * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(amp, j->amplitude, per * sizeof(float), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(freq, j->freq, nfp * sizeof(double), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(phase, j->phase, nfp * sizeof(double), cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
-    cudaFree(taps);
-    cudaFree(delays);
-    cudaFree(amp);
-    cudaFree(freq);
-    cudaFree(phase);
+    dfree(c->e, taps);
+    dfree(c->e, delays);
+    dfree(c->e, amp);
+    dfree(c->e, freq);
+    dfree(c->e, phase);
     return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "model upload: %s", cudaGetErrorString(err));
   }
   st = install_trace(c, taps, delays, bytes, ring_len, j->n_taps, 0.0, 1, g);
@@ -1190,10 +1248,10 @@ tt_status tt_chan_load_cir(tt_chan *c, const tt_cir_desc *cir) {
   float2 *taps = nullptr, *d_gains = nullptr;
   int32_t *delays = nullptr;
   double *d_tau = nullptr;
-  cudaError_t err = cudaMalloc(&taps, nval * sizeof(float2));
-  if (err == cudaSuccess) err = cudaMalloc(&delays, cir->n_taps * sizeof(int32_t));
-  if (err == cudaSuccess) err = cudaMalloc(&d_gains, ng * sizeof(float));
-  if (err == cudaSuccess) err = cudaMalloc(&d_tau, nd * sizeof(double));
+  cudaError_t err = dmalloc(c->e, &taps, nval * sizeof(float2));
+  if (err == cudaSuccess) err = dmalloc(c->e, &delays, cir->n_taps * sizeof(int32_t));
+  if (err == cudaSuccess) err = dmalloc(c->e, &d_gains, ng * sizeof(float));
+  if (err == cudaSuccess) err = dmalloc(c->e, &d_tau, nd * sizeof(double));
   if (err == cudaSuccess) err = cudaMemcpy(delays, grid.data(), cir->n_taps * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(d_gains, cir->gains, ng * sizeof(float), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(d_tau, cir->delays, nd * sizeof(double), cudaMemcpyHostToDevice);
@@ -1201,11 +1259,11 @@ tt_status tt_chan_load_cir(tt_chan *c, const tt_cir_desc *cir) {
     err = tt_launch_cir_resample(d_gains, d_tau, (int)cir->n_steps, n_links, (int)cir->n_paths, (int)cir->n_taps,
                                  taps, e->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(e->stream);
-  cudaFree(d_gains);
-  cudaFree(d_tau);
+  dfree(c->e, d_gains);
+  dfree(c->e, d_tau);
   if (err != cudaSuccess) {
-    cudaFree(taps);
-    cudaFree(delays);
+    dfree(c->e, taps);
+    dfree(c->e, delays);
     return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "CIR resampling: %s",
                 cudaGetErrorString(err));
   }
@@ -1257,6 +1315,7 @@ static cudaError_t wait_ring_readers(tt_chan *c, uint64_t first, uint32_t n, cud
 }
 
 tt_status tt_chan_push_slots(tt_chan *c, uint64_t first, uint32_t n, const int16_t *iq_in) {
+  const ttx::NvtxScope nvtx_range("tt push (host)");
   if (!valid_chan(c) || (!iq_in && n)) return fail(TT_ERR_INVALID, "tt_chan_push_slots: bad argument");
   if (n == 0) return TT_OK;
   tt_engine *e = c->e;
@@ -1329,6 +1388,7 @@ tt_status tt_engine_push_slots(tt_engine *e, uint32_t n_chans, tt_chan *const *c
 
 tt_status tt_chan_push_slots_dev(tt_chan *c, uint64_t first, uint32_t n, const int16_t *d_iq_in,
                                  void *stream) {
+  const ttx::NvtxScope nvtx_range("tt push (device)");
   if (!valid_chan(c) || (!d_iq_in && n)) return fail(TT_ERR_INVALID, "tt_chan_push_slots_dev: bad argument");
   if (n == 0) return TT_OK;
   tt_engine *e = c->e;
@@ -1363,6 +1423,7 @@ tt_status tt_chan_slot_input(tt_chan *c, uint64_t slot, int16_t **d_ptr) {
 }
 
 tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n) {
+  const ttx::NvtxScope nvtx_range("tt commit");
   if (!valid_chan(c)) return fail(TT_ERR_INVALID, "null channel");
   if (n == 0) return TT_OK;
   tt_engine *e = c->e;
@@ -1406,10 +1467,10 @@ static tt_status launch_retime(tt_engine *e, const std::vector<tt_chan *> &chans
   if (jobs.empty()) return TT_OK;
   if (jobs.size() > e->retime_cap) {
     TT_CK(cudaStreamSynchronize(e->stream));  // the old list may still be read
-    cudaFree(e->d_retime);
+    dfree(e, e->d_retime);
     e->d_retime = nullptr;
     e->retime_cap = 0;
-    TT_CK(cudaMalloc(&e->d_retime, sizeof(TTRetimeJob) * jobs.size() * 2));
+    TT_CK(dmalloc(e, &e->d_retime, sizeof(TTRetimeJob) * jobs.size() * 2));
     e->retime_cap = jobs.size() * 2;
   }
   TT_CK(cudaMemcpyAsync(e->d_retime, jobs.data(), sizeof(TTRetimeJob) * jobs.size(), cudaMemcpyHostToDevice,
@@ -1446,10 +1507,10 @@ static tt_status launch_synth(tt_engine *e, const std::vector<tt_chan *> &chans)
   if (jobs.empty()) return TT_OK;
   if (jobs.size() > e->sos_cap) {
     TT_CK(cudaStreamSynchronize(e->stream));  // the old list may still be read
-    cudaFree(e->d_sos);
+    dfree(e, e->d_sos);
     e->d_sos = nullptr;
     e->sos_cap = 0;
-    TT_CK(cudaMalloc(&e->d_sos, sizeof(TTSosJob) * jobs.size() * 2));
+    TT_CK(dmalloc(e, &e->d_sos, sizeof(TTSosJob) * jobs.size() * 2));
     e->sos_cap = jobs.size() * 2;
   }
   TT_CK(cudaMemcpyAsync(e->d_sos, jobs.data(), sizeof(TTSosJob) * jobs.size(), cudaMemcpyHostToDevice, e->stream));
@@ -1480,10 +1541,10 @@ static tt_status launch_topn(tt_engine *e, const std::vector<tt_chan *> &chans) 
   if (jobs.empty()) return TT_OK;
   if (jobs.size() > e->topn_cap) {
     TT_CK(cudaStreamSynchronize(e->stream));  // the old list may still be read
-    cudaFree(e->d_topn);
+    dfree(e, e->d_topn);
     e->d_topn = nullptr;
     e->topn_cap = 0;
-    TT_CK(cudaMalloc(&e->d_topn, sizeof(TTTopnJob) * jobs.size() * 2));
+    TT_CK(dmalloc(e, &e->d_topn, sizeof(TTTopnJob) * jobs.size() * 2));
     e->topn_cap = jobs.size() * 2;
   }
   TT_CK(cudaMemcpyAsync(e->d_topn, jobs.data(), sizeof(TTTopnJob) * jobs.size(), cudaMemcpyHostToDevice, e->stream));
@@ -1575,10 +1636,10 @@ tt_status tt_cell_create(tt_engine *e, const tt_cell_config *cfg, tt_cell **out)
   cl->n = (int)cfg->samples_per_slot;
   cl->Q = Q;
   cl->slot_out_elems = out_e;
-  cudaError_t err = cudaMalloc(&cl->d_out, (size_t)Q * out_e * sizeof(int16_t));
+  cudaError_t err = dmalloc(e, &cl->d_out, (size_t)Q * out_e * sizeof(int16_t));
   if (err == cudaSuccess) err = cudaMemsetAsync(cl->d_out, 0, (size_t)Q * out_e * sizeof(int16_t), e->stream);
   if (err != cudaSuccess) {
-    cudaFree(cl->d_out);
+    dfree(e, cl->d_out);
     delete cl;
     return fail(err == cudaErrorMemoryAllocation ? TT_ERR_NO_MEMORY : TT_ERR_CUDA, "cell ring: %s", cudaGetErrorString(err));
   }
@@ -1604,8 +1665,8 @@ tt_status tt_cell_attach(tt_cell *cl, tt_chan *c) {
     const size_t cap = std::max<size_t>(8, 2 * cl->members_cap);
     TTCellMember *d = nullptr;
     TT_CK(cudaStreamSynchronize(e->stream));  // the old table may still be read
-    TT_CK(cudaMalloc(&d, sizeof(TTCellMember) * cap));
-    cudaFree(cl->d_members);
+    TT_CK(dmalloc(e, &d, sizeof(TTCellMember) * cap));
+    dfree(e, cl->d_members);
     cl->d_members = d;
     cl->members_cap = cap;
   }
@@ -1621,6 +1682,7 @@ tt_status tt_cell_attach(tt_cell *cl, tt_chan *c) {
 }
 
 tt_status tt_cell_pull_slots(tt_cell *cl, uint64_t first, uint32_t n, void *out, int64_t timeout_us) {
+  const ttx::NvtxScope nvtx_range("tt cell pull");
   if (!cl || !cl->e || (!out && n)) return fail(TT_ERR_INVALID, "tt_cell_pull_slots: bad argument");
   if (n == 0) return TT_OK;
   tt_engine *e = cl->e;
@@ -1660,8 +1722,8 @@ tt_status tt_cell_destroy(tt_cell *cl) {
   cudaSetDevice(e->device);
   cudaStreamSynchronize(e->stream);
   for (tt_chan *m : cl->members) m->cell = nullptr;
-  cudaFree(cl->d_out);
-  cudaFree(cl->d_members);
+  dfree(e, cl->d_out);
+  dfree(e, cl->d_members);
   e->in_use -= cl->ring_bytes;
   e->cells.erase(std::remove(e->cells.begin(), e->cells.end(), cl), e->cells.end());
   cl->e = nullptr;
@@ -1670,6 +1732,7 @@ tt_status tt_cell_destroy(tt_cell *cl) {
 }
 
 tt_status tt_engine_run(tt_engine *e) {
+  const ttx::NvtxScope nvtx_range("tt run");
   if (!e) return fail(TT_ERR_INVALID, "null engine");
   std::lock_guard<std::mutex> lk(e->mu);
   if (e->server && !ttx::is_server_thread(e))
@@ -1791,6 +1854,7 @@ tt_status tt_engine_run(tt_engine *e) {
 }
 
 tt_status tt_engine_replay(tt_engine *e, uint32_t n_steps, uint32_t slots_per_step) {
+  const ttx::NvtxScope nvtx_range("tt replay");
   if (!e || slots_per_step == 0) return fail(TT_ERR_INVALID, "tt_engine_replay: bad argument");
   for (uint32_t step = 0; step < n_steps; ++step) {
     {
@@ -1851,6 +1915,7 @@ tt_status tt_engine_get_check(tt_engine *e, tt_check_report *out) {
 }
 
 static tt_status pull_common(tt_chan *c, uint64_t first, uint32_t n, void *out, int64_t timeout_us) {
+  const ttx::NvtxScope nvtx_range("tt pull");
   tt_engine *e = c->e;
   std::unique_lock<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));

@@ -29,6 +29,11 @@ struct tt_engine {
   uint64_t in_use = 0;
   uint32_t form = TT_FORM_BATCHED;
   uint32_t max_ues = 1024;
+  // allocator hook (tt_engine_config.dev_alloc/dev_free); null: cudaMalloc/cudaFree
+  void *(*alloc_fn)(size_t, void *) = nullptr;
+  void (*free_fn)(void *, void *) = nullptr;
+  void *alloc_ctx = nullptr;
+  bool quiesced = false;  // being destroyed, every stream idle
   uint32_t spt_override = 0;
   uint32_t tpb_override = 0;  // tiled kernel's threads per CTA forced for every channel (0: 128 or tuned)
   uint32_t persistent = 0;
@@ -162,6 +167,23 @@ struct tt_cell {
 
 
 namespace ttx {
+
+// Device memory of the engine: through the allocator hook if one is set, else cudaMalloc/cudaFree.
+// dev_free waits for the engine's streams first (cudaFree's implicit synchronisation, kept for
+// the hook) and ignores null.
+cudaError_t dev_alloc(tt_engine *e, void **p, size_t bytes);
+void dev_free(tt_engine *e, void *p);
+template <class T>
+cudaError_t dmalloc(tt_engine *e, T **p, size_t bytes) {
+  return dev_alloc(e, reinterpret_cast<void **>(p), bytes);
+}
+inline void dfree(tt_engine *e, void *p) { dev_free(e, p); }
+
+// NVTX range for the duration of a scope (names the engine's calls in a profiler's timeline).
+struct NvtxScope {
+  explicit NvtxScope(const char *name);
+  ~NvtxScope();
+};
 
 // Record a message for tt_last_error() and return the status.
 tt_status fail(tt_status s, const char *fmt, ...);

@@ -151,6 +151,7 @@ void tune_load(tt_engine *e) {
 }  // namespace ttx
 
 tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned) {
+  const ttx::NvtxScope nvtx_range("tt autotune");
   if (!e) return fail(TT_ERR_INVALID, "null engine");
   if (reps < 1) reps = 3;
   std::lock_guard<std::mutex> lk(e->mu);

@@ -36,10 +36,45 @@ class TTError(RuntimeError):
         self.status = status
 
 
+DEV_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class EngineConfig(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("device", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
                 ("form", C.c_uint32), ("max_ues", C.c_uint32), ("samples_per_thread", C.c_uint32),
-                ("threads_per_block", C.c_uint32), ("persistent", C.c_uint32), ("graphs", C.c_uint32)]
+                ("threads_per_block", C.c_uint32), ("persistent", C.c_uint32), ("graphs", C.c_uint32),
+                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("alloc_ctx", C.c_void_p)]
+
+
+class TorchAllocator:
+    """Allocator hook backed by PyTorch's caching allocator: the engine's device buffers then come
+    from (and return to) the same pool as the harness's tensors.  Keep the object alive as long as
+    the engine (the C side holds its callbacks).  Counts live allocations for tests."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.device = device
+        self.live = {}
+
+        def alloc(nbytes, _ctx):
+            try:
+                p = torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device)
+            except Exception:  # out of memory: the engine reports the failure
+                return None
+            self.live[p] = int(nbytes)
+            return p
+
+        def free(ptr, _ctx):
+            self.live.pop(ptr, None)
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = DEV_ALLOC_FN(alloc)
+        self.free_fn = DEV_FREE_FN(free)
+
+    @property
+    def live_bytes(self) -> int:
+        return sum(self.live.values())
 
 
 class ChanConfig(C.Structure):
@@ -241,10 +276,14 @@ def _stream_ptr(stream) -> int:
 # ---------------------------------------------------------------- C-named calls
 def tt_engine_create(device: int = 0, form: int = TT_FORM_BATCHED, hbm_budget_bytes: int = 0,
                      max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False,
-                     graphs: bool = False, threads_per_block: int = 0) -> int:
+                     graphs: bool = False, threads_per_block: int = 0, allocator=None) -> int:
+    """allocator: None (cudaMalloc) or an object with alloc_fn/free_fn ctypes callbacks (TorchAllocator)."""
     lib = load()
     cfg = EngineConfig(C.sizeof(EngineConfig), device, hbm_budget_bytes, form, max_ues,
                        samples_per_thread, threads_per_block, int(bool(persistent)), int(bool(graphs)))
+    if allocator is not None:
+        cfg.dev_alloc = allocator.alloc_fn
+        cfg.dev_free = allocator.free_fn
     h = _VP()
     _check(lib.tt_engine_create(C.byref(cfg), C.byref(h)))
     return h.value
@@ -536,10 +575,15 @@ def tt_abi_version() -> int:
 class Engine:
     def __init__(self, device: int = 0, form: str = "batched", hbm_budget_bytes: int = 0,
                  max_ues: int = 0, samples_per_thread: int = 0, persistent: bool = False, graphs: bool = False,
-                 threads_per_block: int = 0):
+                 threads_per_block: int = 0, allocator=None):
+        """allocator: None (the engine calls cudaMalloc), "torch" (PyTorch's caching allocator), or a
+        TorchAllocator-like object with alloc_fn/free_fn callbacks."""
         f = {"batched": TT_FORM_BATCHED, "plain": TT_FORM_PLAIN}[form]
+        if allocator == "torch":
+            allocator = TorchAllocator(device)
+        self.allocator = allocator  # the C side holds its callbacks: keep them alive with the engine
         self.h = tt_engine_create(device, f, hbm_budget_bytes, max_ues, samples_per_thread, persistent, graphs,
-                                  threads_per_block)
+                                  threads_per_block, allocator)
         self.chans = []
         self.cells = []
 
