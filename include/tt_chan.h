@@ -192,7 +192,8 @@ tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us);
 /* Bounds-checked build.  The library can be built a second time with
  * TT_CHECKED=1 (libttchan_checked.so beside libttchan.so; the Python binding
  * loads it when the environment variable TT_CHECKED is 1).  There the tiled
- * FP32 kernel tests every shared- and global-memory index before the access.
+ * FP32 kernel and the tensor-core kernel test every shared-, tensor- and
+ * global-memory index before the access.
  * An index out of bounds is not accessed: the kernel counts it in the
  * engine's check report and keeps the code of the first one, without a trap,
  * so the GPU and the process stay usable (the affected slots' outputs are
@@ -200,11 +201,12 @@ tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us);
  * read, 3 tap buffer (shared), 4 trace or sparse tap ring read, 5 delay
  * buffer (shared), 6 symbol table (shared), 7 phase planes (shared) written,
  * 8 staged input window read, 9 phase planes read, 10 tap or delay buffer
- * read by the tap loop, 11 output ring written.  tt_engine_get_check waits
- * for the launched work, reads the report and clears it.  In the normal
- * build checked_build is 0 and the report stays empty.  The kernels of the
- * tensor-core form, the static entry and the auxiliary passes are not
- * instrumented. */
+ * read by the tap loop, 11 output ring written, 12 tensor-memory column
+ * (tensor-core kernel; there codes 1 and 3 also cover its staged signal and
+ * tap tables).  tt_engine_get_check waits for the launched work, reads the
+ * report and clears it.  In the normal build checked_build is 0 and the
+ * report stays empty.  The static entry (tt_conv_static) and the auxiliary
+ * passes (synthesis, retiming, top-n selection, cells) are not instrumented. */
 typedef struct {
   uint32_t checked_build; /* 1: this library tests indices */
   uint32_t violations;    /* out-of-bounds indices since the last call (not accessed) */

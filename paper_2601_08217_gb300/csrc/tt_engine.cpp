@@ -614,6 +614,8 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
     L.n_segs = (int)(s1 - s0);
     L.total_items = items;
     L.counter = nullptr;
+    L.check.report = e->d_check;
+    L.check.shrink = e->check_shrink;
     L.grid = -1;
     cudaError_t err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->tc_no_mma, e->stream);
     if (err != cudaSuccess) return fail(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(err));

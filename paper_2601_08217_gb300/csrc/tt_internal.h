@@ -82,8 +82,8 @@ struct TTSeg {
   uint32_t items;       // n_slots * items_per_slot
 };
 
-// Bounds-checked build.  Compiled with -DTT_CHECKED=1 (a separate library), the tiled kernel tests
-// every shared- and global-memory index before the access; an index out of bounds skips the access
+// Bounds-checked build.  Compiled with -DTT_CHECKED=1 (a separate library), the tiled kernel and the
+// tensor-core kernel test every shared-, tensor- and global-memory index before the access; an index out of bounds skips the access
 // and is recorded here instead of faulting: report[0] counts violations, report[1] holds the code
 // (TT_CHK_*) of the first.  In the normal build the tests compile away.
 struct TTCheck {
@@ -103,7 +103,8 @@ enum {
   TT_CHK_RAW_READ = 8,    // staged raw window (shared), read by the conversion
   TT_CHK_PLANE_READ = 9,  // phase planes (shared), read by the tap loop
   TT_CHK_TAP_READ = 10,   // tap and delay-offset buffers (shared), read by the tap loop
-  TT_CHK_RING_OUT = 11    // output ring (global), written by the epilogue
+  TT_CHK_RING_OUT = 11,   // output ring (global), written by the epilogue
+  TT_CHK_TMEM = 12        // tensor memory column (tensor-core kernel)
 };
 int tt_checked_build();  // 1 in the TT_CHECKED library, else 0
 

@@ -222,7 +222,7 @@ template <bool FP16>
 __global__ void __launch_bounds__(kTPB, 2)
     tt_toeplitz_tc_kernel(const TTUEDesc *__restrict__ ues, const TTSeg *__restrict__ segs, int n_segs,
                           uint32_t total_items, uint32_t *__restrict__ counter, int *__restrict__ status,
-                          int no_mma) {
+                          int no_mma, TTCheck ck) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) unsigned long long s_full[kSteps];   // builders -> MMA warp: step's chunks written
   __shared__ __align__(8) unsigned long long s_empty[kSteps];  // MMA completion -> builders: step's slots free
@@ -361,6 +361,11 @@ __global__ void __launch_bounds__(kTPB, 2)
         for (int k = lane; k < K; k += 32) {  // delays may repeat: accumulate
           const int e = rt * K + k;
           const int d = __ldg(U->delays + k);
+          if (!TT_IN(d >= 0 && d <= kMaxDelayTC, TT_CHK_TAP_SMEM)) continue;
+          if (!TT_IN(U->step_samples != 0.0 ||
+                         (it.idx0 < (uint64_t)U->n_anchors && it.idx1 < (uint64_t)U->n_anchors),
+                     TT_CHK_TAP_GLOBAL))
+            continue;
           float2 h0, h1;
           if (U->step_samples == 0.0) {
             h0 = __ldg(U->taps + it.idx0 * (uint64_t)per + (uint64_t)e);
@@ -434,6 +439,8 @@ __global__ void __launch_bounds__(kTPB, 2)
               while (pos < 0) pos += Q;
             }
             const uint4 *src = reinterpret_cast<const uint4 *>(rin + ((size_t)pos * n_tx * n + w));
+            if (!TT_IN(!live || (pos >= 0 && pos < Q && w >= 0 && w + 4 <= n), TT_CHK_RING_IN)) continue;
+            if (!TT_IN(u + 4 <= kSig, TT_CHK_RAW_WRITE)) continue;
             uint4 v[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t)
@@ -480,12 +487,18 @@ __global__ void __launch_bounds__(kTPB, 2)
           }
           if (kend - kk0 == kPer && ++jc == kKC) { jc = jlo; ++tp; }  // advance past the step's last chunk
 #pragma unroll
+          for (int e = 0; e < kPer; ++e) {
+            const long long off = srcs[e] - comp_w;
+            if (!TT_IN(off >= 0 && off + 4 <= 16 * kComps * 2 * kQW, TT_CHK_TAP_READ)) srcs[e] = comp_w;
+          }
+#pragma unroll
           for (int e = 0; e < kPer; ++e)
 #pragma unroll
             for (int q = 0; q < 4; ++q) wv[e][q] = srcs[e][q];
 #pragma unroll
           for (int e = 0; e < kPer; ++e)
-            if (kk0 + e < kend)
+            if (kk0 + e < kend &&
+                TT_IN(kAccCols + ss * (kPer * kChunkCols) + kg * 4 + e * kChunkCols + 4 <= kTmemCols, TT_CHK_TMEM))
               tmem_st4(tdst + e * kChunkCols, (wv[e][0] ^ ngs[e]) & keep, (wv[e][1] ^ ngs[e]) & keep,
                        (wv[e][2] ^ ngs[e]) & keep, (wv[e][3] ^ ngs[e]) & keep);
           tmem_wait_st();
@@ -556,7 +569,10 @@ __global__ void __launch_bounds__(kTPB, 2)
               const float2 ylo = hi16 ? got : y[0], yhi = hi16 ? y[1] : got;  // samples i_even, i_even + 1
               const int c_st = cc * 16 + (2 * h + hi16) * 4 + j4;
               const int m_st = gs + c_st * kB + quad * 2;
-              if (live_r && c_st < blocks && m_st < ge) {
+              if (live_r && c_st < blocks && m_st < ge &&
+                  TT_IN(m_st >= 0 && m_st + 2 <= n &&
+                            (int64_t)(slot_pos * n_rx + r) * n + m_st + 2 <= (int64_t)Q * n_rx * n - ck.shrink,
+                        TT_CHK_RING_OUT)) {
                 const size_t o = (size_t)(slot_pos * n_rx + r) * n + m_st;
                 if (U->out_f32) {
                   *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(U->ring_out) + o) =
@@ -616,6 +632,7 @@ cudaError_t tt_launch_toeplitz_tc(const TTLaunch &L, bool fp16, int *status, int
     return cudaSuccess;
   }
   if (L.grid == 0 || L.total_items == 0) return cudaSuccess;
-  kern<<<L.grid, kTPB, kSmemBytes, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter, status, no_mma);
+  kern<<<L.grid, kTPB, kSmemBytes, st>>>(L.ues, L.segs, L.n_segs, L.total_items, L.counter, status, no_mma,
+                                         L.check);
   return cudaGetLastError();
 }
