@@ -45,8 +45,8 @@ DISTINCT_IQ_SLOTS = 64        # synthetic IQ slots per UE, cycled through the re
 METRIC = "UE-slots/s and GMAC/s at 1 GB300 vs plain form; p99 slot latency vs 0.5 ms"
 # DRAM traffic per full launch from the ncu capture summarised in
 # profiles/tt_conv_fp32_kernel_40mhz_16ue.md, valid only for the kernel source it was taken on.
-TRAFFIC_BYTES = 3.52e9
-TRAFFIC_KERNEL_SHA = "a0965b3ae157d128"
+TRAFFIC_BYTES = 3.51e9
+TRAFFIC_KERNEL_SHA = "d44ebac8aef3c4f2"
 WORKLOAD = ("16 UEs SISO, 40 MHz (30720 samples/slot), 1000 slots each, 24 taps (delays <= 256), "
             "100 Hz Jakes, AWGN 20 dB, int16 IQ, FP32 accumulation")
 
