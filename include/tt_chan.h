@@ -282,7 +282,7 @@ typedef struct {
   double deadline_us;             /* latency bound counted as a miss (0 = 500) */
   uint64_t seed;                  /* arrival-process seed */
   uint32_t release_outputs;
-  uint32_t max_inflight_batches;  /* as tt_server_config (0 = 3) */
+  uint32_t max_inflight_batches;  /* as tt_server_config (0 = 8) */
 } tt_serve_config;
 
 typedef struct {
@@ -315,7 +315,9 @@ tt_status tt_engine_serve(tt_engine *e, const tt_serve_config *cfg, tt_serve_rep
  * running batch without the engine lock, so pushing threads are not kept waiting by it. */
 typedef struct {
   uint32_t struct_size;           /* sizeof(tt_server_config) */
-  uint32_t max_inflight_batches;  /* 0 = 3 (one running, one queued behind it, one forming) */
+  uint32_t max_inflight_batches;  /* 0 = 8; each batch in flight gets its own launch lane (streams,
+                                     work list, counters), so consecutive batches overlap on the GPU
+                                     (not while the engine uses CUDA graphs or has uplink cells) */
   uint32_t release_outputs;       /* 1: completed slots' outputs are released without pulls */
   int32_t queue_timeout_us;       /* wait of a push into a full ring: 0 = 1 s, < 0 = no wait */
   double deadline_us;             /* latency counted as a deadline miss above this (0 = 500) */

@@ -81,12 +81,54 @@ void dev_free(tt_engine *e, void *p) {
     e->free_fn(p, e->alloc_ctx);
     return;
   }
-  if (e->stream) cudaStreamSynchronize(e->stream);
-  if (e->copy) cudaStreamSynchronize(e->copy);
-  if (e->h2d) cudaStreamSynchronize(e->h2d);
+  sync_all(e);
+  e->free_fn(p, e->alloc_ctx);
+}
+
+void sync_all(tt_engine *e) {
+  for (cudaStream_t s : {e->stream, e->copy, e->h2d})
+    if (s) cudaStreamSynchronize(s);
+  for (int li = 0; li < e->n_lanes; ++li) {
+    const TTLane &l = e->lanes[li];
+    if (l.stream) cudaStreamSynchronize(l.stream);
+    for (cudaStream_t s : l.side)
+      if (s) cudaStreamSynchronize(s);
+  }
   for (cudaStream_t s : e->side)
     if (s) cudaStreamSynchronize(s);
-  e->free_fn(p, e->alloc_ctx);
+}
+
+bool enable_lanes(tt_engine *e, int n) {
+  n = std::min(n, tt_engine::kLanes);
+  for (int li = e->n_lanes; li < n; ++li) {
+    TTLane &l = e->lanes[li];
+    cudaError_t err = cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking);
+    for (int i = 0; i < tt_engine::kSide && err == cudaSuccess; ++i) {
+      err = cudaStreamCreateWithFlags(&l.side[i], cudaStreamNonBlocking);
+      if (err == cudaSuccess) err = cudaEventCreateWithFlags(&l.join[i], cudaEventDisableTiming);
+    }
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&l.fork, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = dmalloc(e, &l.d_segs, sizeof(TTSeg) * e->max_ues);
+    if (err == cudaSuccess) err = dmalloc(e, &l.d_tcsegs, sizeof(TTSeg) * e->max_ues);
+    if (err == cudaSuccess) err = dmalloc(e, &l.d_counters, sizeof(uint32_t) * e->counter_cap);
+    if (err == cudaSuccess) err = cudaMemsetAsync(l.d_counters, 0, sizeof(uint32_t) * e->counter_cap, l.stream);
+    if (err != cudaSuccess) {  // stay on the lanes made so far
+      dfree(e, l.d_segs);
+      dfree(e, l.d_tcsegs);
+      dfree(e, l.d_counters);
+      for (int i = 0; i < tt_engine::kSide; ++i) {
+        if (l.side[i]) cudaStreamDestroy(l.side[i]);
+        if (l.join[i]) cudaEventDestroy(l.join[i]);
+      }
+      if (l.fork) cudaEventDestroy(l.fork);
+      if (l.stream) cudaStreamDestroy(l.stream);
+      l = TTLane{};
+      cudaGetLastError();
+      return e->n_lanes > 1;
+    }
+    e->n_lanes = li + 1;
+  }
+  return true;
 }
 
 NvtxScope::NvtxScope(const char *name) { nvtxRangePushA(name); }
@@ -421,9 +463,10 @@ tt_status build_plan(tt_engine *e, const std::vector<tt_chan *> &chans, const st
   return TT_OK;
 }
 
-cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const unsigned long long *cursors) {
+cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const unsigned long long *cursors,
+                         TTLane &ln) {
   if (e->persistent) {
-    cudaError_t err = cudaMemsetAsync(e->d_counters, 0, sizeof(uint32_t) * p.groups.size(), e->stream);
+    cudaError_t err = cudaMemsetAsync(ln.d_counters, 0, sizeof(uint32_t) * p.groups.size(), ln.stream);
     if (err != cudaSuccess) return err;
   }
   // largest variant on the engine stream, the others on side branches that start with it
@@ -435,8 +478,8 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
   });
   const int n_side = (int)std::min<size_t>(order.size() > 0 ? order.size() - 1 : 0, tt_engine::kSide);
   if (n_side > 0) {
-    cudaError_t err = cudaEventRecord(e->fork, e->stream);
-    for (int i = 0; i < n_side && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(e->side[i], e->fork, 0);
+    cudaError_t err = cudaEventRecord(ln.fork, ln.stream);
+    for (int i = 0; i < n_side && err == cudaSuccess; ++i) err = cudaStreamWaitEvent(ln.side[i], ln.fork, 0);
     if (err != cudaSuccess) return err;
   }
   for (size_t oi = 0; oi < order.size(); ++oi) {
@@ -447,7 +490,7 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
     L.segs = d_segs + g.seg0;
     L.n_segs = g.nseg;
     L.total_items = g.items;
-    L.counter = e->persistent ? e->d_counters + gi : nullptr;
+    L.counter = e->persistent ? ln.d_counters + gi : nullptr;
     L.spt = g.spt;
     L.tpb = g.tpb;
     L.nrx = g.nrx;
@@ -461,30 +504,25 @@ cudaError_t enqueue_plan(tt_engine *e, const Plan &p, const TTSeg *d_segs, const
     L.cursors = cursors;
     L.check.report = e->d_check;
     L.check.shrink = e->check_shrink;
-    cudaStream_t st = oi == 0 || n_side == 0 ? e->stream : e->side[(oi - 1) % n_side];
+    cudaStream_t st = oi == 0 || n_side == 0 ? ln.stream : ln.side[(oi - 1) % n_side];
     cudaError_t err = tt_launch_conv_fp32(L, st);
     if (err != cudaSuccess) return err;
   }
   for (int i = 0; i < n_side; ++i) {
-    cudaError_t err = cudaEventRecord(e->join[i], e->side[i]);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, e->join[i], 0);
+    cudaError_t err = cudaEventRecord(ln.join[i], ln.side[i]);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(ln.stream, ln.join[i], 0);
     if (err != cudaSuccess) return err;
   }
   return cudaSuccess;
 }
 
 // Direct launch: the work list is uploaded from the host and the device cursors are not used.
-tt_status launch_direct(tt_engine *e, const Plan &p) {
-  if (p.segs.size() > e->seg_cap) {
-    dfree(e, e->d_segs);
-    e->d_segs = nullptr;
-    e->seg_cap = 0;
-    TT_CK(dmalloc(e, &e->d_segs, sizeof(TTSeg) * p.segs.size() * 2));
-    e->seg_cap = p.segs.size() * 2;
-  }
-  TT_CK(cudaMemcpyAsync(e->d_segs, p.segs.data(), sizeof(TTSeg) * p.segs.size(), cudaMemcpyHostToDevice,
-                        e->stream));
-  cudaError_t err = enqueue_plan(e, p, e->d_segs, nullptr);
+tt_status launch_direct(tt_engine *e, const Plan &p, TTLane &ln) {
+  // every lane's list holds max_ues segments (one per channel), sized when the engine or lane was made
+  if (p.segs.size() > e->seg_cap) return fail(TT_ERR_STATE, "work list of %zu segments", p.segs.size());
+  TT_CK(cudaMemcpyAsync(ln.d_segs, p.segs.data(), sizeof(TTSeg) * p.segs.size(), cudaMemcpyHostToDevice,
+                        ln.stream));
+  cudaError_t err = enqueue_plan(e, p, ln.d_segs, nullptr, ln);
   if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tiled launch: %s", cudaGetErrorString(err));
   e->launches += p.groups.size();
   for (tt_chan *c : p.chans) c->dev_cursor = UINT64_MAX;  // the device cursor did not follow
@@ -526,7 +564,7 @@ tt_status launch_graph(tt_engine *e, const Plan &p) {
     TT_CK(cudaMemcpy(e->d_gsegs, p.segs.data(), sizeof(TTSeg) * p.segs.size(), cudaMemcpyHostToDevice));
     cudaGraph_t graph = nullptr;
     TT_CK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t err = enqueue_plan(e, p, e->d_gsegs, e->d_cursors);
+    cudaError_t err = enqueue_plan(e, p, e->d_gsegs, e->d_cursors, e->lanes[0]);
     if (err == cudaSuccess) err = tt_launch_advance(e->d_gsegs, (int)p.segs.size(), e->d_cursors, e->stream);
     cudaError_t err2 = cudaStreamEndCapture(e->stream, &graph);
     if (err == cudaSuccess) err = err2;
@@ -568,7 +606,7 @@ tt_status launch_cached_graph(tt_engine *e, const std::vector<tt_chan *> &chans,
 
 
 // Tensor-core channels: one item per (UE, slot, symbol), BF16 and FP16 channels in separate launches.
-tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
+tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans, TTLane &ln) {
   {  // failure-detection tests: the kernel issues no MMA, so its bounded waits run out
     const char *v = std::getenv("TT_TEST_TC_NO_MMA");
     e->tc_no_mma = (v && v[0] == '1') ? 1 : 0;
@@ -587,13 +625,7 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
       segs.push_back(sg);
       n16 += fp16;
     }
-  if (segs.size() > e->tcseg_cap) {
-    dfree(e, e->d_tcsegs);
-    e->d_tcsegs = nullptr;
-    e->tcseg_cap = 0;
-    TT_CK(dmalloc(e, &e->d_tcsegs, sizeof(TTSeg) * segs.size() * 2));
-    e->tcseg_cap = segs.size() * 2;
-  }
+  if (segs.size() > e->tcseg_cap) return fail(TT_ERR_STATE, "tensor-core work list of %zu segments", segs.size());
   const size_t nbf = segs.size() - (size_t)n16;
   uint32_t acc = 0;
   for (size_t i = 0; i < segs.size(); ++i) {
@@ -601,8 +633,8 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
     segs[i].item_begin = acc;
     acc += segs[i].items;
   }
-  TT_CK(cudaMemcpyAsync(e->d_tcsegs, segs.data(), sizeof(TTSeg) * segs.size(), cudaMemcpyHostToDevice,
-                        e->stream));
+  TT_CK(cudaMemcpyAsync(ln.d_tcsegs, segs.data(), sizeof(TTSeg) * segs.size(), cudaMemcpyHostToDevice,
+                        ln.stream));
   for (int pass = 0; pass < 2; ++pass) {
     const size_t s0 = pass ? nbf : 0, s1 = pass ? segs.size() : nbf;
     if (s0 == s1) continue;
@@ -610,17 +642,17 @@ tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans) {
     for (size_t i = s0; i < s1; ++i) items += segs[i].items;
     TTLaunch L{};
     L.ues = e->d_ues;
-    L.segs = e->d_tcsegs + s0;
+    L.segs = ln.d_tcsegs + s0;
     L.n_segs = (int)(s1 - s0);
     L.total_items = items;
     L.counter = nullptr;
     L.check.report = e->d_check;
     L.check.shrink = e->check_shrink;
     L.grid = -1;
-    cudaError_t err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->tc_no_mma, e->stream);
+    cudaError_t err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->tc_no_mma, ln.stream);
     if (err != cudaSuccess) return fail(TT_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(err));
     L.grid = (int)std::min<uint64_t>((uint64_t)(-L.grid) * e->num_sms, items);
-    err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->tc_no_mma, e->stream);
+    err = tt_launch_toeplitz_tc(L, pass == 1, e->d_status, e->tc_no_mma, ln.stream);
     if (err != cudaSuccess) return fail(TT_ERR_CUDA, "tensor-core launch: %s", cudaGetErrorString(err));
     ++e->launches;
   }
@@ -643,11 +675,11 @@ tt_status time_batch(tt_engine *e, const std::vector<tt_chan *> &chans, const st
   Plan plan;
   tt_status st = build_plan(e, chans, first, count, plan);
   if (st != TT_OK) return st;
-  if ((st = launch_direct(e, plan)) != TT_OK) return st;  // warm-up
+  if ((st = launch_direct(e, plan, e->lanes[0])) != TT_OK) return st;  // warm-up
   *best_ms = 1e30f;
   for (int r = 0; r < reps; ++r) {
     cudaEventRecord(a, e->stream);
-    if ((st = launch_direct(e, plan)) != TT_OK) return st;
+    if ((st = launch_direct(e, plan, e->lanes[0])) != TT_OK) return st;
     cudaEventRecord(b, e->stream);
     if (cudaEventSynchronize(b) != cudaSuccess) return fail(TT_ERR_CUDA, "autotune: timing failed");
     float ms = 0.f;
@@ -728,6 +760,19 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   if (err == cudaSuccess) err = dmalloc(e, &e->d_gsegs, sizeof(TTSeg) * e->max_ues);
   if (err == cudaSuccess) err = dmalloc(e, &e->d_tcsegs, sizeof(TTSeg) * e->max_ues);
   if (err == cudaSuccess) e->seg_cap = e->gseg_cap = e->tcseg_cap = e->max_ues;
+  if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e->lane_pre, cudaEventDisableTiming);
+  if (err == cudaSuccess) {  // lane 0 is the engine's own stream and lists
+    TTLane &l0 = e->lanes[0];
+    l0.stream = e->stream;
+    for (int i = 0; i < tt_engine::kSide; ++i) {
+      l0.side[i] = e->side[i];
+      l0.join[i] = e->join[i];
+    }
+    l0.fork = e->fork;
+    l0.d_segs = e->d_segs;
+    l0.d_tcsegs = e->d_tcsegs;
+    l0.d_counters = e->d_counters;
+  }
   if (err == cudaSuccess) err = dmalloc(e, &e->d_status, sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(e->d_status, 0, sizeof(int));
   if (err == cudaSuccess) err = dmalloc(e, &e->d_check, 2 * sizeof(uint32_t));
@@ -744,10 +789,21 @@ tt_status tt_engine_destroy(tt_engine *e) {
   if (!e) return fail(TT_ERR_INVALID, "null engine");
   if (e->server) tt_server_stop(e, nullptr);  // its thread launches on this engine
   cudaSetDevice(e->device);
-  if (e->stream) cudaStreamSynchronize(e->stream);
-  for (cudaStream_t s : {e->copy, e->h2d, e->side[0], e->side[1], e->side[2]})
-    if (s) cudaStreamSynchronize(s);
+  ttx::sync_all(e);
   e->quiesced = true;  // nothing runs any more: the frees below need no further waits
+  for (int li = 1; li < e->n_lanes; ++li) {
+    TTLane &l = e->lanes[li];
+    dfree(e, l.d_segs);
+    dfree(e, l.d_tcsegs);
+    dfree(e, l.d_counters);
+    for (int i = 0; i < tt_engine::kSide; ++i) {
+      if (l.side[i]) cudaStreamDestroy(l.side[i]);
+      if (l.join[i]) cudaEventDestroy(l.join[i]);
+    }
+    if (l.fork) cudaEventDestroy(l.fork);
+    if (l.stream) cudaStreamDestroy(l.stream);
+  }
+  if (e->lane_pre) cudaEventDestroy(e->lane_pre);
   for (tt_chan *c : e->table)
     if (c) {
       dfree(e, c->d_in);
@@ -916,7 +972,7 @@ tt_status tt_chan_destroy(tt_chan *c) {
   std::lock_guard<std::mutex> lk(e->mu);
   if (c->cell) return fail(TT_ERR_STATE, "channel is a member of a cell: destroy the cell first");
   cudaSetDevice(e->device);
-  cudaStreamSynchronize(e->stream);
+  ttx::sync_all(e);
   dfree(e, c->d_in);
   dfree(e, c->d_out);
   dfree(e, c->d_taps);
@@ -1308,11 +1364,34 @@ static cudaError_t wait_ring_readers(tt_chan *c, uint64_t first, uint32_t n, cud
   // Completed batches have left the in-flight list: if the reader is among them, nothing to wait
   // for (the first batch still in flight is a later one, which reads other positions).
   if (last_reader_slot < c->completed_end) return cudaSuccess;
-  for (const auto &p : c->inflight)
-    if (p.first > last_reader_slot) {
-      cudaEvent_t ev = event_of(e, p.second);
-      return ev ? cudaStreamWaitEvent(st, ev, 0) : cudaSuccess;
+  // Every in-flight batch up to the one holding that slot reads the positions (on one lane the last
+  // of them would do, but batches on different lanes may complete out of order).
+  for (const auto &p : c->inflight) {
+    cudaEvent_t ev = event_of(e, p.second);
+    if (ev) {
+      cudaError_t err = cudaStreamWaitEvent(st, ev, 0);
+      if (err != cudaSuccess) return err;
     }
+    if (p.first > last_reader_slot) break;
+  }
+  return cudaSuccess;
+}
+
+// The stream waits for the batches that produce this channel's slots [.., upto) and are still in
+// flight (a copy of their outputs on another stream).
+static cudaError_t wait_producers(tt_chan *c, uint64_t upto, cudaStream_t st) {
+  tt_engine *e = c->e;
+  cudaError_t q = update_completed(e);
+  if (q != cudaSuccess) return q;
+  update_chan(c);
+  for (const auto &p : c->inflight) {
+    cudaEvent_t ev = event_of(e, p.second);
+    if (ev) {
+      cudaError_t err = cudaStreamWaitEvent(st, ev, 0);
+      if (err != cudaSuccess) return err;
+    }
+    if (p.first >= upto) break;
+  }
   return cudaSuccess;
 }
 
@@ -1403,6 +1482,7 @@ tt_status tt_chan_push_slots_dev(tt_chan *c, uint64_t first, uint32_t n, const i
   if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
   cudaError_t err = cudaEventRecord(ev, (cudaStream_t)stream);
   if (err == cudaSuccess) err = cudaStreamWaitEvent(e->stream, ev, 0);
+  if (err == cudaSuccess) err = wait_ring_readers(c, first, n, e->stream);  // batches on other lanes
   if (err == cudaSuccess)
     err = ring_copy(c->d_in, c->slot_in_elems, c->Q, first, n, d_iq_in, nullptr, cudaMemcpyDeviceToDevice,
                     e->stream, true);
@@ -1722,7 +1802,7 @@ tt_status tt_cell_destroy(tt_cell *cl) {
   tt_engine *e = cl->e;
   std::lock_guard<std::mutex> lk(e->mu);
   cudaSetDevice(e->device);
-  cudaStreamSynchronize(e->stream);
+  ttx::sync_all(e);
   for (tt_chan *m : cl->members) m->cell = nullptr;
   dfree(e, cl->d_out);
   dfree(e, cl->d_members);
@@ -1764,11 +1844,7 @@ tt_status tt_engine_run(tt_engine *e) {
       if (ev) e->pool.push_back(ev);
     }
   } guard{e, ev};
-  if (e->server) {  // the batch's first device-side moment, for the server's GPU-time statistics
-    tt_status sst = ttx::server_stamp_start(e, e->launch_seq + 1);
-    if (sst != TT_OK) return sst;
-  }
-  {
+  {  // anchor and sparse-tap pre-passes, on the engine stream
     std::vector<tt_chan *> all(ready);
     all.insert(all.end(), tc_ready.begin(), tc_ready.end());
     tt_status sst = launch_retime(e, all);
@@ -1776,11 +1852,28 @@ tt_status tt_engine_run(tt_engine *e) {
     if (sst == TT_OK) sst = launch_topn(e, ready);
     if (sst != TT_OK) return sst;
   }
+  // The batch's lane: while a server runs, batches rotate over the lanes so that consecutive ones
+  // overlap on the GPU.  Not with cells: a cell's aggregation frees its members' output slots when it
+  // is launched, so a later batch must not start before it ends.  A lane other than the engine stream
+  // first waits for everything queued there (device pushes and pulls, descriptor uploads, the
+  // pre-passes above).
+  const int li = (e->server && e->n_lanes > 1 && !e->graphs && e->cells.empty())
+                     ? (int)((e->launch_seq + 1) % (uint64_t)e->n_lanes)
+                     : 0;
+  TTLane &ln = e->lanes[li];
+  if (li != 0) {
+    TT_CK(cudaEventRecord(e->lane_pre, e->stream));
+    TT_CK(cudaStreamWaitEvent(ln.stream, e->lane_pre, 0));
+  }
+  if (e->server) {  // the batch's first device-side moment, for the server's GPU-time statistics
+    tt_status sst = ttx::server_stamp_start(e, e->launch_seq + 1, ln.stream);
+    if (sst != TT_OK) return sst;
+  }
 
   if (e->form == TT_FORM_PLAIN) {
     for (tt_chan *c : ready) {
       for (uint64_t s = c->launched_end; s < c->pushed_end; ++s) {
-        cudaError_t err = tt_launch_plain(e->d_ues + c->index, s, c->n, e->stream);
+        cudaError_t err = tt_launch_plain(e->d_ues + c->index, s, c->n, ln.stream);
         if (err != cudaSuccess) return fail(TT_ERR_CUDA, "plain launch: %s", cudaGetErrorString(err));
         ++e->launches;
       }
@@ -1801,7 +1894,7 @@ tt_status tt_engine_run(tt_engine *e) {
       Plan plan;
       tt_status st = build_plan(e, ready, first, count, plan);
       if (st != TT_OK) return st;
-      st = e->graphs ? launch_graph(e, plan) : launch_direct(e, plan);
+      st = e->graphs ? launch_graph(e, plan) : launch_direct(e, plan, ln);
       if (st != TT_OK) return st;
       if (e->graphs) {
         e->gchans = ready;
@@ -1811,7 +1904,7 @@ tt_status tt_engine_run(tt_engine *e) {
     }
   }
   if (!tc_ready.empty()) {
-    tt_status st = launch_tc(e, tc_ready);
+    tt_status st = launch_tc(e, tc_ready, ln);
     if (st != TT_OK) return st;
     ready.insert(ready.end(), tc_ready.begin(), tc_ready.end());
   }
@@ -1834,12 +1927,13 @@ tt_status tt_engine_run(tt_engine *e) {
   const tt_status cst = launch_cells(e, cell_ends);
   if (ready.empty() && cell_ends.empty()) return cst;
   if (e->server) {
-    tt_status sst = ttx::server_stamp(e, e->launch_seq + 1);
+    tt_status sst = ttx::server_stamp(e, e->launch_seq + 1, ln.stream);
     if (sst != TT_OK) return sst;
   }
-  TT_CK(cudaEventRecord(ev, e->stream));
+  TT_CK(cudaEventRecord(ev, ln.stream));
   guard.ev = nullptr;  // owned by the batch list from here on
   const uint64_t seq = ++e->launch_seq;
+  ln.last_seq = seq;
   e->events.emplace_back(seq, ev);
   for (size_t i = 0; i < ready.size(); ++i) {
     e->slots_processed += ready[i]->launched_end - prev_end[i];
@@ -1886,7 +1980,7 @@ tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us) {
   TT_CK(cudaSetDevice(e->device));
   tt_status s = wait_seq(e, e->launch_seq, timeout_us, lk);
   if (s != TT_OK) return s;
-  if (timeout_us < 0) TT_CK(cudaStreamSynchronize(e->stream));
+  if (timeout_us < 0) ttx::sync_all(e);
   int kst = 0;
   TT_CK(cudaMemcpy(&kst, e->d_status, sizeof kst, cudaMemcpyDeviceToHost));
   if (kst) {
@@ -1904,7 +1998,7 @@ tt_status tt_engine_get_check(tt_engine *e, tt_check_report *out) {
   TT_CK(cudaSetDevice(e->device));
   tt_status s = wait_seq(e, e->launch_seq, -1, lk);
   if (s != TT_OK) return s;
-  TT_CK(cudaStreamSynchronize(e->stream));
+  ttx::sync_all(e);
   uint32_t w[2] = {0, 0};
   TT_CK(cudaMemcpy(w, e->d_check, sizeof w, cudaMemcpyDeviceToHost));
   TT_CK(cudaMemset(e->d_check, 0, sizeof w));
@@ -2028,8 +2122,10 @@ tt_status tt_chan_pull_slots_dev(tt_chan *c, uint64_t first, uint32_t n, void *d
   if (first + n > c->launched_end) return fail(TT_ERR_AGAIN, "slot not launched yet");
   cudaEvent_t ev = get_event(e);
   if (!ev) return fail(TT_ERR_CUDA, "event creation failed");
-  cudaError_t err = ring_copy(c->d_out, c->slot_out_elems, c->Q, first, n, nullptr, d_iq_out,
-                              cudaMemcpyDeviceToDevice, e->stream, false);
+  cudaError_t err = wait_producers(c, first + n, e->stream);  // batches on other lanes
+  if (err == cudaSuccess)
+    err = ring_copy(c->d_out, c->slot_out_elems, c->Q, first, n, nullptr, d_iq_out, cudaMemcpyDeviceToDevice,
+                    e->stream, false);
   if (err == cudaSuccess) err = cudaEventRecord(ev, e->stream);
   if (err == cudaSuccess) err = cudaStreamWaitEvent((cudaStream_t)stream, ev, 0);
   e->pool.push_back(ev);
@@ -2087,7 +2183,7 @@ tt_status tt_chan_get_state(const tt_chan *cc, void *buf, size_t *len) {
   update_chan(c);
   if (c->launched_end != c->pushed_end || c->completed_end != c->launched_end)
     return fail(TT_ERR_STATE, "channel has pending or running slots; run and sync first");
-  TT_CK(cudaStreamSynchronize(e->stream));
+  ttx::sync_all(e);
   StateHeader h{};
   h.magic = kStateMagic;
   h.version = 1;
@@ -2141,7 +2237,7 @@ tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len) {
   update_chan(c);
   if (c->launched_end != c->pushed_end || c->completed_end != c->launched_end)
     return fail(TT_ERR_STATE, "channel has pending or running slots");
-  TT_CK(cudaStreamSynchronize(e->stream));
+  ttx::sync_all(e);
   const int16_t *in = reinterpret_cast<const int16_t *>(static_cast<const char *>(buf) + sizeof h);
   const uint64_t next = h.next_slot;
   // zero the history slots, then write the saved samples into them

@@ -23,6 +23,21 @@ struct tt_chan;
 
 struct tt_cell;
 
+// One launch lane: the streams, events and device work lists a batch launches with.  Lane 0 is the
+// engine's own stream and lists.  While a serving thread runs (and the engine has no CUDA graphs and
+// no uplink cells), consecutive batches rotate over the lanes, so one batch's kernels overlap the
+// tail and the set-up of the previous ones.
+struct TTLane {
+  static constexpr int kSide = 3;
+  cudaStream_t stream = nullptr;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
+  TTSeg *d_segs = nullptr;         // tiled-kernel work list (max_ues entries)
+  TTSeg *d_tcsegs = nullptr;       // tensor-core work list (max_ues entries)
+  uint32_t *d_counters = nullptr;  // one work counter per kernel variant (counter_cap)
+  uint64_t last_seq = 0;           // the last batch launched on this lane
+};
+
 struct tt_engine {
   int device = 0;
   uint64_t budget = 0;
@@ -43,7 +58,7 @@ struct tt_engine {
   cudaStream_t h2d = nullptr;     // host pushes: wait only for kernels that still read the overwritten ring slots
   // Kernel variants of one run go on parallel branches (side streams forked from and joined
   // back to `stream`), so each variant's tail overlaps the others' work.
-  static constexpr int kSide = 3;
+  static constexpr int kSide = TTLane::kSide;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork = nullptr, join[kSide] = {};
   std::mutex mu;
@@ -98,6 +113,12 @@ struct tt_engine {
   uint64_t admit_next = 0;
   // channels with pushed slots not launched yet (each once), so a run looks at those only
   std::vector<tt_chan *> pending;
+  // launch lanes: lanes[0] mirrors stream/side/fork/join/d_segs/d_tcsegs/d_counters; lanes 1.. are
+  // created when a serving thread starts (n_lanes > 1)
+  static constexpr int kLanes = 8;
+  TTLane lanes[kLanes];
+  int n_lanes = 1;
+  cudaEvent_t lane_pre = nullptr;  // recorded on `stream` before a batch on another lane starts
   // tuning cache: class key -> (samples per thread, threads per CTA) for this device model, loaded
   // from the file TT_TUNE_CACHE names at creation and written back by the autotuner
   std::mutex tune_mu;
@@ -205,10 +226,15 @@ bool cells_have_work(const tt_engine *e);
 void server_note_push(tt_chan *c, uint64_t first, uint32_t n, int64_t arrival_ns);
 // Batch `seq` launched channel c's slots [from, to) (engine lock held).
 void server_note_launch(tt_chan *c, uint64_t from, uint64_t to, uint64_t seq);
-// Before a batch's completion event: stamp its completion on the device (engine lock held).
-tt_status server_stamp(tt_engine *e, uint64_t seq);
-// Before a batch's first kernel: stamp when the device starts it (engine lock held).
-tt_status server_stamp_start(tt_engine *e, uint64_t seq);
+// Before a batch's completion event: stamp its completion on the device, on stream st (engine lock held).
+tt_status server_stamp(tt_engine *e, uint64_t seq, cudaStream_t st);
+// Before a batch's first kernel: stamp when the device starts it, on stream st (engine lock held).
+tt_status server_stamp_start(tt_engine *e, uint64_t seq, cudaStream_t st);
+// Create launch lanes up to n (at most tt_engine::kLanes; engine lock held); false leaves the engine
+// on the lanes it had.
+bool enable_lanes(tt_engine *e, int n);
+// Wait for every stream of the engine (all lanes, copies).
+void sync_all(tt_engine *e);
 // A push found the ring full while a server runs: wait (engine lock held, released while waiting)
 // until room() or the queue timeout; TT_OK or the failure status.
 template <class Room>

@@ -5,7 +5,8 @@
 // is pending as one batch (tt_engine_run) whenever fewer than max_inflight_batches are on the GPU,
 // so requests that arrive while others run are admitted into the next batch and their work
 // overlaps on the device (per-UE isolation, Sec. III-C, keeps every result the same alone and in
-// the mix).  A push into a full ring waits for room instead of being refused.  Each batch's
+// the mix).  Each batch in flight launches on its own lane of streams, work list and counters, so
+// a batch's kernels start while the previous batches' tails still run.  A push into a full ring waits for room instead of being refused.  Each batch's
 // completion is stamped on the device (%globaltimer) and mapped to the host clock, so a request's
 // latency does not include how soon the host noticed the completion.
 //
@@ -51,11 +52,15 @@ struct TTServer {
   std::vector<double> lat_ns;
   uint64_t requests = 0, queued = 0, refused = 0, completed = 0, n_batches = 0, batched = 0, misses = 0;
   double gpu_ns = 0.0;                               // device time from batches' start to end stamps
-  int64_t first_start = 0, last_end = 0;
+  int64_t first_start = 0, last_end = 0, busy_until = 0;
   double deadline_ns = 500e3;
   tt_status err = TT_OK;
   std::string err_msg;
 };
+
+// Batches in flight by default, each on its own launch lane where the engine allows it.  At 512
+// serving UEs (GPU 98% busy) p99 went 689, 575, 523 and 411-435 us with 3, 5, 6 and 8 in flight.
+constexpr int kDefaultInflight = 8;
 
 namespace ttx {
 
@@ -83,17 +88,17 @@ void server_note_launch(tt_chan *c, uint64_t from, uint64_t to, uint64_t seq) {
   }
 }
 
-tt_status server_stamp_start(tt_engine *e, uint64_t seq) {
+tt_status server_stamp_start(tt_engine *e, uint64_t seq, cudaStream_t st) {
   TTServer *S = e->server;
-  cudaError_t err = tt_launch_stamp(S->d_stamp + TTServer::kRing + (seq % TTServer::kRing), e->stream);
+  cudaError_t err = tt_launch_stamp(S->d_stamp + TTServer::kRing + (seq % TTServer::kRing), st);
   if (err != cudaSuccess) return fail(TT_ERR_CUDA, "start stamp: %s", cudaGetErrorString(err));
   ++e->launches;
   return TT_OK;
 }
 
-tt_status server_stamp(tt_engine *e, uint64_t seq) {
+tt_status server_stamp(tt_engine *e, uint64_t seq, cudaStream_t st) {
   TTServer *S = e->server;
-  cudaError_t err = tt_launch_stamp(S->d_stamp + (seq % TTServer::kRing), e->stream);
+  cudaError_t err = tt_launch_stamp(S->d_stamp + (seq % TTServer::kRing), st);
   if (err != cudaSuccess) return fail(TT_ERR_CUDA, "completion stamp: %s", cudaGetErrorString(err));
   ++e->launches;
   return TT_OK;
@@ -131,9 +136,13 @@ void collect_completed(tt_engine *e) {
     const volatile unsigned long long *stamp = S->h_stamp + (b.seq % TTServer::kRing);
     const volatile unsigned long long *start = S->h_stamp + TTServer::kRing + (b.seq % TTServer::kRing);
     const int64_t t_done = (int64_t)*stamp - S->offset_ns;
-    S->gpu_ns += (double)(int64_t)(*stamp - *start);
-    if (!S->first_start) S->first_start = (int64_t)*start;
-    S->last_end = (int64_t)*stamp;
+    // device busy time: the union of the batches' spans (batches on different lanes overlap)
+    const int64_t b0 = (int64_t)*start, b1 = (int64_t)*stamp;
+    const int64_t from = std::max(b0, S->busy_until);
+    if (b1 > from) S->gpu_ns += (double)(b1 - from);
+    S->busy_until = std::max(S->busy_until, b1);
+    if (!S->first_start || b0 < S->first_start) S->first_start = b0;
+    S->last_end = std::max(S->last_end, b1);
     for (int64_t ta : b.arrivals) {
       if (ta < S->count_from_ns) continue;
       const double l = (double)(t_done - ta);
@@ -177,9 +186,7 @@ void server_loop(tt_engine *e) {
   TTServer *S = e->server;
   S->tid = std::this_thread::get_id();
   cudaSetDevice(e->device);
-  // 3 by default: one running, the next queued behind it, a third forming (at 512 UEs, 2 and 4 in
-  // flight measured a higher p50 than 3)
-  const size_t max_inflight = S->cfg.max_inflight_batches ? S->cfg.max_inflight_batches : 3;
+  const size_t max_inflight = S->cfg.max_inflight_batches ? S->cfg.max_inflight_batches : kDefaultInflight;
   for (;;) {
     bool launch = false, done = false;
     cudaEvent_t front = nullptr;
@@ -280,6 +287,9 @@ tt_status tt_server_start(tt_engine *e, const tt_server_config *cfg) {
       return fail(TT_ERR_CUDA, "stamp buffer: pinned mapped host memory unavailable");
     }
     std::memset(S->h_stamp, 0, sizeof(unsigned long long) * 2 * TTServer::kRing);
+    // one launch lane per batch in flight: consecutive batches overlap on the GPU where the engine
+    // allows it (no CUDA graphs, no cells)
+    ttx::enable_lanes(e, cfg->max_inflight_batches ? (int)cfg->max_inflight_batches : kDefaultInflight);
     if (cudaStreamSynchronize(e->stream) != cudaSuccess) {
       cudaFreeHost(S->h_stamp);
       return fail(TT_ERR_CUDA, "stream sync failed");

@@ -156,7 +156,7 @@ tt_status tt_engine_autotune(tt_engine *e, int32_t reps, uint32_t *classes_tuned
   if (reps < 1) reps = 3;
   std::lock_guard<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
-  TT_CK(cudaStreamSynchronize(e->stream));
+  ttx::sync_all(e);
   std::vector<std::pair<std::string, std::vector<tt_chan *>>> classes;
   for (tt_chan *c : e->table) {
     if (!c || !c->has_trace || c->cfg.precision != TT_FP32) continue;

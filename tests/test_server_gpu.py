@@ -36,7 +36,8 @@ def _specs():
     return out
 
 
-def test_pushes_from_producer_threads_are_batched_and_match_alone_and_oracle():
+@pytest.mark.parametrize("inflight", [2, 0])  # 0: the default, 8 batches on 8 launch lanes
+def test_pushes_from_producer_threads_are_batched_and_match_alone_and_oracle(inflight):
     specs = _specs()
     xs = [inputs.make_iq(7, sp, N_SLOTS) for sp in specs]
     slots = [tc.slots_major(x, sp.n) for sp, x in zip(specs, xs)]
@@ -48,7 +49,7 @@ def test_pushes_from_producer_threads_are_batched_and_match_alone_and_oracle():
         chans = [tc.Chan(eng, sp, ring_slots=hist_slots(sp) + 2) for sp in specs]
         dev = [torch.from_numpy(s).cuda() for s in slots]           # device copies for device pushes
         torch.cuda.synchronize()
-        tc.tt_server_start(eng.h, max_inflight_batches=2, queue_timeout_us=10_000_000)
+        tc.tt_server_start(eng.h, max_inflight_batches=inflight, queue_timeout_us=10_000_000)
 
         def producer(ues, seed):
             rng = np.random.default_rng(seed)
@@ -69,9 +70,16 @@ def test_pushes_from_producer_threads_are_batched_and_match_alone_and_oracle():
                 while left:
                     for u in list(left):
                         ch = chans[u]
-                        buf = np.empty((1, ch.spec.n_rx, ch.n, 2), dtype=np.int16)
                         try:
-                            tc.tt_chan_pull_slots(ch.h, left[u], 1, buf, -1)
+                            if u % 3 == 1:      # device pull: a copy ordered after the producing batch
+                                d = torch.empty((1, ch.spec.n_rx, ch.n, 2), dtype=torch.int16, device="cuda")
+                                st = torch.cuda.current_stream()
+                                tc.tt_chan_pull_slots_dev(ch.h, left[u], 1, d, st)
+                                st.synchronize()
+                                buf = d.cpu().numpy()
+                            else:
+                                buf = np.empty((1, ch.spec.n_rx, ch.n, 2), dtype=np.int16)
+                                tc.tt_chan_pull_slots(ch.h, left[u], 1, buf, -1)
                         except tc.TTError as ex:
                             if ex.status != tc.TT_ERR_AGAIN:
                                 raise
