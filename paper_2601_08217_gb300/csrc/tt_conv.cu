@@ -70,15 +70,18 @@ cudaError_t tt_launch_conv_fp32(const TTLaunch &L, cudaStream_t st) {
   }
 }
 
-// Device-resident slot cursors: after a graph replay every run advances by its slot count.
-__global__ void tt_advance_kernel(const TTSeg *__restrict__ segs, int n_segs, unsigned long long *cursors) {
+// Device-resident slot cursors: after a graph replay every run advances by its slot count times
+// the number of lanes the replays rotate over (a lane's next replay is that many steps later).
+__global__ void tt_advance_kernel(const TTSeg *__restrict__ segs, int n_segs, unsigned long long *cursors,
+                                  unsigned stride) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_segs) cursors[segs[i].ue] += segs[i].n_slots;
+  if (i < n_segs) cursors[segs[i].ue] += (unsigned long long)segs[i].n_slots * stride;
 }
 
-cudaError_t tt_launch_advance(const TTSeg *segs, int n_segs, unsigned long long *cursors, cudaStream_t st) {
+cudaError_t tt_launch_advance(const TTSeg *segs, int n_segs, unsigned long long *cursors, unsigned stride,
+                              cudaStream_t st) {
   if (n_segs <= 0) return cudaSuccess;
-  tt_advance_kernel<<<(n_segs + 127) / 128, 128, 0, st>>>(segs, n_segs, cursors);
+  tt_advance_kernel<<<(n_segs + 127) / 128, 128, 0, st>>>(segs, n_segs, cursors, stride);
   return cudaGetLastError();
 }
 

@@ -24,15 +24,18 @@ struct tt_chan;
 struct tt_cell;
 
 // One launch lane: the streams, events and device work lists a batch launches with.  Lane 0 is the
-// engine's own stream and lists.  While a serving thread runs (and the engine has no CUDA graphs and
-// no uplink cells), consecutive batches rotate over the lanes, so one batch's kernels overlap the
-// tail and the set-up of the previous ones.
+// engine's own stream and lists.  While a serving thread runs, or when the engine replays CUDA
+// graphs, and the engine has no uplink cells, consecutive batches rotate over the lanes, so one
+// batch's kernels overlap the tail and the set-up of the previous ones.  Each lane keeps its own
+// instance of the cached graph and its own device slot cursors.
 struct TTLane {
   static constexpr int kSide = 3;
   cudaStream_t stream = nullptr;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork = nullptr, join[kSide] = {};
   TTSeg *d_segs = nullptr;         // tiled-kernel work list (max_ues entries)
+  unsigned long long *d_cursors = nullptr;  // graph replay: next slot of every UE table entry on this lane
+  cudaGraphExec_t gexec = nullptr;          // this lane's instance of the cached graph (shape gkey)
   TTSeg *d_tcsegs = nullptr;       // tensor-core work list (max_ues entries)
   uint32_t *d_counters = nullptr;  // one work counter per kernel variant (counter_cap)
   uint64_t last_seq = 0;           // the last batch launched on this lane
@@ -78,8 +81,8 @@ struct tt_engine {
   unsigned long long *d_cursors = nullptr;  // device-resident next slot of every UE table entry
   TTSeg *d_gsegs = nullptr;                 // work list owned by the cached graph
   size_t gseg_cap = 0;
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<uint64_t> gkey;               // shape of the cached graph
+  std::vector<uint64_t> gkey;               // shape of the cached graph (one instance per lane)
+  int gstride = 1;                          // lanes the cached graph's replays rotate over
   std::vector<tt_chan *> gchans;            // channels of the cached graph, in table order
   std::vector<uint64_t> gcounts;            // their slots per run
   std::vector<tt_chan *> gplan_chans;       // the same channels in the graph's segment order
@@ -113,8 +116,8 @@ struct tt_engine {
   uint64_t admit_next = 0;
   // channels with pushed slots not launched yet (each once), so a run looks at those only
   std::vector<tt_chan *> pending;
-  // launch lanes: lanes[0] mirrors stream/side/fork/join/d_segs/d_tcsegs/d_counters; lanes 1.. are
-  // created when a serving thread starts (n_lanes > 1)
+  // launch lanes: lanes[0] mirrors stream/side/fork/join/d_segs/d_tcsegs/d_counters/d_cursors;
+  // lanes 1.. are created with a graph-replaying engine and when a serving thread starts
   static constexpr int kLanes = 8;
   TTLane lanes[kLanes];
   int n_lanes = 1;
@@ -151,7 +154,9 @@ struct tt_chan {
   float4 *d_sparse = nullptr;        // sparse convolution: kept taps per anchor and link (ring)
   int32_t *d_sparse_dly = nullptr;
   uint64_t sparse_bytes = 0;
-  uint64_t dev_cursor = UINT64_MAX;  // what the engine's device cursor holds for this UE (after queued work)
+  // what each lane's device cursor holds for this UE (after queued work); UINT64_MAX: unknown
+  uint64_t dev_cursor[tt_engine::kLanes] = {UINT64_MAX, UINT64_MAX, UINT64_MAX, UINT64_MAX,
+                                            UINT64_MAX, UINT64_MAX, UINT64_MAX, UINT64_MAX};
   std::deque<std::pair<uint64_t, uint64_t>> inflight;  // (slot_end, batch seq)
   std::deque<std::pair<uint64_t, int64_t>> arrivals;   // served requests not launched yet: (slot, arrival ns)
   bool in_pending = false;                             // listed in the engine's pending list

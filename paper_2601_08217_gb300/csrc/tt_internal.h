@@ -129,8 +129,9 @@ struct TTLaunch {
   TTCheck check;        // bounds-checked build: where violations are recorded
 };
 
-// cursors[segs[i].ue] += segs[i].n_slots for every segment (device-resident slot cursors).
-cudaError_t tt_launch_advance(const TTSeg *segs, int n_segs, unsigned long long *cursors, cudaStream_t st);
+// cursors[segs[i].ue] += segs[i].n_slots * stride for every segment (device-resident slot cursors).
+cudaError_t tt_launch_advance(const TTSeg *segs, int n_segs, unsigned long long *cursors, unsigned stride,
+                              cudaStream_t st);
 
 // Dynamic shared memory of the tiled kernel for a launch.
 size_t tt_conv_smem_bytes(int spt, int tpb, int dclass, int n_tx, int tap_max, int k_max);
