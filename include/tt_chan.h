@@ -103,7 +103,9 @@ typedef struct {
                                   only, and cached choices of the other count are ignored) */
   uint32_t persistent;       /* 1: persistent CTAs claim work items from a device counter; 0: by stride */
   uint32_t graphs;           /* 1: tt_engine_run captures its launches in a CUDA graph and replays it
-                                while the set of channels and slots per run stays the same */
+                                while the set of channels and slots per run stays the same;
+                                consecutive replays rotate over four launch lanes (each with its own
+                                graph instance), so they overlap on the GPU (not with uplink cells) */
   /* Optional allocator hook (both set, or both NULL for cudaMalloc/cudaFree).  Every device buffer
    * the engine owns (rings, traces, tables, work lists) comes from dev_alloc(bytes, alloc_ctx), which
    * returns device memory on cfg->device aligned to 256 bytes, or NULL (then the call fails with
@@ -317,7 +319,7 @@ typedef struct {
   uint32_t struct_size;           /* sizeof(tt_server_config) */
   uint32_t max_inflight_batches;  /* 0 = 8; each batch in flight gets its own launch lane (streams,
                                      work list, counters), so consecutive batches overlap on the GPU
-                                     (not while the engine uses CUDA graphs or has uplink cells) */
+                                     (not while the engine has uplink cells) */
   uint32_t release_outputs;       /* 1: completed slots' outputs are released without pulls */
   int32_t queue_timeout_us;       /* wait of a push into a full ring: 0 = 1 s, < 0 = no wait */
   double deadline_us;             /* latency counted as a deadline miss above this (0 = 500) */
