@@ -166,6 +166,10 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t a, uint32_t b,
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(taddr), "r"(a), "r"(b), "r"(c),
                "r"(d));
 }
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]));
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 // Transpose of a 4 x 4 block held by lanes 4g .. 4g + 3 (lane 4g + j holds row j in v): afterwards
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(kTPB, 2)
   }
   if (tid == 0) {
     for (int b = 0; b < kSteps; ++b) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&s_full[b])), "n"(kBuildWarps));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&s_full[b])), "n"(kBuildWarps / 2));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_empty[b])));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s_acc)));
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(kTPB, 2)
   const int quad = warp & 3, kg = warp >> 2;
   const int row = quad * 32 + lane;
   const int ii = row >> 4, nn = row & 15, rr = nn >> 2, op = (nn >> 1) & 1, ab = nn & 1;
-  const int qoff = kg * 8 - ii + 8, par = qoff & 1;
+  const int qoff = 8 - ii, par = qoff & 1;  // K-half 0; half 1 is the next 4 words of the tables
   // (op, p) -> component: (0,0) hr, (0,1) -hi, (1,0) hi, (1,1) hr
   const int c_p0 = ab * 2 + (op == 0 ? 0 : 1), c_p1 = ab * 2 + (op == 0 ? 1 : 0);
   const uint32_t neg_p1 = op == 0 ? 0x80008000u : 0u;
@@ -462,20 +466,15 @@ __global__ void __launch_bounds__(kTPB, 2)
           }
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the signal, for the tensor core
+        builders_sync();  // a step's arrivals come from one group: every warp's staging must be done
         // tap chunks, kPer per step, into the step's ring columns once the MMAs of the step that
         // last used them are done; each warp then arrives on the step's full barrier
+        // Builder group kg (warps 4 kg .. 4 kg + 3) fills the steps with gstep % 2 == kg, both K-halves
+        // of its lanes' rows, so two steps' load, store and wait chains run at once.
         int tp = 0, jc = jlo;
         for (int s = 0; s < steps; ++s, ++gstep) {
           const uint32_t ss = gstep % kSteps;
-          if (gstep >= kSteps) {
-            warp_wait(smem_u32(&s_empty[ss]), (gstep / kSteps - 1) & 1u, status, abort_flag);
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-          }
           const int kk0 = s * kPer, kend = min(kk0 + kPer, nk);
-          const uint32_t tdst = t_row + kAccCols + ss * (kPer * kChunkCols) + kg * 4;
-          uint32_t wv[kPer][4];
-          // every chunk of the step loads (a chunk past the end re-reads the last one and stores
-          // nothing), so the step's 16 loads are independent and all in flight at once
           const uint32_t *srcs[kPer];
           uint32_t ngs[kPer];
 #pragma unroll
@@ -486,21 +485,26 @@ __global__ void __launch_bounds__(kTPB, 2)
             if (kk0 + e + 1 < kend && ++jc == kKC) { jc = jlo; ++tp; }
           }
           if (kend - kk0 == kPer && ++jc == kKC) { jc = jlo; ++tp; }  // advance past the step's last chunk
+          if ((int)(gstep & 1u) != kg) continue;                   // the other group's step
+          if (gstep >= kSteps) {
+            warp_wait(smem_u32(&s_empty[ss]), (gstep / kSteps - 1) & 1u, status, abort_flag);
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+          }
+          const uint32_t tdst = t_row + kAccCols + ss * (kPer * kChunkCols);
 #pragma unroll
           for (int e = 0; e < kPer; ++e) {
             const long long off = srcs[e] - comp_w;
-            if (!TT_IN(off >= 0 && off + 4 <= 16 * kComps * 2 * kQW, TT_CHK_TAP_READ)) srcs[e] = comp_w;
+            if (!TT_IN(off >= 0 && off + 8 <= 16 * kComps * 2 * kQW, TT_CHK_TAP_READ)) srcs[e] = comp_w;
           }
 #pragma unroll
-          for (int e = 0; e < kPer; ++e)
+          for (int e = 0; e < kPer; ++e) {
+            if (kk0 + e >= kend) break;
+            uint32_t wv[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) wv[e][q] = srcs[e][q];
-#pragma unroll
-          for (int e = 0; e < kPer; ++e)
-            if (kk0 + e < kend &&
-                TT_IN(kAccCols + ss * (kPer * kChunkCols) + kg * 4 + e * kChunkCols + 4 <= kTmemCols, TT_CHK_TMEM))
-              tmem_st4(tdst + e * kChunkCols, (wv[e][0] ^ ngs[e]) & keep, (wv[e][1] ^ ngs[e]) & keep,
-                       (wv[e][2] ^ ngs[e]) & keep, (wv[e][3] ^ ngs[e]) & keep);
+            for (int q = 0; q < 8; ++q) wv[q] = (srcs[e][q] ^ ngs[e]) & keep;
+            if (TT_IN(kAccCols + ss * (kPer * kChunkCols) + e * kChunkCols + 8 <= kTmemCols, TT_CHK_TMEM))
+              tmem_st8(tdst + e * kChunkCols, wv);
+          }
           tmem_wait_st();
           asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
           __syncwarp();
