@@ -134,3 +134,33 @@ def test_eight_mixed_ues_over_200_slots_against_oracle():
     for sp, x, y in zip(specs, xs, ys):
         y_ref, _ = oracle.run_ue(oracle.OracleUE.from_spec(sp), x)
         assert nrmse(y, y_ref) <= 1e-5
+
+
+def _replay_last_outputs(specs, xs, steps, engine_kw):
+    """The benchmark's replay (slot 0 pushed, then `steps` slot-synchronous steps that commit each
+    UE's next slot in place and release the previous ones at launch) on the smallest ring the
+    engine admits (two slots beyond the delay line); returns every UE's last output slot."""
+    eng = tc.Engine(persistent=True, **engine_kw)
+    try:
+        chans = [tc.Chan(eng, sp, ring_slots=hist_slots(sp) + 2) for sp in specs]
+        for ch, x in zip(chans, xs):
+            ch.push(0, tc.slots_major(x, ch.n)[:1])
+        eng.run()
+        tc.tt_engine_replay(eng.h, steps, 1)
+        return [ch.pull(steps, 1) for ch in chans]         # the last step's slot (not yet released)
+    finally:
+        eng.close()
+
+
+def test_replays_on_launch_lanes_equal_one_stream_on_a_minimal_ring():
+    """Graph replays rotate over four launch lanes, so consecutive steps overlap on the GPU.  A
+    replay releases each step's outputs at launch, so on the smallest ring every step rewrites the
+    output position of the step one ring depth (3 to 4 slots here) earlier, which may still run
+    on another lane: the writes must still land in launch order.  Against the same replay on one
+    stream (direct launches), bit for bit."""
+    specs = inputs.workload_batching(n_ues=12, n_slots_trace=2)
+    xs = [inputs.make_iq(9, sp, 1) for sp in specs]
+    one = _replay_last_outputs(specs, xs, 64, dict())
+    lanes = _replay_last_outputs(specs, xs, 64, dict(graphs=True))
+    for a, b in zip(one, lanes):
+        assert np.array_equal(a, b)
