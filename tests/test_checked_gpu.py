@@ -3,8 +3,9 @@ run clean against the oracle, and an out-of-bounds store provoked through a lowe
 is then skipped, so nothing outside the buffers is touched) is reported with its code while the GPU
 and the engine stay usable.
 
-compute-sanitizer is not used here; this build takes its place for both kernels.  The cases run in
-a child process (tests/checked_run.py) because a process loads one build of the library.
+compute-sanitizer is not used here; the bounds-checked library takes its place for both kernels.
+The cases run in a child process (tests/checked_run.py) because a process loads one build of the
+library.
 """
 import json
 import os
