@@ -1,7 +1,7 @@
 // Internal state of the channel engine (host side), shared by the engine's translation units:
-// tt_engine.cpp (the C ABI of channels, runs and copies), tt_server.cpp (serving: the batching
-// thread, request latencies, admission waiting list) and tt_tune.cpp (the autotuner and its
-// on-disk cache).  Not part of the public ABI.
+// tt_engine.cpp (the C ABI of channels, runs and copies), tt_cells.cpp (uplink cells),
+// tt_server.cpp (serving: the batching thread, request latencies, admission waiting list) and
+// tt_tune.cpp (the autotuner and its on-disk cache).  Not part of the public ABI.
 #pragma once
 
 #include <chrono>
@@ -223,8 +223,18 @@ void update_chan(tt_chan *c);
 tt_status check_room(tt_chan *c, uint64_t first, uint32_t n);
 void mark_pushed(tt_chan *c, uint64_t first, uint32_t n);                      // arrival: now
 void mark_pushed_at(tt_chan *c, uint64_t first, uint32_t n, int64_t arrival_ns);
+// Wait (bounded) until batch `seq` is complete (engine lock held, released while blocking).
+tt_status wait_seq(tt_engine *e, uint64_t seq, int64_t timeout_us, std::unique_lock<std::mutex> &lk);
+// Copy slots [first, first + n) between a linear buffer and a ring of Q slots (at most 2 copies).
+cudaError_t ring_copy(int16_t *ring, size_t slot_elems, int Q, uint64_t first, uint32_t n, const void *src, void *dst,
+                      cudaMemcpyKind kind, cudaStream_t st, bool to_ring);
+
+// ---- uplink cells (tt_cells.cpp) ----
 // Engine lock held: an uplink cell has member slots to aggregate and ring room for them.
 bool cells_have_work(const tt_engine *e);
+// Engine lock held: aggregate every slot all members of each cell have launched (after their
+// kernels, on the engine stream); ends receives (cell, new launched end) per launched cell.
+tt_status launch_cells(tt_engine *e, std::vector<std::pair<tt_cell *, uint64_t>> &ends);
 
 // ---- serving hooks (tt_server.cpp) ----
 // A push of [first, first + n) became visible (engine lock held): its arrival is recorded.
