@@ -1,5 +1,6 @@
 // Internal state of the channel engine (host side), shared by the engine's translation units:
-// tt_engine.cpp (the C ABI of channels, runs and copies), tt_cells.cpp (uplink cells),
+// tt_engine.cpp (the C ABI of channels, runs and copies), tt_traces.cpp (trace loading and the
+// per-run anchor pre-passes), tt_cells.cpp (uplink cells),
 // tt_server.cpp (serving: the batching thread, request latencies, admission waiting list) and
 // tt_tune.cpp (the autotuner and its on-disk cache).  Not part of the public ABI.
 #pragma once
@@ -228,6 +229,19 @@ tt_status wait_seq(tt_engine *e, uint64_t seq, int64_t timeout_us, std::unique_l
 // Copy slots [first, first + n) between a linear buffer and a ring of Q slots (at most 2 copies).
 cudaError_t ring_copy(int16_t *ring, size_t slot_elems, int Q, uint64_t first, uint32_t n, const void *src, void *dst,
                       cudaMemcpyKind kind, cudaStream_t st, bool to_ring);
+
+// Tiled-kernel geometry helpers (tt_engine.cpp): chunk table of a channel, delay class, switch
+// of a channel's geometry, sparse convolution on, handle validity.
+std::vector<int32_t> chunk_table(const std::vector<uint32_t> &L, int spt, int tpb, int *max_touched);
+int pick_dclass(int d_max);
+tt_status set_geom(tt_chan *c, int spt, int tpb);
+bool sparse(const tt_chan *c);
+bool valid_chan(const tt_chan *c);
+
+// ---- traces and the per-run anchor pre-passes (tt_traces.cpp; engine lock held) ----
+tt_status launch_retime(tt_engine *e, const std::vector<tt_chan *> &chans);
+tt_status launch_synth(tt_engine *e, const std::vector<tt_chan *> &chans);
+tt_status launch_topn(tt_engine *e, const std::vector<tt_chan *> &chans);
 
 // ---- uplink cells (tt_cells.cpp) ----
 // Engine lock held: an uplink cell has member slots to aggregate and ring room for them.
