@@ -496,7 +496,8 @@ def run_precision(args, device, n_ues=64, n_slots=20, warmup=3, forms=("bf16_tc"
     for name, prec in (("bf16_tc", tc.TT_BF16_TC), ("fp16_tc", tc.TT_FP16_TC), ("fp32", tc.TT_FP32)):
         if name not in forms:
             continue
-        eng = tc.Engine(device=device, persistent=True, graphs=(prec == tc.TT_FP32))
+        # graph-replaying engines rotate consecutive slots over launch lanes (tensor-core channels too)
+        eng = tc.Engine(device=device, persistent=True, graphs=True)
         chans = [tc.Chan(eng, sp, ring_slots=n_slots + 2, precision=prec) for sp in specs]
         for ch, x in zip(chans, iq):
             ch.push(0, x[np.arange(n_slots + 1) % 4])

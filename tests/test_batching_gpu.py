@@ -136,13 +136,13 @@ def test_eight_mixed_ues_over_200_slots_against_oracle():
         assert nrmse(y, y_ref) <= 1e-5
 
 
-def _replay_last_outputs(specs, xs, steps, engine_kw):
+def _replay_last_outputs(specs, xs, steps, engine_kw, chan_kw=None):
     """The benchmark's replay (slot 0 pushed, then `steps` slot-synchronous steps that commit each
     UE's next slot in place and release the previous ones at launch) on the smallest ring the
     engine admits (two slots beyond the delay line); returns every UE's last output slot."""
     eng = tc.Engine(persistent=True, **engine_kw)
     try:
-        chans = [tc.Chan(eng, sp, ring_slots=hist_slots(sp) + 2) for sp in specs]
+        chans = [tc.Chan(eng, sp, ring_slots=hist_slots(sp) + 2, **(chan_kw or {})) for sp in specs]
         for ch, x in zip(chans, xs):
             ch.push(0, tc.slots_major(x, ch.n)[:1])
         eng.run()
@@ -162,5 +162,18 @@ def test_replays_on_launch_lanes_equal_one_stream_on_a_minimal_ring():
     xs = [inputs.make_iq(9, sp, 1) for sp in specs]
     one = _replay_last_outputs(specs, xs, 64, dict())
     lanes = _replay_last_outputs(specs, xs, 64, dict(graphs=True))
+    for a, b in zip(one, lanes):
+        assert np.array_equal(a, b)
+
+
+def test_tensor_core_replays_on_launch_lanes_equal_one_stream():
+    """The same for tensor-core channels (BF16, 4x4, dense taps), whose kernels of consecutive slots
+    overlap on the lanes of a graph-replaying engine: bit for bit against one stream."""
+    specs = [inputs.make_ue(17, u, 1024, 48, 95, 100.0, 2, n_tx=4 if u % 2 else 2, n_rx=4, pdp="per_tap",
+                            delays=list(range(48))) for u in range(6)]
+    xs = [inputs.make_iq(17, sp, 1) for sp in specs]
+    kw = dict(precision=tc.TT_BF16_TC, cf32=True)
+    one = _replay_last_outputs(specs, xs, 48, dict(), kw)
+    lanes = _replay_last_outputs(specs, xs, 48, dict(graphs=True), kw)
     for a, b in zip(one, lanes):
         assert np.array_equal(a, b)
