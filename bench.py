@@ -211,6 +211,7 @@ def run_ours(args, rank, world, device):
             ev[0].record(stream)
         eng.run()
         if ev is not None:
+            tc.tt_engine_join(eng.h)  # the end event follows every launch lane's batches
             ev[1].record(stream)
         for ch in chans:
             tc.tt_chan_release_slots(ch.h, s0, N_SLOTS)
@@ -233,6 +234,7 @@ def run_ours(args, rank, world, device):
         t0.record(stream)
         for i in range(args.steps):
             step(kev[i])
+        tc.tt_engine_join(eng.h)  # the end event follows every launch lane's batches
         t1.record(stream)
         eng.sync()
         torch.cuda.synchronize()
@@ -369,6 +371,7 @@ def run_batching(args, device, n_ues=256, steps=400, warmup=20):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         tc.tt_engine_replay(eng.h, steps, 1)
+        tc.tt_engine_join(eng.h)  # the end event follows every launch lane's batches
         ev1.record(stream)
         eng.sync()
         return ev0.elapsed_time(ev1) / steps
@@ -396,6 +399,7 @@ def run_batching(args, device, n_ues=256, steps=400, warmup=20):
     t_host = time.perf_counter()
     a.record(stream)
     tc.tt_engine_replay(eng.h, steps, 1)
+    tc.tt_engine_join(eng.h)  # the end event follows every launch lane's batches
     b.record(stream)
     eng.sync()
     t_host = time.perf_counter() - t_host
@@ -511,6 +515,7 @@ def run_precision(args, device, n_ues=64, n_slots=20, warmup=3, forms=("bf16_tc"
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         tc.tt_engine_replay(eng.h, n_slots, 1)
+        tc.tt_engine_join(eng.h)  # the end event follows every launch lane's batches
         b.record(stream)
         eng.sync()
         ms = a.elapsed_time(b) / n_slots
@@ -564,6 +569,7 @@ def run_sparse(args, device, top_n=8, n_slots=200, warmup=3):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         tc.tt_engine_replay(eng.h, 5, n_slots)
+        tc.tt_engine_join(eng.h)  # the end event follows every launch lane's batches
         b.record(stream)
         eng.sync()
         ms = a.elapsed_time(b) / 5
@@ -625,6 +631,7 @@ def run_cell(args, device, n_slots=200, warmup=3, steps=5):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         tc.tt_engine_replay(eng.h, steps, n_slots)
+        tc.tt_engine_join(eng.h)  # the end event follows every launch lane's batches
         b.record(stream)
         eng.sync()
         res[name] = a.elapsed_time(b) / steps
@@ -678,6 +685,7 @@ def run_synth(args, device, n_slots=200, warmup=3, steps=5):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         tc.tt_engine_replay(eng.h, steps, n_slots)
+        tc.tt_engine_join(eng.h)  # the end event follows every launch lane's batches
         b.record(stream)
         eng.sync()
         res[mode] = {"ms_per_step": a.elapsed_time(b) / steps,

@@ -186,6 +186,12 @@ tt_status tt_engine_run_slot(tt_engine *e);
  * Asynchronous like tt_engine_run.  TT_ERR_AGAIN if a ring has no room. */
 tt_status tt_engine_replay(tt_engine *e, uint32_t n_steps, uint32_t slots_per_step);
 
+/* Make the engine's stream (tt_engine_stream) wait, on the device, for every batch launched so
+ * far, whichever launch lane it runs on, so that work or a CUDA event queued on that stream
+ * afterwards follows all of them (for example the end event when timing a series of runs: batches
+ * of a graph-replaying or serving engine run on several lanes).  Does not block the host. */
+tt_status tt_engine_join(tt_engine *e);
+
 /* Block until all launched work is complete, at most timeout_us (< 0: no limit).
  * TT_ERR_TIMEOUT if it is still running, or if a tensor-core kernel reported
  * that one of its bounded waits expired (the affected slots are invalid). */

@@ -1427,6 +1427,15 @@ tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us) {
   return TT_OK;
 }
 
+tt_status tt_engine_join(tt_engine *e) {
+  if (!e) return fail(TT_ERR_INVALID, "null engine");
+  std::lock_guard<std::mutex> lk(e->mu);
+  TT_CK(cudaSetDevice(e->device));
+  for (const auto &p : e->events)  // batches not yet seen complete (the others are done)
+    TT_CK(cudaStreamWaitEvent(e->stream, p.second, 0));
+  return TT_OK;
+}
+
 tt_status tt_engine_get_check(tt_engine *e, tt_check_report *out) {
   if (!e || !out) return fail(TT_ERR_INVALID, "null engine or output");
   std::unique_lock<std::mutex> lk(e->mu);

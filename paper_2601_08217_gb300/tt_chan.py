@@ -179,6 +179,7 @@ _SIGS = {
     "tt_engine_autotune": [_VP, C.c_int32, C.POINTER(C.c_uint32)],
     "tt_chan_get_geometry": [_VP, C.POINTER(ChanGeometry)],
     "tt_engine_get_check": [_VP, C.POINTER(CheckReport)],
+    "tt_engine_join": [_VP],
     "tt_engine_replay": [_VP, C.c_uint32, C.c_uint32],
     "tt_engine_serve": [_VP, C.POINTER(ServeConfig), C.POINTER(ServeReport)],
     "tt_chan_create": [_VP, C.POINTER(ChanConfig), C.POINTER(_VP)],
@@ -321,6 +322,10 @@ def tt_engine_autotune(e: int, reps: int = 3) -> int:
     n = C.c_uint32(0)
     _check(load().tt_engine_autotune(e, reps, C.byref(n)))
     return n.value
+
+
+def tt_engine_join(e: int):
+    _check(load().tt_engine_join(e))
 
 
 def tt_engine_get_check(e: int) -> dict:
@@ -605,6 +610,10 @@ class Engine:
 
     def check_report(self) -> dict:
         return tt_engine_get_check(self.h)
+
+    def join(self):
+        """The engine stream waits (on the device) for every batch launched so far, on any lane."""
+        tt_engine_join(self.h)
 
     def close(self):
         """Destroy the engine.  The C side frees every channel and cell with it, so their handles are
