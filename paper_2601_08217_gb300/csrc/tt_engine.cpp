@@ -810,8 +810,9 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
     l0.d_counters = e->d_counters;
     l0.d_cursors = e->d_cursors;
   }
-  // graph replays overlap consecutive steps on four lanes (about 12% less GPU time per step of
-  // 256 mixed UEs than one stream); an engine that cannot make them stays on one
+  // graph replays overlap consecutive steps on four lanes (about 10% less GPU time per step of
+  // 256 mixed UEs than one stream; eight measured the same within noise); an engine that cannot
+  // make them stays on one
   if (err == cudaSuccess && e->graphs) ttx::enable_lanes(e, 4);
   if (err == cudaSuccess) err = dmalloc(e, &e->d_status, sizeof(int));
   if (err == cudaSuccess) err = cudaMemset(e->d_status, 0, sizeof(int));
