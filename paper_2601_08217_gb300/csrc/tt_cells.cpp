@@ -17,12 +17,6 @@ using ttx::dfree;
 using ttx::dmalloc;
 using ttx::fail;
 
-#define TT_CK(call)                                                                            \
-  do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
-    if (e_ != cudaSuccess) return fail(TT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
-
 namespace ttx {
 
 // Engine lock held: whether launch_cells would aggregate something now (every member started and

@@ -145,12 +145,6 @@ using ttx::fail;
 using ttx::now_ns;
 using ttx::now_us;
 
-#define TT_CK(call)                                                                   \
-  do {                                                                                \
-    cudaError_t e_ = (call);                                                          \
-    if (e_ != cudaSuccess) return fail(TT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
-
 namespace {
 
 cudaEvent_t get_event(tt_engine *e) {
@@ -377,7 +371,6 @@ tt_status apply_geom(tt_chan *c, int spt, int tpb) {
   c->smem = b;
   return TT_OK;
 }
-
 
 // ---- batched launch planning (engine lock held) ----
 struct PlanGroup {
@@ -626,7 +619,6 @@ tt_status launch_cached_graph(tt_engine *e, const std::vector<tt_chan *> &chans,
     chans[i]->dev_cursor[li] = segs[i].first_slot + (uint64_t)e->gstride * segs[i].n_slots;
   return TT_OK;
 }
-
 
 // Tensor-core channels: one item per (UE, slot, symbol), BF16 and FP16 channels in separate launches.
 tt_status launch_tc(tt_engine *e, const std::vector<tt_chan *> &chans, TTLane &ln) {
@@ -1720,7 +1712,5 @@ tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len) {
   return upload_desc(c);
 }
 
-
-// ---------------------------------------------------------------- serving form
 }  // extern "C"
 

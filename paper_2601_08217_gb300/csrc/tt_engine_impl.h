@@ -193,6 +193,13 @@ struct tt_cell {
 };
 
 
+// Return TT_ERR_CUDA with the failing call and CUDA's message (inside a function returning tt_status).
+#define TT_CK(call)                                                                                  \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return ttx::fail(TT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+  } while (0)
+
 namespace ttx {
 
 // Device memory of the engine: through the allocator hook if one is set, else cudaMalloc/cudaFree.

@@ -27,12 +27,6 @@ using ttx::update_completed;
 using ttx::upload_desc;
 using ttx::valid_chan;
 
-#define TT_CK(call)                                                                            \
-  do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
-    if (e_ != cudaSuccess) return fail(TT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
-
 namespace {
 
 // Check a trace's delays and geometry against the channel and pick the tiled-kernel geometry
@@ -371,7 +365,6 @@ tt_status tt_chan_load_cir(tt_chan *c, const tt_cir_desc *cir) {
   return install_trace(c, taps, delays, bytes, cir->n_steps, cir->n_taps, cir->step_samples, cir->loop, g);
 }
 
-
 namespace ttx {
 
 // Timed traces: refill the anchor rings for the slots this run launches (every symbol of slots
@@ -490,6 +483,5 @@ tt_status launch_topn(tt_engine *e, const std::vector<tt_chan *> &chans) {
   ++e->launches;
   return TT_OK;
 }
-
 
 }  // namespace ttx

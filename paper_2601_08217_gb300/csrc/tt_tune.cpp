@@ -28,12 +28,6 @@
 
 using ttx::fail;
 
-#define TT_CK(call)                                                                            \
-  do {                                                                                         \
-    cudaError_t e_ = (call);                                                                   \
-    if (e_ != cudaSuccess) return fail(TT_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
-  } while (0)
-
 namespace {
 
 struct CacheLine {
