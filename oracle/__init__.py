@@ -22,7 +22,8 @@ Functions and the passages they follow:
 * :func:`anchor` -- the trace value at one OFDM-symbol anchor.
 * :mod:`oracle.brute` -- exact rational brute force for tiny inputs.
 
-Pins: ``tests/test_oracle_*.py`` (run with ``-m "not gpu"``).
+Pins: ``tests/test_oracle_pins.py`` and, for the raw Philox words against a library
+implementation, ``tests/test_philox_library_pin.py`` (both run with ``-m "not gpu"``).
 """
 from .oracle import (OracleUE, anchor, build, lib_path, max_threads, noise, philox4x32_10,  # noqa: F401
                      resample_cir, run_cell, run_ue, sos_taps)
