@@ -556,12 +556,14 @@ def run_sparse(args, device, top_n=8, n_slots=200, warmup=3):
     out = {}
     for name, tn in (("all_taps", 0), ("top_n", top_n)):
         eng = tc.Engine(device=device, persistent=True, graphs=True)
-        chans = [tc.Chan(eng, sp, ring_slots=n_slots + 2, top_n=tn) for sp in specs]
+        # rings of two steps plus the delay line: a step's top-n pre-pass then rewrites only sparse-tap
+        # ring positions of steps already finished, so consecutive steps overlap on the launch lanes
+        chans = [tc.Chan(eng, sp, ring_slots=2 * n_slots + 2, top_n=tn) for sp in specs]
         for ch, x in zip(chans, iq):
-            ch.push(0, cycled_slots(x, n, n_slots + 1))
+            ch.push(0, cycled_slots(x, n, 2 * n_slots + 1))
         eng.run()
         for ch in chans:
-            tc.tt_chan_release_slots(ch.h, 0, n_slots + 1)
+            tc.tt_chan_release_slots(ch.h, 0, 2 * n_slots + 1)
         eng.sync()
         stream = torch.cuda.ExternalStream(eng.stream)
         tc.tt_engine_replay(eng.h, warmup, n_slots)
@@ -662,7 +664,9 @@ def run_synth(args, device, n_slots=200, warmup=3, steps=5):
         eng = tc.Engine(device=device, persistent=True, graphs=True)
         chans = []
         for u, sp in enumerate(specs):
-            ch = tc.Chan(eng, sp, ring_slots=n_slots + 2, load=(mode == "trace"))
+            # rings of two steps plus the delay line, in every mode: a step's anchor pre-pass then
+            # rewrites only positions of steps already finished, so consecutive steps overlap
+            ch = tc.Chan(eng, sp, ring_slots=2 * n_slots + 2, load=(mode == "trace"))
             if mode == "trace_1ms":   # the same UE's delays, its taps every 61440 samples (1 ms)
                 sp1 = inputs.make_ue(2, sp.ue_id, 2048, N_TAPS, D_MAX, 100.0, n_slots, snr_db=20.0, loop=True,
                                      delays=sp.delays, step_samples=61440.0)
@@ -673,10 +677,10 @@ def run_synth(args, device, n_slots=200, warmup=3, steps=5):
                 tc.tt_chan_load_jakes(ch.h, sp.delays, amp, freq, phase, 61.44e6)
             chans.append(ch)
         for ch, x in zip(chans, iq):
-            ch.push(0, cycled_slots(x, n, n_slots + 1))
+            ch.push(0, cycled_slots(x, n, 2 * n_slots + 1))
         eng.run()
         for ch in chans:
-            tc.tt_chan_release_slots(ch.h, 0, n_slots + 1)
+            tc.tt_chan_release_slots(ch.h, 0, 2 * n_slots + 1)
         eng.sync()
         st0 = eng.stats()
         stream = torch.cuda.ExternalStream(eng.stream)

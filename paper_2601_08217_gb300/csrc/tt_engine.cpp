@@ -1096,6 +1096,39 @@ static cudaError_t wait_producers(tt_chan *c, uint64_t upto, cudaStream_t st) {
   return cudaSuccess;
 }
 
+// The per-run pre-passes (timed-trace anchors, synthesised anchors, top-n selection) rewrite a
+// channel's anchor and sparse-tap rings, (Q + 1) * nsym + 1 anchors long, from the first anchor of
+// slot launched_end to the first anchor of slot pushed_end.  A rewritten position last held the
+// anchor one ring length earlier, read by batches holding a slot at most pushed_end - Q - 2.  On
+// one stream those finished before the pre-pass started; on other launch lanes they may still run
+// (replays release outputs at launch, so the host runs ahead), so the engine stream waits for
+// them first.  Engine lock held.
+static cudaError_t wait_anchor_readers(tt_engine *e, const std::vector<tt_chan *> &chans) {
+  bool polled = false;
+  for (tt_chan *c : chans) {
+    if (!(c->retime || c->synth || (sparse(c) && c->d_sparse)) || c->pushed_end <= c->launched_end) continue;
+    const uint64_t reach = (uint64_t)c->Q + 2;
+    if (c->pushed_end < reach) continue;
+    const uint64_t last = c->pushed_end - reach;  // the newest slot whose anchors may share a position
+    if (!polled) {
+      cudaError_t q = update_completed(e);
+      if (q != cudaSuccess) return q;
+      polled = true;
+    }
+    update_chan(c);
+    uint64_t start = c->completed_end;  // first slot of the oldest batch still in flight
+    for (const auto &p : c->inflight) {
+      if (start > last) break;
+      if (cudaEvent_t w = event_of(e, p.second)) {
+        cudaError_t err = cudaStreamWaitEvent(e->stream, w, 0);
+        if (err != cudaSuccess) return err;
+      }
+      start = p.first;
+    }
+  }
+  return cudaSuccess;
+}
+
 tt_status tt_chan_push_slots(tt_chan *c, uint64_t first, uint32_t n, const int16_t *iq_in) {
   const ttx::NvtxScope nvtx_range("tt push (host)");
   if (!valid_chan(c) || (!iq_in && n)) return fail(TT_ERR_INVALID, "tt_chan_push_slots: bad argument");
@@ -1253,6 +1286,7 @@ tt_status tt_engine_run(tt_engine *e) {
   {  // anchor and sparse-tap pre-passes, on the engine stream
     std::vector<tt_chan *> all(ready);
     all.insert(all.end(), tc_ready.begin(), tc_ready.end());
+    TT_CK(wait_anchor_readers(e, all));
     tt_status sst = ttx::launch_retime(e, all);
     if (sst == TT_OK) sst = ttx::launch_synth(e, all);
     if (sst == TT_OK) sst = ttx::launch_topn(e, ready);

@@ -409,8 +409,9 @@ tt_status launch_retime(tt_engine *e, const std::vector<tt_chan *> &chans) {
 }
 
 // Synthesised channels: fill the anchor rings for the slots this run launches (same anchors as
-// above), all channels in one launch (engine lock held).  Anchors rewritten here get the same value
-// as before, and the stream orders the rewrite after every kernel that read them.
+// above), all channels in one launch (engine lock held).  An anchor rewritten here gets the value it
+// had; a position that held an earlier anchor is rewritten only after every batch that read it (the
+// engine stream waits for those on other launch lanes before the pre-passes).
 tt_status launch_synth(tt_engine *e, const std::vector<tt_chan *> &chans) {
   std::vector<TTSosJob> &jobs = e->sos_jobs;
   jobs.clear();

@@ -177,3 +177,55 @@ def test_tensor_core_replays_on_launch_lanes_equal_one_stream():
     lanes = _replay_last_outputs(specs, xs, 48, dict(graphs=True), kw)
     for a, b in zip(one, lanes):
         assert np.array_equal(a, b)
+
+
+def _replay_steps(specs, xs, steps, k, engine_kw, make_chan):
+    """The benchmark's replay with k slots per step (the first k pushed, then `steps` steps that
+    commit k slots per UE in place and release the previous ones at launch) on a ring of
+    k + hist + 1 slots; returns every UE's last k output slots."""
+    eng = tc.Engine(persistent=True, **engine_kw)
+    try:
+        chans = [make_chan(eng, sp, k + hist_slots(sp) + 1) for sp in specs]
+        for ch, x in zip(chans, xs):
+            ch.push(0, tc.slots_major(x, ch.n)[:k])
+        eng.run()
+        tc.tt_engine_replay(eng.h, steps, k)
+        return [ch.pull(steps * k, k) for ch in chans]
+    finally:
+        eng.close()
+
+
+def _synthesised_chan(eng, sp, ring):
+    ch = tc.Chan(eng, sp, ring_slots=ring, load=False)
+    rng = np.random.default_rng([0x7717000B, sp.ue_id])
+    amp, freq, phase = inputs.sos_params(rng, 300.0, inputs.pdp_span_decay(sp.delays, 20.0), sp.n_rx, sp.n_tx)
+    tc.tt_chan_load_jakes(ch.h, sp.delays, amp, freq, phase, sp.fs)
+    return ch
+
+
+@pytest.mark.parametrize("kind", ["synthesised", "timed_1ms", "top_n"])
+def test_replays_with_anchor_prepasses_on_launch_lanes_equal_one_stream(kind):
+    """Synthesised, 1 ms-timed and top-n channels rewrite their anchor (or sparse-tap) ring before
+    each run, on the engine stream.  With 4 slots per step on a ring of 4 + hist + 1 slots, each
+    step's pre-pass rewrites ring positions whose earlier anchors the previous step reads, and that
+    step may still run on another launch lane: the rewrite must wait for it.  Graph replays on four
+    lanes against the same replay on one stream, bit for bit."""
+    k, steps = 4, 24
+    if kind == "timed_1ms":      # 20 MHz: one trace entry per 30720 samples (1 ms)
+        specs = [inputs.make_ue(19, u, 1024, 12, 100, 300.0, 8, n_rx=1 + u % 2, loop=True,
+                                step_samples=30720.0) for u in range(8)]
+    else:
+        specs = [inputs.make_ue(19, u, 1024, 16, 100, 300.0, 8, n_rx=1 + u % 2, loop=True) for u in range(8)]
+    xs = [inputs.make_iq(19, sp, k) for sp in specs]
+    if kind == "synthesised":
+        make = _synthesised_chan
+    elif kind == "top_n":
+        def make(eng, sp, ring):
+            return tc.Chan(eng, sp, ring_slots=ring, top_n=5)
+    else:
+        def make(eng, sp, ring):
+            return tc.Chan(eng, sp, ring_slots=ring)
+    one = _replay_steps(specs, xs, steps, k, dict(), make)
+    lanes = _replay_steps(specs, xs, steps, k, dict(graphs=True), make)
+    for a, b in zip(one, lanes):
+        assert np.array_equal(a, b)
