@@ -97,6 +97,9 @@ tt_status tt_cell_create(tt_engine *e, const tt_cell_config *cfg, tt_cell **out)
   if (Q < 1 || Q > (1 << 20)) return fail(TT_ERR_INVALID, "cell ring_slots out of range");
   std::lock_guard<std::mutex> lk(e->mu);
   TT_CK(cudaSetDevice(e->device));
+  // With a cell, every later batch launches on the engine stream; batches launched so far may
+  // still run on other launch lanes, so that stream first waits for all of them.
+  for (const auto &p : e->events) TT_CK(cudaStreamWaitEvent(e->stream, p.second, 0));
   const size_t out_e = (size_t)cfg->n_rx * cfg->samples_per_slot * (cfg->output_format == TT_OUT_CF32 ? 4 : 2);
   const uint64_t bytes = (uint64_t)Q * out_e * sizeof(int16_t);
   if (e->budget && e->in_use + bytes > e->budget)
