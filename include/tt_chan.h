@@ -303,8 +303,8 @@ typedef struct {
 
 tt_status tt_engine_serve(tt_engine *e, const tt_serve_config *cfg, tt_serve_report *out);
 
-/* Serving with callers' own pushes (spec: continuous batching of slot pushes from many UEs
- * as they arrive; Sec. III-C: per-UE isolation).  tt_server_start starts an engine-owned batching
+/* Serving with callers' own pushes: continuous batching of slot pushes from many UEs as they
+ * arrive, each UE isolated from the others (Sec. III-C).  tt_server_start starts an engine-owned batching
  * thread.  From then on every slot pushed by any thread, through tt_chan_push_slot(s)(_dev),
  * tt_engine_push_slots or tt_chan_commit_slots, is a request.  Its arrival time is the push call's
  * host steady-clock time.  The thread launches whatever is pending as one batch whenever fewer
