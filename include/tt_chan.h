@@ -442,7 +442,13 @@ tt_status tt_chan_push_slot_dev(tt_chan *c, uint64_t slot, const int16_t *d_iq_i
 /* Zero-copy input: *d_ptr receives the device address inside the ring where
  * slot `slot`'s input ([n_tx][N][2]) lives.  Write it (on any stream, then
  * order that stream before the next tt_engine_run, e.g. by synchronising) and
- * commit it.  Valid for the next slot to push and the ring's free positions. */
+ * commit it.  Valid for the next slot to push and the ring's free positions.
+ * A position is free once the slot one ring depth earlier was pulled or
+ * released.  tt_chan_release_slots needs only a launched slot, so after a
+ * release ahead of completion, batches still running may read the position as
+ * delay-line history: order the write after them too (tt_engine_sync, or the
+ * engine stream after tt_engine_join).  The push calls order their copies
+ * after such batches themselves. */
 tt_status tt_chan_slot_input(tt_chan *c, uint64_t slot, int16_t **d_ptr);
 tt_status tt_chan_commit_slots(tt_chan *c, uint64_t first, uint32_t n);
 
