@@ -1736,6 +1736,9 @@ tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len) {
                        c->slot_in_elems * sizeof(int16_t), cudaMemcpyHostToDevice));
     }
   }
+  // A device memset and a copy from pageable memory may return before their writes land, and the
+  // engine's non-blocking streams are not ordered after the default stream: finish them here.
+  TT_CK(cudaStreamSynchronize(nullptr));
   c->cfg.seed = h.seed;
   c->cfg.ue_id = h.ue_id;
   c->desc.seed = h.seed;
