@@ -810,6 +810,9 @@ tt_status tt_engine_create(const tt_engine_config *cfg, tt_engine **out) {
   if (err == cudaSuccess) err = cudaMemset(e->d_status, 0, sizeof(int));
   if (err == cudaSuccess) err = dmalloc(e, &e->d_check, 2 * sizeof(uint32_t));
   if (err == cudaSuccess) err = cudaMemset(e->d_check, 0, 2 * sizeof(uint32_t));
+  // a device memset may return before it lands, and the engine's non-blocking streams are not
+  // ordered after the default stream: finish it before any kernel can write these words
+  if (err == cudaSuccess) err = cudaStreamSynchronize(nullptr);
   if (err != cudaSuccess) {
     tt_engine_destroy(e);
     return fail(TT_ERR_CUDA, "engine setup: %s", cudaGetErrorString(err));
@@ -1447,6 +1450,7 @@ tt_status tt_engine_sync(tt_engine *e, int64_t timeout_us) {
   TT_CK(cudaMemcpy(&kst, e->d_status, sizeof kst, cudaMemcpyDeviceToHost));
   if (kst) {
     cudaMemset(e->d_status, 0, sizeof(int));
+    cudaStreamSynchronize(nullptr);  // landed before the next run's kernels can set it again
     return fail(TT_ERR_TIMEOUT, "a kernel's bounded wait on the tensor core expired; its slots are invalid");
   }
   for (tt_chan *c : e->table)
@@ -1473,6 +1477,7 @@ tt_status tt_engine_get_check(tt_engine *e, tt_check_report *out) {
   uint32_t w[2] = {0, 0};
   TT_CK(cudaMemcpy(w, e->d_check, sizeof w, cudaMemcpyDeviceToHost));
   TT_CK(cudaMemset(e->d_check, 0, sizeof w));
+  TT_CK(cudaStreamSynchronize(nullptr));  // landed before the next run's kernels count again
   tt_check_report r{};
   r.checked_build = (uint32_t)tt_checked_build();
   r.violations = w[0];
