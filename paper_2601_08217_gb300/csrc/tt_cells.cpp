@@ -152,6 +152,9 @@ tt_status tt_cell_attach(tt_cell *cl, tt_chan *c) {
     h[i].ring_q = cl->members[i]->Q;
   }
   TT_CK(cudaMemcpy(cl->d_members, h.data(), sizeof(TTCellMember) * h.size(), cudaMemcpyHostToDevice));
+  // copies from pageable memory may return before the DMA lands, and the engine's non-blocking
+  // streams are not ordered after the default stream: let them land before any kernel reads them
+  TT_CK(cudaStreamSynchronize(nullptr));
   return TT_OK;
 }
 

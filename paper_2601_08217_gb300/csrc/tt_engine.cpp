@@ -314,6 +314,9 @@ tt_status set_geom(tt_chan *c, int spt, int tpb) {
   cudaError_t err = dmalloc(c->e, &d_chunks, chunks.size() * sizeof(int32_t));
   if (err == cudaSuccess)
     err = cudaMemcpy(d_chunks, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  // copies from pageable memory may return before the DMA lands, and the engine's non-blocking
+  // streams are not ordered after the default stream: let them land before any kernel reads them
+  if (err == cudaSuccess) err = cudaStreamSynchronize(nullptr);
   if (err != cudaSuccess) {
     dfree(c->e, d_chunks);
     return fail(TT_ERR_CUDA, "chunk table: %s", cudaGetErrorString(err));
@@ -566,6 +569,9 @@ tt_status launch_graph(tt_engine *e, const Plan &p, int li) {
       e->gseg_cap = p.segs.size() * 2;
     }
     TT_CK(cudaMemcpy(e->d_gsegs, p.segs.data(), sizeof(TTSeg) * p.segs.size(), cudaMemcpyHostToDevice));
+    // copies from pageable memory may return before the DMA lands, and the engine's non-blocking
+    // streams are not ordered after the default stream: let them land before any kernel reads them
+    TT_CK(cudaStreamSynchronize(nullptr));
     for (int l = 0; l < stride; ++l) {
       TTLane &ln = e->lanes[l];
       cudaGraph_t graph = nullptr;

@@ -240,6 +240,9 @@ tt_status tt_chan_load_trace(tt_chan *c, const tt_trace_desc *tr) {
   if (err == cudaSuccess) err = dmalloc(c->e, &delays, tr->n_taps * sizeof(int32_t));
   if (err == cudaSuccess) err = cudaMemcpy(taps, tr->taps, nval * sizeof(float), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(delays, tr->delays, tr->n_taps * sizeof(int32_t), cudaMemcpyHostToDevice);
+  // copies from pageable memory may return before the DMA lands, and the engine's non-blocking
+  // streams are not ordered after the default stream: let them land before any kernel reads them
+  if (err == cudaSuccess) err = cudaStreamSynchronize(nullptr);
   if (err != cudaSuccess) {
     dfree(c->e, taps);
     dfree(c->e, delays);
@@ -290,6 +293,9 @@ tt_status tt_chan_load_jakes(tt_chan *c, const tt_jakes_desc *j) {
   if (err == cudaSuccess) err = cudaMemcpy(amp, j->amplitude, per * sizeof(float), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(freq, j->freq, nfp * sizeof(double), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(phase, j->phase, nfp * sizeof(double), cudaMemcpyHostToDevice);
+  // copies from pageable memory may return before the DMA lands, and the engine's non-blocking
+  // streams are not ordered after the default stream: let them land before any kernel reads them
+  if (err == cudaSuccess) err = cudaStreamSynchronize(nullptr);
   if (err != cudaSuccess) {
     dfree(c->e, taps);
     dfree(c->e, delays);
@@ -350,6 +356,9 @@ tt_status tt_chan_load_cir(tt_chan *c, const tt_cir_desc *cir) {
   if (err == cudaSuccess) err = cudaMemcpy(delays, grid.data(), cir->n_taps * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(d_gains, cir->gains, ng * sizeof(float), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMemcpy(d_tau, cir->delays, nd * sizeof(double), cudaMemcpyHostToDevice);
+  // copies from pageable memory may return before the DMA lands, and the engine's non-blocking
+  // streams are not ordered after the default stream: let them land before any kernel reads them
+  if (err == cudaSuccess) err = cudaStreamSynchronize(nullptr);
   if (err == cudaSuccess)
     err = tt_launch_cir_resample(d_gains, d_tau, (int)cir->n_steps, n_links, (int)cir->n_paths, (int)cir->n_taps,
                                  taps, e->stream);
