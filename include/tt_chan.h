@@ -566,8 +566,7 @@ tt_status tt_chan_set_state(tt_chan *c, const void *buf, size_t len);
  * the first slot).  Asynchronous on `stream` (cudaStream_t, NULL = legacy).
  *
  * The first call on a device looks up the scratch array's device address with
- * that device current; make that first call before any stream capture.
- * Every call shares the array and leaves its contents behind; each call
+ * that device current.  Every call shares the array and leaves its contents behind; each call
  * rewrites what it reads and zeroes its counters.  Calls that overlap on the
  * GPU (different streams or threads) race on the array: order them on one
  * stream. */

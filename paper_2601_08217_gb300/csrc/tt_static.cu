@@ -12,8 +12,8 @@
 // array until the process exits.
 //
 // Setup: the first call on a device looks up the array's device address with
-// cudaGetSymbolAddress, with that device current, and remembers it. Make that
-// first call before any stream capture. Host code must never pass the array's
+// cudaGetSymbolAddress, with that device current, and remembers it. Host code
+// must never pass the array's
 // name to a kernel: in host code the name is a host-side stand-in, not the
 // device address.
 //
