@@ -13,9 +13,8 @@
 //
 // Setup: the first call on a device looks up the array's device address with
 // cudaGetSymbolAddress, with that device current, and remembers it. Host code
-// must never pass the array's
-// name to a kernel: in host code the name is a host-side stand-in, not the
-// device address.
+// must never pass the array's name to a kernel: in host code the name is a
+// host-side stand-in, not the device address.
 //
 // Sharing: all calls use the same array, and it keeps the last call's
 // contents. Each call rewrites everything it reads and zeroes its work
